@@ -1,0 +1,251 @@
+/*
+ * swe.c -- FP64 CPU oracle: Riemann solver, MC wave limiter and the
+ * dimensionally split wave-propagation update of one patch.
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).  Plain loops, no blocking, no
+ * fusion: each function follows the paper's equations in order.
+ *
+ *   Sec. 2.1, Eq. (swe)                      shallow water equations with bathymetry B
+ *   Sec. 2.2, Eq. (wave_propagation_form)    first-order fluctuation update
+ *   Sec. 2.2, Eq. (wave_propagation_2nd_order) and the correction flux
+ *                                            F~ = 1/2 sum (1 - dt/dx |l|) |l| W~
+ *   Sec. 2.2, Eq. (theta) and the upwind index I   wave limiter ratio
+ *   Sec. 2.2, Eqs. (..._x), (..._y)          Godunov dimensional splitting, x then y
+ *   Sec. 2.2, CFL condition                  nu = |s dt / dx| <= 1
+ *
+ * Readings of points the paper leaves open (each is listed in the design doc):
+ *   - f-wave form: the solver decomposes the flux jump (including the
+ *     bathymetry source -g hbar dB folded into the momentum flux jump as
+ *     g hbar d(eta)) into f-waves Z^p = s^p W^p, so A-dQ/A+dQ are the sums of
+ *     the left/right-going Z^p and the correction flux is
+ *     1/2 sum sgn(s)(1 - dt/dx|s|) Z~^p, which equals the paper's form when
+ *     Z = s W.  theta uses the squared norm Z_I.Z_i / Z_i.Z_i (the printed
+ *     single-norm form is not dimensionless).
+ *   - MC limiter phi(theta) = max(0, min((1+theta)/2, 2, 2 theta)).
+ *   - Upwind edge: s >= 0 -> I = i-1, s < 0 -> I = i+1.
+ *   - Riemann solver (the paper only cites George 2008): Einfeldt-type speeds
+ *     from Roe averages, two acoustic f-waves from an HLLE-type decomposition
+ *     of the augmented jump (d eta, d hu) and the flux jump with the bed
+ *     source, a contact wave carrying the transverse momentum at the Roe
+ *     speed, dry-bed speeds u - c, u + 2c (mirrored for a dry left side), and a
+ *     reflecting wall when a dry cell's bed lies above the wet side's
+ *     two-rarefaction middle-state surface.  A wave of speed exactly 0 is
+ *     split half into each cell.
+ *   - After each sweep: h < 0 -> 0, and h < drytol -> zero momenta.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "ora_internal.h"
+
+/* Augmented f-wave Riemann solver for the normal direction.
+ * Inputs per side: depth h, normal momentum hn, transverse momentum ht, bed B.
+ * Output: f-waves Z[p][m] (m = mass, normal, transverse), speeds s[p], and
+ * wall flags (the dry side was replaced by the mirror of the wet side). */
+void ora_riemann(double g, double drytol,
+                 double hL, double hnL, double htL, double BL,
+                 double hR, double hnR, double htR, double BR, ora_rp *r)
+{
+    memset(r, 0, sizeof *r);
+    int wetL = hL >= drytol;
+    int wetR = hR >= drytol;
+    if (!wetL && !wetR)
+        return;
+
+    double uL = 0.0, vL = 0.0, uR = 0.0, vR = 0.0;
+    if (wetL) { uL = hnL / hL; vL = htL / hL; }
+    if (wetR) { uR = hnR / hR; vR = htR / hR; }
+
+    /* wet/dry: can the wet water reach the dry cell?  Two-rarefaction
+     * estimate of the middle depth against a wall: sqrt(g hm) = c + u/2
+     * (u measured toward the dry cell). */
+    if (wetL && !wetR) {
+        double a = sqrt(g * hL) + 0.5 * uL;
+        double hm = a > 0.0 ? a * a / g : 0.0;
+        if (hm + BL <= BR) {
+            r->wallR = 1;
+            hR = hL; hnR = -hnL; htR = htL; BR = BL; uR = -uL; vR = vL; wetR = 1;
+        }
+    } else if (!wetL && wetR) {
+        double a = sqrt(g * hR) - 0.5 * uR;
+        double hm = a > 0.0 ? a * a / g : 0.0;
+        if (hm + BR <= BL) {
+            r->wallL = 1;
+            hL = hR; hnL = -hnR; htL = htR; BL = BR; uL = -uR; vL = vR; wetL = 1;
+        }
+    }
+
+    double s1, s2, s3;
+    if (wetL && wetR) {
+        double cL = sqrt(g * hL), cR = sqrt(g * hR);
+        double sqL = sqrt(hL), sqR = sqrt(hR);
+        double uhat = (sqL * uL + sqR * uR) / (sqL + sqR);
+        double chat = sqrt(g * (0.5 * (hL + hR)));
+        s1 = fmin(uL - cL, uhat - chat);
+        s3 = fmax(uR + cR, uhat + chat);
+        s2 = uhat;
+    } else if (wetL) {              /* right side is a dry bed below the water */
+        double cL = sqrt(g * hL);
+        s1 = uL - cL;
+        s3 = uL + 2.0 * cL;
+        s2 = uL;
+    } else {                        /* left side is a dry bed */
+        double cR = sqrt(g * hR);
+        s1 = uR - 2.0 * cR;
+        s3 = uR + cR;
+        s2 = uR;
+    }
+
+    /* Augmented jump: the surface jump d(eta) stands in for the depth jump
+     * (the bed is static, and a bed step with still water is a steady state),
+     * and the momentum flux jump has the bathymetry source folded in:
+     * d(hu^2 + g h^2/2) + g hbar dB = d(hu^2) + g hbar d(eta).
+     * HLLE-type decomposition into two acoustic f-waves: W1 = Q* - Q_l with
+     * the middle state of the two-speed approximation, W3 = dQ - W1,
+     * Z = s W, so Z1 + Z3 equals the flux jump exactly; a third (contact)
+     * wave at the Roe speed carries what remains of the transverse momentum
+     * flux after each acoustic wave has advected v of its upwind side. */
+    double hbar = 0.5 * (hL + hR);
+    double d1 = (hR + BR) - (hL + BL);
+    double d2 = hnR - hnL;
+    double d3 = (hnR * uR - hnL * uL) + (g * hbar) * d1;
+    double d4 = hnR * vR - hnL * vL;
+    double den = s3 - s1;
+    double w1m = (s3 * d1 - d2) / den;
+    double w1n = (s3 * d2 - d3) / den;
+    double b1 = s1 * w1m, g1 = s1 * w1n;
+    double b3 = s3 * (d1 - w1m), g3 = s3 * (d2 - w1n);
+
+    r->Z[0][0] = b1;  r->Z[0][1] = g1;  r->Z[0][2] = b1 * vL;
+    r->Z[2][0] = b3;  r->Z[2][1] = g3;  r->Z[2][2] = b3 * vR;
+    r->Z[1][0] = 0.0; r->Z[1][1] = 0.0; r->Z[1][2] = (d4 - b1 * vL) - b3 * vR;
+    r->s[0] = s1; r->s[1] = s2; r->s[2] = s3;
+}
+
+/* MC limiter, Sec. 2.2 (limiter named in Sec. 5.1.1) */
+double ora_mc_limiter(double theta)
+{
+    double t = 0.5 * (1.0 + theta);
+    t = fmin(t, 2.0);
+    t = fmin(t, 2.0 * theta);
+    return fmax(0.0, t);
+}
+
+/* share of a wave of speed s going left (A-dQ) and right (A+dQ) */
+static double w_left(double s) { return s < 0.0 ? 1.0 : (s == 0.0 ? 0.5 : 0.0); }
+static double w_right(double s) { return s > 0.0 ? 1.0 : (s == 0.0 ? 0.5 : 0.0); }
+
+/* One 1D sweep over n interior cells with 2 ghost cells on each side.
+ * Input arrays have n+4 entries (cell c at index c+2).  The updated interior
+ * is written to the output arrays (n entries).  Returns max |s| over the
+ * edges 0..n (the edges that touch an interior cell). */
+static double sweep_1d(double g, double drytol, int n, double dtdx,
+                       const double *h, const double *hn, const double *ht, const double *B,
+                       double *ho, double *hno, double *hto)
+{
+    /* Riemann problems at edges e = -1 .. n+1 (edge e between cells e-1 and e) */
+    ora_rp *rp = (ora_rp *)malloc((size_t)(n + 3) * sizeof *rp);
+    for (int e = -1; e <= n + 1; e++) {
+        int cl = e - 1 + 2, cr = e + 2;
+        ora_riemann(g, drytol, h[cl], hn[cl], ht[cl], B[cl], h[cr], hn[cr], ht[cr], B[cr], &rp[e + 1]);
+    }
+
+    double (*amdq)[3] = malloc((size_t)(n + 1) * sizeof *amdq);
+    double (*apdq)[3] = malloc((size_t)(n + 1) * sizeof *apdq);
+    double (*F)[3] = malloc((size_t)(n + 1) * sizeof *F);
+    double smax = 0.0;
+
+    for (int e = 0; e <= n; e++) {
+        const ora_rp *r = &rp[e + 1];
+        /* fluctuations, Eq. (wave_propagation_form) in f-wave form */
+        for (int m = 0; m < 3; m++) {
+            amdq[e][m] = (w_left(r->s[0]) * r->Z[0][m] + w_left(r->s[1]) * r->Z[1][m]) + w_left(r->s[2]) * r->Z[2][m];
+            apdq[e][m] = (w_right(r->s[0]) * r->Z[0][m] + w_right(r->s[1]) * r->Z[1][m]) + w_right(r->s[2]) * r->Z[2][m];
+        }
+        if (r->wallR) { apdq[e][0] = 0.0; apdq[e][1] = 0.0; apdq[e][2] = 0.0; }
+        if (r->wallL) { amdq[e][0] = 0.0; amdq[e][1] = 0.0; amdq[e][2] = 0.0; }
+
+        /* limited second-order correction flux */
+        double c[3] = {0.0, 0.0, 0.0};
+        if (!r->wallL && !r->wallR) {
+            for (int p = 0; p < 3; p++) {
+                const double *Zi = r->Z[p];
+                double dii = (Zi[0] * Zi[0] + Zi[1] * Zi[1]) + Zi[2] * Zi[2];
+                double phi = 0.0;
+                if (dii != 0.0) {
+                    int I = r->s[p] >= 0.0 ? e - 1 : e + 1;
+                    const double *ZI = rp[I + 1].Z[p];
+                    double dIi = (ZI[0] * Zi[0] + ZI[1] * Zi[1]) + ZI[2] * Zi[2];
+                    phi = ora_mc_limiter(dIi / dii);
+                }
+                double s = r->s[p];
+                double cp = (1.0 - dtdx * fabs(s)) * phi;
+                if (s < 0.0) cp = -cp;
+                else if (s == 0.0) cp = 0.0;
+                c[p] = cp;
+            }
+        }
+        for (int m = 0; m < 3; m++)
+            F[e][m] = 0.5 * ((c[0] * r->Z[0][m] + c[1] * r->Z[1][m]) + c[2] * r->Z[2][m]);
+
+        double se = fmax(-r->s[0], r->s[2]);
+        smax = fmax(smax, se);
+    }
+
+    /* cell update, Eq. (wave_propagation_2nd_order) */
+    for (int i = 0; i < n; i++) {
+        const double *q[3] = {h, hn, ht};
+        double *qo[3] = {ho, hno, hto};
+        for (int m = 0; m < 3; m++) {
+            double upd = (apdq[i][m] + amdq[i + 1][m]) + (F[i + 1][m] - F[i][m]);
+            qo[m][i] = q[m][i + 2] - dtdx * upd;
+        }
+        if (ho[i] < 0.0) ho[i] = 0.0;
+        if (ho[i] < drytol) { hno[i] = 0.0; hto[i] = 0.0; }
+    }
+    free(rp); free(amdq); free(apdq); free(F);
+    return smax;
+}
+
+/* Q* = x-sweep(Q^n) on every row including the ghost rows (so the y-sweep
+ * sees Q* in its ghost cells), then Q^{n+1} = y-sweep(Q*) on the interior,
+ * Eqs. (wave_propagation_2nd_order_x/_y). */
+void ora_step_patch(OPatch *p, double g, double drytol, double dt, double dx, double dy,
+                    double *sx_out, double *sy_out)
+{
+    int nx = p->nx, ny = p->ny;
+    int nmax = (nx > ny ? nx : ny) + 4;
+    double *a = malloc(4 * (size_t)nmax * sizeof(double));
+    double *o = malloc(3 * (size_t)nmax * sizeof(double));
+    double *ah = a, *an = a + nmax, *at = a + 2 * nmax, *aB = a + 3 * nmax;
+    double *oh = o, *on = o + nmax, *ot = o + 2 * nmax;
+    double sx = 0.0, sy = 0.0;
+    double dtdx = dt / dx, dtdy = dt / dy;
+
+    for (int j = -2; j < ny + 2; j++) {
+        for (int i = -2; i < nx + 2; i++) {
+            size_t k = OIDX(p, i, j);
+            ah[i + 2] = p->h[k]; an[i + 2] = p->hu[k]; at[i + 2] = p->hv[k]; aB[i + 2] = p->B[k];
+        }
+        double s = sweep_1d(g, drytol, nx, dtdx, ah, an, at, aB, oh, on, ot);
+        if (j >= 0 && j < ny) sx = fmax(sx, s);
+        for (int i = 0; i < nx; i++) {
+            size_t k = OIDX(p, i, j);
+            p->h[k] = oh[i]; p->hu[k] = on[i]; p->hv[k] = ot[i];
+        }
+    }
+    for (int i = 0; i < nx; i++) {
+        for (int j = -2; j < ny + 2; j++) {
+            size_t k = OIDX(p, i, j);
+            ah[j + 2] = p->h[k]; an[j + 2] = p->hv[k]; at[j + 2] = p->hu[k]; aB[j + 2] = p->B[k];
+        }
+        double s = sweep_1d(g, drytol, ny, dtdy, ah, an, at, aB, oh, on, ot);
+        sy = fmax(sy, s);
+        for (int j = 0; j < ny; j++) {
+            size_t k = OIDX(p, i, j);
+            p->h[k] = oh[j]; p->hv[k] = on[j]; p->hu[k] = ot[j];
+        }
+    }
+    free(a); free(o);
+    *sx_out = sx; *sy_out = sy;
+}

@@ -1,0 +1,416 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: textbook
+closed forms (MC limiter table, the 1D dam-break solutions of Stoker and
+Ritter), invariants the method must keep (lake at rest over bathymetry with
+dry land, mass conservation between walls, mirror symmetry), exact
+equalities the algorithm implies (one patch vs a tiled level; a fully
+refined level vs a uniform fine grid; exact reproduction of linear data by
+the interpolation) and hand-drawn clustering cases.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_06798_gb300 import workloads as W
+
+G = 9.81
+
+
+# --------------------------------------------------------------------------
+# Riemann solver (Sec. 2.2; solver internals: the reading in the design doc)
+
+def _flux(h, hn, ht):
+    """Physical flux of the x-split shallow water equations (Eq. swe)."""
+    if h <= 0:
+        return np.zeros(3)
+    u = hn / h
+    return np.array([hn, hn * u + 0.5 * G * h * h, hn * ht / h])
+
+
+def test_riemann_equal_states_zero():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        h = rng.uniform(1e-2, 50)
+        hn, ht, B = rng.normal(0, 5), rng.normal(0, 5), rng.uniform(-50, 0)
+        Z, s, wl, wr = oracle.riemann(h, hn, ht, B, h, hn, ht, B)
+        assert np.all(Z == 0.0)
+        assert wl == 0 and wr == 0
+    Z, s, wl, wr = oracle.riemann(0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 2.0)   # both dry
+    assert np.all(Z == 0.0) and np.all(s == 0.0)
+
+
+def test_riemann_lake_at_rest_exact():
+    """Still water over any bed step (both wet) and at a dry shore: zero waves."""
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        BL, BR = -rng.uniform(0.01, 4000), -rng.uniform(0.01, 4000)
+        Z, s, wl, wr = oracle.riemann(-BL, 0.0, 0.0, BL, -BR, 0.0, 0.0, BR)
+        assert np.all(Z == 0.0)
+    # wet cell next to dry land above the sea surface -> wall, still zero
+    Z, s, wl, wr = oracle.riemann(3.0, 0.0, 0.0, -3.0, 0.0, 0.0, 0.0, 2.0)
+    assert wr == 1 and np.all(Z == 0.0)
+    Z, s, wl, wr = oracle.riemann(0.0, 0.0, 0.0, 5.0, 3.0, 0.0, 0.0, -3.0)
+    assert wl == 1 and np.all(Z == 0.0)
+
+
+def test_riemann_fwaves_sum_to_flux_jump_with_source():
+    """f-wave decomposition: sum_p Z^p = f(Q_r) - f(Q_l) + g hbar (B_r - B_l)
+    (the momentum source -g h B_x integrated across the edge)."""
+    rng = np.random.default_rng(2)
+    for _ in range(300):
+        hL, hR = rng.uniform(0.5, 100, 2)
+        BL, BR = rng.uniform(-200, -110, 2)
+        hnL, hnR, htL, htR = rng.normal(0, 20, 4)
+        Z, s, wl, wr = oracle.riemann(hL, hnL, htL, BL, hR, hnR, htR, BR)
+        df = _flux(hR, hnR, htR) - _flux(hL, hnL, htL)
+        df[1] += G * 0.5 * (hL + hR) * (BR - BL)
+        tot = Z.sum(axis=0)
+        scale = np.abs(df).max() + 1.0
+        assert np.allclose(tot, df, rtol=0, atol=1e-11 * scale), (tot, df)
+        assert s[0] <= s[1] <= s[2]
+        # Einfeldt-type bounds contain the characteristic speeds of both sides
+        assert s[0] <= hnL / hL - math.sqrt(G * hL) + 1e-12
+        assert s[2] >= hnR / hR + math.sqrt(G * hR) - 1e-12
+
+
+def test_riemann_mirror_symmetry():
+    """x -> -x: the problem (mirror R, mirror L) has speeds -s reversed and
+    wave 1 <-> wave 3 with the normal-momentum component negated."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        hL, hR = rng.uniform(0.5, 60, 2)
+        BL, BR = rng.uniform(-100, -70, 2)
+        hnL, hnR, htL, htR = rng.normal(0, 10, 4)
+        Z, s, _, _ = oracle.riemann(hL, hnL, htL, BL, hR, hnR, htR, BR)
+        Zm, sm, _, _ = oracle.riemann(hR, -hnR, htR, BR, hL, -hnL, htL, BL)
+        assert np.allclose(sm, -s[::-1], rtol=1e-14, atol=1e-14)
+        flip = np.array([1.0, -1.0, 1.0])
+        sc = np.abs(Z).max() + 1e-300
+        assert np.allclose(Zm[0], Z[2] * flip, atol=1e-13 * sc)
+        assert np.allclose(Zm[2], Z[0] * flip, atol=1e-13 * sc)
+        assert np.allclose(Zm[1], Z[1] * flip, atol=1e-12 * sc)
+
+
+def test_riemann_wall_no_mass_flux():
+    """Against a wall the effective mass flux f(Q_l) + A-dQ vanishes."""
+    rng = np.random.default_rng(4)
+    for _ in range(100):
+        hL = rng.uniform(0.5, 5)
+        uL = rng.uniform(-1, 1)
+        Z, s, wl, wr = oracle.riemann(hL, hL * uL, 0.3 * hL, -hL, 0.0, 0.0, 0.0, 10.0)
+        assert wr == 1
+        amdq = sum(Z[p] * (1.0 if s[p] < 0 else (0.5 if s[p] == 0 else 0.0)) for p in range(3))
+        assert abs(hL * uL + amdq[0]) < 1e-12
+
+
+def test_mc_limiter_table():
+    """MC limiter phi = max(0, min((1+t)/2, 2, 2t)) at tabulated points."""
+    table = {-1.0: 0.0, 0.0: 0.0, 0.25: 0.5, 1 / 3: 2 / 3, 0.5: 0.75, 1.0: 1.0, 2.0: 1.5, 3.0: 2.0, 10.0: 2.0}
+    for th, ph in table.items():
+        assert oracle.mc_limiter(th) == pytest.approx(ph, rel=1e-15, abs=1e-15)
+
+
+# --------------------------------------------------------------------------
+# 1D dam break closed forms (posed as y-uniform 2D grids)
+
+def _stoker_middle(hl, hr):
+    """Middle state of the dam break: left rarefaction, right shock."""
+    cl = math.sqrt(G * hl)
+
+    def f(hm):
+        u_raref = 2.0 * (cl - math.sqrt(G * hm))
+        u_shock = (hm - hr) * math.sqrt(0.5 * G * (1.0 / hm + 1.0 / hr))
+        return u_raref - u_shock
+    a, b = hr, hl
+    for _ in range(200):
+        m = 0.5 * (a + b)
+        if f(m) > 0:
+            a = m
+        else:
+            b = m
+    hm = 0.5 * (a + b)
+    um = 2.0 * (cl - math.sqrt(G * hm))
+    return hm, um
+
+
+def dam_break_exact(x, t, x0, hl, hr):
+    cl = math.sqrt(G * hl)
+    xi = (x - x0) / t
+    h = np.empty_like(x)
+    if hr == 0.0:
+        raref = (xi > -cl) & (xi < 2 * cl)
+        h[:] = np.where(xi <= -cl, hl, 0.0)
+        h[raref] = (2 * cl - xi[raref]) ** 2 / (9 * G)
+        return h
+    hm, um = _stoker_middle(hl, hr)
+    cm = math.sqrt(G * hm)
+    ss = hm * um / (hm - hr)
+    h[:] = hl
+    raref = (xi > -cl) & (xi < um - cm)
+    h[raref] = (2 * cl - xi[raref]) ** 2 / (9 * G)
+    h[(xi >= um - cm) & (xi < ss)] = hm
+    h[xi >= ss] = hr
+    return h
+
+
+def _run_dam(n, hl, hr, T=40.0):
+    w = W.dam_break_1d(n, hl, hr)
+    o = W.load(oracle.Oracle(w["cfg"]), w)
+    t = 0.0
+    while t < T:
+        t = o.step(1)[0]
+    h = o.level_array(0, 1, "h")
+    assert np.all(h == h[0:1, :]), "solution must stay uniform in y"
+    dx = w["cfg"]["dx"]
+    x = (np.arange(n) + 0.5) * dx
+    ex = dam_break_exact(x, t, 500.0, hl, hr)
+    return np.abs(h[0] - ex).sum() * dx / 1000.0
+
+
+@pytest.mark.parametrize("hl,hr", [(2.0, 1.0), (1.0, 0.0)])
+def test_dam_break_converges(hl, hr):
+    errs = [_run_dam(n, hl, hr) for n in (100, 200, 400, 800)]
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(3)]
+    assert errs[-1] < 1e-2, errs
+    assert np.mean(rates) >= 0.8, (errs, rates)
+
+
+# --------------------------------------------------------------------------
+# invariants of the 2D update
+
+def test_hump_mass_and_mirror_symmetry():
+    w = W.hump200()
+    o = W.load(oracle.Oracle(w["cfg"]), w)
+    m0 = o.stats()["mass"]
+    o.step(100)
+    st = o.stats()
+    assert abs(st["mass"] - m0) <= 1e-13 * m0
+    assert st["cfl_violations"] == 0
+    h = o.level_array(0, 1, "h")
+    assert np.abs(h - h[:, ::-1]).max() <= 1e-12 * np.abs(h).max()
+    assert np.abs(h - h[::-1, :]).max() <= 1e-12 * np.abs(h).max()
+    # transpose symmetry holds only to the splitting error (reported, loose bound)
+    assert np.abs(h - h.T).max() < 1e-2
+
+
+def test_mass_conservation_varying_bed():
+    cfg = W.base_config(nx=60, ny=50, dx=50.0, dy=50.0, bc=[W.BC_WALL] * 4)
+    xs = np.linspace(0, 3000, 61)
+    B = -20.0 + 8.0 * np.sin(xs[None, :] / 400.0) * np.cos(np.linspace(0, 2500, 51)[:, None] / 300.0)
+    eta = W.gaussian_grid(0, 0, 3000, 2500, 61, 51, 1200, 1400, 1.5, 300, 200)
+    w = dict(cfg=cfg, topo=[(B, 0.0, 0.0, 50.0, 50.0)], eta=[(0, *eta)], uplift=[], gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    m0 = o.stats()["mass"]
+    o.step(100)
+    assert abs(o.stats()["mass"] - m0) <= 1e-13 * m0
+
+
+def test_lake_at_rest_with_dry_land():
+    """Still sea over the shelf profile with beach and dry land: nothing moves."""
+    w = W.lake_at_rest_shelf(n=96)
+    o = W.load(oracle.Oracle(w["cfg"]), w)
+    o.step(300)
+    for f in ("hu", "hv"):
+        assert np.abs(o.level_array(0, 1, f)).max() == 0.0
+    h = o.level_array(0, 1, "h")
+    B = o.level_array(0, 1, "B")
+    wet = h > 0
+    assert np.abs((h + B)[wet]).max() == 0.0
+    assert (~wet).sum() > 0 and wet.sum() > 0
+
+
+def test_one_patch_equals_tiled_level():
+    """Ghost fill by same-level copy: a tiled level 1 is bitwise the single patch."""
+    w = W.hump200()
+    a = W.load(oracle.Oracle(w["cfg"]), w)
+    cfg = dict(w["cfg"], level1_tile=37)
+    b = W.load(oracle.Oracle(cfg), dict(w, cfg=cfg))
+    assert b.num_patches(0, 1) == 36
+    a.step(30)
+    b.step(30)
+    for f in ("h", "hu", "hv"):
+        assert np.array_equal(a.level_array(0, 1, f), b.level_array(0, 1, f))
+    assert a.stats()["dt"] == b.stats()["dt"]
+
+
+# --------------------------------------------------------------------------
+# AMR
+
+def test_interpolation_reproduces_linear_surface():
+    """Minmod-limited linear interpolation is exact on a linear surface
+    (pins the fine-cell offsets xi = ((I mod r) + 1/2)/r - 1/2)."""
+    cfg = W.base_config(nx=24, ny=20, dx=100.0, dy=100.0, num_levels=2, ratios=[4], bc=[W.BC_EXTRAP] * 4,
+                        regions=[[700.0, 500.0, 1700.0, 1500.0, 2, 2]], regrid_interval=0, patch_max=64)
+    xs = np.linspace(0, 2400, 25)
+    ys = np.linspace(0, 2000, 21)
+    eta = 0.01 * xs[None, :] - 0.02 * ys[:, None] + 1.0
+    w = dict(cfg=cfg, topo=[(np.full((2, 2), -50.0), 0.0, 0.0, 2400.0, 2000.0)],
+             eta=[(0, eta, 0.0, 0.0, 100.0, 100.0)], uplift=[], gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    pats = o.patches(0, 2)
+    assert len(pats) >= 1
+    dxf = 25.0
+    for (i0, j0, nx, ny), a in pats:
+        x = (i0 + np.arange(nx) + 0.5) * dxf
+        y = (j0 + np.arange(ny) + 0.5) * dxf
+        exact = 0.01 * x[None, :] - 0.02 * y[:, None] + 1.0
+        assert np.abs(a["h"] + a["B"] - exact).max() < 1e-12
+
+
+def test_amr_lake_at_rest():
+    """Still sea under 3-level AMR with regridding: exactly at rest on every level."""
+    w = W.amr3(L=120e3, dx1=4000.0, steps=8, eta_tol=0.01, depth_below=200.0)
+    cfg = dict(w["cfg"], regrid_interval=2)
+    w = dict(w, cfg=cfg, uplift=[])
+    o = W.load(oracle.Oracle(cfg), w)
+    assert o.num_patches(0, 2) > 0 and o.num_patches(0, 3) > 0
+    o.step(6)
+    for lev in (1, 2, 3):
+        for box, a in o.patches(0, lev):
+            assert np.abs(a["hu"]).max() == 0.0 and np.abs(a["hv"]).max() == 0.0
+            wet = a["h"] > 0
+            assert np.abs((a["h"] + a["B"])[wet]).max() == 0.0
+
+
+def _fixed_dt_cfg(cfg, dt):
+    c = dict(cfg)
+    c["dt_max"] = dt
+    c["cfl_desired"] = 0.9
+    return c
+
+
+def test_full_coverage_level2_equals_uniform_fine():
+    """Level 2 covering the whole domain (forced region) evolves exactly like
+    a uniform grid at the fine resolution with the same time steps."""
+    nx, dx, r = 16, 400.0, 4
+    L = nx * dx
+    base = W.base_config(nx=nx, ny=nx, dx=dx, dy=dx, bc=[W.BC_WALL] * 4)
+    topo = [(np.array([[-30.0, -10.0], [-30.0, -10.0]]), 0.0, 0.0, L, L)]
+    up = W.gaussian_grid(0.0, 0.0, L, L, 65, 65, 3000.0, 3400.0, 0.8, 700.0, 500.0)
+    dt = 2.0
+    amr_cfg = _fixed_dt_cfg(dict(base, num_levels=2, ratios=[r], regrid_interval=2, patch_max=24,
+                                 regions=[[-1.0, -1.0, L + 1, L + 1, 2, 2]]), dt)
+    fine_cfg = _fixed_dt_cfg(W.base_config(nx=nx * r, ny=nx * r, dx=dx / r, dy=dx / r, bc=[W.BC_WALL] * 4,
+                                           level1_tile=29), dt / r)
+    a = oracle.Oracle(amr_cfg)
+    b = oracle.Oracle(fine_cfg)
+    for o in (a, b):
+        o.add_topo(*topo[0])
+        o.init()
+        o.add_uplift(0, *up)
+    for _ in range(3):
+        a.step(1)
+        b.step(r)
+    assert a.stats()["cfl_violations"] == 0
+    for f in ("h", "hu", "hv"):
+        assert np.array_equal(a.level_array(0, 2, f), b.level_array(0, 1, f))
+
+
+def test_averaging_conserves_mass_flat_bed():
+    """Full coverage over a flat bed with no dry cells: the averaged level-1
+    mass equals the level-2 mass."""
+    nx, dx, r = 12, 300.0, 4
+    L = nx * dx
+    cfg = _fixed_dt_cfg(W.base_config(nx=nx, ny=nx, dx=dx, dy=dx, bc=[W.BC_WALL] * 4, num_levels=2,
+                                      ratios=[r], regrid_interval=3, patch_max=16,
+                                      regions=[[-1.0, -1.0, L + 1, L + 1, 2, 2]]), 1.5)
+    o = oracle.Oracle(cfg)
+    o.add_topo(np.full((2, 2), -20.0), 0.0, 0.0, L, L)
+    o.set_eta(0, *W.gaussian_grid(0, 0, L, L, 49, 49, 1500, 2000, 1.0, 400, 300))
+    o.init()
+    o.step(4)
+    m1 = np.nansum(o.level_array(0, 1, "h")) * dx * dx
+    m2 = np.nansum(o.level_array(0, 2, "h")) * (dx / r) ** 2
+    assert abs(m1 - m2) <= 1e-12 * m2
+
+
+def test_partial_refinement_closer_to_fine_than_coarse():
+    """A refined patch around a wave is closer to the uniform fine solution
+    than the coarse grid is (space-time interpolation at its boundary)."""
+    nx, dx, r = 24, 400.0, 4
+    L = nx * dx
+    topo = (np.full((2, 2), -40.0), 0.0, 0.0, L, L)
+    up = W.gaussian_grid(0.0, 0.0, L, L, 97, 97, 4800.0, 4800.0, 1.0, 900.0, 900.0)
+    reg = [[2400.0, 2400.0, 7200.0, 7200.0, 2, 2]]
+    dt = 3.0
+    amr = _fixed_dt_cfg(W.base_config(nx=nx, ny=nx, dx=dx, dy=dx, num_levels=2, ratios=[r], patch_max=64,
+                                      regrid_interval=0, regions=reg), dt)
+    crs = _fixed_dt_cfg(W.base_config(nx=nx, ny=nx, dx=dx, dy=dx), dt)
+    fin = _fixed_dt_cfg(W.base_config(nx=nx * r, ny=nx * r, dx=dx / r, dy=dx / r), dt / r)
+    runs = []
+    for cfg, k in ((amr, 1), (crs, 1), (fin, r)):
+        o = oracle.Oracle(cfg)
+        o.add_topo(*topo)
+        o.init()
+        o.add_uplift(0, *up)
+        for _ in range(6):
+            o.step(k)
+        runs.append(o)
+    a, c, f = runs
+    xs = np.arange(3000.0, 6600.0, 100.0) + 12.5
+    fa = a.read_field(0, 0, "eta", len(xs), len(xs), xs[0], xs[0], 100.0, 100.0)
+    fc = c.read_field(0, 0, "eta", len(xs), len(xs), xs[0], xs[0], 100.0, 100.0)
+    ff = f.read_field(0, 0, "eta", len(xs), len(xs), xs[0], xs[0], 100.0, 100.0)
+    assert np.abs(fa - ff).max() < 0.5 * np.abs(fc - ff).max()
+
+
+# --------------------------------------------------------------------------
+# clustering (Sec. 3.2, Berger & Rigoutsos)
+
+def _check_boxes(flags, boxes, pm=None):
+    ny, nx = flags.shape
+    cover = np.zeros_like(flags, dtype=int)
+    for i0, j0, w, h in boxes:
+        assert w > 0 and h > 0 and i0 >= 0 and j0 >= 0 and i0 + w <= nx and j0 + h <= ny
+        if pm is not None:
+            assert w <= pm and h <= pm
+        cover[j0:j0 + h, i0:i0 + w] += 1
+    assert cover.max() <= 1, "boxes overlap"
+    assert np.all(cover[flags.astype(bool)] == 1), "a flag is not covered"
+
+
+def test_cluster_single_rectangle():
+    f = np.zeros((20, 30), np.uint8)
+    f[3:9, 5:17] = 1
+    b = oracle.cluster(f)
+    assert b.tolist() == [[5, 3, 12, 6]]
+
+
+def test_cluster_hole_cut():
+    f = np.zeros((10, 20), np.uint8)
+    f[2:6, 1:5] = 1
+    f[2:6, 12:16] = 1
+    b = oracle.cluster(f)
+    assert sorted(b.tolist()) == [[1, 2, 4, 4], [12, 2, 4, 4]]
+
+
+def test_cluster_L_shape_and_random_invariants():
+    f = np.zeros((16, 16), np.uint8)
+    f[0:12, 0:3] = 1
+    f[9:12, 0:14] = 1
+    b = oracle.cluster(f)
+    _check_boxes(f, b)
+    assert len(b) >= 2
+    for i0, j0, w, h in b:
+        assert f[j0:j0 + h, i0:i0 + w].mean() >= 0.7
+    rng = np.random.default_rng(7)
+    for _ in range(60):
+        f = (rng.random((23, 31)) < rng.uniform(0.02, 0.4)).astype(np.uint8)
+        b = oracle.cluster(f, ratio=4, patch_max=24)
+        _check_boxes(f, b, pm=6)
+
+
+def test_cluster_respects_nesting():
+    f = np.zeros((12, 12), np.uint8)
+    f[1, 1] = 1
+    f[10, 10] = 1
+    f[1, 10] = 1
+    nest = np.ones_like(f)
+    nest[5:8, 5:8] = 0
+    b = oracle.cluster(f, nest, eff=0.0)
+    _check_boxes(f, b)
+    for i0, j0, w, h in b:
+        assert nest[j0:j0 + h, i0:i0 + w].all()

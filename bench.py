@@ -1,0 +1,303 @@
+#!/usr/bin/env python3
+"""Benchmark: cell updates per second of the shallow-water wave-propagation
+update on one GB300, FP32 surface-perturbation form (headline) and FP64.
+
+Workload (the 4096^2 uniform run): 4096 x 4096 cells, dx = 500 m, synthetic
+shelf bathymetry (4000 m abyssal plain, slope to a 200 m shelf, beach rising
+to +50 m dry land along one edge), 2 m elliptical Gaussian seafloor uplift at
+t = 0, extrapolating boundaries.  The state (537 MB in FP32, 1.07 GB in FP64
+per buffer pair) is larger than the 129 MB L2, so no flush is needed between
+steps.
+
+One JSON line on rank 0.  Under torchrun every rank runs an independent
+replica (the uniform grid is not sharded: replicas only) and `value` is the
+cell updates of all ranks over the slowest rank's time.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell updates/sec (all AMR levels) FP32-pert vs FP64 on 1 GB300; % HBM roofline"
+UNIT = "cell updates/s"
+BYTES_PER_CELL = {"f32p": 28, "f64": 56}   # read q0,q1,q2,B + write q0,q1,q2 per interior cell update
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("step_kernel.cuh", "step_f32p.cu", "step_f64.cu", "tsu_device.h"):
+        h.update(open(os.path.join(ROOT, "paper_1901_06798_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    only if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(prec)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_workload(prec_name, stream):
+    from paper_1901_06798_gb300 import binding
+    from paper_1901_06798_gb300 import workloads as W
+    w = W.shelf(n=4096, dx=500.0)
+    prec = binding.TSU_F32P if prec_name == "f32p" else binding.TSU_F64
+    ctx = binding.Tsunami(w["cfg"], precision=prec, stream=stream)
+    W.load(ctx, w)
+    return ctx, w
+
+
+def run_ours(args, rank, world, dist, torch):
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    clocks.start()
+    for prec in ("f32p", "f64"):
+        ctx, w = load_workload(prec, stream)
+        cells = w["cfg"]["nx"] * w["cfg"]["ny"]
+        K = args.steps if prec == "f32p" else max(1, min(args.steps, args.fp64_steps))
+        ctx.step(args.warmup)
+        l0 = ctx.stats()["kernel_launches"]
+        barrier()
+        torch.cuda.synchronize()
+        kernel_ms, step_ms = ctx.time_level1_steps(0, K)   # CUDA events on this stream
+        torch.cuda.synchronize()
+        barrier()
+        launches = ctx.stats()["kernel_launches"] - l0
+        elapsed = max_over_ranks(step_ms * K / 1000.0)
+        kern = max_over_ranks(kernel_ms)
+        results[prec] = dict(K=K, cells=cells, elapsed=elapsed, kernel_ms=kern, launches=launches,
+                             value=world * cells * K / elapsed)
+        ctx.close()
+        del ctx
+        torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    # end to end through the C ABI with host buffers: inputs uploaded from host
+    # arrays, every step returns the simulated time to the host, and the final
+    # surface field comes back to the host.
+    from paper_1901_06798_gb300 import binding
+    from paper_1901_06798_gb300 import workloads as W
+    w = W.shelf(n=4096, dx=500.0)
+    Ke = args.steps
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = binding.Tsunami(w["cfg"], precision=binding.TSU_F32P, stream=stream)
+    W.load(ctx, dict(w, gauges=np.zeros((0, 2))))
+    for _ in range(Ke):
+        ctx.step(1)
+    n = 4096
+    eta = ctx.read_field(0, 1, "eta", n, n, 250.0, 250.0, 500.0, 500.0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ctx.close()
+    e2e_elapsed = max_over_ranks(t1 - t0)
+    h2d = sum(g[0].nbytes for g in w["topo"]) + sum(u[1].nbytes for u in w["uplift"])
+    e2e = {"value": world * n * n * Ke / e2e_elapsed, "unit": UNIT, "h2d_bytes_per_step": h2d / Ke,
+           "d2h_bytes_per_step": 8 + eta.nbytes / Ke, "steps": Ke,
+           "note": "create + upload inputs + init + K tsu_step calls each returning t + final eta read"}
+    return results, clk, e2e
+
+
+def cpu_baseline():
+    """The FP64 oracle as it stands (one thread) on a bounded sample of the
+    workload: the full 4096^2 grid, 2 steps."""
+    import oracle
+    from paper_1901_06798_gb300 import workloads as W
+    w = W.shelf(n=4096, dx=500.0)
+    o = W.load(oracle.Oracle(w["cfg"], variant="fast"), dict(w, gauges=np.zeros((0, 2))))
+    t0 = time.perf_counter()
+    o.step(2)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * 4096 * 4096 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "full 4096x4096 shelf workload, 2 steps, FP64 oracle built -O3 -ffp-contract=off, 1 thread"}
+
+
+def _ref_worker(a):
+    """One host core: the oracle on a 512 x 512 window of the 4096^2 workload."""
+    steps, seed = a
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1901_06798_gb300 import workloads as W
+    w = W.shelf(n=4096, dx=500.0)
+    n = 512
+    i0 = 4096 - 1200 - n // 2 + (seed % 4) * 8
+    j0 = 2048 - n // 2 + (seed // 4) * 8
+    cfg = dict(w["cfg"], nx=n, ny=n, x0=i0 * 500.0, y0=j0 * 500.0)
+    o = W.load(oracle.Oracle(cfg, variant="fast"), dict(w, cfg=cfg, gauges=np.zeros((0, 2))))
+    t0 = time.perf_counter()
+    o.step(steps)
+    return n * n * steps, time.perf_counter() - t0
+
+
+def run_reference(args):
+    import multiprocessing as mp
+    import oracle
+    oracle.build("fast")
+    cores = min(os.cpu_count() or 1, 16)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_ref_worker, [(args.warmup, k) for k in range(cores)])
+        t0 = time.perf_counter()
+        res = pool.map(_ref_worker, [(args.steps, k) for k in range(cores)])
+        wall = time.perf_counter() - t0
+    cells = sum(r[0] for r in res)
+    v = cells / wall
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "shelf4096: 512x512 windows of the 4096x4096 dx=500 m shelf/uplift workload, "
+                                   f"one per host core ({cores})"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} x 512x512 windows of the 4096^2 workload, {args.steps} steps each"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 0)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    results, clk, e2e = run_ours(args, rank, world, dist, torch)
+    if rank == 0:
+        hbm, src = peaks()
+        r = results["f32p"]
+        bpl = BYTES_PER_CELL["f32p"] * r["cells"]
+        achieved = bpl / (r["kernel_ms"] / 1e3) / 1e9
+        traffic = ncu_traffic("f32p")
+        r64 = results["f64"]
+        b64 = BYTES_PER_CELL["f64"] * r64["cells"]
+        line = {
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": r["K"],
+            "warmup": args.warmup, "ms_per_step": r["elapsed"] / r["K"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "shelf4096: 4096x4096 cells, dx=500 m, shelf bathymetry with beach and dry land, "
+                                   "2 m Gaussian uplift (25x50 km sigma) at t=0, extrapolating boundaries",
+                       "precision": "FP32 surface-perturbation form (eta', hu, hv, B in FP32)",
+                       "l2": "inputs larger than L2 (state 537 MB FP32 / 1.07 GB FP64); no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "kernel": "step_kernel<float,pert>", "kernel_ms": r["kernel_ms"],
+                         "bytes_per_launch": bpl, "peak_source": src},
+            "fp64": {"value": r64["value"], "steps": r64["K"], "ms_per_step": r64["elapsed"] / r64["K"] * 1e3,
+                     "kernel_ms": r64["kernel_ms"],
+                     "hbm_frac": (b64 / (r64["kernel_ms"] / 1e3) / 1e9) / hbm},
+            "fp32p_over_fp64": r["value"] / r64["value"],
+            "gpu_launches": results["f32p"]["launches"],
+            "clocks": clk,
+            "e2e": e2e,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * tsunami.h -- C ABI of the GB300 shallow-water AMR library.
+ *
+ * The library advances the shallow water equations over bathymetry (Sec. 2.1,
+ * Eq. swe, without the drag term) with the wave-propagation form of Godunov's
+ * method, limited second-order corrections and Godunov dimensional splitting
+ * (Sec. 2.2, Eqs. wave_propagation_form, wave_propagation_2nd_order, _x, _y,
+ * theta), on block-structured AMR patches (Sec. 3: hierarchy, recursive time
+ * integration of Sec. 3.1 steps 1-4 -- refluxing (step 5) is omitted as in the
+ * paper's GPU code -- and the regridding of Sec. 3.2).  All state lives in
+ * device memory; every step of the method runs in the library's CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *   - returns TSU_OK (0) or a negative TSU_ERR_* code; nothing throws across
+ *     the ABI; tsu_last_error() describes the last failure of a context;
+ *   - the library owns all device memory (a pooled arena, Sec. 4.2 "Memory
+ *     Pool"); the caller owns every host buffer it passes and the library
+ *     never keeps a caller pointer after the call returns;
+ *   - host arrays are row-major, x fastest: element (i, j) at [j * nx + i];
+ *   - grids passed in (topography, surface, uplift) are node grids: value k
+ *     sits at x0 + i dx, y0 + j dy and is sampled bilinearly; nx, ny >= 2;
+ *   - levels are 1-based (level 1 covers the whole domain), scenarios 0-based;
+ *   - a context is not thread-safe; calls on one context must be serialised.
+ *
+ * Error codes: TSU_ERR_ARG (bad argument or call order), TSU_ERR_CUDA (a CUDA
+ * runtime error; the message names it), TSU_ERR_CFL (a level step ran with
+ * Courant number above cfl_max; the step is kept and the run continues),
+ * TSU_ERR_NESTING (an AMR invariant failed), TSU_ERR_OOM (device memory),
+ * TSU_ERR_NOT_BUILT (the CUDA library is not loaded on a GPU).
+ */
+#ifndef TSUNAMI_H
+#define TSUNAMI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSU_MAX_LEVELS 8
+#define TSU_MAX_REGIONS 8
+
+enum {
+    TSU_OK = 0,
+    TSU_ERR_ARG = -1,
+    TSU_ERR_CUDA = -2,
+    TSU_ERR_CFL = -3,
+    TSU_ERR_NESTING = -4,
+    TSU_ERR_OOM = -5,
+    TSU_ERR_NOT_BUILT = -6
+};
+
+enum { TSU_F64 = 0, TSU_F32P = 1 };              /* precision of the state */
+enum { TSU_BC_WALL = 0, TSU_BC_EXTRAP = 1 };     /* physical boundary rule */
+enum { TSU_H = 0, TSU_HU = 1, TSU_HV = 2, TSU_ETA = 3, TSU_ZETA = 4, TSU_B = 5 };
+
+typedef struct tsu_ctx tsu_ctx;
+
+/* Run configuration.  Units: metres, seconds. */
+typedef struct tsu_config {
+    int precision;              /* TSU_F64: state (h, hu, hv) and B in FP64.
+                                   TSU_F32P: state (eta' = h + B, hu, hv) and B in
+                                   FP32 -- the surface-perturbation form */
+    int nx, ny;                 /* level-1 cells */
+    double x0, y0, dx, dy;      /* lower-left corner and level-1 cell size */
+    int num_levels;             /* 1 .. TSU_MAX_LEVELS */
+    int ratios[TSU_MAX_LEVELS]; /* ratios[k] refines level k+1 into level k+2 (space and time, Sec. 3) */
+    int bc[4];                  /* left, right, bottom, top */
+    double g;                   /* gravity, 9.81 */
+    double drytol;              /* a cell is dry if h < drytol */
+    double cfl_desired;         /* nu_d used to choose dt (Sec. 2.2 CFL condition) */
+    double cfl_max;             /* a level step with nu > cfl_max returns TSU_ERR_CFL */
+    double dt_max;              /* cap on the level-1 time step */
+    int regrid_interval;        /* b: regrid every b steps of a level; also the flag buffer (Sec. 3.2) */
+    double flag_eta_tol;        /* flag wet cells with |eta| > tol; <= 0 disables */
+    double flag_depth_below;    /* flag cells with still-water depth -B < value; <= 0 disables */
+    int patch_max;              /* largest fine patch side in fine cells */
+    int level1_tile;            /* 0: level 1 is one patch; else square tiles of this side */
+    int n_regions;
+    double regions[TSU_MAX_REGIONS][6]; /* x1, y1, x2, y2, min_level, max_level (1-based levels) */
+    int n_scenarios;            /* independent scenarios advanced together (>= 1) */
+    int transverse;             /* must be 0: dimensional splitting (the paper's GPU scheme) */
+    double cluster_eff;         /* Berger-Rigoutsos box efficiency, 0.7 if <= 0 */
+    int use_graphs;             /* capture repeated coarse steps as a CUDA graph */
+} tsu_config;
+
+typedef struct tsu_stats {
+    double dt;                  /* last level-1 time step */
+    double t;                   /* simulated time */
+    double mass;                /* sum of h dx dy over level 1, FP64 */
+    double cell_updates;        /* interior cells x steps summed over levels */
+    long long cfl_violations;
+    int patches[TSU_MAX_LEVELS];
+    long long kernel_launches;  /* kernels this context has launched */
+} tsu_stats;
+
+/* Create a context.  cfg is copied.  cuda_stream: a cudaStream_t (for example
+ * torch.cuda.current_stream().cuda_stream) or NULL for a stream the library
+ * creates.  Allocates the device arena lazily.  Errors: TSU_ERR_ARG for an
+ * invalid configuration, TSU_ERR_CUDA, TSU_ERR_NOT_BUILT. */
+int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out);
+
+/* Destroy a context and release its device memory.  NULL is accepted. */
+int tsu_destroy(tsu_ctx *ctx);
+
+/* Message of the last failure of ctx (owned by ctx; valid until the next call). */
+const char *tsu_last_error(tsu_ctx *ctx);
+
+/* Add a bathymetry/topography grid B (metres, B < 0 under sea level; Sec. 2.1).
+ * Where several grids cover a point the finest wins (later grids win ties).
+ * Before tsu_init only.  B: nx*ny host doubles, copied. */
+int tsu_add_topo(tsu_ctx *ctx, const double *B, int nx, int ny, double x0, double y0, double dx, double dy);
+
+/* Initial sea surface eta of one scenario (default 0); h = max(0, eta - B).
+ * Before tsu_init only.  eta: nx*ny host doubles, copied. */
+int tsu_set_eta(tsu_ctx *ctx, int scenario, const double *eta, int nx, int ny,
+                double x0, double y0, double dx, double dy);
+
+/* Instantaneous seafloor deformation (Sec. 5.1.1 dtopo, applied at once):
+ * B += dB on every cell of every level with h unchanged, so the surface rises
+ * with the seafloor; later patches sample it too.  May be called before or
+ * after tsu_init.  dB: nx*ny host doubles, copied. */
+int tsu_add_uplift(tsu_ctx *ctx, int scenario, const double *dB, int nx, int ny,
+                   double x0, double y0, double dx, double dy);
+
+/* Build level 1 (tiled per cfg), sample B, set the state, and build the finer
+ * levels by flagging and clustering (Sec. 3.2).  Requires one tsu_add_topo. */
+int tsu_init(tsu_ctx *ctx);
+
+/* Advance n coarse (level-1) steps with the recursive integration of Sec. 3.1,
+ * regridding every regrid_interval steps of each level.  t_out (may be NULL)
+ * receives n_scenarios doubles: the simulated time of each scenario.
+ * Returns TSU_ERR_CFL if any level step exceeded cfl_max (work is done). */
+int tsu_step(tsu_ctx *ctx, int n_coarse_steps, double *t_out);
+
+/* Regenerate levels level+1 .. num_levels from flags on `level` (Sec. 3.2). */
+int tsu_regrid(tsu_ctx *ctx, int scenario, int level);
+
+/* Number of patches of a level, and their boxes: 4 ints per patch (i0, j0, nx,
+ * ny) in global cell indices of that level, in the library's patch order. */
+int tsu_num_patches(tsu_ctx *ctx, int scenario, int level, int *n);
+int tsu_get_patches(tsu_ctx *ctx, int scenario, int level, int *boxes, int max_patches, int *n);
+
+/* Copy the interior of patch k of a level to host: h, hu, hv, B, each
+ * nx*ny doubles (any may be NULL).  h is the depth in both precisions. */
+int tsu_get_patch(tsu_ctx *ctx, int scenario, int level, int k, double *h, double *hu, double *hv, double *B);
+
+/* Sample a field on the points (x0 + i dx, y0 + j dy), i < nx, j < ny:
+ * piecewise constant from the finest patch (level == 0) or from level
+ * `level` only; NaN where nothing covers a point.  Fields: TSU_H, TSU_HU,
+ * TSU_HV, TSU_ETA (h + B), TSU_ZETA (Eq. zeta: h where B > 0, else h + B),
+ * TSU_B.  dst: nx*ny host doubles. */
+int tsu_read_field(tsu_ctx *ctx, int scenario, int level, int field, double *dst, int nx, int ny,
+                   double x0, double y0, double dx, double dy);
+
+/* Gauges (Sec. 5.1.2): points xy[2k], xy[2k+1]; before the first tsu_step.
+ * After every coarse step the library records eta at each gauge from the
+ * finest patch containing it (bilinear between cell centres). */
+int tsu_add_gauges(tsu_ctx *ctx, const double *xy, int n);
+
+/* Read the recorded samples: t[s*ns + scen], eta[(s*ns + scen)*ngauges + g]
+ * for samples s < *n_written <= max_samples. */
+int tsu_read_gauges(tsu_ctx *ctx, double *t, double *eta, int max_samples, int *n_written);
+
+/* Statistics of one scenario (synchronises the stream). */
+int tsu_get_stats(tsu_ctx *ctx, int scenario, tsu_stats *out);
+
+/* Launch shape of the patch update (the autotuner's knobs): step_threads
+ * threads per CTA (64, 128 or 256; a CTA updates a strip of step_threads - 4
+ * columns) and seg_rows rows per CTA (patches taller than that are cut into
+ * row segments).  0 restores the defaults.  Results do not depend on either. */
+int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows);
+
+/* Synchronise the context's stream. */
+int tsu_sync(tsu_ctx *ctx);
+
+/* Device pointer of level-1 patch 0's current state buffers, for tests and
+ * the benchmark (fields h|eta', hu, hv, B; element type by precision;
+ * row pitch in elements; interior cell (i, j) at [(j + 2) * pitch + i + 2]). */
+int tsu_level1_buffers(tsu_ctx *ctx, void **h, void **hu, void **hv, void **B, int *pitch);
+
+/* Time n level-1 steps of the patch update alone (no AMR bookkeeping) with CUDA
+ * events on the library's stream after `warmup` untimed steps; ms_out gets the
+ * mean milliseconds of the step kernel per step and total_ms_out the whole
+ * step (ghost fill + update + reductions).  Advances the solution. */
+int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out, double *step_ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -191,50 +191,41 @@ static OPatch *find_patch(const Ora *o, int s, int l, int I, int J, const OPatch
     return NULL;
 }
 
-/* Physical boundary conditions on the ghost cells outside the domain:
- * left/right ghost columns on every row first, then bottom/top ghost rows on
- * every column (so corners end up defined by the y rule).  wall: mirror with
- * the normal momentum negated; extrapolation: copy of the edge cell.
- * mom = 0 for B (never negated). */
+/* Physical boundary conditions on the ghost cells outside the domain, in
+ * global indices: a ghost cell beyond the left edge at I < 0 takes cell -1-I
+ * (wall: mirror, normal momentum negated) or cell 0 (extrapolation); beyond
+ * the right edge at I >= nx_l it takes 2 nx_l - 1 - I or nx_l - 1; the same in
+ * y.  The source lies in the patch's own storage (interior or a ghost cell
+ * already filled by copy or interpolation), also when a thin neighbour patch
+ * sits between this patch and the boundary.  Left/right ghost columns on
+ * every row first, then bottom/top ghost rows on every column, so corners end
+ * up defined by the y rule.  normal_x/normal_y: negate under a wall (never
+ * for B). */
 static void apply_bc_field(const Ora *o, OPatch *p, double *f, int normal_x, int normal_y)
 {
-    int l = p->level, nx = p->nx, ny = p->ny;
-    if (p->i0 == 0) {
-        for (int j = -2; j < ny + 2; j++)
-            for (int k = 0; k < 2; k++) {
-                double v;
-                if (o->c.bc[0] == ORA_BC_WALL) { v = f[OIDX(p, k, j)]; if (normal_x) v = -v; }
-                else v = f[OIDX(p, 0, j)];
-                f[OIDX(p, -1 - k, j)] = v;
-            }
-    }
-    if (p->i0 + nx == o->nxl[l]) {
-        for (int j = -2; j < ny + 2; j++)
-            for (int k = 0; k < 2; k++) {
-                double v;
-                if (o->c.bc[1] == ORA_BC_WALL) { v = f[OIDX(p, nx - 1 - k, j)]; if (normal_x) v = -v; }
-                else v = f[OIDX(p, nx - 1, j)];
-                f[OIDX(p, nx + k, j)] = v;
-            }
-    }
-    if (p->j0 == 0) {
-        for (int i = -2; i < nx + 2; i++)
-            for (int k = 0; k < 2; k++) {
-                double v;
-                if (o->c.bc[2] == ORA_BC_WALL) { v = f[OIDX(p, i, k)]; if (normal_y) v = -v; }
-                else v = f[OIDX(p, i, 0)];
-                f[OIDX(p, i, -1 - k)] = v;
-            }
-    }
-    if (p->j0 + ny == o->nyl[l]) {
-        for (int i = -2; i < nx + 2; i++)
-            for (int k = 0; k < 2; k++) {
-                double v;
-                if (o->c.bc[3] == ORA_BC_WALL) { v = f[OIDX(p, i, ny - 1 - k)]; if (normal_y) v = -v; }
-                else v = f[OIDX(p, i, ny - 1)];
-                f[OIDX(p, i, ny + k)] = v;
-            }
-    }
+    int l = p->level, nx = p->nx, ny = p->ny, nxl = o->nxl[l], nyl = o->nyl[l];
+    for (int j = -2; j < ny + 2; j++)
+        for (int i = -2; i < nx + 2; i++) {
+            int I = p->i0 + i, src, neg = 0;
+            if (I < 0) {
+                if (o->c.bc[0] == ORA_BC_WALL) { src = -1 - I; neg = normal_x; } else src = 0;
+            } else if (I >= nxl) {
+                if (o->c.bc[1] == ORA_BC_WALL) { src = 2 * nxl - 1 - I; neg = normal_x; } else src = nxl - 1;
+            } else continue;
+            double v = f[OIDX(p, src - p->i0, j)];
+            f[OIDX(p, i, j)] = neg ? -v : v;
+        }
+    for (int i = -2; i < nx + 2; i++)
+        for (int j = -2; j < ny + 2; j++) {
+            int J = p->j0 + j, src, neg = 0;
+            if (J < 0) {
+                if (o->c.bc[2] == ORA_BC_WALL) { src = -1 - J; neg = normal_y; } else src = 0;
+            } else if (J >= nyl) {
+                if (o->c.bc[3] == ORA_BC_WALL) { src = 2 * nyl - 1 - J; neg = normal_y; } else src = nyl - 1;
+            } else continue;
+            double v = f[OIDX(p, i, src - p->j0)];
+            f[OIDX(p, i, j)] = neg ? -v : v;
+        }
 }
 
 /* The x rule must run on all three fields before the y rule, field order

@@ -1,0 +1,870 @@
+// amr_kernels.cu -- the kernels around the patch update: ghost-cell fill
+// (same-level copy, coarse-to-fine space-time interpolation, physical
+// boundaries), fine-to-coarse averaging, flagging with buffer dilation and
+// proper nesting, topography sampling, seafloor uplift, the CFL / dt
+// bookkeeping that keeps dt on the device, gauges and field reads.
+//
+// Built with --fmad=false: the FP64 instantiations round every operation as
+// the FP64 oracle does.  Each kernel batches all patches of a level (and all
+// scenarios) into one launch.
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "amr_kernels.h"
+
+namespace tsu {
+
+// ---------------------------------------------------------------- helpers
+
+template <typename T> struct Acc {
+    T *base;
+    long long fs;
+    int pitch;
+    __device__ __forceinline__ long long idx(int i, int j) const { return (long long)(j + 2) * pitch + (i + 2); }
+    __device__ __forceinline__ T *f(int buf, int m) const { return base + (long long)(buf * 3 + m) * fs; }
+    __device__ __forceinline__ T *Bp() const { return base + 6LL * fs; }
+};
+
+template <typename T> __device__ __forceinline__ Acc<T> acc(void *arena, const PatchDesc &P)
+{
+    Acc<T> a;
+    a.base = reinterpret_cast<T *>(arena) + P.off;
+    a.fs = P.fs;
+    a.pitch = P.pitch;
+    return a;
+}
+
+__device__ __forceinline__ int ring_count(const PatchDesc &P) { return (P.nx + 4) * (P.ny + 4) - P.nx * P.ny; }
+
+// ghost cell g of a patch -> (i, j): 2 bottom rows, 2 top rows, then the 2+2
+// side columns of the interior rows.
+__device__ __forceinline__ void ring_cell(const PatchDesc &P, int g, int &i, int &j)
+{
+    int W = P.nx + 4;
+    if (g < 2 * W) { j = -2 + g / W; i = -2 + g % W; return; }
+    g -= 2 * W;
+    if (g < 2 * W) { j = P.ny + g / W; i = -2 + g % W; return; }
+    g -= 2 * W;
+    j = g / 4;
+    int k = g % 4;
+    i = k < 2 ? -2 + k : P.nx + (k - 2);
+}
+
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    if (a > 0.0 && b > 0.0) return fmin(a, b);
+    if (a < 0.0 && b < 0.0) return fmax(a, b);
+    return 0.0;
+}
+
+// one coarse cell's (eta, hu, hv) at time fraction alpha, in double
+struct CVal {
+    int found, wet;
+    double q[3];
+};
+
+template <typename T, bool PERT>
+__device__ CVal coarse_value(const LevelView &C, int cur_c, const int *cmap, const PatchDesc &F, int I, int J,
+                             double alpha, double drytol)
+{
+    CVal v;
+    v.found = 0; v.wet = 0; v.q[0] = v.q[1] = v.q[2] = 0.0;
+    if (I < 0 || I >= C.nxl || J < 0 || J >= C.nyl) return v;
+    int mi = I - F.cmap_i0, mj = J - F.cmap_j0;
+    if (mi < 0 || mi >= F.cmap_w || mj < 0 || mj >= F.cmap_h) return v;
+    int cp = cmap[F.cmap_off + mj * F.cmap_w + mi];
+    if (cp < 0) return v;
+    const PatchDesc P = C.descs[cp];
+    Acc<T> a = acc<T>(C.arena, P);
+    long long k = a.idx(I - P.i0, J - P.j0);
+    double B = (double)a.Bp()[k];
+    double q0n = (double)a.f(cur_c, 0)[k], q1n = (double)a.f(cur_c, 1)[k], q2n = (double)a.f(cur_c, 2)[k];
+    double q0, q1, q2;
+    if (alpha == 1.0) { q0 = q0n; q1 = q1n; q2 = q2n; }
+    else {
+        double q0o = (double)a.f(1 - cur_c, 0)[k], q1o = (double)a.f(1 - cur_c, 1)[k], q2o = (double)a.f(1 - cur_c, 2)[k];
+        q0 = q0o + alpha * (q0n - q0o);
+        q1 = q1o + alpha * (q1n - q1o);
+        q2 = q2o + alpha * (q2n - q2o);
+    }
+    v.found = 1;
+    double h = PERT ? q0 - B : q0;
+    v.wet = h >= drytol;
+    v.q[0] = PERT ? q0 : h + B;
+    v.q[1] = q1;
+    v.q[2] = q2;
+    return v;
+}
+
+// Space-time interpolation of fine cell (I, J) of level F from the coarse
+// level (minmod-limited linear in space of eta, hu, hv over wet neighbours;
+// a dry coarse centre takes the lowest wet surface of its 3x3 neighbourhood).
+// Writes q0 (h or eta'), q1, q2; returns false on a nesting error.
+template <typename T, bool PERT>
+__device__ bool interp_fine(const LevelView &C, int cur_c, const int *cmap, const PatchDesc &F, int r, int I, int J,
+                            double Bf, double alpha, double drytol, T &o0, T &o1, T &o2)
+{
+    int Ic = I / r, Jc = J / r;
+    CVal c = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic, Jc, alpha, drytol);
+    if (!c.found) return false;
+    double hf, hu, hv;
+    if (!c.wet) {
+        double eref = 0.0;
+        int any = 0;
+        for (int dj = -1; dj <= 1; dj++)
+            for (int di = -1; di <= 1; di++) {
+                if (di == 0 && dj == 0) continue;
+                CVal nb = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic + di, Jc + dj, alpha, drytol);
+                if (nb.found && nb.wet && (!any || nb.q[0] < eref)) { eref = nb.q[0]; any = 1; }
+            }
+        hf = any ? eref - Bf : 0.0;
+        if (hf < 0.0) hf = 0.0;
+        hu = 0.0; hv = 0.0;
+    } else {
+        CVal xm = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic - 1, Jc, alpha, drytol);
+        CVal xp = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic + 1, Jc, alpha, drytol);
+        CVal ym = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic, Jc - 1, alpha, drytol);
+        CVal yp = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic, Jc + 1, alpha, drytol);
+        double xi = ((double)(I - Ic * r) + 0.5) / (double)r - 0.5;
+        double et = ((double)(J - Jc * r) + 0.5) / (double)r - 0.5;
+        double qf[3];
+        for (int m = 0; m < 3; m++) {
+            double dxp = (xp.found && xp.wet) ? xp.q[m] - c.q[m] : 0.0;
+            double dxm = (xm.found && xm.wet) ? c.q[m] - xm.q[m] : 0.0;
+            double dyp = (yp.found && yp.wet) ? yp.q[m] - c.q[m] : 0.0;
+            double dym = (ym.found && ym.wet) ? c.q[m] - ym.q[m] : 0.0;
+            double sx = minmod(dxp, dxm), sy = minmod(dyp, dym);
+            qf[m] = (c.q[m] + xi * sx) + et * sy;
+        }
+        hf = qf[0] - Bf;
+        if (hf < 0.0) hf = 0.0;
+        if (hf < drytol) { hu = 0.0; hv = 0.0; }
+        else { hu = qf[1]; hv = qf[2]; }
+    }
+    o0 = PERT ? (T)(hf + Bf) : (T)hf;
+    o1 = (T)hu;
+    o2 = (T)hv;
+    return true;
+}
+
+// ---------------------------------------------------------------- ghost fill
+
+template <typename T, bool PERT>
+__global__ void ghost_fill_kernel(LevelView L, LevelView C, int cur, int cur_c, int ratio, double alpha, double drytol,
+                                  int *err)
+{
+    const PatchDesc P = L.descs[blockIdx.y];
+    const int n = ring_count(P);
+    Acc<T> a = acc<T>(L.arena, P);
+    T *q0 = a.f(cur, 0), *q1 = a.f(cur, 1), *q2 = a.f(cur, 2);
+    const T *Bp = a.Bp();
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        int i, j;
+        ring_cell(P, g, i, j);
+        int I = P.i0 + i, J = P.j0 + j;
+        if (I < 0 || I >= L.nxl || J < 0 || J >= L.nyl) continue;
+        long long k = a.idx(i, j);
+        int src = -1;
+        for (int m = 0; m < P.nbr_cnt; m++) {
+            int qi = L.nbrs[P.nbr_off + m];
+            const PatchDesc &Q = L.descs[qi];
+            if (I >= Q.i0 && I < Q.i0 + Q.nx && J >= Q.j0 && J < Q.j0 + Q.ny) { src = qi; break; }
+        }
+        if (src >= 0) {
+            const PatchDesc Q = L.descs[src];
+            Acc<T> b = acc<T>(L.arena, Q);
+            long long kq = b.idx(I - Q.i0, J - Q.j0);
+            q0[k] = b.f(cur, 0)[kq];
+            q1[k] = b.f(cur, 1)[kq];
+            q2[k] = b.f(cur, 2)[kq];
+        } else if (ratio > 0) {
+            T o0, o1, o2;
+            if (interp_fine<T, PERT>(C, cur_c, L.cmap, P, ratio, I, J, (double)Bp[k], alpha, drytol, o0, o1, o2)) {
+                q0[k] = o0; q1[k] = o1; q2[k] = o2;
+            } else {
+                atomicOr(err, 1);
+            }
+        } else {
+            atomicOr(err, 1);
+        }
+    }
+}
+
+// Physical boundaries: every ghost cell outside the domain takes the value of
+// its source cell in global indices -- wall: the mirror image across the
+// domain edge with the normal momentum negated; extrapolation: the edge cell
+// -- applied in x and then in y (the composition gives the corners).  The
+// source always lies in the patch's own storage: an interior cell or a ghost
+// cell inside the domain that the fill kernel wrote before.
+__device__ __forceinline__ bool bc_source(const PatchDesc &P, int nxl, int nyl, const int *bc, int i, int j, int &si,
+                                          int &sj, bool &negx, bool &negy)
+{
+    int I = P.i0 + i, J = P.j0 + j;
+    bool out = false;
+    si = i; sj = j; negx = false; negy = false;
+    if (I < 0) {
+        out = true;
+        if (bc[0] == 0) { si = (-1 - I) - P.i0; negx = true; } else si = -P.i0;
+    } else if (I >= nxl) {
+        out = true;
+        if (bc[1] == 0) { si = (2 * nxl - 1 - I) - P.i0; negx = true; } else si = nxl - 1 - P.i0;
+    }
+    if (J < 0) {
+        out = true;
+        if (bc[2] == 0) { sj = (-1 - J) - P.j0; negy = true; } else sj = -P.j0;
+    } else if (J >= nyl) {
+        out = true;
+        if (bc[3] == 0) { sj = (2 * nyl - 1 - J) - P.j0; negy = true; } else sj = nyl - 1 - P.j0;
+    }
+    return out;
+}
+
+template <typename T>
+__global__ void bc_kernel(LevelView L, int cur, BcArgs bcs, int do_state, int do_B)
+{
+    const PatchDesc P = L.descs[bcs.list[blockIdx.y]];
+    const int n = ring_count(P);
+    Acc<T> a = acc<T>(L.arena, P);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        int i, j, si, sj;
+        bool nx_, ny_;
+        ring_cell(P, g, i, j);
+        if (!bc_source(P, L.nxl, L.nyl, bcs.bc, i, j, si, sj, nx_, ny_)) continue;
+        long long k = a.idx(i, j), ks = a.idx(si, sj);
+        if (do_state) {
+            T *q0 = a.f(cur, 0), *q1 = a.f(cur, 1), *q2 = a.f(cur, 2);
+            T v1 = q1[ks], v2 = q2[ks];
+            q0[k] = q0[ks];
+            q1[k] = nx_ ? -v1 : v1;
+            q2[k] = ny_ ? -v2 : v2;
+        }
+        if (do_B) a.Bp()[k] = a.Bp()[ks];
+    }
+}
+
+// ---------------------------------------------------------------- averaging
+
+template <typename T, bool PERT>
+__global__ void average_kernel(LevelView Fv, LevelView C, int cur_f, int cur_c, int r, double drytol, int *err)
+{
+    const PatchDesc F = Fv.descs[blockIdx.y];
+    const int cw = F.nx / r, ch = F.ny / r;
+    const int n = cw * ch;
+    Acc<T> fa = acc<T>(Fv.arena, F);
+    const T *f0 = fa.f(cur_f, 0), *f1 = fa.f(cur_f, 1), *f2 = fa.f(cur_f, 2), *fB = fa.Bp();
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int Ic = F.i0 / r + c % cw, Jc = F.j0 / r + c / cw;
+        int mi = Ic - F.cmap_i0, mj = Jc - F.cmap_j0;
+        int cp = Fv.cmap[F.cmap_off + mj * F.cmap_w + mi];
+        if (cp < 0) { atomicOr(err, 2); continue; }
+        double se = 0.0, su = 0.0, sv = 0.0;
+        int nwet = 0;
+        for (int jj = 0; jj < r; jj++)
+            for (int ii = 0; ii < r; ii++) {
+                long long kf = fa.idx(Ic * r + ii - F.i0, Jc * r + jj - F.j0);
+                double B = (double)fB[kf];
+                double q0 = (double)f0[kf];
+                double h = PERT ? q0 - B : q0;
+                if (h >= drytol) { se = se + (PERT ? q0 : h + B); nwet++; }
+                su = su + (double)f1[kf];
+                sv = sv + (double)f2[kf];
+            }
+        const PatchDesc P = C.descs[cp];
+        Acc<T> ca = acc<T>(C.arena, P);
+        long long kc = ca.idx(Ic - P.i0, Jc - P.j0);
+        double Bc = (double)ca.Bp()[kc];
+        double hc = 0.0;
+        if (nwet > 0) {
+            hc = se / (double)nwet - Bc;
+            if (hc < 0.0) hc = 0.0;
+        }
+        double rr = (double)(r * r);
+        ca.f(cur_c, 0)[kc] = PERT ? (T)(hc + Bc) : (T)hc;
+        if (hc < drytol) { ca.f(cur_c, 1)[kc] = T(0); ca.f(cur_c, 2)[kc] = T(0); }
+        else { ca.f(cur_c, 1)[kc] = (T)(su / rr); ca.f(cur_c, 2)[kc] = (T)(sv / rr); }
+    }
+}
+
+// ---------------------------------------------------------------- topography
+
+__device__ __forceinline__ bool grid_contains(const TopoDev &g, double x, double y)
+{
+    return x >= g.x0 && x <= g.x0 + (double)(g.nx - 1) * g.dx && y >= g.y0 && y <= g.y0 + (double)(g.ny - 1) * g.dy;
+}
+
+__device__ double grid_bilinear(const TopoDev &g, double x, double y)
+{
+    double fx = (x - g.x0) / g.dx, fy = (y - g.y0) / g.dy;
+    int i = (int)floor(fx), j = (int)floor(fy);
+    if (i < 0) i = 0;
+    if (i > g.nx - 2) i = g.nx - 2;
+    if (j < 0) j = 0;
+    if (j > g.ny - 2) j = g.ny - 2;
+    double tx = fx - (double)i, ty = fy - (double)j;
+    if (tx < 0.0) tx = 0.0;
+    if (tx > 1.0) tx = 1.0;
+    if (ty < 0.0) ty = 0.0;
+    if (ty > 1.0) ty = 1.0;
+    const double *v = g.v;
+    double v00 = v[(long long)j * g.nx + i], v10 = v[(long long)j * g.nx + i + 1];
+    double v01 = v[(long long)(j + 1) * g.nx + i], v11 = v[(long long)(j + 1) * g.nx + i + 1];
+    double a = v00 + tx * (v10 - v00);
+    double b = v01 + tx * (v11 - v01);
+    return a + ty * (b - a);
+}
+
+__device__ double base_topo(const TopoSet &ts, double x, double y)
+{
+    int best = -1;
+    double barea = 0.0;
+    for (int k = 0; k < ts.nbase; k++) {
+        if (!grid_contains(ts.grids[k], x, y)) continue;
+        double area = ts.grids[k].dx * ts.grids[k].dy;
+        if (best < 0 || area <= barea) { best = k; barea = area; }
+    }
+    if (best < 0) best = 0;
+    return grid_bilinear(ts.grids[best], x, y);
+}
+
+__device__ double uplift_sum(const TopoSet &ts, int scen, double B, double x, double y)
+{
+    for (int k = ts.nbase; k < ts.ngrids; k++) {
+        if (ts.scen[k] != scen) continue;
+        if (grid_contains(ts.grids[k], x, y)) B = B + grid_bilinear(ts.grids[k], x, y);
+    }
+    return B;
+}
+
+// B (and, for level-1 initialisation, the state) of the patches in `list`
+// at every cell inside the domain; cells outside are filled by bc_kernel.
+template <typename T, bool PERT>
+__global__ void init_patch_kernel(LevelView L, const int *list, TopoSet ts, int cur, int set_state, double x0,
+                                  double y0, double dxl, double dyl)
+{
+    const PatchDesc P = L.descs[list[blockIdx.y]];
+    const int n = (P.nx + 4) * (P.ny + 4);
+    Acc<T> a = acc<T>(L.arena, P);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int i = c % (P.nx + 4) - 2, j = c / (P.nx + 4) - 2;
+        int I = P.i0 + i, J = P.j0 + j;
+        if (I < 0 || I >= L.nxl || J < 0 || J >= L.nyl) continue;
+        double x = x0 + ((double)I + 0.5) * dxl, y = y0 + ((double)J + 0.5) * dyl;
+        long long k = a.idx(i, j);
+        double B0 = base_topo(ts, x, y);
+        double B = uplift_sum(ts, P.scen, B0, x, y);
+        a.Bp()[k] = (T)B;
+        if (set_state) {
+            double eta = 0.0;
+            int eg = ts.eta_index[P.scen];
+            if (eg >= 0 && grid_contains(ts.grids[eg], x, y)) eta = grid_bilinear(ts.grids[eg], x, y);
+            double hh = eta - B0;
+            if (hh < 0.0) hh = 0.0;
+            a.f(cur, 0)[k] = PERT ? (T)(hh + B) : (T)hh;
+            a.f(cur, 1)[k] = T(0);
+            a.f(cur, 2)[k] = T(0);
+        }
+    }
+}
+
+// seafloor uplift of one layer on the patches of a level: B += dB, h unchanged
+template <typename T, bool PERT>
+__global__ void uplift_kernel(LevelView L, TopoDev U, int scen, int cur, double x0, double y0, double dxl, double dyl)
+{
+    const PatchDesc P = L.descs[blockIdx.y];
+    if (P.scen != scen) return;
+    const int n = (P.nx + 4) * (P.ny + 4);
+    Acc<T> a = acc<T>(L.arena, P);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int i = c % (P.nx + 4) - 2, j = c / (P.nx + 4) - 2;
+        int I = P.i0 + i, J = P.j0 + j;
+        if (I < 0 || I >= L.nxl || J < 0 || J >= L.nyl) continue;
+        double x = x0 + ((double)I + 0.5) * dxl, y = y0 + ((double)J + 0.5) * dyl;
+        if (!grid_contains(U, x, y)) continue;
+        double d = grid_bilinear(U, x, y);
+        long long k = a.idx(i, j);
+        double Bo = (double)a.Bp()[k];
+        a.Bp()[k] = (T)(Bo + d);
+        if (PERT) {
+            // eta' = h + B moves with the bed: shift both buffers by the deformation
+            a.f(0, 0)[k] = (T)((double)a.f(0, 0)[k] + d);
+            a.f(1, 0)[k] = (T)((double)a.f(1, 0)[k] + d);
+        }
+    }
+}
+
+// New patches of a regridded level: copy from old same-level patches where
+// they overlap, else interpolate from the coarse level at its current time.
+template <typename T, bool PERT>
+__global__ void regrid_init_kernel(LevelView L, LevelView Old, LevelView C, const int *list, int cur, int cur_c,
+                                   int ratio, double drytol, int *err)
+{
+    const PatchDesc P = L.descs[list[blockIdx.y]];
+    const int n = P.nx * P.ny;
+    Acc<T> a = acc<T>(L.arena, P);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int i = c % P.nx, j = c / P.nx;
+        int I = P.i0 + i, J = P.j0 + j;
+        long long k = a.idx(i, j);
+        int src = -1;
+        for (int m = 0; m < P.old_cnt; m++) {
+            int qi = L.olds[P.old_off + m];
+            const PatchDesc &Q = Old.descs[qi];
+            if (I >= Q.i0 && I < Q.i0 + Q.nx && J >= Q.j0 && J < Q.j0 + Q.ny) { src = qi; break; }
+        }
+        if (src >= 0) {
+            const PatchDesc Q = Old.descs[src];
+            Acc<T> b = acc<T>(Old.arena, Q);
+            long long kq = b.idx(I - Q.i0, J - Q.j0);
+            a.f(cur, 0)[k] = b.f(cur, 0)[kq];
+            a.f(cur, 1)[k] = b.f(cur, 1)[kq];
+            a.f(cur, 2)[k] = b.f(cur, 2)[kq];
+        } else {
+            T o0, o1, o2;
+            if (interp_fine<T, PERT>(C, cur_c, L.cmap, P, ratio, I, J, (double)a.Bp()[k], 1.0, drytol, o0, o1, o2)) {
+                a.f(cur, 0)[k] = o0; a.f(cur, 1)[k] = o1; a.f(cur, 2)[k] = o2;
+            } else {
+                atomicOr(err, 4);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- flagging
+
+template <typename T, bool PERT>
+__global__ void flag_kernel(LevelView L, int cur, FlagArgs fa)
+{
+    const PatchDesc P = L.descs[blockIdx.y];
+    const int n = P.nx * P.ny;
+    Acc<T> a = acc<T>(L.arena, P);
+    const long long plane = (long long)L.nxl * L.nyl;
+    uint8_t *raw = fa.raw + plane * fa.scen_slot[P.scen];
+    uint8_t *cov = fa.cov + plane * fa.scen_slot[P.scen];
+    if (fa.scen_slot[P.scen] < 0) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int i = c % P.nx, j = c / P.nx;
+        int I = P.i0 + i, J = P.j0 + j;
+        long long k = a.idx(i, j);
+        double B = (double)a.Bp()[k];
+        double q0 = (double)a.f(cur, 0)[k];
+        double h = PERT ? q0 - B : q0;
+        double eta = PERT ? q0 : h + B;
+        int f = 0;
+        if (fa.eta_tol > 0.0 && h >= fa.drytol && fabs(eta) > fa.eta_tol) f = 1;
+        if (fa.depth_below > 0.0 && -B < fa.depth_below) f = 1;
+        double x = fa.x0 + ((double)I + 0.5) * fa.dxl, y = fa.y0 + ((double)J + 0.5) * fa.dyl;
+        for (int rg = 0; rg < fa.n_regions; rg++) {
+            const double *R = fa.regions + 6 * rg;
+            if (x >= R[0] && x <= R[2] && y >= R[1] && y <= R[3] && (double)fa.newlev <= R[4]) f = 1;
+        }
+        long long gk = (long long)J * L.nxl + I;
+        raw[gk] = (uint8_t)f;
+        cov[gk] = 1;
+    }
+}
+
+// Chebyshev dilation, separable: dir 0 dilates along x, dir 1 along y.
+__global__ void dilate_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir)
+{
+    long long n = (long long)nx * ny * nplanes;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        long long pl = c / ((long long)nx * ny);
+        long long rem = c - pl * (long long)nx * ny;
+        int I = (int)(rem % nx), J = (int)(rem / nx);
+        const uint8_t *s = src + pl * (long long)nx * ny;
+        uint8_t v = 0;
+        if (dir == 0) {
+            for (int d = -b; d <= b && !v; d++) {
+                int a = I + d;
+                if (a >= 0 && a < nx) v = s[(long long)J * nx + a];
+            }
+        } else {
+            for (int d = -b; d <= b && !v; d++) {
+                int a = J + d;
+                if (a >= 0 && a < ny) v = s[(long long)a * nx + I];
+            }
+        }
+        dst[c] = v ? 1 : 0;
+    }
+}
+
+// region caps and proper nesting: F &= N, N = every cell within 2 covered or outside
+__global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, FlagArgs fa)
+{
+    long long n = (long long)nx * ny * nplanes;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        long long pl = c / ((long long)nx * ny);
+        long long rem = c - pl * (long long)nx * ny;
+        int I = (int)(rem % nx), J = (int)(rem / nx);
+        const uint8_t *cv = cov + pl * (long long)nx * ny;
+        double x = fa.x0 + ((double)I + 0.5) * fa.dxl, y = fa.y0 + ((double)J + 0.5) * fa.dyl;
+        uint8_t f = F[c];
+        for (int rg = 0; rg < fa.n_regions; rg++) {
+            const double *R = fa.regions + 6 * rg;
+            if (x >= R[0] && x <= R[2] && y >= R[1] && y <= R[3] && (double)fa.newlev > R[5]) f = 0;
+        }
+        int ok = 1;
+        for (int dj = -2; dj <= 2 && ok; dj++)
+            for (int di = -2; di <= 2; di++) {
+                int a = I + di, b = J + dj;
+                if (a < 0 || a >= nx || b < 0 || b >= ny) continue;
+                if (!cv[(long long)b * nx + a]) { ok = 0; break; }
+            }
+        N[c] = (uint8_t)ok;
+        F[c] = ok ? f : 0;
+    }
+}
+
+// ---------------------------------------------------------------- rates, dt
+
+template <typename T, bool PERT>
+__global__ void cell_speed_kernel(LevelView L, const int *list, int cur, double g, double drytol,
+                                  unsigned long long *smax)
+{
+    const PatchDesc P = L.descs[list ? list[blockIdx.y] : blockIdx.y];
+    const int n = P.nx * P.ny;
+    Acc<T> a = acc<T>(L.arena, P);
+    double sx = 0.0, sy = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int i = c % P.nx, j = c / P.nx;
+        long long k = a.idx(i, j);
+        T q0 = a.f(cur, 0)[k];
+        T h = PERT ? q0 - a.Bp()[k] : q0;
+        if (h < (T)drytol) continue;
+        T cc = PERT ? (T)sqrtf((float)((T)g * h)) : (T)sqrt((double)((T)g * h));
+        T ux = a.f(cur, 1)[k] / h, uy = a.f(cur, 2)[k] / h;
+        T ax = (ux < T(0) ? -ux : ux) + cc, ay = (uy < T(0) ? -uy : uy) + cc;
+        sx = fmax(sx, (double)ax);
+        sy = fmax(sy, (double)ay);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx = fmax(sx, __shfl_xor_sync(0xffffffffu, sx, o));
+        sy = fmax(sy, __shfl_xor_sync(0xffffffffu, sy, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (sx > 0.0) atomicMax(smax + 2 * P.scen, (unsigned long long)__double_as_longlong(sx));
+        if (sy > 0.0) atomicMax(smax + 2 * P.scen + 1, (unsigned long long)__double_as_longlong(sy));
+    }
+}
+
+// After a level step (mode 0) or a cell-speed scan (mode 1): fold the level's
+// max speeds into its rate max(sx/dx, sy/dy), check the CFL number of the step
+// just taken and count cell updates (mode 0).
+__global__ void post_level_kernel(CtrlView cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
+                                  int mode)
+{
+    for (int s = threadIdx.x; s < nscen; s += blockDim.x) {
+        unsigned long long *sm = cv.smax + 2 * s;
+        double sx = __longlong_as_double((long long)sm[0]);
+        double sy = __longlong_as_double((long long)sm[1]);
+        sm[0] = 0ull;
+        sm[1] = 0ull;
+        double rate = fmax(sx / dx, sy / dy);
+        double *ra = cv.rate + (long long)s * cv.max_levels + level;
+        if (mode == 0) {
+            double dt = cv.dt1[s] / R;
+            if (dt * rate > cfl_max) cv.cfl_viol[s] += 1;
+            cv.cell_updates[s] += cv.cells[(long long)s * cv.max_levels + level];
+        }
+        *ra = fmax(*ra, rate);
+    }
+}
+
+// Start of a coarse step: dt^1 = min(dt_max, nu_d / max_l(rate_l / R_l)).
+__global__ void begin_step_kernel(CtrlView cv, int nscen, int nlev, const double *Rl, double cfl_desired,
+                                  double dt_max)
+{
+    for (int s = threadIdx.x; s < nscen; s += blockDim.x) {
+        double m = 0.0;
+        for (int l = 0; l < nlev; l++) m = fmax(m, cv.rate[(long long)s * cv.max_levels + l] / Rl[l]);
+        double dt = m > 0.0 ? cfl_desired / m : dt_max;
+        cv.dt1[s] = fmin(dt, dt_max);
+        for (int l = 0; l < cv.max_levels; l++) cv.rate[(long long)s * cv.max_levels + l] = 0.0;
+    }
+}
+
+__global__ void end_step_kernel(CtrlView cv, int nscen)
+{
+    for (int s = threadIdx.x; s < nscen; s += blockDim.x) cv.t[s] = cv.t[s] + cv.dt1[s];
+}
+
+// ---------------------------------------------------------------- gauges, fields
+
+template <typename T, bool PERT>
+__global__ void gauge_kernel(GaugeArgs ga, CtrlView cv)
+{
+    const int total = ga.nscen * ga.ngauges;
+    const long long sidx = *ga.nsamp;
+    for (int c = threadIdx.x; c < total; c += blockDim.x) {
+        int s = c / ga.ngauges;
+        const GaugeLoc gl = ga.loc[c];
+        double eta = __longlong_as_double(0x7ff8000000000000LL);
+        if (gl.patch >= 0) {
+            const LevelView &L = ga.levels[gl.level];
+            const PatchDesc P = L.descs[gl.patch];
+            Acc<T> a = acc<T>(L.arena, P);
+            int cur = ga.curs[gl.level];
+            double dxl = ga.dxl[gl.level], dyl = ga.dyl[gl.level];
+            double x = ga.xy[2 * (c % ga.ngauges)], y = ga.xy[2 * (c % ga.ngauges) + 1];
+            double fx = (x - ga.x0) / dxl - 0.5, fy = (y - ga.y0) / dyl - 0.5;
+            int ia = (int)floor(fx), ja = (int)floor(fy);
+            double tx = fx - (double)ia, ty = fy - (double)ja;
+            if (ia < P.i0) { ia = P.i0; tx = 0.0; }
+            if (ia > P.i0 + P.nx - 2) { ia = P.i0 + P.nx - 2; tx = 1.0; }
+            if (ja < P.j0) { ja = P.j0; ty = 0.0; }
+            if (ja > P.j0 + P.ny - 2) { ja = P.j0 + P.ny - 2; ty = 1.0; }
+            int i = ia - P.i0, j = ja - P.j0;
+            const T *q0 = a.f(cur, 0), *B = a.Bp();
+            double e[4];
+            int di[4] = {0, 1, 0, 1}, dj[4] = {0, 0, 1, 1};
+            for (int m = 0; m < 4; m++) {
+                long long k = a.idx(i + di[m], j + dj[m]);
+                e[m] = PERT ? (double)q0[k] : (double)q0[k] + (double)B[k];
+            }
+            double aa = e[0] + tx * (e[1] - e[0]);
+            double bb = e[2] + tx * (e[3] - e[2]);
+            eta = aa + ty * (bb - aa);
+        }
+        ga.eta[(sidx * ga.nscen + s) * ga.ngauges + (c % ga.ngauges)] = eta;
+        if (c % ga.ngauges == 0) ga.t[sidx * ga.nscen + s] = cv.t[s];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *ga.nsamp = sidx + 1;
+}
+
+template <typename T, bool PERT>
+__global__ void read_field_kernel(LevelView L, int cur, int scen, int field, double *dst, int nx, int ny, double x0,
+                                  double y0, double dx, double dy, double X0, double Y0, double dxl, double dyl)
+{
+    const PatchDesc P = L.descs[blockIdx.y];
+    if (P.scen != scen) return;
+    // output index range whose points fall inside the patch interior
+    double xl = X0 + (double)P.i0 * dxl, xh = X0 + (double)(P.i0 + P.nx) * dxl;
+    double yl = Y0 + (double)P.j0 * dyl, yh = Y0 + (double)(P.j0 + P.ny) * dyl;
+    int ia = (int)floor((xl - x0) / dx) - 1, ib = (int)ceil((xh - x0) / dx) + 1;
+    int ja = (int)floor((yl - y0) / dy) - 1, jb = (int)ceil((yh - y0) / dy) + 1;
+    if (ia < 0) ia = 0;
+    if (ja < 0) ja = 0;
+    if (ib > nx) ib = nx;
+    if (jb > ny) jb = ny;
+    if (ia >= ib || ja >= jb) return;
+    Acc<T> a = acc<T>(L.arena, P);
+    const int w = ib - ia, n = w * (jb - ja);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int i = ia + c % w, j = ja + c / w;
+        double x = x0 + (double)i * dx, y = y0 + (double)j * dy;
+        int I = (int)floor((x - X0) / dxl), J = (int)floor((y - Y0) / dyl);
+        if (I < P.i0 || I >= P.i0 + P.nx || J < P.j0 || J >= P.j0 + P.ny) continue;
+        long long k = a.idx(I - P.i0, J - P.j0);
+        double B = (double)a.Bp()[k], q0 = (double)a.f(cur, 0)[k];
+        double h = PERT ? q0 - B : q0;
+        double v;
+        switch (field) {
+        case 0: v = h; break;
+        case 1: v = (double)a.f(cur, 1)[k]; break;
+        case 2: v = (double)a.f(cur, 2)[k]; break;
+        case 3: v = PERT ? q0 : h + B; break;
+        case 4: v = B > 0.0 ? h : (PERT ? q0 : h + B); break;
+        default: v = B; break;
+        }
+        dst[(long long)j * nx + i] = v;
+    }
+}
+
+// interior of one patch to FP64 staging (h, hu, hv, B), for reads to host
+template <typename T, bool PERT>
+__global__ void patch_out_kernel(LevelView L, int p, int cur, double *out)
+{
+    const PatchDesc P = L.descs[p];
+    const int n = P.nx * P.ny;
+    Acc<T> a = acc<T>(L.arena, P);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int i = c % P.nx, j = c / P.nx;
+        long long k = a.idx(i, j);
+        double B = (double)a.Bp()[k], q0 = (double)a.f(cur, 0)[k];
+        out[c] = PERT ? q0 - B : q0;
+        out[n + c] = (double)a.f(cur, 1)[k];
+        out[2 * n + c] = (double)a.f(cur, 2)[k];
+        out[3 * n + c] = B;
+    }
+}
+
+template <typename T, bool PERT>
+__global__ void mass_kernel(LevelView L, int cur, double *mass)
+{
+    const PatchDesc P = L.descs[blockIdx.y];
+    const int n = P.nx * P.ny;
+    Acc<T> a = acc<T>(L.arena, P);
+    double s = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        long long k = a.idx(c % P.nx, c / P.nx);
+        double q0 = (double)a.f(cur, 0)[k];
+        s += PERT ? q0 - (double)a.Bp()[k] : q0;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(mass + P.scen, s);
+}
+
+// ---------------------------------------------------------------- launchers
+
+static dim3 grid_for(int per_patch, int npatch, int threads)
+{
+    int bx = (per_patch + threads - 1) / threads;
+    if (bx < 1) bx = 1;
+    if (bx > 64) bx = 64;
+    return dim3(bx, npatch);
+}
+
+#define TSU_DISPATCH(PREC, KERNEL, ...)                                  \
+    do {                                                                 \
+        if (PREC == 0) KERNEL<double, false>__VA_ARGS__;                 \
+        else KERNEL<float, true>__VA_ARGS__;                             \
+    } while (0)
+
+int k_ghost_fill(int prec, const LevelView &L, const LevelView &C, int npatch, int maxring, int cur, int cur_c,
+                 int ratio, double alpha, double drytol, int *err, cudaStream_t st)
+{
+    if (npatch <= 0) return 0;
+    dim3 g = grid_for(maxring, npatch, 128);
+    TSU_DISPATCH(prec, ghost_fill_kernel, <<<g, 128, 0, st>>>(L, C, cur, cur_c, ratio, alpha, drytol, err));
+    return (int)cudaGetLastError();
+}
+
+int k_bc(int prec, const LevelView &L, const BcArgs &b, int nlist, int maxring, int cur, int do_state, int do_B,
+         cudaStream_t st)
+{
+    if (nlist <= 0) return 0;
+    dim3 g = grid_for(maxring, nlist, 128);
+    if (prec == 0) bc_kernel<double><<<g, 128, 0, st>>>(L, cur, b, do_state, do_B);
+    else bc_kernel<float><<<g, 128, 0, st>>>(L, cur, b, do_state, do_B);
+    return (int)cudaGetLastError();
+}
+
+int k_average(int prec, const LevelView &F, const LevelView &C, int npatch, int maxcells, int cur_f, int cur_c, int r,
+              double drytol, int *err, cudaStream_t st)
+{
+    if (npatch <= 0) return 0;
+    dim3 g = grid_for(maxcells, npatch, 128);
+    TSU_DISPATCH(prec, average_kernel, <<<g, 128, 0, st>>>(F, C, cur_f, cur_c, r, drytol, err));
+    return (int)cudaGetLastError();
+}
+
+int k_init_patches(int prec, const LevelView &L, const int *list, int nlist, int maxcells, const TopoSet &ts, int cur,
+                   int set_state, double x0, double y0, double dxl, double dyl, cudaStream_t st)
+{
+    if (nlist <= 0) return 0;
+    dim3 g = grid_for(maxcells, nlist, 128);
+    TSU_DISPATCH(prec, init_patch_kernel, <<<g, 128, 0, st>>>(L, list, ts, cur, set_state, x0, y0, dxl, dyl));
+    return (int)cudaGetLastError();
+}
+
+int k_uplift(int prec, const LevelView &L, int npatch, int maxcells, const TopoDev &U, int scen, int cur, double x0,
+             double y0, double dxl, double dyl, cudaStream_t st)
+{
+    if (npatch <= 0) return 0;
+    dim3 g = grid_for(maxcells, npatch, 128);
+    TSU_DISPATCH(prec, uplift_kernel, <<<g, 128, 0, st>>>(L, U, scen, cur, x0, y0, dxl, dyl));
+    return (int)cudaGetLastError();
+}
+
+int k_regrid_init(int prec, const LevelView &L, const LevelView &Old, const LevelView &C, const int *list, int nlist,
+                  int maxcells, int cur, int cur_c, int ratio, double drytol, int *err, cudaStream_t st)
+{
+    if (nlist <= 0) return 0;
+    dim3 g = grid_for(maxcells, nlist, 128);
+    TSU_DISPATCH(prec, regrid_init_kernel, <<<g, 128, 0, st>>>(L, Old, C, list, cur, cur_c, ratio, drytol, err));
+    return (int)cudaGetLastError();
+}
+
+int k_flag(int prec, const LevelView &L, int npatch, int maxcells, int cur, const FlagArgs &fa, cudaStream_t st)
+{
+    if (npatch <= 0) return 0;
+    dim3 g = grid_for(maxcells, npatch, 128);
+    TSU_DISPATCH(prec, flag_kernel, <<<g, 128, 0, st>>>(L, cur, fa));
+    return (int)cudaGetLastError();
+}
+
+int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir, cudaStream_t st)
+{
+    long long n = (long long)nx * ny * nplanes;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    dilate_kernel<<<blocks, 256, 0, st>>>(src, dst, nx, ny, nplanes, b, dir);
+    return (int)cudaGetLastError();
+}
+
+int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa,
+           cudaStream_t st)
+{
+    long long n = (long long)nx * ny * nplanes;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    nest_kernel<<<blocks, 256, 0, st>>>(F, N, cov, nx, ny, nplanes, fa);
+    return (int)cudaGetLastError();
+}
+
+int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int maxcells, int cur, double g,
+                 double drytol, unsigned long long *smax, cudaStream_t st)
+{
+    if (nlist <= 0) return 0;
+    dim3 gr = grid_for(maxcells, nlist, 128);
+    TSU_DISPATCH(prec, cell_speed_kernel, <<<gr, 128, 0, st>>>(L, list, cur, g, drytol, smax));
+    return (int)cudaGetLastError();
+}
+
+int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max, int mode,
+                 cudaStream_t st)
+{
+    post_level_kernel<<<1, 128, 0, st>>>(cv, level, nscen, R, dx, dy, cfl_max, mode);
+    return (int)cudaGetLastError();
+}
+
+int k_begin_step(const CtrlView &cv, int nscen, int nlev, const double *Rl, double cfl_desired, double dt_max,
+                 cudaStream_t st)
+{
+    begin_step_kernel<<<1, 128, 0, st>>>(cv, nscen, nlev, Rl, cfl_desired, dt_max);
+    return (int)cudaGetLastError();
+}
+
+int k_end_step(const CtrlView &cv, int nscen, cudaStream_t st)
+{
+    end_step_kernel<<<1, 128, 0, st>>>(cv, nscen);
+    return (int)cudaGetLastError();
+}
+
+int k_gauges(int prec, const GaugeArgs &ga, const CtrlView &cv, cudaStream_t st)
+{
+    TSU_DISPATCH(prec, gauge_kernel, <<<1, 256, 0, st>>>(ga, cv));
+    return (int)cudaGetLastError();
+}
+
+int k_read_field(int prec, const LevelView &L, int npatch, int cur, int scen, int field, double *dst, int nx, int ny,
+                 double x0, double y0, double dx, double dy, double X0, double Y0, double dxl, double dyl,
+                 cudaStream_t st)
+{
+    if (npatch <= 0) return 0;
+    dim3 g(16, npatch);
+    TSU_DISPATCH(prec, read_field_kernel,
+                 <<<g, 128, 0, st>>>(L, cur, scen, field, dst, nx, ny, x0, y0, dx, dy, X0, Y0, dxl, dyl));
+    return (int)cudaGetLastError();
+}
+
+int k_patch_out(int prec, const LevelView &L, int p, int ncells, int cur, double *out, cudaStream_t st)
+{
+    int blocks = (ncells + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    TSU_DISPATCH(prec, patch_out_kernel, <<<blocks, 256, 0, st>>>(L, p, cur, out));
+    return (int)cudaGetLastError();
+}
+
+int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, double *mass, cudaStream_t st)
+{
+    if (npatch <= 0) return 0;
+    dim3 g = grid_for(maxcells, npatch, 256);
+    TSU_DISPATCH(prec, mass_kernel, <<<g, 256, 0, st>>>(L, cur, mass));
+    return (int)cudaGetLastError();
+}
+
+}  // namespace tsu

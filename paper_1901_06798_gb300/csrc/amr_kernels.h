@@ -1,0 +1,107 @@
+// amr_kernels.h -- views and launchers of the kernels around the patch update.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "tsu_device.h"
+
+namespace tsu {
+
+constexpr int kMaxLevels = 8;
+
+// Device view of one level's tables (all scenarios).
+struct LevelView {
+    const PatchDesc *descs;
+    void *arena;
+    int nxl, nyl;           // level index space
+    const int *nbrs;        // same-level neighbour lists
+    const int *cmap;        // coarse-level patch index maps
+    const int *olds;        // regrid: overlapping old patches
+};
+
+// Device control block of a context: per scenario dt, time, rates, counters.
+struct CtrlView {
+    double *dt1, *t;
+    double *rate;                // [scen][max_levels]
+    double *cell_updates;        // [scen]
+    const double *cells;         // [scen][max_levels] interior cells per level
+    long long *cfl_viol;         // [scen]
+    unsigned long long *smax;    // [scen][2]
+    int max_levels;
+};
+
+struct TopoDev {
+    int nx, ny;
+    double x0, y0, dx, dy;
+    const double *v;
+};
+
+// Base topography grids [0, nbase), then uplift layers and surface grids;
+// scen[k] tells which scenario a layer belongs to (-1: not an uplift layer).
+struct TopoSet {
+    const TopoDev *grids;
+    const int *scen;
+    const int *eta_index;        // per scenario: grid index of its initial surface or -1
+    int nbase, ngrids;
+};
+
+struct FlagArgs {
+    uint8_t *raw, *cov;
+    const int *scen_slot;        // plane of each scenario or -1
+    double eta_tol, depth_below, drytol;
+    double x0, y0, dxl, dyl;
+    int n_regions, newlev;
+    double regions[6 * kMaxLevels];
+};
+
+struct BcArgs {
+    const int *list;             // patches with a side on the domain boundary
+    int bc[4];
+};
+
+struct GaugeLoc {
+    int level, patch;            // finest patch containing the gauge, or patch = -1
+};
+
+struct GaugeArgs {
+    const GaugeLoc *loc;         // [scen][gauge]
+    const double *xy;
+    double *eta, *t;
+    long long *nsamp;
+    int nscen, ngauges;
+    double x0, y0;
+    LevelView levels[kMaxLevels];
+    int curs[kMaxLevels];
+    double dxl[kMaxLevels], dyl[kMaxLevels];
+};
+
+int k_ghost_fill(int prec, const LevelView &L, const LevelView &C, int npatch, int maxring, int cur, int cur_c,
+                 int ratio, double alpha, double drytol, int *err, cudaStream_t st);
+int k_bc(int prec, const LevelView &L, const BcArgs &b, int nlist, int maxring, int cur, int do_state, int do_B,
+         cudaStream_t st);
+int k_average(int prec, const LevelView &F, const LevelView &C, int npatch, int maxcells, int cur_f, int cur_c, int r,
+              double drytol, int *err, cudaStream_t st);
+int k_init_patches(int prec, const LevelView &L, const int *list, int nlist, int maxcells, const TopoSet &ts, int cur,
+                   int set_state, double x0, double y0, double dxl, double dyl, cudaStream_t st);
+int k_uplift(int prec, const LevelView &L, int npatch, int maxcells, const TopoDev &U, int scen, int cur, double x0,
+             double y0, double dxl, double dyl, cudaStream_t st);
+int k_regrid_init(int prec, const LevelView &L, const LevelView &Old, const LevelView &C, const int *list, int nlist,
+                  int maxcells, int cur, int cur_c, int ratio, double drytol, int *err, cudaStream_t st);
+int k_flag(int prec, const LevelView &L, int npatch, int maxcells, int cur, const FlagArgs &fa, cudaStream_t st);
+int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir, cudaStream_t st);
+int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa,
+           cudaStream_t st);
+int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int maxcells, int cur, double g,
+                 double drytol, unsigned long long *smax, cudaStream_t st);
+int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max, int mode,
+                 cudaStream_t st);
+int k_begin_step(const CtrlView &cv, int nscen, int nlev, const double *Rl, double cfl_desired, double dt_max,
+                 cudaStream_t st);
+int k_end_step(const CtrlView &cv, int nscen, cudaStream_t st);
+int k_gauges(int prec, const GaugeArgs &ga, const CtrlView &cv, cudaStream_t st);
+int k_read_field(int prec, const LevelView &L, int npatch, int cur, int scen, int field, double *dst, int nx, int ny,
+                 double x0, double y0, double dx, double dy, double X0, double Y0, double dxl, double dyl,
+                 cudaStream_t st);
+int k_patch_out(int prec, const LevelView &L, int p, int ncells, int cur, double *out, cudaStream_t st);
+int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, double *mass, cudaStream_t st);
+
+}  // namespace tsu

@@ -1,0 +1,24 @@
+// step_f64.cu -- FP64 instantiation of the fused patch update.  Built with
+// --fmad=false so every multiply and add rounds exactly as the FP64 oracle's.
+#include "step_kernel.cuh"
+
+namespace tsu {
+
+static constexpr int kThreadsF64 = 64;
+
+int step_threads_f64() { return kThreadsF64; }
+
+// threads per CTA: 64, 128 or 256 (strip width threads - 4 columns)
+int launch_step_f64(const StepArgs &a, int n_items, int threads, cudaStream_t st)
+{
+    if (n_items <= 0) return 0;
+    switch (threads) {
+    case 64: step_kernel<double, false, 64, 4><<<n_items, 64, 0, st>>>(a); break;
+    case 128: step_kernel<double, false, 128, 4><<<n_items, 128, 0, st>>>(a); break;
+    case 256: step_kernel<double, false, 256, 4><<<n_items, 256, 0, st>>>(a); break;
+    default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
+}  // namespace tsu

@@ -1,0 +1,1180 @@
+// tsu_api.cpp -- host runtime of the library behind the C ABI of tsunami.h.
+//
+// It owns the device memory pool (Sec. 4.2), the per-level patch tables, the
+// recursive level integration of Sec. 3.1 (steps 1-4; refluxing omitted as
+// in the paper's GPU code), the regridding of Sec. 3.2 (flags, buffer and
+// nesting on the device, clustering on the host, new patches initialised on
+// the device) and CUDA-graph replay of repeated coarse steps.  dt, t, wave
+// speeds and CFL checks stay on the device; the host only reads them back at
+// the end of a call.  Every numerical step runs in the library's kernels.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tsunami.h"
+#include "amr_kernels.h"
+#include "tsu_device.h"
+
+namespace tsu {
+void cluster_boxes(const uint8_t *F, const uint8_t *N, int nx, int ny, double eff, int ratio, int patch_max,
+                   std::vector<std::array<int, 4>> &out);
+}
+
+using namespace tsu;
+
+namespace {
+
+struct Err : std::runtime_error {
+    int code;
+    Err(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(x)                                                                                           \
+    do {                                                                                                \
+        cudaError_t e_ = (x);                                                                           \
+        if (e_ != cudaSuccess) throw Err(TSU_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <typename T> struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    cudaStream_t st = nullptr;
+    void ensure(size_t n, cudaStream_t s)
+    {
+        st = s;
+        if (n <= cap && p) return;
+        size_t nc = std::max<size_t>(n, 16);
+        if (p) CK(cudaFreeAsync(p, s));
+        p = nullptr;
+        CK(cudaMallocAsync((void **)&p, nc * sizeof(T), s));
+        cap = nc;
+    }
+    void upload(const std::vector<T> &v, cudaStream_t s)
+    {
+        ensure(v.size(), s);
+        if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    void release()
+    {
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+// Device memory pool (Sec. 4.2): one chunk sub-allocated first-fit; when it is
+// full it is replaced by a chunk twice as large and the contents are copied,
+// so patch offsets stay valid and regrids never call the CUDA allocator for
+// individual patches.
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0;
+    std::map<size_t, size_t> freel;   // offset -> bytes
+    static size_t rnd(size_t b) { return (b + 255) & ~(size_t)255; }
+    void reserve(size_t bytes, cudaStream_t st)
+    {
+        if (bytes <= cap) return;
+        size_t nc = std::max(bytes, cap * 2);
+        char *nb = nullptr;
+        CK(cudaMallocAsync((void **)&nb, nc, st));
+        if (base) {
+            CK(cudaMemcpyAsync(nb, base, cap, cudaMemcpyDeviceToDevice, st));
+            CK(cudaFreeAsync(base, st));
+        }
+        // the new tail is free
+        size_t tail = cap;
+        base = nb;
+        freel[tail] = nc - tail;
+        cap = nc;
+        // merge with a free block ending at the old cap
+        auto it = freel.find(tail);
+        if (it != freel.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) { pv->second += it->second; freel.erase(it); }
+        }
+    }
+    size_t alloc(size_t bytes, cudaStream_t st)
+    {
+        bytes = rnd(bytes);
+        for (int pass = 0; pass < 2; pass++) {
+            for (auto it = freel.begin(); it != freel.end(); ++it) {
+                if (it->second >= bytes) {
+                    size_t off = it->first, rest = it->second - bytes;
+                    freel.erase(it);
+                    if (rest) freel[off + bytes] = rest;
+                    return off;
+                }
+            }
+            reserve(cap + bytes, st);
+        }
+        throw Err(TSU_ERR_OOM, "arena allocation failed");
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = rnd(bytes);
+        auto it = freel.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != freel.end() && it->first + it->second == nx->first) { it->second += nx->second; freel.erase(nx); }
+        if (it != freel.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) { pv->second += it->second; freel.erase(it); }
+        }
+    }
+};
+
+struct Grid {
+    int nx, ny;
+    double x0, y0, dx, dy;
+    std::vector<double> v;
+    int scen;   // -1 base topography, >= 0 uplift layer of that scenario, -2 surface grid
+    double *dev = nullptr;
+};
+
+struct Lvl {
+    std::vector<PatchDesc> P;
+    std::vector<size_t> blk, blkbytes;
+    std::vector<StepItem> items;
+    std::vector<int> nbrs, cmap, bclist, olds;
+    DevBuf<PatchDesc> dP;
+    DevBuf<StepItem> dItems;
+    DevBuf<int> dNbrs, dCmap, dBc, dOlds, dList;
+    int cur = 0, maxring = 0, maxcells = 0;
+    int nxl = 0, nyl = 0;
+    double dx = 0, dy = 0, R = 1;
+};
+
+// Spatial buckets of one scenario's patches on one level, for neighbour and
+// covering-patch lookups while tables are rebuilt.
+struct BoxIndex {
+    int bs = 64, nbx = 0, nby = 0;
+    std::vector<std::vector<int>> b;
+    const std::vector<PatchDesc> *P = nullptr;
+    void build(const std::vector<PatchDesc> &Pv, const std::vector<int> &ids, int nxl, int nyl)
+    {
+        P = &Pv;
+        nbx = (nxl + bs - 1) / bs;
+        nby = (nyl + bs - 1) / bs;
+        b.assign((size_t)nbx * nby, {});
+        for (int id : ids) {
+            const PatchDesc &q = Pv[id];
+            for (int by = q.j0 / bs; by <= (q.j0 + q.ny - 1) / bs; by++)
+                for (int bx = q.i0 / bs; bx <= (q.i0 + q.nx - 1) / bs; bx++) b[(size_t)by * nbx + bx].push_back(id);
+        }
+    }
+    int find(int I, int J) const
+    {
+        if (I < 0 || J < 0 || I >= nbx * bs || J >= nby * bs) return -1;
+        for (int id : b[(size_t)(J / bs) * nbx + I / bs]) {
+            const PatchDesc &q = (*P)[id];
+            if (I >= q.i0 && I < q.i0 + q.nx && J >= q.j0 && J < q.j0 + q.ny) return id;
+        }
+        return -1;
+    }
+    void overlapping(int ia, int ja, int ib, int jb, std::vector<int> &out) const   // half-open box
+    {
+        out.clear();
+        int bxa = std::max(0, floordiv(ia, bs)), bxb = std::min(nbx - 1, floordiv(ib - 1, bs));
+        int bya = std::max(0, floordiv(ja, bs)), byb = std::min(nby - 1, floordiv(jb - 1, bs));
+        for (int by = bya; by <= byb; by++)
+            for (int bx = bxa; bx <= bxb; bx++)
+                for (int id : b[(size_t)by * nbx + bx]) {
+                    const PatchDesc &q = (*P)[id];
+                    if (q.i0 < ib && q.i0 + q.nx > ia && q.j0 < jb && q.j0 + q.ny > ja) out.push_back(id);
+                }
+        std::sort(out.begin(), out.end());
+        out.erase(std::unique(out.begin(), out.end()), out.end());
+    }
+};
+
+}  // namespace
+
+struct tsu_ctx {
+    tsu_config c{};
+    int prec = 0;
+    size_t esz = 8;
+    int nlev = 1, nscen = 1;
+    int ratio[kMaxLevels] = {0};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    Arena arena;
+    Lvl lv[kMaxLevels];
+    std::vector<Grid> grids;   // base topography first, then layers and surfaces in call order
+    int nbase = 0;
+    std::vector<int> eta_index;
+    DevBuf<TopoDev> dGrids;
+    DevBuf<int> dGridScen, dEtaIdx;
+    bool topo_dirty = true;
+    // control block
+    DevBuf<double> dt1, t, rate, cellupd, cells, Rl, mass;
+    DevBuf<long long> viol;
+    DevBuf<unsigned long long> smax;
+    DevBuf<int> derr;
+    std::vector<double> cells_h;
+    std::vector<std::array<long long, kMaxLevels>> nsteps;
+    bool initialized = false;
+    // gauges
+    std::vector<double> gxy;
+    DevBuf<double> dgxy, dgeta, dgt;
+    DevBuf<long long> dnsamp;
+    DevBuf<GaugeLoc> dgloc;
+    long long samp_cap = 0, nsamp = 0;
+    // flags
+    DevBuf<uint8_t> fraw, fcov, ftmp, fF, fN;
+    DevBuf<int> fslot;
+    // statistics and graphs
+    long long launches = 0;
+    long long viol_seen = 0;
+    int seg_rows = 128;
+    int step_nt = 0;   // threads per CTA of the patch update (0: library default)
+    long long hier_version = 0;
+    cudaGraphExec_t gexec = nullptr;
+    long long graph_version = -1;
+    long long graph_kernels = 0;
+    DevBuf<double> dstage;
+
+    // ------------------------------------------------------------ helpers
+    int nt() const { return step_nt > 0 ? step_nt : (prec == TSU_F64 ? step_threads_f64() : step_threads_f32p()); }
+    void kl(int e, const char *what)
+    {
+        launches++;
+        if (e != 0) throw Err(TSU_ERR_CUDA, std::string("kernel launch (") + what + "): " + cudaGetErrorString((cudaError_t)e));
+    }
+    CtrlView ctrl()
+    {
+        CtrlView v;
+        v.dt1 = dt1.p; v.t = t.p; v.rate = rate.p; v.cell_updates = cellupd.p; v.cells = cells.p;
+        v.cfl_viol = viol.p; v.smax = smax.p; v.max_levels = kMaxLevels;
+        return v;
+    }
+    LevelView view(int l, const PatchDesc *descs = nullptr)
+    {
+        LevelView v;
+        v.descs = descs ? descs : lv[l].dP.p;
+        v.arena = arena.base;
+        v.nxl = lv[l].nxl; v.nyl = lv[l].nyl;
+        v.nbrs = lv[l].dNbrs.p; v.cmap = lv[l].dCmap.p; v.olds = lv[l].dOlds.p;
+        return v;
+    }
+    TopoSet topo()
+    {
+        TopoSet ts;
+        ts.grids = dGrids.p; ts.scen = dGridScen.p; ts.eta_index = dEtaIdx.p;
+        ts.nbase = nbase; ts.ngrids = (int)grids.size();
+        return ts;
+    }
+    void sync() { CK(cudaStreamSynchronize(st)); }
+    bool has_patches(int s, int l) const
+    {
+        for (const auto &p : lv[l].P) if (p.scen == s) return true;
+        return false;
+    }
+
+    void upload_topo()
+    {
+        std::vector<TopoDev> td(grids.size());
+        std::vector<int> sc(grids.size());
+        for (size_t k = 0; k < grids.size(); k++) {
+            Grid &g = grids[k];
+            if (!g.dev) {
+                CK(cudaMallocAsync((void **)&g.dev, g.v.size() * sizeof(double), st));
+                CK(cudaMemcpyAsync(g.dev, g.v.data(), g.v.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+            }
+            td[k] = TopoDev{g.nx, g.ny, g.x0, g.y0, g.dx, g.dy, g.dev};
+            sc[k] = g.scen >= 0 ? g.scen : -1;
+        }
+        dGrids.upload(td, st);
+        dGridScen.upload(sc, st);
+        dEtaIdx.upload(eta_index, st);
+        topo_dirty = false;
+    }
+
+    // ------------------------------------------------------------ level tables
+    PatchDesc make_desc(int l, int s, int i0, int j0, int nx, int ny)
+    {
+        PatchDesc d{};
+        d.i0 = i0; d.j0 = j0; d.nx = nx; d.ny = ny; d.scen = s;
+        d.pitch = (nx + 4 + 3) & ~3;
+        long long fs = (long long)d.pitch * (ny + 4);
+        fs = (fs + 63) & ~63LL;
+        d.fs = fs;
+        // ghost cells reach outside the domain (the patch lies within 2 cells of an edge)
+        d.bcmask = (i0 < 2 ? 1 : 0) | (i0 + nx > lv[l].nxl - 2 ? 2 : 0) | (j0 < 2 ? 4 : 0) |
+                   (j0 + ny > lv[l].nyl - 2 ? 8 : 0);
+        return d;
+    }
+
+    // Rebuild everything derived from the patch list of level l: step items,
+    // same-level neighbour lists, coarse maps, boundary lists, cell counts.
+    void finish_level(int l)
+    {
+        Lvl &L = lv[l];
+        const int n = (int)L.P.size();
+        L.items.clear();
+        L.nbrs.clear();
+        L.cmap.clear();
+        L.bclist.clear();
+        L.maxring = 0;
+        L.maxcells = 0;
+        const int W = nt() - 4;
+        for (int k = 0; k < n; k++) {
+            const PatchDesc &p = L.P[k];
+            for (int x0 = 0; x0 < p.nx; x0 += W)
+                for (int y0 = 0; y0 < p.ny; y0 += seg_rows)
+                    L.items.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(seg_rows, p.ny - y0)});
+            L.maxring = std::max(L.maxring, (p.nx + 4) * (p.ny + 4) - p.nx * p.ny);
+            L.maxcells = std::max(L.maxcells, (p.nx + 4) * (p.ny + 4));
+            if (p.bcmask) L.bclist.push_back(k);
+        }
+        // per scenario spatial indices of this level and the coarser one
+        std::vector<std::vector<int>> ids(nscen), cids(nscen);
+        for (int k = 0; k < n; k++) ids[L.P[k].scen].push_back(k);
+        if (l > 0)
+            for (int k = 0; k < (int)lv[l - 1].P.size(); k++) cids[lv[l - 1].P[k].scen].push_back(k);
+        std::vector<int> tmp;
+        for (int s = 0; s < nscen; s++) {
+            if (ids[s].empty()) continue;
+            BoxIndex bi;
+            bi.build(L.P, ids[s], L.nxl, L.nyl);
+            BoxIndex ci;
+            if (l > 0) ci.build(lv[l - 1].P, cids[s], lv[l - 1].nxl, lv[l - 1].nyl);
+            for (int k : ids[s]) {
+                PatchDesc &p = L.P[k];
+                bi.overlapping(p.i0 - 2, p.j0 - 2, p.i0 + p.nx + 2, p.j0 + p.ny + 2, tmp);
+                p.nbr_off = (int)L.nbrs.size();
+                p.nbr_cnt = 0;
+                for (int q : tmp)
+                    if (q != k) { L.nbrs.push_back(q); p.nbr_cnt++; }
+                if (l > 0) {
+                    int r = ratio[l - 1];
+                    int ci0 = floordiv(p.i0 - 2, r) - 1, cj0 = floordiv(p.j0 - 2, r) - 1;
+                    int ci1 = floordiv(p.i0 + p.nx + 1, r) + 1, cj1 = floordiv(p.j0 + p.ny + 1, r) + 1;
+                    p.cmap_i0 = ci0; p.cmap_j0 = cj0; p.cmap_w = ci1 - ci0 + 1; p.cmap_h = cj1 - cj0 + 1;
+                    p.cmap_off = (int)L.cmap.size();
+                    for (int J = cj0; J <= cj1; J++)
+                        for (int I = ci0; I <= ci1; I++) {
+                            int id = -1;
+                            if (I >= 0 && J >= 0 && I < lv[l - 1].nxl && J < lv[l - 1].nyl) id = ci.find(I, J);
+                            L.cmap.push_back(id);
+                        }
+                }
+            }
+        }
+        L.dP.upload(L.P, st);
+        L.dItems.upload(L.items, st);
+        L.dNbrs.upload(L.nbrs, st);
+        if (l > 0) L.dCmap.upload(L.cmap, st);
+        L.dBc.upload(L.bclist, st);
+        for (int s = 0; s < nscen; s++) cells_h[(size_t)s * kMaxLevels + l] = 0.0;
+        for (const auto &p : L.P) cells_h[(size_t)p.scen * kMaxLevels + l] += (double)p.nx * p.ny;
+        cells.upload(cells_h, st);
+        hier_version++;
+    }
+
+    // ------------------------------------------------------------ gauges
+    void update_gauges()
+    {
+        int ng = (int)gxy.size() / 2;
+        if (!ng) return;
+        std::vector<GaugeLoc> loc((size_t)nscen * ng);
+        for (int s = 0; s < nscen; s++)
+            for (int g = 0; g < ng; g++) {
+                GaugeLoc gl{0, -1};
+                for (int l = nlev - 1; l >= 0 && gl.patch < 0; l--) {
+                    int I = (int)std::floor((gxy[2 * g] - c.x0) / lv[l].dx);
+                    int J = (int)std::floor((gxy[2 * g + 1] - c.y0) / lv[l].dy);
+                    if (I < 0 || J < 0 || I >= lv[l].nxl || J >= lv[l].nyl) continue;
+                    for (int k = 0; k < (int)lv[l].P.size(); k++) {
+                        const PatchDesc &p = lv[l].P[k];
+                        if (p.scen == s && I >= p.i0 && I < p.i0 + p.nx && J >= p.j0 && J < p.j0 + p.ny) {
+                            gl = GaugeLoc{l, k};
+                            break;
+                        }
+                    }
+                }
+                loc[(size_t)s * ng + g] = gl;
+            }
+        dgloc.upload(loc, st);
+    }
+
+    void ensure_samples(long long n)
+    {
+        int ng = (int)gxy.size() / 2;
+        if (!ng || n <= samp_cap) return;
+        long long nc = std::max(n, samp_cap * 2 + 64);
+        double *ne = nullptr, *nt = nullptr;
+        CK(cudaMallocAsync((void **)&ne, (size_t)nc * nscen * ng * sizeof(double), st));
+        CK(cudaMallocAsync((void **)&nt, (size_t)nc * nscen * sizeof(double), st));
+        if (dgeta.p && samp_cap) {
+            CK(cudaMemcpyAsync(ne, dgeta.p, (size_t)samp_cap * nscen * ng * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(nt, dgt.p, (size_t)samp_cap * nscen * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+        dgeta.release();
+        dgt.release();
+        dgeta.p = ne; dgeta.cap = (size_t)nc * nscen * ng; dgeta.st = st;
+        dgt.p = nt; dgt.cap = (size_t)nc * nscen; dgt.st = st;
+        samp_cap = nc;
+        hier_version++;   // the gauge kernel's pointers changed
+    }
+
+    void sample_gauges()
+    {
+        int ng = (int)gxy.size() / 2;
+        if (!ng) return;
+        GaugeArgs ga{};
+        ga.loc = dgloc.p; ga.xy = dgxy.p; ga.eta = dgeta.p; ga.t = dgt.p; ga.nsamp = dnsamp.p;
+        ga.nscen = nscen; ga.ngauges = ng; ga.x0 = c.x0; ga.y0 = c.y0;
+        for (int l = 0; l < nlev; l++) {
+            ga.levels[l] = view(l);
+            ga.curs[l] = lv[l].cur;
+            ga.dxl[l] = lv[l].dx;
+            ga.dyl[l] = lv[l].dy;
+        }
+        kl(k_gauges(prec, ga, ctrl(), st), "gauges");
+        nsamp++;
+    }
+
+    // ------------------------------------------------------------ regrid
+    // Build level l+1 of the scenarios in `which` from flags on level l.
+    void regrid_one(int l, const std::vector<int> &which)
+    {
+        const int lf = l + 1, r = ratio[l];
+        Lvl &C = lv[l];
+        const int nx = C.nxl, ny = C.nyl;
+        std::vector<int> slot(nscen, -1);
+        int np = 0;
+        for (int s : which) slot[s] = np++;
+        const size_t plane = (size_t)nx * ny;
+        std::vector<std::vector<std::array<int, 4>>> boxes(nscen);
+        if (np > 0) {
+            fraw.ensure(plane * np, st); fcov.ensure(plane * np, st); ftmp.ensure(plane * np, st);
+            fF.ensure(plane * np, st); fN.ensure(plane * np, st);
+            fslot.upload(slot, st);
+            CK(cudaMemsetAsync(fraw.p, 0, plane * np, st));
+            CK(cudaMemsetAsync(fcov.p, 0, plane * np, st));
+            FlagArgs fa{};
+            fa.raw = fraw.p; fa.cov = fcov.p; fa.scen_slot = fslot.p;
+            fa.eta_tol = c.flag_eta_tol; fa.depth_below = c.flag_depth_below; fa.drytol = c.drytol;
+            fa.x0 = c.x0; fa.y0 = c.y0; fa.dxl = C.dx; fa.dyl = C.dy;
+            fa.n_regions = c.n_regions; fa.newlev = l + 2;
+            for (int k = 0; k < c.n_regions; k++)
+                for (int m = 0; m < 6; m++) fa.regions[6 * k + m] = c.regions[k][m];
+            kl(k_flag(prec, view(l), (int)C.P.size(), C.maxcells, C.cur, fa, st), "flag");
+            int b = c.regrid_interval > 0 ? c.regrid_interval : 0;
+            kl(k_dilate(fraw.p, ftmp.p, nx, ny, np, b, 0, st), "dilate x");
+            kl(k_dilate(ftmp.p, fF.p, nx, ny, np, b, 1, st), "dilate y");
+            kl(k_nest(fF.p, fN.p, fcov.p, nx, ny, np, fa, st), "nest");
+            std::vector<uint8_t> hF(plane * np), hN(plane * np);
+            CK(cudaMemcpyAsync(hF.data(), fF.p, plane * np, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hN.data(), fN.p, plane * np, cudaMemcpyDeviceToHost, st));
+            sync();
+            for (int s : which)
+                cluster_boxes(hF.data() + plane * slot[s], hN.data() + plane * slot[s], nx, ny, c.cluster_eff, r,
+                              c.patch_max, boxes[s]);
+        }
+        rebuild_level(lf, slot, boxes);
+    }
+
+    void rebuild_level(int lf, const std::vector<int> &slot, std::vector<std::vector<std::array<int, 4>>> &boxes)
+    {
+        Lvl &L = lv[lf];
+        const int r = ratio[lf - 1];
+        // the old table stays readable on the device until the initialisation kernels ran
+        std::vector<PatchDesc> oldP = L.P;
+        std::vector<size_t> oldblk = L.blk, oldbytes = L.blkbytes;
+        DevBuf<PatchDesc> oldD = L.dP;
+        L.dP.p = nullptr; L.dP.cap = 0;
+        std::vector<PatchDesc> P;
+        std::vector<size_t> blk, bytes;
+        std::vector<int> fresh;
+        for (int s = 0; s < nscen; s++) {
+            if (slot[s] < 0) {
+                for (size_t k = 0; k < oldP.size(); k++)
+                    if (oldP[k].scen == s) { P.push_back(oldP[k]); blk.push_back(oldblk[k]); bytes.push_back(oldbytes[k]); }
+            } else {
+                for (const auto &b : boxes[s]) {
+                    PatchDesc d = make_desc(lf, s, b[0] * r, b[1] * r, b[2] * r, b[3] * r);
+                    size_t by = (size_t)d.fs * 7 * esz;
+                    size_t off = arena.alloc(by, st);
+                    d.off = (long long)(off / esz);
+                    fresh.push_back((int)P.size());
+                    P.push_back(d); blk.push_back(off); bytes.push_back(by);
+                }
+            }
+        }
+        L.P = P; L.blk = blk; L.blkbytes = bytes;
+        // old patches overlapping each new one (indices into the old table)
+        L.olds.clear();
+        {
+            std::vector<std::vector<int>> ids(nscen);
+            for (int k = 0; k < (int)oldP.size(); k++) ids[oldP[k].scen].push_back(k);
+            std::vector<BoxIndex> oi(nscen);
+            for (int s = 0; s < nscen; s++)
+                if (slot[s] >= 0 && !ids[s].empty()) oi[s].build(oldP, ids[s], L.nxl, L.nyl);
+            std::vector<int> tmp;
+            for (int k : fresh) {
+                PatchDesc &p = L.P[k];
+                p.old_off = (int)L.olds.size();
+                p.old_cnt = 0;
+                if (ids[p.scen].empty()) continue;
+                oi[p.scen].overlapping(p.i0, p.j0, p.i0 + p.nx, p.j0 + p.ny, tmp);
+                for (int q : tmp) { L.olds.push_back(q); p.old_cnt++; }
+            }
+        }
+        L.dOlds.upload(L.olds, st);
+        finish_level(lf);
+        if (!fresh.empty()) {
+            L.dList.upload(fresh, st);
+            kl(k_init_patches(prec, view(lf), L.dList.p, (int)fresh.size(), L.maxcells, topo(), L.cur, 0, c.x0, c.y0,
+                              L.dx, L.dy, st), "init B");
+            // B outside the domain for new boundary patches
+            std::vector<int> bl;
+            for (int k : fresh) if (L.P[k].bcmask) bl.push_back(k);
+            if (!bl.empty()) {
+                DevBuf<int> dbl;
+                dbl.upload(bl, st);
+                BcArgs ba{dbl.p, {c.bc[0], c.bc[1], c.bc[2], c.bc[3]}};
+                kl(k_bc(prec, view(lf), ba, (int)bl.size(), L.maxring, L.cur, 0, 1, st), "bc B");
+                dbl.release();
+            }
+            kl(k_regrid_init(prec, view(lf), view(lf, oldD.p), view(lf - 1), L.dList.p, (int)fresh.size(), L.maxcells,
+                             L.cur, lv[lf - 1].cur, r, c.drytol, derr.p, st), "regrid init");
+            // wave-speed rate of the new patches for the next dt
+            kl(k_cell_speed(prec, view(lf), L.dList.p, (int)fresh.size(), L.maxcells, L.cur, c.g, c.drytol, smax.p, st),
+               "cell speed");
+            kl(k_post_level(ctrl(), lf, nscen, L.R, L.dx, L.dy, c.cfl_max, 1, st), "post rate");
+        }
+        // release the replaced patches of the regridded scenarios
+        for (size_t k = 0; k < oldP.size(); k++)
+            if (slot[oldP[k].scen] >= 0) arena.release(oldblk[k], oldbytes[k]);
+        oldD.release();
+        // the next finer level's coarse maps point into this table
+        if (lf + 1 < nlev && !lv[lf + 1].P.empty()) finish_level(lf + 1);
+        update_gauges();
+    }
+
+    void regrid_from(int l, const std::vector<int> &which)
+    {
+        for (int k = l; k + 1 < nlev; k++) regrid_one(k, which);
+    }
+
+    // ------------------------------------------------------------ stepping
+    void advance(int l, int k)
+    {
+        Lvl &L = lv[l];
+        const int n = (int)L.P.size();
+        std::vector<char> stepped(nscen, 0);
+        for (const auto &p : L.P) stepped[p.scen] = 1;
+        if (l == 0) std::fill(stepped.begin(), stepped.end(), 1);
+        if (n > 0) {
+            if (l > 0 || n > 1) {
+                double alpha = l > 0 ? (double)k / (double)ratio[l - 1] : 0.0;
+                LevelView Cv = l > 0 ? view(l - 1) : view(l);
+                kl(k_ghost_fill(prec, view(l), Cv, n, L.maxring, L.cur, l > 0 ? lv[l - 1].cur : 0,
+                                l > 0 ? ratio[l - 1] : 0, alpha, c.drytol, derr.p, st), "ghost fill");
+            }
+            if (!L.bclist.empty()) {
+                BcArgs ba{L.dBc.p, {c.bc[0], c.bc[1], c.bc[2], c.bc[3]}};
+                kl(k_bc(prec, view(l), ba, (int)L.bclist.size(), L.maxring, L.cur, 1, 0, st), "bc");
+            }
+            StepArgs a{};
+            a.descs = L.dP.p; a.items = L.dItems.p; a.arena = arena.base; a.cur = L.cur; a.dt1 = dt1.p;
+            a.smax = smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = c.g; a.drytol = c.drytol;
+            int e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
+                                    : launch_step_f32p(a, (int)L.items.size(), nt(), st);
+            kl(e, "patch step");
+            kl(k_post_level(ctrl(), l, nscen, L.R, L.dx, L.dy, c.cfl_max, 0, st), "post step");
+            L.cur ^= 1;
+        }
+        if (l + 1 < nlev && !lv[l + 1].P.empty()) {
+            for (int kk = 0; kk < ratio[l]; kk++) advance(l + 1, kk);
+            if (!lv[l + 1].P.empty())
+                kl(k_average(prec, view(l + 1), view(l), (int)lv[l + 1].P.size(), lv[l + 1].maxcells, lv[l + 1].cur,
+                             L.cur, ratio[l], c.drytol, derr.p, st), "average");
+        }
+        std::vector<int> which;
+        for (int s = 0; s < nscen; s++)
+            if (stepped[s]) {
+                nsteps[s][l]++;
+                if (l + 1 < nlev && c.regrid_interval > 0 && nsteps[s][l] % c.regrid_interval == 0) which.push_back(s);
+            }
+        if (!which.empty()) regrid_from(l, which);
+    }
+
+    // would a regrid fire during the next `n` coarse steps?  (host counters only)
+    bool regrid_ahead(int n)
+    {
+        if (nlev == 1 || c.regrid_interval <= 0) return false;
+        // steps of level l per coarse step
+        long long per = 1;
+        for (int l = 0; l + 1 < nlev; l++) {
+            for (int s = 0; s < nscen; s++) {
+                bool active = l == 0 || has_patches(s, l);
+                if (!active) continue;
+                for (long long k = 1; k <= per * n; k++)
+                    if ((nsteps[s][l] + k) % c.regrid_interval == 0) return true;
+            }
+            per *= ratio[l];
+        }
+        return false;
+    }
+
+    void coarse_step()
+    {
+        kl(k_begin_step(ctrl(), nscen, nlev, Rl.p, c.cfl_desired, c.dt_max, st), "begin step");
+        advance(0, 0);
+        kl(k_end_step(ctrl(), nscen, st), "end step");
+        sample_gauges();
+    }
+
+    void step(int n)
+    {
+        if (!initialized) throw Err(TSU_ERR_ARG, "tsu_init has not been called");
+        ensure_samples(nsamp + n + 2);
+        int done = 0;
+        while (done < n) {
+            if (c.use_graphs && n - done >= 2 && !regrid_ahead(2)) {
+                if (!gexec || graph_version != hier_version) {
+                    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+                    cudaGraph_t g = nullptr;
+                    long long l0 = launches;
+                    std::vector<std::array<long long, kMaxLevels>> ns = nsteps;
+                    long long ns0 = nsamp;
+                    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                    try {
+                        coarse_step();
+                        coarse_step();
+                    } catch (...) {
+                        cudaStreamEndCapture(st, &g);
+                        if (g) cudaGraphDestroy(g);
+                        throw;
+                    }
+                    CK(cudaStreamEndCapture(st, &g));
+                    CK(cudaGraphInstantiate(&gexec, g, 0));
+                    cudaGraphDestroy(g);
+                    graph_kernels = launches - l0;
+                    launches = l0;
+                    nsteps = ns;
+                    nsamp = ns0;
+                    graph_version = hier_version;
+                }
+                CK(cudaGraphLaunch(gexec, st));
+                launches += graph_kernels;
+                // host mirrors of what the two captured coarse steps did
+                long long per = 1;
+                for (int l = 0; l < nlev; l++) {
+                    for (int s = 0; s < nscen; s++)
+                        if (l == 0 || has_patches(s, l)) nsteps[s][l] += 2 * per;
+                    if (l + 1 < nlev) per *= ratio[l];
+                }
+                nsamp += gxy.empty() ? 0 : 2;
+                done += 2;
+            } else {
+                coarse_step();
+                done++;
+            }
+        }
+    }
+
+    void check_device_errors(bool &cfl)
+    {
+        int e = 0;
+        std::vector<long long> v(nscen);
+        CK(cudaMemcpyAsync(&e, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(v.data(), viol.p, nscen * sizeof(long long), cudaMemcpyDeviceToHost, st));
+        sync();
+        if (e) throw Err(TSU_ERR_NESTING, "a ghost cell or coarse cell had no covering patch (nesting)");
+        long long tot = 0;
+        for (auto x : v) tot += x;
+        cfl = tot > viol_seen;
+        viol_seen = tot;
+    }
+
+    // ------------------------------------------------------------ init
+    void init()
+    {
+        if (initialized) throw Err(TSU_ERR_ARG, "tsu_init called twice");
+        if (nbase == 0) throw Err(TSU_ERR_ARG, "no topography: call tsu_add_topo first");
+        upload_topo();
+        Lvl &L = lv[0];
+        int T = c.level1_tile > 0 ? c.level1_tile : std::max(c.nx, c.ny);
+        size_t need = 0;
+        for (int s = 0; s < nscen; s++)
+            for (int j0 = 0; j0 < c.ny; j0 += T)
+                for (int i0 = 0; i0 < c.nx; i0 += T) {
+                    PatchDesc d = make_desc(0, s, i0, j0, std::min(T, c.nx - i0), std::min(T, c.ny - j0));
+                    need += Arena::rnd((size_t)d.fs * 7 * esz);
+                }
+        arena.reserve(need + need / 2 + (64u << 20), st);
+        std::vector<int> all;
+        for (int s = 0; s < nscen; s++)
+            for (int j0 = 0; j0 < c.ny; j0 += T)
+                for (int i0 = 0; i0 < c.nx; i0 += T) {
+                    PatchDesc d = make_desc(0, s, i0, j0, std::min(T, c.nx - i0), std::min(T, c.ny - j0));
+                    size_t by = (size_t)d.fs * 7 * esz;
+                    size_t off = arena.alloc(by, st);
+                    d.off = (long long)(off / esz);
+                    all.push_back((int)L.P.size());
+                    L.P.push_back(d); L.blk.push_back(off); L.blkbytes.push_back(by);
+                }
+        finish_level(0);
+        L.dList.upload(all, st);
+        kl(k_init_patches(prec, view(0), L.dList.p, (int)all.size(), L.maxcells, topo(), L.cur, 1, c.x0, c.y0, L.dx, L.dy,
+                          st), "init level 1");
+        if (!L.bclist.empty()) {
+            BcArgs ba{L.dBc.p, {c.bc[0], c.bc[1], c.bc[2], c.bc[3]}};
+            kl(k_bc(prec, view(0), ba, (int)L.bclist.size(), L.maxring, L.cur, 0, 1, st), "bc B");
+        }
+        kl(k_cell_speed(prec, view(0), L.dList.p, (int)all.size(), L.maxcells, L.cur, c.g, c.drytol, smax.p, st),
+           "cell speed");
+        kl(k_post_level(ctrl(), 0, nscen, L.R, L.dx, L.dy, c.cfl_max, 1, st), "post rate");
+        initialized = true;
+        std::vector<int> everyone(nscen);
+        for (int s = 0; s < nscen; s++) everyone[s] = s;
+        if (nlev > 1) regrid_from(0, everyone);
+        update_gauges();
+        bool cfl;
+        check_device_errors(cfl);
+    }
+
+    void add_uplift_now(int s, const Grid &g)
+    {
+        TopoDev U{g.nx, g.ny, g.x0, g.y0, g.dx, g.dy, g.dev};
+        for (int l = 0; l < nlev; l++) {
+            Lvl &L = lv[l];
+            if (L.P.empty()) continue;
+            kl(k_uplift(prec, view(l), (int)L.P.size(), L.maxcells, U, s, L.cur, c.x0, c.y0, L.dx, L.dy, st), "uplift");
+            if (!L.bclist.empty()) {
+                BcArgs ba{L.dBc.p, {c.bc[0], c.bc[1], c.bc[2], c.bc[3]}};
+                kl(k_bc(prec, view(l), ba, (int)L.bclist.size(), L.maxring, L.cur, 0, 1, st), "bc B");
+            }
+        }
+    }
+
+    ~tsu_ctx()
+    {
+        if (st) cudaStreamSynchronize(st);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        for (auto &L : lv) {
+            L.dP.release(); L.dItems.release(); L.dNbrs.release(); L.dCmap.release(); L.dBc.release();
+            L.dOlds.release(); L.dList.release();
+        }
+        for (auto &g : grids) if (g.dev) cudaFreeAsync(g.dev, st);
+        dGrids.release(); dGridScen.release(); dEtaIdx.release();
+        dt1.release(); t.release(); rate.release(); cellupd.release(); cells.release(); Rl.release(); mass.release();
+        viol.release(); smax.release(); derr.release();
+        dgxy.release(); dgeta.release(); dgt.release(); dnsamp.release(); dgloc.release();
+        fraw.release(); fcov.release(); ftmp.release(); fF.release(); fN.release(); fslot.release();
+        dstage.release();
+        if (arena.base) cudaFreeAsync(arena.base, st);
+        if (st) cudaStreamSynchronize(st);
+        if (own_stream && st) cudaStreamDestroy(st);
+    }
+};
+
+// ------------------------------------------------------------------ C ABI
+
+namespace {
+
+template <typename F> int guard(tsu_ctx *ctx, F &&f)
+{
+    if (!ctx) return TSU_ERR_ARG;
+    try {
+        f();
+        return TSU_OK;
+    } catch (const Err &e) {
+        ctx->err = e.what();
+        return e.code;
+    } catch (const std::exception &e) {
+        ctx->err = e.what();
+        return TSU_ERR_ARG;
+    } catch (...) {
+        ctx->err = "unknown error";
+        return TSU_ERR_ARG;
+    }
+}
+
+void check_grid(const double *v, int nx, int ny, double dx, double dy)
+{
+    if (!v || nx < 2 || ny < 2 || !(dx > 0) || !(dy > 0)) throw Err(TSU_ERR_ARG, "grid needs nx, ny >= 2 and dx, dy > 0");
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out)
+{
+    if (!cfg || !out) return TSU_ERR_ARG;
+    *out = nullptr;
+    const tsu_config &c = *cfg;
+    if (c.precision != TSU_F64 && c.precision != TSU_F32P) return TSU_ERR_ARG;
+    if (c.nx < 2 || c.ny < 2 || !(c.dx > 0) || !(c.dy > 0)) return TSU_ERR_ARG;
+    if (c.num_levels < 1 || c.num_levels > TSU_MAX_LEVELS || c.n_scenarios < 1 || c.transverse != 0) return TSU_ERR_ARG;
+    for (int l = 0; l + 1 < c.num_levels; l++)
+        if (c.ratios[l] < 2) return TSU_ERR_ARG;
+    if (c.n_regions < 0 || c.n_regions > TSU_MAX_REGIONS || c.patch_max < 1) return TSU_ERR_ARG;
+    if (!(c.cfl_desired > 0) || !(c.cfl_max > 0) || !(c.dt_max > 0) || !(c.g > 0) || !(c.drytol > 0)) return TSU_ERR_ARG;
+    for (int k = 0; k < 4; k++)
+        if (c.bc[k] != TSU_BC_WALL && c.bc[k] != TSU_BC_EXTRAP) return TSU_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TSU_ERR_NOT_BUILT;
+    tsu_ctx *x = new tsu_ctx();
+    int rc = guard(x, [&] {
+        x->c = c;
+        if (x->c.cluster_eff <= 0) x->c.cluster_eff = 0.7;
+        x->prec = c.precision;
+        x->esz = c.precision == TSU_F64 ? 8 : 4;
+        x->nlev = c.num_levels;
+        x->nscen = c.n_scenarios;
+        for (int l = 0; l + 1 < x->nlev; l++) x->ratio[l] = c.ratios[l];
+        if (cuda_stream) x->st = (cudaStream_t)cuda_stream;
+        else {
+            CK(cudaStreamCreateWithFlags(&x->st, cudaStreamNonBlocking));
+            x->own_stream = true;
+        }
+        int R = 1;
+        std::vector<double> rl(kMaxLevels, 1.0);
+        for (int l = 0; l < x->nlev; l++) {
+            if (l > 0) R *= x->ratio[l - 1];
+            x->lv[l].R = (double)R;
+            x->lv[l].nxl = c.nx * R;
+            x->lv[l].nyl = c.ny * R;
+            x->lv[l].dx = c.dx / (double)R;
+            x->lv[l].dy = c.dy / (double)R;
+            rl[l] = (double)R;
+        }
+        const int S = x->nscen;
+        cudaStream_t st = x->st;
+        x->dt1.ensure(S, st); x->t.ensure(S, st); x->rate.ensure((size_t)S * kMaxLevels, st);
+        x->cellupd.ensure(S, st); x->viol.ensure(S, st); x->smax.ensure(2 * (size_t)S, st);
+        x->derr.ensure(1, st); x->mass.ensure(S, st); x->dnsamp.ensure(1, st);
+        CK(cudaMemsetAsync(x->dt1.p, 0, S * sizeof(double), st));
+        CK(cudaMemsetAsync(x->t.p, 0, S * sizeof(double), st));
+        CK(cudaMemsetAsync(x->rate.p, 0, (size_t)S * kMaxLevels * sizeof(double), st));
+        CK(cudaMemsetAsync(x->cellupd.p, 0, S * sizeof(double), st));
+        CK(cudaMemsetAsync(x->viol.p, 0, S * sizeof(long long), st));
+        CK(cudaMemsetAsync(x->smax.p, 0, 2 * S * sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(x->derr.p, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(x->dnsamp.p, 0, sizeof(long long), st));
+        x->Rl.upload(rl, st);
+        x->cells_h.assign((size_t)S * kMaxLevels, 0.0);
+        x->cells.upload(x->cells_h, st);
+        x->nsteps.assign(S, {});
+        x->eta_index.assign(S, -1);
+        x->sync();
+    });
+    if (rc != TSU_OK) {
+        delete x;
+        return rc;
+    }
+    *out = x;
+    return TSU_OK;
+}
+
+int tsu_destroy(tsu_ctx *ctx)
+{
+    delete ctx;
+    return TSU_OK;
+}
+
+const char *tsu_last_error(tsu_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tsu_add_topo(tsu_ctx *ctx, const double *B, int nx, int ny, double x0, double y0, double dx, double dy)
+{
+    return guard(ctx, [&] {
+        if (ctx->initialized) throw Err(TSU_ERR_ARG, "topography must be added before tsu_init");
+        check_grid(B, nx, ny, dx, dy);
+        Grid g{nx, ny, x0, y0, dx, dy, std::vector<double>(B, B + (size_t)nx * ny), -1, nullptr};
+        // base grids first: insert after the existing base grids and shift layer indices
+        ctx->grids.insert(ctx->grids.begin() + ctx->nbase, g);
+        ctx->nbase++;
+        for (auto &e : ctx->eta_index) if (e >= 0) e++;
+    });
+}
+
+int tsu_set_eta(tsu_ctx *ctx, int scen, const double *eta, int nx, int ny, double x0, double y0, double dx, double dy)
+{
+    return guard(ctx, [&] {
+        if (ctx->initialized) throw Err(TSU_ERR_ARG, "the initial surface must be set before tsu_init");
+        if (scen < 0 || scen >= ctx->nscen) throw Err(TSU_ERR_ARG, "bad scenario");
+        check_grid(eta, nx, ny, dx, dy);
+        ctx->grids.push_back(Grid{nx, ny, x0, y0, dx, dy, std::vector<double>(eta, eta + (size_t)nx * ny), -2, nullptr});
+        ctx->eta_index[scen] = (int)ctx->grids.size() - 1;
+    });
+}
+
+int tsu_add_uplift(tsu_ctx *ctx, int scen, const double *dB, int nx, int ny, double x0, double y0, double dx, double dy)
+{
+    return guard(ctx, [&] {
+        if (scen < 0 || scen >= ctx->nscen) throw Err(TSU_ERR_ARG, "bad scenario");
+        check_grid(dB, nx, ny, dx, dy);
+        ctx->grids.push_back(Grid{nx, ny, x0, y0, dx, dy, std::vector<double>(dB, dB + (size_t)nx * ny), scen, nullptr});
+        if (ctx->initialized) {
+            ctx->upload_topo();
+            ctx->add_uplift_now(scen, ctx->grids.back());
+            ctx->sync();
+        }
+    });
+}
+
+int tsu_init(tsu_ctx *ctx)
+{
+    return guard(ctx, [&] { ctx->init(); });
+}
+
+int tsu_step(tsu_ctx *ctx, int n, double *t_out)
+{
+    bool cfl = false;
+    int rc = guard(ctx, [&] {
+        if (n < 0) throw Err(TSU_ERR_ARG, "negative step count");
+        ctx->step(n);
+        ctx->check_device_errors(cfl);
+        if (t_out) {
+            CK(cudaMemcpyAsync(t_out, ctx->t.p, ctx->nscen * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            ctx->sync();
+        }
+    });
+    if (rc == TSU_OK && cfl) {
+        ctx->err = "a level step ran with a Courant number above cfl_max";
+        return TSU_ERR_CFL;
+    }
+    return rc;
+}
+
+int tsu_regrid(tsu_ctx *ctx, int scen, int level)
+{
+    return guard(ctx, [&] {
+        if (!ctx->initialized) throw Err(TSU_ERR_ARG, "tsu_init has not been called");
+        if (scen < 0 || scen >= ctx->nscen || level < 1 || level >= ctx->nlev) throw Err(TSU_ERR_ARG, "bad scenario/level");
+        ctx->regrid_from(level - 1, std::vector<int>{scen});
+        bool cfl;
+        ctx->check_device_errors(cfl);
+    });
+}
+
+int tsu_num_patches(tsu_ctx *ctx, int scen, int level, int *n)
+{
+    return guard(ctx, [&] {
+        if (scen < 0 || scen >= ctx->nscen || level < 1 || level > ctx->nlev || !n) throw Err(TSU_ERR_ARG, "bad argument");
+        int k = 0;
+        for (const auto &p : ctx->lv[level - 1].P) k += p.scen == scen;
+        *n = k;
+    });
+}
+
+int tsu_get_patches(tsu_ctx *ctx, int scen, int level, int *boxes, int max_patches, int *n)
+{
+    return guard(ctx, [&] {
+        if (scen < 0 || scen >= ctx->nscen || level < 1 || level > ctx->nlev || !n) throw Err(TSU_ERR_ARG, "bad argument");
+        int k = 0;
+        for (const auto &p : ctx->lv[level - 1].P) {
+            if (p.scen != scen) continue;
+            if (k < max_patches && boxes) {
+                boxes[4 * k] = p.i0; boxes[4 * k + 1] = p.j0; boxes[4 * k + 2] = p.nx; boxes[4 * k + 3] = p.ny;
+            }
+            k++;
+        }
+        *n = k;
+    });
+}
+
+int tsu_get_patch(tsu_ctx *ctx, int scen, int level, int k, double *h, double *hu, double *hv, double *B)
+{
+    return guard(ctx, [&] {
+        if (scen < 0 || scen >= ctx->nscen || level < 1 || level > ctx->nlev) throw Err(TSU_ERR_ARG, "bad argument");
+        Lvl &L = ctx->lv[level - 1];
+        int idx = -1, m = 0;
+        for (int q = 0; q < (int)L.P.size(); q++)
+            if (L.P[q].scen == scen) { if (m == k) { idx = q; break; } m++; }
+        if (idx < 0) throw Err(TSU_ERR_ARG, "no such patch");
+        const PatchDesc &p = L.P[idx];
+        int nc = p.nx * p.ny;
+        ctx->dstage.ensure((size_t)4 * nc, ctx->st);
+        ctx->kl(k_patch_out(ctx->prec, ctx->view(level - 1), idx, nc, L.cur, ctx->dstage.p, ctx->st), "patch out");
+        std::vector<double> hb((size_t)4 * nc);
+        CK(cudaMemcpyAsync(hb.data(), ctx->dstage.p, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        ctx->sync();
+        double *dst[4] = {h, hu, hv, B};
+        for (int f = 0; f < 4; f++)
+            if (dst[f]) std::memcpy(dst[f], hb.data() + (size_t)f * nc, nc * sizeof(double));
+    });
+}
+
+int tsu_read_field(tsu_ctx *ctx, int scen, int level, int field, double *dst, int nx, int ny, double x0, double y0,
+                   double dx, double dy)
+{
+    return guard(ctx, [&] {
+        if (scen < 0 || scen >= ctx->nscen || level < 0 || level > ctx->nlev || field < 0 || field > 5 || !dst ||
+            nx < 1 || ny < 1)
+            throw Err(TSU_ERR_ARG, "bad argument");
+        size_t n = (size_t)nx * ny;
+        ctx->dstage.ensure(n, ctx->st);
+        CK(cudaMemsetAsync(ctx->dstage.p, 0xff, n * sizeof(double), ctx->st));
+        int la = level == 0 ? 0 : level - 1, lb = level == 0 ? ctx->nlev - 1 : level - 1;
+        for (int l = la; l <= lb; l++) {
+            Lvl &L = ctx->lv[l];
+            if (L.P.empty()) continue;
+            ctx->kl(k_read_field(ctx->prec, ctx->view(l), (int)L.P.size(), L.cur, scen, field, ctx->dstage.p, nx, ny, x0,
+                                 y0, dx, dy, ctx->c.x0, ctx->c.y0, L.dx, L.dy, ctx->st), "read field");
+        }
+        CK(cudaMemcpyAsync(dst, ctx->dstage.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        ctx->sync();
+        for (size_t k = 0; k < n; k++)
+            if (std::isnan(dst[k])) dst[k] = NAN;
+    });
+}
+
+int tsu_add_gauges(tsu_ctx *ctx, const double *xy, int n)
+{
+    return guard(ctx, [&] {
+        if (n < 0 || (n > 0 && !xy)) throw Err(TSU_ERR_ARG, "bad gauges");
+        if (ctx->nsamp > 0) throw Err(TSU_ERR_ARG, "gauges must be added before the first step");
+        ctx->gxy.insert(ctx->gxy.end(), xy, xy + 2 * (size_t)n);
+        ctx->dgxy.upload(ctx->gxy, ctx->st);
+        if (ctx->initialized) ctx->update_gauges();
+        ctx->hier_version++;
+        ctx->sync();
+    });
+}
+
+int tsu_read_gauges(tsu_ctx *ctx, double *t, double *eta, int max_samples, int *n_written)
+{
+    return guard(ctx, [&] {
+        if (!n_written || max_samples < 0) throw Err(TSU_ERR_ARG, "bad argument");
+        int ng = (int)ctx->gxy.size() / 2;
+        long long n = std::min<long long>(ctx->nsamp, max_samples);
+        if (ng && n > 0) {
+            CK(cudaMemcpyAsync(t, ctx->dgt.p, (size_t)n * ctx->nscen * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaMemcpyAsync(eta, ctx->dgeta.p, (size_t)n * ctx->nscen * ng * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->st));
+        }
+        ctx->sync();
+        *n_written = ng ? (int)n : 0;
+    });
+}
+
+int tsu_get_stats(tsu_ctx *ctx, int scen, tsu_stats *out)
+{
+    return guard(ctx, [&] {
+        if (scen < 0 || scen >= ctx->nscen || !out) throw Err(TSU_ERR_ARG, "bad argument");
+        std::memset(out, 0, sizeof *out);
+        CK(cudaMemsetAsync(ctx->mass.p, 0, ctx->nscen * sizeof(double), ctx->st));
+        Lvl &L = ctx->lv[0];
+        if (!L.P.empty())
+            ctx->kl(k_mass(ctx->prec, ctx->view(0), (int)L.P.size(), L.maxcells, L.cur, ctx->mass.p, ctx->st), "mass");
+        double v[4];
+        long long vi;
+        CK(cudaMemcpyAsync(&v[0], ctx->dt1.p + scen, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(&v[1], ctx->t.p + scen, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(&v[2], ctx->mass.p + scen, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(&v[3], ctx->cellupd.p + scen, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(&vi, ctx->viol.p + scen, sizeof(long long), cudaMemcpyDeviceToHost, ctx->st));
+        ctx->sync();
+        out->dt = v[0];
+        out->t = v[1];
+        out->mass = v[2] * ctx->c.dx * ctx->c.dy;
+        out->cell_updates = v[3];
+        out->cfl_violations = vi;
+        for (int l = 0; l < ctx->nlev; l++)
+            for (const auto &p : ctx->lv[l].P) out->patches[l] += p.scen == scen;
+        out->kernel_launches = ctx->launches;
+    });
+}
+
+int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows)
+{
+    return guard(ctx, [&] {
+        if (!(step_threads == 0 || step_threads == 64 || step_threads == 128 || step_threads == 256) || seg_rows < 0)
+            throw Err(TSU_ERR_ARG, "step_threads must be 0, 64, 128 or 256 and seg_rows >= 0");
+        ctx->step_nt = step_threads;
+        ctx->seg_rows = seg_rows > 0 ? seg_rows : 128;
+        for (int l = 0; l < ctx->nlev; l++)
+            if (!ctx->lv[l].P.empty()) ctx->finish_level(l);
+        ctx->sync();
+    });
+}
+
+int tsu_sync(tsu_ctx *ctx)
+{
+    return guard(ctx, [&] { ctx->sync(); });
+}
+
+int tsu_level1_buffers(tsu_ctx *ctx, void **h, void **hu, void **hv, void **B, int *pitch)
+{
+    return guard(ctx, [&] {
+        if (ctx->lv[0].P.empty()) throw Err(TSU_ERR_ARG, "not initialised");
+        const PatchDesc &p = ctx->lv[0].P[0];
+        char *base = ctx->arena.base + (size_t)p.off * ctx->esz;
+        int cur = ctx->lv[0].cur;
+        size_t fsb = (size_t)p.fs * ctx->esz;
+        if (h) *h = base + (cur * 3 + 0) * fsb;
+        if (hu) *hu = base + (cur * 3 + 1) * fsb;
+        if (hv) *hv = base + (cur * 3 + 2) * fsb;
+        if (B) *B = base + 6 * fsb;
+        if (pitch) *pitch = p.pitch;
+    });
+}
+
+int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out, double *step_ms_out)
+{
+    return guard(ctx, [&] {
+        if (!ctx->initialized || ctx->nlev != 1 || n < 1 || warmup < 0)
+            throw Err(TSU_ERR_ARG, "single-level context after tsu_init required");
+        for (int k = 0; k < warmup; k++) ctx->coarse_step();
+        std::vector<cudaEvent_t> ev(2 * n + 2);
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+        Lvl &L = ctx->lv[0];
+        CK(cudaEventRecord(ev[2 * n], ctx->st));
+        for (int k = 0; k < n; k++) {
+            ctx->kl(k_begin_step(ctx->ctrl(), ctx->nscen, ctx->nlev, ctx->Rl.p, ctx->c.cfl_desired, ctx->c.dt_max, ctx->st),
+                    "begin step");
+            if (L.P.size() > 1) {
+                ctx->kl(k_ghost_fill(ctx->prec, ctx->view(0), ctx->view(0), (int)L.P.size(), L.maxring, L.cur, 0, 0, 0.0,
+                                     ctx->c.drytol, ctx->derr.p, ctx->st), "ghost fill");
+            }
+            if (!L.bclist.empty()) {
+                BcArgs ba{L.dBc.p, {ctx->c.bc[0], ctx->c.bc[1], ctx->c.bc[2], ctx->c.bc[3]}};
+                ctx->kl(k_bc(ctx->prec, ctx->view(0), ba, (int)L.bclist.size(), L.maxring, L.cur, 1, 0, ctx->st), "bc");
+            }
+            StepArgs a{};
+            a.descs = L.dP.p; a.items = L.dItems.p; a.arena = ctx->arena.base; a.cur = L.cur; a.dt1 = ctx->dt1.p;
+            a.smax = ctx->smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = ctx->c.g; a.drytol = ctx->c.drytol;
+            CK(cudaEventRecord(ev[2 * k], ctx->st));
+            int e = ctx->prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), ctx->nt(), ctx->st)
+                                         : launch_step_f32p(a, (int)L.items.size(), ctx->nt(), ctx->st);
+            ctx->kl(e, "patch step");
+            CK(cudaEventRecord(ev[2 * k + 1], ctx->st));
+            ctx->kl(k_post_level(ctx->ctrl(), 0, ctx->nscen, L.R, L.dx, L.dy, ctx->c.cfl_max, 0, ctx->st), "post step");
+            L.cur ^= 1;
+            ctx->kl(k_end_step(ctx->ctrl(), ctx->nscen, ctx->st), "end step");
+            for (int s = 0; s < ctx->nscen; s++) ctx->nsteps[s][0]++;
+        }
+        CK(cudaEventRecord(ev[2 * n + 1], ctx->st));
+        ctx->sync();
+        double ks = 0;
+        for (int k = 0; k < n; k++) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+            ks += ms;
+        }
+        float tot = 0;
+        CK(cudaEventElapsedTime(&tot, ev[2 * n], ev[2 * n + 1]));
+        for (auto &e : ev) cudaEventDestroy(e);
+        if (kernel_ms_out) *kernel_ms_out = ks / n;
+        if (step_ms_out) *step_ms_out = tot / n;
+        ctx->hier_version++;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// tsu_device.h -- structures shared by the library's host code and kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tsu {
+
+// One patch of a level: interior box [i0, i0+nx) x [j0, j0+ny) in global
+// level indices, stored with 2 ghost cells per side.  The patch's block in the
+// arena holds 7 fields of fs elements each: buffer 0 (q0, q1, q2), buffer 1
+// (q0, q1, q2), B.  q0 is h (FP64 form) or eta' = h + B (FP32 perturbation
+// form); q1 = hu, q2 = hv.  Element (i, j), -2 <= i < nx+2, at
+// (j + 2) * pitch + (i + 2).
+struct PatchDesc {
+    long long off;      // element offset of the block in the arena
+    long long fs;       // elements per field
+    int i0, j0, nx, ny, pitch;
+    int scen;
+    int bcmask;         // 1 left, 2 right, 4 bottom, 8 top: ghost cells reach past that domain edge
+    int nbr_off, nbr_cnt;      // same-level patches whose interior may feed this patch's ghosts
+    int cmap_off, cmap_i0, cmap_j0, cmap_w, cmap_h;  // coarse-level patch index per coarse cell (levels >= 2)
+    int old_off, old_cnt;      // old same-level patches overlapping (regrid initialisation)
+};
+
+// One work item of the patch update: a strip of columns [x0, x0+w) and a row
+// segment [y0, y0+h) of one patch (patch-local interior indices).
+struct StepItem {
+    int patch;
+    int x0, y0, w, h;
+};
+
+struct StepArgs {
+    const PatchDesc *descs;
+    const StepItem *items;
+    void *arena;
+    int cur;                    // current buffer of this level (0 or 1)
+    const double *dt1;          // level-1 time step per scenario
+    unsigned long long *smax;   // per scenario: [2] max speed bits (x, y)
+    double R;                   // refinement of this level relative to level 1
+    double dx, dy, g, drytol;
+};
+
+// Launch helpers implemented in the .cu files.
+int launch_step_f64(const StepArgs &a, int n_items, int threads, cudaStream_t st);
+int launch_step_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t st);
+int step_threads_f64();
+int step_threads_f32p();
+
+}  // namespace tsu

@@ -1,0 +1,34 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/tsunami.h (no compute call: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+from paper_1901_06798_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "tsunami.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tsu_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    syms = declared_symbols()
+    assert len(syms) >= 19
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+    assert sorted(binding.SYMBOLS) == syms
+
+
+def test_config_struct_matches_header_field_order():
+    txt = open(os.path.join(ROOT, "include", "tsunami.h")).read()
+    body = txt[txt.index("typedef struct tsu_config {"):txt.index("} tsu_config;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b([a-z_0-9]+)(?:\[[A-Z_0-9]+\])*(?:\[\d+\])?\s*[;,]", body)
+    fields = [f[0] for f in binding.tsu_config._fields_]
+    assert names == fields

@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Bars (written here, derived in the design doc):
+  * FP64: relative error per field (max |gpu - oracle| / max |oracle|) <= 1e-12
+    after the stated steps; patch lists (integer work) bit-exact; the FP64
+    kernels are built without contraction and follow the oracle's operation
+    order, so most cases are checked bit for bit as well.
+  * FP32 perturbation form: surface elevation within 1e-4 m of the oracle,
+    per field and per gauge.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_06798_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+F64_REL = 1e-12
+F32P_ETA = 1e-4
+
+
+def _gpu(cfg, precision=0, use_graphs=True):
+    from paper_1901_06798_gb300 import binding
+    return binding.Tsunami(cfg, precision=precision, use_graphs=use_graphs)
+
+
+def run_pair(w, steps, precision=0, use_graphs=True, cfg=None):
+    cfg = cfg or w["cfg"]
+    w = dict(w, cfg=cfg)
+    o = W.load(oracle.Oracle(cfg), w)
+    g = W.load(_gpu(cfg, precision, use_graphs), w)
+    if steps:
+        o.step(steps)
+        g.step(steps)
+    return o, g
+
+
+def rel_err(a, b):
+    m = np.nanmax(np.abs(b))
+    return np.nanmax(np.abs(a - b)) / (m if m > 0 else 1.0)
+
+
+def compare_levels(o, g, nlev, nscen=1, bitwise=False, tol=F64_REL):
+    for s in range(nscen):
+        for lev in range(1, nlev + 1):
+            ob = [p[0] for p in o.patches(s, lev)]
+            gb = [tuple(int(v) for v in b) for b in g.boxes(s, lev)]
+            assert ob == gb, f"patch lists differ on level {lev} scenario {s}"
+            for (box, a), (_, b) in zip(o.patches(s, lev), g.patches(s, lev)):
+                for f in ("h", "hu", "hv", "B"):
+                    if bitwise:
+                        assert np.array_equal(a[f], b[f]), (lev, box, f, np.abs(a[f] - b[f]).max())
+                    else:
+                        assert rel_err(b[f], a[f]) <= tol, (lev, box, f, rel_err(b[f], a[f]))
+
+
+def test_hump200_f64_matches_oracle():
+    w = W.hump200()
+    o, g = run_pair(w, 100)
+    compare_levels(o, g, 1)
+    so, sg = o.stats(), g.stats()
+    assert so["dt"] == sg["dt"] and so["t"] == sg["t"]
+    assert sg["cell_updates"] == 4.0e6
+
+
+def test_hump200_f64_bitwise():
+    w = W.hump200()
+    o, g = run_pair(w, 100)
+    compare_levels(o, g, 1, bitwise=True)
+
+
+def test_ragged_tiles_and_strips():
+    """Uneven tiles (37) and widths that leave ragged strips and segments."""
+    w = W.hump200()
+    cfg = dict(w["cfg"], level1_tile=37)
+    o, g = run_pair(w, 40, cfg=cfg)
+    assert g.num_patches(0, 1) == 36
+    compare_levels(o, g, 1, bitwise=True)
+    cfg = dict(w["cfg"], nx=133, ny=71, level1_tile=0)
+    o, g = run_pair(dict(w, cfg=cfg), 25, cfg=cfg)
+    compare_levels(o, g, 1, bitwise=True)
+
+
+def test_tiny_grid_and_single_column_patches():
+    w = W.hump200()
+    cfg = dict(w["cfg"], nx=5, ny=3, dx=400.0, dy=400.0, level1_tile=2)
+    o, g = run_pair(dict(w, cfg=cfg), 10, cfg=cfg)
+    compare_levels(o, g, 1, bitwise=True)
+
+
+def test_shelf_with_dry_land_f64():
+    w = W.shelf(n=192, dx=2000.0, steps=60)
+    o, g = run_pair(w, 60)
+    compare_levels(o, g, 1, bitwise=True)
+
+
+def test_lake_at_rest_gpu_both_precisions():
+    w = W.lake_at_rest_shelf(n=96)
+    for prec in (0, 1):
+        g = W.load(_gpu(w["cfg"], prec), w)
+        g.step(200)
+        for f in ("hu", "hv"):
+            assert np.abs(g.level_array(0, 1, f)).max() == 0.0
+        eta = g.read_field(0, 1, "eta", 96, 96, 1000.0, 1000.0, 2000.0, 2000.0)
+        h = g.read_field(0, 1, "h", 96, 96, 1000.0, 1000.0, 2000.0, 2000.0)
+        assert np.abs(eta[h > 0]).max() == 0.0
+
+
+@pytest.mark.parametrize("name", ["hump", "shelf"])
+def test_f32_perturbation_within_1e4_m(name):
+    w = W.hump200() if name == "hump" else W.shelf(n=192, dx=2000.0, steps=100)
+    steps = 100
+    o, g = run_pair(w, steps, precision=1)
+    e_o = o.level_array(0, 1, "eta")
+    e_g = g.level_array(0, 1, "eta")
+    wet = o.level_array(0, 1, "h") > 0
+    assert np.abs(e_g - e_o)[wet].max() <= F32P_ETA
+    to, eo = o.read_gauges()
+    tg, eg = g.read_gauges()
+    assert np.abs(eg - eo).max() <= F32P_ETA
+    assert np.allclose(tg, to, rtol=1e-5)
+
+
+def test_graph_replay_equals_eager():
+    w = W.shelf(n=128, dx=2000.0)
+    a = W.load(_gpu(w["cfg"], 0, use_graphs=True), w)
+    b = W.load(_gpu(w["cfg"], 0, use_graphs=False), w)
+    a.step(9)
+    b.step(9)
+    for f in ("h", "hu", "hv"):
+        assert np.array_equal(a.level_array(0, 1, f), b.level_array(0, 1, f))
+    ta, ea = a.read_gauges()
+    tb, eb = b.read_gauges()
+    assert np.array_equal(ta, tb) and np.array_equal(ea, eb)
+
+
+def _amr_small():
+    w = W.amr3(L=240e3, dx1=4000.0, steps=6)
+    return w
+
+
+def test_amr3_f64_patch_lists_fields_and_gauges():
+    w = _amr_small()
+    o, g = run_pair(w, 6)
+    assert o.num_patches(0, 3) > 0
+    compare_levels(o, g, 3, bitwise=True)
+    to, eo = o.read_gauges()
+    tg, eg = g.read_gauges()
+    assert np.array_equal(to, tg)
+    assert np.array_equal(eo, eg)
+    so, sg = o.stats(), g.stats()
+    assert so["cell_updates"] == sg["cell_updates"]
+    # finest-level field sampling
+    L = w["cfg"]["nx"] * w["cfg"]["dx"]
+    fo = o.read_field(0, 0, "zeta", 97, 89, 100.0, 50.0, L / 97, L / 89)
+    fg = g.read_field(0, 0, "zeta", 97, 89, 100.0, 50.0, L / 97, L / 89)
+    assert np.array_equal(np.isnan(fo), np.isnan(fg))
+    assert np.array_equal(fo[~np.isnan(fo)], fg[~np.isnan(fg)])
+
+
+def test_amr3_f32p_gauges_within_1e4_m():
+    w = _amr_small()
+    o, g = run_pair(w, 6, precision=1)
+    to, eo = o.read_gauges()
+    tg, eg = g.read_gauges()
+    assert np.abs(eg - eo).max() <= F32P_ETA
+
+
+def test_amr_lake_at_rest_gpu():
+    w = W.amr3(L=120e3, dx1=4000.0, steps=6)
+    cfg = dict(w["cfg"], regrid_interval=2)
+    w = dict(w, cfg=cfg, uplift=[])
+    for prec in (0, 1):
+        g = W.load(_gpu(cfg, prec), w)
+        assert g.num_patches(0, 3) > 0
+        g.step(6)
+        for lev in (1, 2, 3):
+            for box, a in g.patches(0, lev):
+                assert np.abs(a["hu"]).max() == 0.0 and np.abs(a["hv"]).max() == 0.0
+
+
+def test_ensemble_scenarios_match_oracle():
+    w = W.ensemble(n_scen=3, n=64, dx=8000.0, steps=6)
+    o, g = run_pair(w, 6)
+    compare_levels(o, g, 2, nscen=3, bitwise=True)
+    to, eo = o.read_gauges()
+    tg, eg = g.read_gauges()
+    assert np.array_equal(eo, eg)
+
+
+def test_empty_finer_level():
+    """No cell is flagged: level 2 stays empty and level 1 still matches."""
+    w = W.hump200()
+    cfg = dict(w["cfg"], num_levels=2, ratios=[4], regrid_interval=2, flag_eta_tol=10.0)
+    o, g = run_pair(dict(w, cfg=cfg), 8, cfg=cfg)
+    assert g.num_patches(0, 2) == 0
+    compare_levels(o, g, 2, bitwise=True)
+
+
+def test_full_size_shelf4096_properties():
+    """The 4096^2 uniform run in the benchmark's launch configuration: at rest
+    it stays exactly at rest; with the uplift (symmetric about mid-y) the
+    solution stays mirror-symmetric in y; a window around the uplift matches
+    the oracle run on a crop holding the whole domain of dependence."""
+    from paper_1901_06798_gb300 import binding
+    w = W.shelf(n=4096, dx=500.0)
+    for prec in (0, 1):
+        g = W.load(_gpu(w["cfg"], prec), dict(w, uplift=[], gauges=np.zeros((0, 2))))
+        g.step(4)
+        b = g.boxes(0, 1)
+        assert len(b) == 1
+        pts = np.linspace(1000.0, 4096 * 500.0 - 1000.0, 256)
+        hu = g.read_field(0, 1, "hu", 256, 256, pts[0], pts[0], pts[1] - pts[0], pts[1] - pts[0])
+        assert np.abs(hu).max() == 0.0
+        g.close()
+    k = 3
+    g = W.load(_gpu(w["cfg"], 0), dict(w, gauges=np.zeros((0, 2))))
+    g.step(k)
+    n, dx = 4096, 500.0
+    # y-mirror symmetry of the full field (sampled on a symmetric set of rows)
+    xs = 1024e3 - 600e3 + (np.arange(-300, 300) + 0.5) * dx + 1024e3 * 0.0
+    xs = (2048e3 - 600e3) + (np.arange(-300, 300) + 0.5) * dx
+    ys = 1024e3 + (np.arange(-400, 400) + 0.5) * dx
+    eta = g.read_field(0, 1, "eta", len(xs), len(ys), xs[0], ys[0], dx, dx)
+    assert np.abs(eta - eta[::-1, :]).max() <= 1e-12 * np.abs(eta).max()
+    # oracle on a crop that contains the uplift and the domain of dependence
+    ci0, cj0 = int(xs[0] / dx) - 4 * k - 8, int(ys[0] / dx) - 4 * k - 8
+    cw, ch = len(xs) + 2 * (4 * k + 8), len(ys) + 2 * (4 * k + 8)
+    ccfg = dict(w["cfg"], nx=cw, ny=ch, x0=ci0 * dx, y0=cj0 * dx)
+    o = W.load(oracle.Oracle(ccfg), dict(w, cfg=ccfg, gauges=np.zeros((0, 2))))
+    o.step(k)
+    assert o.stats()["dt"] == g.stats()["dt"]
+    eo = o.read_field(0, 1, "eta", len(xs), len(ys), xs[0], ys[0], dx, dx)
+    assert rel_err(eta, eo) <= F64_REL

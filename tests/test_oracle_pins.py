@@ -234,6 +234,17 @@ def test_one_patch_equals_tiled_level():
     for f in ("h", "hu", "hv"):
         assert np.array_equal(a.level_array(0, 1, f), b.level_array(0, 1, f))
     assert a.stats()["dt"] == b.stats()["dt"]
+    # thin tiles next to the boundary: ghost cells past the domain edge of a
+    # patch whose own side is not on it
+    for bc in ([W.BC_WALL] * 4, [W.BC_EXTRAP] * 4):
+        cfg = dict(w["cfg"], nx=9, ny=7, dx=200.0, dy=200.0, bc=bc)
+        a = W.load(oracle.Oracle(cfg), dict(w, cfg=cfg))
+        cfg2 = dict(cfg, level1_tile=2)
+        b = W.load(oracle.Oracle(cfg2), dict(w, cfg=cfg2))
+        a.step(12)
+        b.step(12)
+        for f in ("h", "hu", "hv"):
+            assert np.array_equal(a.level_array(0, 1, f), b.level_array(0, 1, f))
 
 
 # --------------------------------------------------------------------------

@@ -183,6 +183,46 @@ int tsu_level1_buffers(tsu_ctx *ctx, void **h, void **hu, void **hv, void **B, i
  * step (ghost fill + update + reductions).  Advances the solution. */
 int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out, double *step_ms_out);
 
+/* ---------------------------------------------------------------------------
+ * Stepping without allocating.  The paper has no counterpart to this entry
+ * point; it exists for callers that must not call cudaMalloc: applications
+ * whose device memory is owned end to end by their own allocator (a
+ * framework's caching allocator, or a service that reserves all of HBM up
+ * front), and latency-critical loops where a cudaMalloc could block or fail.
+ *
+ * One dimensionally split step (the same kernels as tsu_step) of a single
+ * uniform grid of nx x ny cells held in the caller's device memory `block`:
+ * 7 fields of field_stride elements each -- buffer 0 (q0, hu, hv), buffer 1
+ * (q0, hu, hv), B -- with element (i, j), -2 <= i < nx + 2, -2 <= j < ny + 2,
+ * at (j + 2) * pitch + (i + 2).  Elements are double (TSU_F64: q0 = h) or
+ * float (TSU_F32P: q0 = eta' = h + B).  The step reads buffer `cur`, first
+ * overwriting the ghost rings of buffer `cur` and of B with the boundary rules
+ * bc[4] (host ints, left, right, bottom, top) -- so the caller fills interiors
+ * only -- and writes the interior of buffer 1 - cur.  dt is the
+ * caller's; max_speeds (2 host doubles) receives the largest |wave speed| of
+ * the x and y sweeps, from which the caller picks the next dt.  The call
+ * returns after the step has finished on `cuda_stream` (NULL: the default
+ * stream).
+ *
+ * It allocates nothing: its scratch (about 1 MiB, mostly the work-item table)
+ * is a file-scope __device__ array that every GPU loading the library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * address (once per device, with that device current), so make the first call
+ * on each device before any stream capture.  Every call shares the array and
+ * leaves its contents behind; each call rewrites what it uses and clears the
+ * speed accumulator, but calls that overlap on the GPU (other streams or host
+ * threads) race on it -- serialise them.
+ *
+ * Limits: 1 <= nx, ny <= TSU_NOALLOC_MAX_SIDE; pitch >= nx + 4; field_stride
+ * >= pitch * (ny + 4); block aligned to its element size.  Anything else,
+ * including a larger grid, returns TSU_ERR_ARG without launching work.
+ * TSU_ERR_CUDA reports a CUDA failure.
+ * ------------------------------------------------------------------------- */
+#define TSU_NOALLOC_MAX_SIDE 16384
+int tsu_grid_step_noalloc(int precision, void *block, int nx, int ny, int pitch, long long field_stride, int cur,
+                          double dx, double dy, double dt, double g, double drytol, const int *bc,
+                          double *max_speeds, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

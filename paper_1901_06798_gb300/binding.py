@@ -28,7 +28,8 @@ FIELDS = {"h": 0, "hu": 1, "hv": 2, "eta": 3, "zeta": 4, "B": 5}
 SYMBOLS = ["tsu_create", "tsu_destroy", "tsu_last_error", "tsu_add_topo", "tsu_set_eta", "tsu_add_uplift",
            "tsu_init", "tsu_step", "tsu_regrid", "tsu_num_patches", "tsu_get_patches", "tsu_get_patch",
            "tsu_read_field", "tsu_add_gauges", "tsu_read_gauges", "tsu_get_stats", "tsu_sync",
-           "tsu_level1_buffers", "tsu_time_level1_steps", "tsu_set_tuning"]
+           "tsu_level1_buffers", "tsu_time_level1_steps", "tsu_set_tuning",
+           "tsu_grid_step_noalloc"]
 
 
 class tsu_config(C.Structure):
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH):
         "tsu_level1_buffers": ([P, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(P), ip], I),
         "tsu_time_level1_steps": ([P, I, I, dp, dp], I),
         "tsu_set_tuning": ([P, I, I], I),
+        "tsu_grid_step_noalloc": ([I, P, I, I, I, C.c_longlong, I, D, D, D, D, D, ip, dp, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -278,6 +280,18 @@ class Tsunami:
         self._check(self._L.tsu_level1_buffers(self._h, *[C.byref(p) for p in ptrs], C.byref(pitch)),
                     "tsu_level1_buffers")
         return [p.value for p in ptrs], pitch.value
+
+
+def tsu_grid_step_noalloc(precision: int, block_ptr: int, nx: int, ny: int, pitch: int, field_stride: int,
+                          cur: int, dx: float, dy: float, dt: float, g: float, drytol: float, bc, stream=None):
+    """One step of a uniform grid in caller-owned device memory, allocating
+    nothing (see include/tsunami.h).  Returns (rc, (max x speed, max y speed))."""
+    L = load()
+    bcv = (C.c_int * 4)(*bc)
+    sp = (C.c_double * 2)()
+    rc = L.tsu_grid_step_noalloc(precision, C.c_void_p(block_ptr), nx, ny, pitch, field_stride, cur, dx, dy, dt, g,
+                                 drytol, bcv, sp, C.c_void_p(stream) if stream else None)
+    return rc, (sp[0], sp[1])
 
 
 # C-named module functions (argument marshalling only)

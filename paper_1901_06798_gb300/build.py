@@ -38,6 +38,7 @@ UNITS = [
     ("amr_kernels.cu", ["--fmad=false"]),
     ("tsu_api.cpp", []),
     ("cluster.cpp", []),
+    ("noalloc.cu", []),
 ]
 
 

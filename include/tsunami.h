@@ -80,6 +80,8 @@ typedef struct tsu_config {
     int transverse;             /* must be 0: dimensional splitting (the paper's GPU scheme) */
     double cluster_eff;         /* Berger-Rigoutsos box efficiency, 0.7 if <= 0 */
     int use_graphs;             /* capture repeated coarse steps as a CUDA graph */
+    int use_cnn;                /* add the flag predictor's cells to the flags (tsu_cnn_set_weights) */
+    int cnn_buffer;             /* flag buffer width used together with the predictor (instead of b) */
 } tsu_config;
 
 typedef struct tsu_stats {
@@ -169,6 +171,13 @@ int tsu_get_stats(tsu_ctx *ctx, int scenario, tsu_stats *out);
  * row segments).  0 restores the defaults.  Results do not depend on either. */
 int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows);
 
+/* Autotuner: time every launch shape of the patch update (threads per CTA
+ * 64/128/256 x rows per work item 32/64/128/256) on the context's current
+ * levels with `reps` zero-length steps each -- the kernels do all their work
+ * but the state is unchanged -- and keep the fastest.  Outputs (any may be
+ * NULL): the chosen shape and its time per step of all levels in ms. */
+int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, double *best_ms);
+
 /* Synchronise the context's stream. */
 int tsu_sync(tsu_ctx *ctx);
 
@@ -182,6 +191,46 @@ int tsu_level1_buffers(tsu_ctx *ctx, void **h, void **hu, void **hv, void **B, i
  * mean milliseconds of the step kernel per step and total_ms_out the whole
  * step (ghost fill + update + reductions).  Advances the solution. */
 int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out, double *step_ms_out);
+
+/* ---------------------------------------------------------------------------
+ * Refinement-flag predictor.  The buffer of b cells around flagged cells
+ * (Sec. 3.2) is there so waves do not leave the refined region before the next
+ * regrid; it widens every patch by 2b cells.  A small CNN -- three 3x3
+ * convolutions with 16 channels and ReLU, a 1x1 head to one logit per cell --
+ * predicts, from 5 features of a level (eta / 0.1 m on wet cells,
+ * clip(-B / 1000 m, -1, 5), |hu| / 10, |hv| / 10 m^2/s, the criterion flag),
+ * which cells the criterion will flag at the next regrid.  With use_cnn the
+ * flags become criterion(now) OR prediction, dilated by cnn_buffer instead of
+ * b; the criterion stays both the fallback and the judge (cells it flags are
+ * always refined).  Parameters: a flat FP32 vector (per layer W (C_out, C_in,
+ * k, k) then b (C_out); layers 5->16 3x3, 16->16 3x3, 16->16 3x3, 16->1 1x1).
+ * ------------------------------------------------------------------------- */
+
+/* Number of parameters of the predictor (5,425). */
+int tsu_cnn_num_params(void);
+
+/* Logits (n, h, w) of host inputs x (n, 5, h, w); fp16 != 0: FP16 activations
+ * and weights with FP32 accumulation (the inference path), else FP32. */
+int tsu_cnn_forward(const float *theta, const float *x, int n, int h, int w, int fp16, float *logits);
+
+/* Mean binary cross-entropy with logits over the cells where m = 1 and its
+ * gradient with respect to theta (host buffers; targets t in {0, 1}). */
+int tsu_cnn_loss_grad(const float *theta, const float *x, const float *t, const float *m, int n, int h, int w,
+                      double *loss, float *grad);
+
+/* Train theta in place on the GPU: `steps` Adam updates (lr) on mini-batches
+ * of `batch` planes drawn from the host dataset (x, t, m) with a generator
+ * seeded by `seed`; returns the loss of the first and last batch. */
+int tsu_cnn_train(float *theta, const float *x, const float *t, const float *m, int n, int h, int w, int steps,
+                  int batch, float lr, unsigned seed, double *loss_first, double *loss_last);
+
+/* Give a context the predictor's parameters (n = tsu_cnn_num_params()). */
+int tsu_cnn_set_weights(tsu_ctx *ctx, const float *theta, int n);
+
+/* The predictor's input planes of one level (5 planes of nx_l x ny_l floats,
+ * zero where no patch covers a cell) and the criterion flags before the
+ * buffer (nx_l x ny_l bytes), both to host; either may be NULL. */
+int tsu_cnn_features(tsu_ctx *ctx, int scenario, int level, float *features, unsigned char *flags);
 
 /* ---------------------------------------------------------------------------
  * Stepping without allocating.  The paper has no counterpart to this entry

@@ -29,7 +29,8 @@ SYMBOLS = ["tsu_create", "tsu_destroy", "tsu_last_error", "tsu_add_topo", "tsu_s
            "tsu_init", "tsu_step", "tsu_regrid", "tsu_num_patches", "tsu_get_patches", "tsu_get_patch",
            "tsu_read_field", "tsu_add_gauges", "tsu_read_gauges", "tsu_get_stats", "tsu_sync",
            "tsu_level1_buffers", "tsu_time_level1_steps", "tsu_set_tuning",
-           "tsu_grid_step_noalloc"]
+           "tsu_grid_step_noalloc", "tsu_autotune", "tsu_cnn_num_params", "tsu_cnn_forward",
+           "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features"]
 
 
 class tsu_config(C.Structure):
@@ -42,6 +43,7 @@ class tsu_config(C.Structure):
         ("flag_depth_below", C.c_double), ("patch_max", C.c_int), ("level1_tile", C.c_int),
         ("n_regions", C.c_int), ("regions", (C.c_double * 6) * MAX_REGIONS), ("n_scenarios", C.c_int),
         ("transverse", C.c_int), ("cluster_eff", C.c_double), ("use_graphs", C.c_int),
+        ("use_cnn", C.c_int), ("cnn_buffer", C.c_int),
     ]
 
 
@@ -67,6 +69,7 @@ def load(path: str = LIB_PATH):
     L = C.CDLL(path)
     P, I, D = C.c_void_p, C.c_int, C.c_double
     dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+    fp = C.POINTER(C.c_float)
     sig = {
         "tsu_create": ([C.POINTER(tsu_config), P, C.POINTER(P)], I),
         "tsu_destroy": ([P], I),
@@ -88,6 +91,13 @@ def load(path: str = LIB_PATH):
         "tsu_level1_buffers": ([P, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(P), ip], I),
         "tsu_time_level1_steps": ([P, I, I, dp, dp], I),
         "tsu_set_tuning": ([P, I, I], I),
+        "tsu_autotune": ([P, I, ip, ip, dp], I),
+        "tsu_cnn_num_params": ([], I),
+        "tsu_cnn_forward": ([fp, fp, I, I, I, I, fp], I),
+        "tsu_cnn_loss_grad": ([fp, fp, fp, fp, I, I, I, dp, fp], I),
+        "tsu_cnn_train": ([fp, fp, fp, fp, I, I, I, I, I, C.c_float, C.c_uint, dp, dp], I),
+        "tsu_cnn_set_weights": ([P, fp, I], I),
+        "tsu_cnn_features": ([P, I, I, fp, C.POINTER(C.c_ubyte)], I),
         "tsu_grid_step_noalloc": ([I, P, I, I, I, C.c_longlong, I, D, D, D, D, D, ip, dp, P], I),
     }
     for name, (args, res) in sig.items():
@@ -137,6 +147,8 @@ def make_config(cfg: dict, precision: int = TSU_F64, use_graphs: bool = True) ->
     c.transverse = cfg.get("transverse", 0)
     c.cluster_eff = cfg.get("cluster_eff", 0.7)
     c.use_graphs = 1 if use_graphs else 0
+    c.use_cnn = cfg.get("use_cnn", 0)
+    c.cnn_buffer = cfg.get("cnn_buffer", 1)
     return c
 
 
@@ -264,6 +276,29 @@ class Tsunami:
     def set_tuning(self, step_threads: int = 0, seg_rows: int = 0):
         self._check(self._L.tsu_set_tuning(self._h, step_threads, seg_rows), "tsu_set_tuning")
 
+    def autotune(self, reps: int = 3):
+        """Pick the fastest launch shape of the patch update; returns (threads, seg_rows, ms)."""
+        a, b, m = C.c_int(), C.c_int(), C.c_double()
+        self._check(self._L.tsu_autotune(self._h, reps, C.byref(a), C.byref(b), C.byref(m)), "tsu_autotune")
+        return a.value, b.value, m.value
+
+    def cnn_set_weights(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        self._check(self._L.tsu_cnn_set_weights(self._h, th.ctypes.data_as(C.POINTER(C.c_float)), th.size),
+                    "tsu_cnn_set_weights")
+
+    def cnn_features(self, scen: int, level: int):
+        """(features (5, ny_l, nx_l) float32, criterion flags (ny_l, nx_l) uint8) of a level."""
+        R = 1
+        for k in range(level - 1):
+            R *= self.cfg["ratios"][k]
+        ny, nx = self.cfg["ny"] * R, self.cfg["nx"] * R
+        f = np.zeros((5, ny, nx), dtype=np.float32)
+        g = np.zeros((ny, nx), dtype=np.uint8)
+        self._check(self._L.tsu_cnn_features(self._h, scen, level, f.ctypes.data_as(C.POINTER(C.c_float)),
+                                             g.ctypes.data_as(C.POINTER(C.c_ubyte))), "tsu_cnn_features")
+        return f, g
+
     def sync(self):
         self._check(self._L.tsu_sync(self._h), "tsu_sync")
 
@@ -280,6 +315,56 @@ class Tsunami:
         self._check(self._L.tsu_level1_buffers(self._h, *[C.byref(p) for p in ptrs], C.byref(pitch)),
                     "tsu_level1_buffers")
         return [p.value for p in ptrs], pitch.value
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def cnn_num_params() -> int:
+    return load().tsu_cnn_num_params()
+
+
+def cnn_forward(theta, x, fp16: bool = False):
+    """Logits (n, h, w) of inputs x (n, 5, h, w) on the GPU."""
+    L = load()
+    th, xx = _f32(theta), _f32(x)
+    n, _, h, w = xx.shape
+    out = np.zeros((n, h, w), dtype=np.float32)
+    rc = L.tsu_cnn_forward(_fptr(th), _fptr(xx), n, h, w, 1 if fp16 else 0, _fptr(out))
+    if rc:
+        raise TsuError(rc, "tsu_cnn_forward")
+    return out
+
+
+def cnn_loss_grad(theta, x, t, m):
+    L = load()
+    th, xx, tt, mm = _f32(theta), _f32(x), _f32(t), _f32(m)
+    n, _, h, w = xx.shape
+    g = np.zeros(th.size, dtype=np.float32)
+    loss = C.c_double()
+    rc = L.tsu_cnn_loss_grad(_fptr(th), _fptr(xx), _fptr(tt), _fptr(mm), n, h, w, C.byref(loss), _fptr(g))
+    if rc:
+        raise TsuError(rc, "tsu_cnn_loss_grad")
+    return loss.value, g
+
+
+def cnn_train(theta, x, t, m, steps: int, batch: int = 4, lr: float = 1e-3, seed: int = 0):
+    """Adam on the GPU; returns (trained theta, first-batch loss, last-batch loss)."""
+    L = load()
+    th = _f32(theta).copy()
+    xx, tt, mm = _f32(x), _f32(t), _f32(m)
+    n, _, h, w = xx.shape
+    l0, l1 = C.c_double(), C.c_double()
+    rc = L.tsu_cnn_train(_fptr(th), _fptr(xx), _fptr(tt), _fptr(mm), n, h, w, steps, batch, lr, seed,
+                         C.byref(l0), C.byref(l1))
+    if rc:
+        raise TsuError(rc, "tsu_cnn_train")
+    return th, l0.value, l1.value
 
 
 def tsu_grid_step_noalloc(precision: int, block_ptr: int, nx: int, ny: int, pitch: int, field_stride: int,

@@ -39,6 +39,8 @@ UNITS = [
     ("tsu_api.cpp", []),
     ("cluster.cpp", []),
     ("noalloc.cu", []),
+    ("cnn.cu", []),
+    ("cnn_api.cpp", []),
 ]
 
 

@@ -514,6 +514,45 @@ __global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, 
     }
 }
 
+// Input planes of the refinement-flag predictor for the scenarios being
+// regridded (one plane set per slot): eta/0.1 on wet cells, clip(-B/1000, -1, 5),
+// |hu|/10, |hv|/10 and the criterion flag, zero where no patch covers a cell.
+template <typename T, bool PERT>
+__global__ void cnn_features_kernel(LevelView L, int cur, const int *scen_slot, const uint8_t *raw, float *feat,
+                                    double drytol)
+{
+    const PatchDesc P = L.descs[blockIdx.y];
+    const int slot = scen_slot[P.scen];
+    if (slot < 0) return;
+    const int n = P.nx * P.ny;
+    Acc<T> a = acc<T>(L.arena, P);
+    const long long plane = (long long)L.nxl * L.nyl;
+    float *f = feat + (long long)slot * 5 * plane;
+    const uint8_t *rw = raw + (long long)slot * plane;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        int i = c % P.nx, j = c / P.nx;
+        long long k = a.idx(i, j);
+        double B = (double)a.Bp()[k], q0 = (double)a.f(cur, 0)[k];
+        double h = PERT ? q0 - B : q0;
+        double eta = PERT ? q0 : h + B;
+        long long gk = (long long)(P.j0 + j) * L.nxl + (P.i0 + i);
+        double dep = -B / 1000.0;
+        dep = dep < -1.0 ? -1.0 : (dep > 5.0 ? 5.0 : dep);
+        f[gk] = h >= drytol ? (float)(eta / 0.1) : 0.0f;
+        f[plane + gk] = (float)dep;
+        f[2 * plane + gk] = (float)(fabs((double)a.f(cur, 1)[k]) / 10.0);
+        f[3 * plane + gk] = (float)(fabs((double)a.f(cur, 2)[k]) / 10.0);
+        f[4 * plane + gk] = rw[gk] ? 1.0f : 0.0f;
+    }
+}
+
+// raw flags |= (logit > 0) on covered cells
+__global__ void cnn_union_kernel(uint8_t *raw, const uint8_t *cov, const float *logits, long long n)
+{
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+        if (cov[p] && logits[p] > 0.0f) raw[p] = 1;
+}
+
 // ---------------------------------------------------------------- rates, dt
 
 template <typename T, bool PERT>
@@ -523,7 +562,7 @@ __global__ void cell_speed_kernel(LevelView L, const int *list, int cur, double 
     const PatchDesc P = L.descs[list ? list[blockIdx.y] : blockIdx.y];
     const int n = P.nx * P.ny;
     Acc<T> a = acc<T>(L.arena, P);
-    double sx = 0.0, sy = 0.0;
+    T sxT = T(0), syT = T(0);   // running maxima in the state's precision (no FP64 work per cell in FP32)
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         int i = c % P.nx, j = c / P.nx;
         long long k = a.idx(i, j);
@@ -533,9 +572,10 @@ __global__ void cell_speed_kernel(LevelView L, const int *list, int cur, double 
         T cc = PERT ? (T)sqrtf((float)((T)g * h)) : (T)sqrt((double)((T)g * h));
         T ux = a.f(cur, 1)[k] / h, uy = a.f(cur, 2)[k] / h;
         T ax = (ux < T(0) ? -ux : ux) + cc, ay = (uy < T(0) ? -uy : uy) + cc;
-        sx = fmax(sx, (double)ax);
-        sy = fmax(sy, (double)ay);
+        sxT = ax > sxT ? ax : sxT;
+        syT = ay > syT ? ay : syT;
     }
+    double sx = (double)sxT, sy = (double)syT;
     for (int o = 16; o > 0; o >>= 1) {
         sx = fmax(sx, __shfl_xor_sync(0xffffffffu, sx, o));
         sy = fmax(sy, __shfl_xor_sync(0xffffffffu, sy, o));
@@ -578,6 +618,7 @@ __global__ void begin_step_kernel(CtrlView cv, int nscen, int nlev, const double
         for (int l = 0; l < nlev; l++) m = fmax(m, cv.rate[(long long)s * cv.max_levels + l] / Rl[l]);
         double dt = m > 0.0 ? cfl_desired / m : dt_max;
         cv.dt1[s] = fmin(dt, dt_max);
+        cv.dt1f[s] = (float)cv.dt1[s];
         for (int l = 0; l < cv.max_levels; l++) cv.rate[(long long)s * cv.max_levels + l] = 0.0;
     }
 }
@@ -856,6 +897,23 @@ int k_patch_out(int prec, const LevelView &L, int p, int ncells, int cur, double
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
     TSU_DISPATCH(prec, patch_out_kernel, <<<blocks, 256, 0, st>>>(L, p, cur, out));
+    return (int)cudaGetLastError();
+}
+
+int k_cnn_features(int prec, const LevelView &L, int npatch, int maxcells, int cur, const int *scen_slot,
+                   const uint8_t *raw, float *feat, double drytol, cudaStream_t st)
+{
+    if (npatch <= 0) return 0;
+    dim3 g = grid_for(maxcells, npatch, 128);
+    TSU_DISPATCH(prec, cnn_features_kernel, <<<g, 128, 0, st>>>(L, cur, scen_slot, raw, feat, drytol));
+    return (int)cudaGetLastError();
+}
+
+int k_cnn_union(uint8_t *raw, const uint8_t *cov, const float *logits, long long n, cudaStream_t st)
+{
+    long long b = (n + 255) / 256;
+    if (b > 152 * 32) b = 152 * 32;
+    cnn_union_kernel<<<(int)(b < 1 ? 1 : b), 256, 0, st>>>(raw, cov, logits, n);
     return (int)cudaGetLastError();
 }
 

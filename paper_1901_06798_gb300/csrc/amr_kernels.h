@@ -21,6 +21,7 @@ struct LevelView {
 // Device control block of a context: per scenario dt, time, rates, counters.
 struct CtrlView {
     double *dt1, *t;
+    float *dt1f;                 // FP32 copy of dt1 for the perturbation-form kernel
     double *rate;                // [scen][max_levels]
     double *cell_updates;        // [scen]
     const double *cells;         // [scen][max_levels] interior cells per level
@@ -102,6 +103,9 @@ int k_read_field(int prec, const LevelView &L, int npatch, int cur, int scen, in
                  double x0, double y0, double dx, double dy, double X0, double Y0, double dxl, double dyl,
                  cudaStream_t st);
 int k_patch_out(int prec, const LevelView &L, int p, int ncells, int cur, double *out, cudaStream_t st);
+int k_cnn_features(int prec, const LevelView &L, int npatch, int maxcells, int cur, const int *scen_slot,
+                   const uint8_t *raw, float *feat, double drytol, cudaStream_t st);
+int k_cnn_union(uint8_t *raw, const uint8_t *cov, const float *logits, long long n, cudaStream_t st);
 int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, double *mass, cudaStream_t st);
 
 }  // namespace tsu

@@ -32,6 +32,7 @@ constexpr size_t kScratchBytes = 1u << 20;          // 1 MiB per GPU
 constexpr size_t kDescOff = 0;                      // PatchDesc
 constexpr size_t kListOff = 256;                    // int bclist[1]
 constexpr size_t kDtOff = 272;                      // double dt
+constexpr size_t kDtfOff = 280;                     // float dt
 constexpr size_t kSmaxOff = 288;                    // unsigned long long smax[2]
 constexpr size_t kItemsOff = 512;                   // StepItem items[]
 constexpr int kMaxItems = (int)((kScratchBytes - kItemsOff) / sizeof(StepItem));
@@ -76,6 +77,7 @@ __global__ void noalloc_prepare_kernel(unsigned char *scratch, long long fstride
         *reinterpret_cast<PatchDesc *>(scratch + kDescOff) = d;
         *reinterpret_cast<int *>(scratch + kListOff) = 0;
         *reinterpret_cast<double *>(scratch + kDtOff) = dt;
+        *reinterpret_cast<float *>(scratch + kDtfOff) = (float)dt;
         unsigned long long *sm = reinterpret_cast<unsigned long long *>(scratch + kSmaxOff);
         sm[0] = 0ull;
         sm[1] = 0ull;
@@ -108,7 +110,7 @@ extern "C" int tsu_grid_step_noalloc(int precision, void *block, int nx, int ny,
     const size_t esz = precision == TSU_F64 ? 8 : 4;
     if (((uintptr_t)block) % esz) return TSU_ERR_ARG;
     const int nt = precision == TSU_F64 ? step_threads_f64() : step_threads_f32p();
-    const int W = nt - 4;
+    const int W = precision == TSU_F64 ? step_strip_width_f64(nt) : step_strip_width_f32p(nt);
     const int nsx = (nx + W - 1) / W, nsy = (ny + kSegRows - 1) / kSegRows;
     if ((long long)nsx * nsy > kMaxItems) return TSU_ERR_ARG;
 
@@ -143,6 +145,8 @@ extern "C" int tsu_grid_step_noalloc(int precision, void *block, int nx, int ny,
     a.dy = dy;
     a.g = g;
     a.drytol = drytol;
+    a.dt1f = reinterpret_cast<const float *>(scratch + kDtfOff);
+    set_f32_constants(a);
     int e = precision == TSU_F64 ? launch_step_f64(a, nsx * nsy, nt, st) : launch_step_f32p(a, nsx * nsy, nt, st);
     if (e != 0) return TSU_ERR_CUDA;
 

@@ -1,23 +1,24 @@
-// step_f32p.cu -- FP32 surface-perturbation instantiation of the fused patch
-// update: state (eta' = h + B, hu, hv) and B in FP32.  The surface jump that
+// step_f32p.cu -- FP32 surface-perturbation form of the fused patch update
+// (step_f32_lean.cuh): state (eta' = h + B, hu, hv) and B in FP32.  The surface jump that
 // drives the waves is formed from eta' directly, so still water is exactly
 // still and the ocean-depth cancellation of h + B never enters the flux.
-#include "step_kernel.cuh"
+#include "step_f32_lean.cuh"
 
 namespace tsu {
 
 static constexpr int kThreadsF32 = 128;
 
 int step_threads_f32p() { return kThreadsF32; }
+int step_strip_width_f32p(int threads) { return threads - 4; }
 
 // threads per CTA: 64, 128 or 256 (strip width threads - 4 columns)
 int launch_step_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t st)
 {
     if (n_items <= 0) return 0;
     switch (threads) {
-    case 64: step_kernel<float, true, 64, 4><<<n_items, 64, 0, st>>>(a); break;
-    case 128: step_kernel<float, true, 128, 4><<<n_items, 128, 0, st>>>(a); break;
-    case 256: step_kernel<float, true, 256, 4><<<n_items, 256, 0, st>>>(a); break;
+    case 64: step_kernel_f32<64, 4><<<n_items, 64, 0, st>>>(a); break;
+    case 128: step_kernel_f32<128, 4><<<n_items, 128, 0, st>>>(a); break;
+    case 256: step_kernel_f32<256, 4><<<n_items, 256, 0, st>>>(a); break;
     default: return (int)cudaErrorInvalidValue;
     }
     return (int)cudaGetLastError();

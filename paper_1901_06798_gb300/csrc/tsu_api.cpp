@@ -21,6 +21,7 @@
 
 #include "../../include/tsunami.h"
 #include "amr_kernels.h"
+#include "cnn.h"
 #include "tsu_device.h"
 
 namespace tsu {
@@ -217,6 +218,7 @@ struct tsu_ctx {
     bool topo_dirty = true;
     // control block
     DevBuf<double> dt1, t, rate, cellupd, cells, Rl, mass;
+    DevBuf<float> dt1f;
     DevBuf<long long> viol;
     DevBuf<unsigned long long> smax;
     DevBuf<int> derr;
@@ -235,8 +237,14 @@ struct tsu_ctx {
     // statistics and graphs
     long long launches = 0;
     long long viol_seen = 0;
-    int seg_rows = 128;
+    int seg_rows = 0;  // rows per work item of the patch update (0: library default)
     int step_nt = 0;   // threads per CTA of the patch update (0: library default)
+    DevBuf<double> zero_dt;
+    DevBuf<float> zero_dtf;
+    // refinement-flag predictor
+    DevBuf<float> cnn_theta, cnn_feat, cnn_logits;
+    DevBuf<char> cnn_half;
+    bool cnn_ready = false;
     long long hier_version = 0;
     cudaGraphExec_t gexec = nullptr;
     long long graph_version = -1;
@@ -245,6 +253,7 @@ struct tsu_ctx {
 
     // ------------------------------------------------------------ helpers
     int nt() const { return step_nt > 0 ? step_nt : (prec == TSU_F64 ? step_threads_f64() : step_threads_f32p()); }
+    int seg() const { return seg_rows > 0 ? seg_rows : (prec == TSU_F64 ? 128 : 64); }
     void kl(int e, const char *what)
     {
         launches++;
@@ -253,7 +262,7 @@ struct tsu_ctx {
     CtrlView ctrl()
     {
         CtrlView v;
-        v.dt1 = dt1.p; v.t = t.p; v.rate = rate.p; v.cell_updates = cellupd.p; v.cells = cells.p;
+        v.dt1 = dt1.p; v.dt1f = dt1f.p; v.t = t.p; v.rate = rate.p; v.cell_updates = cellupd.p; v.cells = cells.p;
         v.cfl_viol = viol.p; v.smax = smax.p; v.max_levels = kMaxLevels;
         return v;
     }
@@ -326,12 +335,12 @@ struct tsu_ctx {
         L.bclist.clear();
         L.maxring = 0;
         L.maxcells = 0;
-        const int W = nt() - 4;
+        const int W = prec == TSU_F64 ? step_strip_width_f64(nt()) : step_strip_width_f32p(nt());
         for (int k = 0; k < n; k++) {
             const PatchDesc &p = L.P[k];
             for (int x0 = 0; x0 < p.nx; x0 += W)
-                for (int y0 = 0; y0 < p.ny; y0 += seg_rows)
-                    L.items.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(seg_rows, p.ny - y0)});
+                for (int y0 = 0; y0 < p.ny; y0 += seg())
+                    L.items.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(seg(), p.ny - y0)});
             L.maxring = std::max(L.maxring, (p.nx + 4) * (p.ny + 4) - p.nx * p.ny);
             L.maxcells = std::max(L.maxcells, (p.nx + 4) * (p.ny + 4));
             if (p.bcmask) L.bclist.push_back(k);
@@ -445,6 +454,22 @@ struct tsu_ctx {
     }
 
     // ------------------------------------------------------------ regrid
+    // Predictor logits for the np planes of level l whose raw criterion flags
+    // and scenario slots (fslot) are set.
+    void cnn_predict(int l, int np)
+    {
+        Lvl &C = lv[l];
+        const size_t plane = (size_t)C.nxl * C.nyl;
+        cnn_feat.ensure(plane * 5 * np, st);
+        cnn_logits.ensure(plane * np, st);
+        cnn_half.ensure(cnn_half_workspace_bytes(np, C.nyl, C.nxl), st);
+        CK(cudaMemsetAsync(cnn_feat.p, 0, plane * 5 * np * sizeof(float), st));
+        kl(k_cnn_features(prec, view(l), (int)C.P.size(), C.maxcells, C.cur, fslot.p, fraw.p, cnn_feat.p, c.drytol, st),
+           "cnn features");
+        kl(cnn_forward(cnn_theta.p, cnn_feat.p, np, C.nyl, C.nxl, true, nullptr, cnn_logits.p, cnn_half.p, st),
+           "cnn forward");
+    }
+
     // Build level l+1 of the scenarios in `which` from flags on level l.
     void regrid_one(int l, const std::vector<int> &which)
     {
@@ -471,6 +496,12 @@ struct tsu_ctx {
                 for (int m = 0; m < 6; m++) fa.regions[6 * k + m] = c.regions[k][m];
             kl(k_flag(prec, view(l), (int)C.P.size(), C.maxcells, C.cur, fa, st), "flag");
             int b = c.regrid_interval > 0 ? c.regrid_interval : 0;
+            if (c.use_cnn && cnn_ready) {
+                // criterion(now) OR predicted flags, then the narrower buffer
+                cnn_predict(l, np);
+                kl(k_cnn_union(fraw.p, fcov.p, cnn_logits.p, (long long)plane * np, st), "cnn union");
+                b = c.cnn_buffer > 0 ? c.cnn_buffer : 0;
+            }
             kl(k_dilate(fraw.p, ftmp.p, nx, ny, np, b, 0, st), "dilate x");
             kl(k_dilate(ftmp.p, fF.p, nx, ny, np, b, 1, st), "dilate y");
             kl(k_nest(fF.p, fN.p, fcov.p, nx, ny, np, fa, st), "nest");
@@ -590,6 +621,8 @@ struct tsu_ctx {
             StepArgs a{};
             a.descs = L.dP.p; a.items = L.dItems.p; a.arena = arena.base; a.cur = L.cur; a.dt1 = dt1.p;
             a.smax = smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = c.g; a.drytol = c.drytol;
+            a.dt1f = dt1f.p;
+            set_f32_constants(a);
             int e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
                                     : launch_step_f32p(a, (int)L.items.size(), nt(), st);
             kl(e, "patch step");
@@ -771,11 +804,12 @@ struct tsu_ctx {
         }
         for (auto &g : grids) if (g.dev) cudaFreeAsync(g.dev, st);
         dGrids.release(); dGridScen.release(); dEtaIdx.release();
-        dt1.release(); t.release(); rate.release(); cellupd.release(); cells.release(); Rl.release(); mass.release();
+        dt1.release(); dt1f.release(); t.release(); rate.release(); cellupd.release(); cells.release(); Rl.release(); mass.release();
         viol.release(); smax.release(); derr.release();
         dgxy.release(); dgeta.release(); dgt.release(); dnsamp.release(); dgloc.release();
         fraw.release(); fcov.release(); ftmp.release(); fF.release(); fN.release(); fslot.release();
-        dstage.release();
+        dstage.release(); zero_dt.release(); zero_dtf.release();
+        cnn_theta.release(); cnn_feat.release(); cnn_logits.release(); cnn_half.release();
         if (arena.base) cudaFreeAsync(arena.base, st);
         if (st) cudaStreamSynchronize(st);
         if (own_stream && st) cudaStreamDestroy(st);
@@ -856,10 +890,11 @@ int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out)
         }
         const int S = x->nscen;
         cudaStream_t st = x->st;
-        x->dt1.ensure(S, st); x->t.ensure(S, st); x->rate.ensure((size_t)S * kMaxLevels, st);
+        x->dt1.ensure(S, st); x->dt1f.ensure(S, st); x->t.ensure(S, st); x->rate.ensure((size_t)S * kMaxLevels, st);
         x->cellupd.ensure(S, st); x->viol.ensure(S, st); x->smax.ensure(2 * (size_t)S, st);
         x->derr.ensure(1, st); x->mass.ensure(S, st); x->dnsamp.ensure(1, st);
         CK(cudaMemsetAsync(x->dt1.p, 0, S * sizeof(double), st));
+        CK(cudaMemsetAsync(x->dt1f.p, 0, S * sizeof(float), st));
         CK(cudaMemsetAsync(x->t.p, 0, S * sizeof(double), st));
         CK(cudaMemsetAsync(x->rate.p, 0, (size_t)S * kMaxLevels * sizeof(double), st));
         CK(cudaMemsetAsync(x->cellupd.p, 0, S * sizeof(double), st));
@@ -1098,9 +1133,113 @@ int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows)
         if (!(step_threads == 0 || step_threads == 64 || step_threads == 128 || step_threads == 256) || seg_rows < 0)
             throw Err(TSU_ERR_ARG, "step_threads must be 0, 64, 128 or 256 and seg_rows >= 0");
         ctx->step_nt = step_threads;
-        ctx->seg_rows = seg_rows > 0 ? seg_rows : 128;
+        ctx->seg_rows = seg_rows;
         for (int l = 0; l < ctx->nlev; l++)
             if (!ctx->lv[l].P.empty()) ctx->finish_level(l);
+        ctx->sync();
+    });
+}
+
+int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, double *best_ms)
+{
+    return guard(ctx, [&] {
+        if (!ctx->initialized) throw Err(TSU_ERR_ARG, "tsu_init has not been called");
+        if (reps < 1) reps = 3;
+        // zero time step: the kernels do all their work but leave the state as it is
+        ctx->zero_dt.ensure(ctx->nscen, ctx->st);
+        ctx->zero_dtf.ensure(ctx->nscen, ctx->st);
+        CK(cudaMemsetAsync(ctx->zero_dt.p, 0, ctx->nscen * sizeof(double), ctx->st));
+        CK(cudaMemsetAsync(ctx->zero_dtf.p, 0, ctx->nscen * sizeof(float), ctx->st));
+        const int nts[3] = {64, 128, 256}, segs[4] = {32, 64, 128, 256};
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        double best = 1e30;
+        int bt = 0, bs = 0;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 4; b++) {
+                ctx->step_nt = nts[a];
+                ctx->seg_rows = segs[b];
+                for (int l = 0; l < ctx->nlev; l++)
+                    if (!ctx->lv[l].P.empty()) ctx->finish_level(l);
+                auto run = [&] {
+                    for (int l = 0; l < ctx->nlev; l++) {
+                        Lvl &L = ctx->lv[l];
+                        if (L.P.empty()) continue;
+                        StepArgs sa{};
+                        sa.descs = L.dP.p; sa.items = L.dItems.p; sa.arena = ctx->arena.base; sa.cur = L.cur;
+                        sa.dt1 = ctx->zero_dt.p; sa.dt1f = ctx->zero_dtf.p; sa.smax = ctx->smax.p; sa.R = L.R;
+                        sa.dx = L.dx; sa.dy = L.dy; sa.g = ctx->c.g; sa.drytol = ctx->c.drytol;
+                        set_f32_constants(sa);
+                        int e = ctx->prec == TSU_F64 ? launch_step_f64(sa, (int)L.items.size(), ctx->nt(), ctx->st)
+                                                     : launch_step_f32p(sa, (int)L.items.size(), ctx->nt(), ctx->st);
+                        ctx->kl(e, "autotune step");
+                    }
+                };
+                run();
+                CK(cudaEventRecord(e0, ctx->st));
+                for (int k = 0; k < reps; k++) run();
+                CK(cudaEventRecord(e1, ctx->st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms / reps < best) { best = ms / reps; bt = nts[a]; bs = segs[b]; }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CK(cudaMemsetAsync(ctx->smax.p, 0, 2 * ctx->nscen * sizeof(unsigned long long), ctx->st));
+        ctx->step_nt = bt;
+        ctx->seg_rows = bs;
+        for (int l = 0; l < ctx->nlev; l++)
+            if (!ctx->lv[l].P.empty()) ctx->finish_level(l);
+        ctx->sync();
+        if (best_threads) *best_threads = bt;
+        if (best_seg_rows) *best_seg_rows = bs;
+        if (best_ms) *best_ms = best;
+    });
+}
+
+int tsu_cnn_set_weights(tsu_ctx *ctx, const float *theta, int n)
+{
+    return guard(ctx, [&] {
+        if (!theta || n != cnn_n_params()) throw Err(TSU_ERR_ARG, "expected tsu_cnn_num_params() weights");
+        std::vector<float> v(theta, theta + n);
+        ctx->cnn_theta.upload(v, ctx->st);
+        ctx->cnn_ready = true;
+        ctx->sync();
+    });
+}
+
+int tsu_cnn_features(tsu_ctx *ctx, int scen, int level, float *features, unsigned char *flags)
+{
+    return guard(ctx, [&] {
+        if (!ctx->initialized) throw Err(TSU_ERR_ARG, "tsu_init has not been called");
+        if (scen < 0 || scen >= ctx->nscen || level < 1 || level > ctx->nlev) throw Err(TSU_ERR_ARG, "bad scenario/level");
+        const int l = level - 1;
+        Lvl &C = ctx->lv[l];
+        const size_t plane = (size_t)C.nxl * C.nyl;
+        std::vector<int> slot(ctx->nscen, -1);
+        slot[scen] = 0;
+        ctx->fslot.upload(slot, ctx->st);
+        ctx->fraw.ensure(plane, ctx->st);
+        ctx->fcov.ensure(plane, ctx->st);
+        CK(cudaMemsetAsync(ctx->fraw.p, 0, plane, ctx->st));
+        CK(cudaMemsetAsync(ctx->fcov.p, 0, plane, ctx->st));
+        FlagArgs fa{};
+        fa.raw = ctx->fraw.p; fa.cov = ctx->fcov.p; fa.scen_slot = ctx->fslot.p;
+        fa.eta_tol = ctx->c.flag_eta_tol; fa.depth_below = ctx->c.flag_depth_below; fa.drytol = ctx->c.drytol;
+        fa.x0 = ctx->c.x0; fa.y0 = ctx->c.y0; fa.dxl = C.dx; fa.dyl = C.dy;
+        fa.n_regions = ctx->c.n_regions; fa.newlev = level + 1;
+        for (int k = 0; k < ctx->c.n_regions; k++)
+            for (int m = 0; m < 6; m++) fa.regions[6 * k + m] = ctx->c.regions[k][m];
+        ctx->kl(k_flag(ctx->prec, ctx->view(l), (int)C.P.size(), C.maxcells, C.cur, fa, ctx->st), "flag");
+        ctx->cnn_feat.ensure(plane * 5, ctx->st);
+        CK(cudaMemsetAsync(ctx->cnn_feat.p, 0, plane * 5 * sizeof(float), ctx->st));
+        ctx->kl(k_cnn_features(ctx->prec, ctx->view(l), (int)C.P.size(), C.maxcells, C.cur, ctx->fslot.p, ctx->fraw.p,
+                               ctx->cnn_feat.p, ctx->c.drytol, ctx->st), "cnn features");
+        if (features)
+            CK(cudaMemcpyAsync(features, ctx->cnn_feat.p, plane * 5 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+        if (flags) CK(cudaMemcpyAsync(flags, ctx->fraw.p, plane, cudaMemcpyDeviceToHost, ctx->st));
         ctx->sync();
     });
 }
@@ -1150,6 +1289,8 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
             StepArgs a{};
             a.descs = L.dP.p; a.items = L.dItems.p; a.arena = ctx->arena.base; a.cur = L.cur; a.dt1 = ctx->dt1.p;
             a.smax = ctx->smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = ctx->c.g; a.drytol = ctx->c.drytol;
+            a.dt1f = ctx->dt1f.p;
+            set_f32_constants(a);
             CK(cudaEventRecord(ev[2 * k], ctx->st));
             int e = ctx->prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), ctx->nt(), ctx->st)
                                          : launch_step_f32p(a, (int)L.items.size(), ctx->nt(), ctx->st);

@@ -38,12 +38,29 @@ struct StepArgs {
     unsigned long long *smax;   // per scenario: [2] max speed bits (x, y)
     double R;                   // refinement of this level relative to level 1
     double dx, dy, g, drytol;
+    // FP32 copies for the perturbation-form kernel (no FP64 work per CTA)
+    const float *dt1f;          // level-1 time step per scenario, FP32
+    float rdx, rdy;             // 1 / (R dx), 1 / (R dy)
+    float gf, drytolf, sqrtgf;
 };
+
+// FP32 launch constants of a level
+inline void set_f32_constants(StepArgs &a)
+{
+    a.rdx = (float)(1.0 / (a.R * a.dx));
+    a.rdy = (float)(1.0 / (a.R * a.dy));
+    a.gf = (float)a.g;
+    a.drytolf = (float)a.drytol;
+    a.sqrtgf = (float)__builtin_sqrt(a.g);
+}
 
 // Launch helpers implemented in the .cu files.
 int launch_step_f64(const StepArgs &a, int n_items, int threads, cudaStream_t st);
 int launch_step_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t st);
 int step_threads_f64();
 int step_threads_f32p();
+// columns one work item of the patch update covers, for a launch of `threads` per CTA
+int step_strip_width_f64(int threads);
+int step_strip_width_f32p(int threads);
 
 }  // namespace tsu

@@ -135,6 +135,25 @@ def test_graph_replay_equals_eager():
     assert np.array_equal(ta, tb) and np.array_equal(ea, eb)
 
 
+def test_autotune_leaves_the_solution_unchanged():
+    """The autotuner times zero-length steps: afterwards the run still matches
+    the oracle bit for bit, in whatever launch shape it chose."""
+    w = W.shelf(n=192, dx=2000.0)
+    o = W.load(oracle.Oracle(w["cfg"]), w)
+    g = W.load(_gpu(w["cfg"], 0), w)
+    o.step(3)
+    g.step(3)
+    nt, seg, ms = g.autotune(2)
+    assert nt in (64, 128, 256) and seg in (32, 64, 128, 256) and ms > 0
+    o.step(5)
+    g.step(5)
+    compare_levels(o, g, 1, bitwise=True)
+    g32 = W.load(_gpu(w["cfg"], 1), w)
+    g32.autotune(2)
+    g32.step(8)
+    assert np.abs(g32.level_array(0, 1, "eta") - o.level_array(0, 1, "eta")).max() <= F32P_ETA
+
+
 def _amr_small():
     w = W.amr3(L=240e3, dx1=4000.0, steps=6)
     return w

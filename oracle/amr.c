@@ -724,7 +724,10 @@ static int advance(Ora *o, int s, int l)
         OPatch *p = L->p[k];
         save_old(p);
         double a, b;
-        ora_step_patch(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
+        if (o->c.transverse)
+            ora_step_patch_unsplit(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
+        else
+            ora_step_patch(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
         sx = fmax(sx, a);
         sy = fmax(sy, b);
         S->cell_updates += (double)p->nx * (double)p->ny;
@@ -806,7 +809,7 @@ static void sample_gauges(Ora *o)
 void *ora_create(const ora_config *cfg)
 {
     if (cfg->num_levels < 1 || cfg->num_levels > ORA_MAX_LEVELS || cfg->nx < 2 || cfg->ny < 2 ||
-        cfg->n_scenarios < 1 || cfg->transverse)
+        cfg->n_scenarios < 1)
         return NULL;
     Ora *o = (Ora *)calloc(1, sizeof *o);
     o->c = *cfg;

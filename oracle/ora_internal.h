@@ -19,4 +19,8 @@ typedef struct OPatch {
 void ora_step_patch(OPatch *p, double g, double drytol, double dt, double dx, double dy,
                     double *sx, double *sy);
 
+/* one unsplit step with transverse corrections (the original GeoClaw scheme) */
+void ora_step_patch_unsplit(OPatch *p, double g, double drytol, double dt, double dx, double dy,
+                            double *sx, double *sy);
+
 #endif

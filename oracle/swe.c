@@ -249,3 +249,265 @@ void ora_step_patch(OPatch *p, double g, double drytol, double dt, double dx, do
     free(a); free(o);
     *sx_out = sx; *sy_out = sy;
 }
+
+/* ------------------------------------------------------------------------
+ * Unsplit wave propagation with transverse corrections (the scheme of the
+ * original GeoClaw that the paper compares against, Sec. 5; corner transport
+ * upwind of LeVeque 1997).  Reading: the fluctuations A+-dQ of every x-edge are
+ * split in y by a Roe decomposition of the two cells above/below the cell they
+ * enter, B-+ parts update the correction fluxes G of that cell's y-edges with
+ * -(dt/dx)/2; likewise y-edge fluctuations split in x update F with
+ * -(dt/dy)/2 (eigenstructure and dry cells: tsplit below).  As in GeoClaw's default, the second-order corrections are
+ * propagated transversely too: the split fluctuations are A-dQ + 2F~ and
+ * A+dQ - 2F~ (2F~ = sum_p c_p Z_p, the limited correction of the edge).
+ * Accumulation order (fixed so two implementations agree bit for bit):
+ *   G(i, j-1/2) = (((Gc - h*B-A+(i-1/2, j)) - h*B-A-(i+1/2, j))
+ *                 - h*B+A+(i-1/2, j-1)) - h*B+A-(i+1/2, j-1),  h = dt/dx / 2
+ *   F(i-1/2, j) = (((Fc - k*A-B+(i, j-1/2)) - k*A-B-(i, j+1/2))
+ *                 - k*A+B+(i-1, j-1/2)) - k*A+B-(i-1, j+1/2),  k = dt/dy / 2
+ * where A+- here are the second-order fluctuations above
+ *   Q = (Q - dt/dx ((A+dQ_l + A-dQ_r) + (F_r - F_l))) - dt/dy ((B+dQ_b + B-dQ_t) + (G_t - G_b))
+ * ------------------------------------------------------------------------ */
+
+/* split fluctuation d (mass, n, t) along direction n between cells a (low) and
+ * b (high) into the parts going towards a (minus) and towards b (plus), with
+ * the eigenvectors of the Roe average of the two cells (both wet), or of the
+ * wet cell alone (one dry cell whose bed lies below the wet surface).  Both
+ * dry, or a dry cell whose bed reaches the wet surface (a wall): no transverse
+ * wave. */
+static void tsplit(double g, double drytol, const double d[3],
+                   double ha, double na, double ta, double Ba, double hb, double nb, double tb, double Bb,
+                   double minus[3], double plus[3])
+{
+    for (int m = 0; m < 3; m++) { minus[m] = 0.0; plus[m] = 0.0; }
+    int wa = ha >= drytol, wb = hb >= drytol;
+    double un, ut, c;
+    if (wa && wb) {
+        double sa = sqrt(ha), sb = sqrt(hb);
+        un = (sa * (na / ha) + sb * (nb / hb)) / (sa + sb);
+        ut = (sa * (ta / ha) + sb * (tb / hb)) / (sa + sb);
+        c = sqrt(g * (0.5 * (ha + hb)));
+    } else if (wa) {
+        if (Bb >= ha + Ba) return;
+        un = na / ha; ut = ta / ha; c = sqrt(g * ha);
+    } else if (wb) {
+        if (Ba >= hb + Bb) return;
+        un = nb / hb; ut = tb / hb; c = sqrt(g * hb);
+    } else {
+        return;
+    }
+    double l1 = un - c, l2 = un, l3 = un + c;
+    double b1 = ((un + c) * d[0] - d[1]) / (2.0 * c);
+    double b3 = (d[1] - (un - c) * d[0]) / (2.0 * c);
+    double b2 = d[2] - ut * d[0];
+    double w1[3] = {b1, b1 * l1, b1 * ut}, w3[3] = {b3, b3 * l3, b3 * ut};
+    double w2[3] = {0.0, 0.0, b2};
+    double m1 = fmin(l1, 0.0), m2 = fmin(l2, 0.0), m3 = fmin(l3, 0.0);
+    double p1 = fmax(l1, 0.0), p2 = fmax(l2, 0.0), p3 = fmax(l3, 0.0);
+    for (int m = 0; m < 3; m++) {
+        minus[m] = (m1 * w1[m] + m2 * w2[m]) + m3 * w3[m];
+        plus[m] = (p1 * w1[m] + p2 * w2[m]) + p3 * w3[m];
+    }
+}
+
+typedef struct EdgeTerms {
+    double am[3], ap[3], F[3];   /* fluctuations and limited correction, edge frame (mass, normal, transverse) */
+    double am2[3], ap2[3];       /* A-dQ + 2F~, A+dQ - 2F~: what is split transversely */
+    double s0, s2;
+} EdgeTerms;
+
+/* edge terms of one 1D row of n interior cells (arrays of n+4 with 2 ghosts):
+ * out[e] for edges e = 0..n (fluctuations, limited correction) */
+static void row_terms(double g, double drytol, int n, double dtdx,
+                      const double *h, const double *hn, const double *ht, const double *B, EdgeTerms *out)
+{
+    ora_rp *rp = (ora_rp *)malloc((size_t)(n + 3) * sizeof *rp);
+    for (int e = -1; e <= n + 1; e++) {
+        int cl = e - 1 + 2, cr = e + 2;
+        ora_riemann(g, drytol, h[cl], hn[cl], ht[cl], B[cl], h[cr], hn[cr], ht[cr], B[cr], &rp[e + 1]);
+    }
+    for (int e = 0; e <= n; e++) {
+        const ora_rp *r = &rp[e + 1];
+        EdgeTerms *o = &out[e];
+        for (int m = 0; m < 3; m++) {
+            o->am[m] = (w_left(r->s[0]) * r->Z[0][m] + w_left(r->s[1]) * r->Z[1][m]) + w_left(r->s[2]) * r->Z[2][m];
+            o->ap[m] = (w_right(r->s[0]) * r->Z[0][m] + w_right(r->s[1]) * r->Z[1][m]) + w_right(r->s[2]) * r->Z[2][m];
+        }
+        if (r->wallR) { o->ap[0] = 0.0; o->ap[1] = 0.0; o->ap[2] = 0.0; }
+        if (r->wallL) { o->am[0] = 0.0; o->am[1] = 0.0; o->am[2] = 0.0; }
+        double c[3] = {0.0, 0.0, 0.0};
+        if (!r->wallL && !r->wallR) {
+            for (int p = 0; p < 3; p++) {
+                const double *Zi = r->Z[p];
+                double dii = (Zi[0] * Zi[0] + Zi[1] * Zi[1]) + Zi[2] * Zi[2];
+                double phi = 0.0;
+                if (dii != 0.0) {
+                    int I = r->s[p] >= 0.0 ? e - 1 : e + 1;
+                    const double *ZI = rp[I + 1].Z[p];
+                    double dIi = (ZI[0] * Zi[0] + ZI[1] * Zi[1]) + ZI[2] * Zi[2];
+                    phi = ora_mc_limiter(dIi / dii);
+                }
+                double s = r->s[p];
+                double cp = (1.0 - dtdx * fabs(s)) * phi;
+                if (s < 0.0) cp = -cp;
+                else if (s == 0.0) cp = 0.0;
+                c[p] = cp;
+            }
+        }
+        for (int m = 0; m < 3; m++) {
+            double cq = (c[0] * r->Z[0][m] + c[1] * r->Z[1][m]) + c[2] * r->Z[2][m];
+            o->F[m] = 0.5 * cq;
+            o->am2[m] = o->am[m] + cq;
+            o->ap2[m] = o->ap[m] - cq;
+        }
+        o->s0 = r->s[0];
+        o->s2 = r->s[2];
+    }
+    free(rp);
+}
+
+void ora_step_patch_unsplit(OPatch *p, double g, double drytol, double dt, double dx, double dy,
+                            double *sx_out, double *sy_out)
+{
+    int nx = p->nx, ny = p->ny;
+    double dtdx = dt / dx, dtdy = dt / dy;
+    int nmax = (nx > ny ? nx : ny) + 4;
+    double *a = malloc(4 * (size_t)nmax * sizeof(double));
+    double *ah = a, *an = a + nmax, *at = a + 2 * nmax, *aB = a + 3 * nmax;
+    /* x-edge terms X[j+1][e] for rows j = -1..ny, edges e = 0..nx (storage frame: mass, hu, hv) */
+    EdgeTerms *X = malloc((size_t)(ny + 2) * (nx + 1) * sizeof *X);
+    EdgeTerms *Y = malloc((size_t)(nx + 2) * (ny + 1) * sizeof *Y);   /* Y[i+1][e], frame (mass, hv, hu) */
+    EdgeTerms *tmp = malloc((size_t)(nmax + 1) * sizeof *tmp);
+    double sx = 0.0, sy = 0.0;
+    for (int j = -1; j <= ny; j++) {
+        for (int i = -2; i < nx + 2; i++) {
+            size_t k = OIDX(p, i, j);
+            ah[i + 2] = p->h[k]; an[i + 2] = p->hu[k]; at[i + 2] = p->hv[k]; aB[i + 2] = p->B[k];
+        }
+        row_terms(g, drytol, nx, dtdx, ah, an, at, aB, tmp);
+        for (int e = 0; e <= nx; e++) {
+            X[(size_t)(j + 1) * (nx + 1) + e] = tmp[e];
+            if (j >= 0 && j < ny) sx = fmax(sx, fmax(-tmp[e].s0, tmp[e].s2));
+        }
+    }
+    for (int i = -1; i <= nx; i++) {
+        for (int j = -2; j < ny + 2; j++) {
+            size_t k = OIDX(p, i, j);
+            ah[j + 2] = p->h[k]; an[j + 2] = p->hv[k]; at[j + 2] = p->hu[k]; aB[j + 2] = p->B[k];
+        }
+        row_terms(g, drytol, ny, dtdy, ah, an, at, aB, tmp);
+        for (int e = 0; e <= ny; e++) {
+            Y[(size_t)(i + 1) * (ny + 1) + e] = tmp[e];
+            if (i >= 0 && i < nx) sy = fmax(sy, fmax(-tmp[e].s0, tmp[e].s2));
+        }
+    }
+#define XT(j, e) X[(size_t)((j) + 1) * (nx + 1) + (e)]
+#define YT(i, e) Y[(size_t)((i) + 1) * (ny + 1) + (e)]
+#define H(i, j) p->h[OIDX(p, i, j)]
+#define HU(i, j) p->hu[OIDX(p, i, j)]
+#define HV(i, j) p->hv[OIDX(p, i, j)]
+#define BB(i, j) p->B[OIDX(p, i, j)]
+    double hx = 0.5 * dtdx, hy = 0.5 * dtdy;
+    /* x-edge fluctuation of edge (e, j) split in y for the cell column c it enters: returns B- and B+
+     * parts in storage frame (mass, hu, hv); frame for tsplit: (mass, hv, hu) */
+#define XSPLIT(fl, c, j, lo, hi_)                                                              \
+    do {                                                                                       \
+        double d_[3] = {(fl)[0], (fl)[2], (fl)[1]}, mi_[3], pl_[3];                            \
+        tsplit(g, drytol, d_, H(c, (j) - 1), HV(c, (j) - 1), HU(c, (j) - 1), BB(c, (j) - 1), H(c, j), HV(c, j), HU(c, j), BB(c, j), mi_, pl_); \
+        lo[0] = mi_[0]; lo[1] = mi_[2]; lo[2] = mi_[1];                                        \
+        tsplit(g, drytol, d_, H(c, j), HV(c, j), HU(c, j), BB(c, j), H(c, (j) + 1), HV(c, (j) + 1), HU(c, (j) + 1), BB(c, (j) + 1), mi_, pl_); \
+        hi_[0] = pl_[0]; hi_[1] = pl_[2]; hi_[2] = pl_[1];                                     \
+    } while (0)
+    /* G(i, e) for y-edges e = 0..ny of columns i = 0..nx-1, in storage frame (mass, hu, hv) */
+    double (*G)[3] = malloc((size_t)nx * (ny + 1) * sizeof *G);
+    for (int i = 0; i < nx; i++)
+        for (int e = 0; e <= ny; e++) {
+            const EdgeTerms *yt = &YT(i, e);
+            double gv[3] = {yt->F[0], yt->F[2], yt->F[1]};   /* to storage frame */
+            int j = e;   /* y-edge between rows j-1 and j */
+            double lo[3], hi[3];
+            /* (a) x-edge (i-1/2, j): A+ into (i, j), down part */
+            XSPLIT(XT(j, i).ap2, i, j, lo, hi);
+            for (int m = 0; m < 3; m++) gv[m] = gv[m] - hx * lo[m];
+            /* (b) x-edge (i+1/2, j): A- into (i, j), down part */
+            XSPLIT(XT(j, i + 1).am2, i, j, lo, hi);
+            for (int m = 0; m < 3; m++) gv[m] = gv[m] - hx * lo[m];
+            /* (c) x-edge (i-1/2, j-1): A+ into (i, j-1), up part */
+            XSPLIT(XT(j - 1, i).ap2, i, j - 1, lo, hi);
+            for (int m = 0; m < 3; m++) gv[m] = gv[m] - hx * hi[m];
+            /* (d) x-edge (i+1/2, j-1): A- into (i, j-1), up part */
+            XSPLIT(XT(j - 1, i + 1).am2, i, j - 1, lo, hi);
+            for (int m = 0; m < 3; m++) gv[m] = gv[m] - hx * hi[m];
+            G[(size_t)i * (ny + 1) + e][0] = gv[0];
+            G[(size_t)i * (ny + 1) + e][1] = gv[1];
+            G[(size_t)i * (ny + 1) + e][2] = gv[2];
+        }
+    /* y-edge fluctuation split in x, frame for tsplit (mass, hu, hv) */
+#define YSPLIT(fl, c, r, lo, hi_)                                                              \
+    do {                                                                                       \
+        double d_[3] = {(fl)[0], (fl)[2], (fl)[1]}, mi_[3], pl_[3];                            \
+        tsplit(g, drytol, d_, H((c) - 1, r), HU((c) - 1, r), HV((c) - 1, r), BB((c) - 1, r), H(c, r), HU(c, r), HV(c, r), BB(c, r), mi_, pl_); \
+        lo[0] = mi_[0]; lo[1] = mi_[1]; lo[2] = mi_[2];                                        \
+        tsplit(g, drytol, d_, H(c, r), HU(c, r), HV(c, r), BB(c, r), H((c) + 1, r), HU((c) + 1, r), HV((c) + 1, r), BB((c) + 1, r), mi_, pl_); \
+        hi_[0] = pl_[0]; hi_[1] = pl_[1]; hi_[2] = pl_[2];                                     \
+    } while (0)
+    double (*Fx)[3] = malloc((size_t)ny * (nx + 1) * sizeof *Fx);
+    for (int j = 0; j < ny; j++)
+        for (int e = 0; e <= nx; e++) {
+            const EdgeTerms *xt = &XT(j, e);
+            double fv[3] = {xt->F[0], xt->F[1], xt->F[2]};
+            int i = e;   /* x-edge between columns i-1 and i */
+            double lo[3], hi[3];
+            /* (a) y-edge (i, j-1/2): B+ into (i, j), left part */
+            YSPLIT(YT(i, j).ap2, i, j, lo, hi);
+            for (int m = 0; m < 3; m++) fv[m] = fv[m] - hy * lo[m];
+            /* (b) y-edge (i, j+1/2): B- into (i, j), left part */
+            YSPLIT(YT(i, j + 1).am2, i, j, lo, hi);
+            for (int m = 0; m < 3; m++) fv[m] = fv[m] - hy * lo[m];
+            /* (c) y-edge (i-1, j-1/2): B+ into (i-1, j), right part */
+            YSPLIT(YT(i - 1, j).ap2, i - 1, j, lo, hi);
+            for (int m = 0; m < 3; m++) fv[m] = fv[m] - hy * hi[m];
+            /* (d) y-edge (i-1, j+1/2): B- into (i-1, j), right part */
+            YSPLIT(YT(i - 1, j + 1).am2, i - 1, j, lo, hi);
+            for (int m = 0; m < 3; m++) fv[m] = fv[m] - hy * hi[m];
+            Fx[(size_t)j * (nx + 1) + e][0] = fv[0];
+            Fx[(size_t)j * (nx + 1) + e][1] = fv[1];
+            Fx[(size_t)j * (nx + 1) + e][2] = fv[2];
+        }
+    /* update (new values to temporary arrays, then copy) */
+    double *qn = malloc(3 * (size_t)nx * ny * sizeof(double));
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            const EdgeTerms *xl = &XT(j, i), *xr = &XT(j, i + 1);
+            const EdgeTerms *yb = &YT(i, j), *ytp = &YT(i, j + 1);
+            const double *Fl = Fx[(size_t)j * (nx + 1) + i], *Fr = Fx[(size_t)j * (nx + 1) + i + 1];
+            const double *Gb = G[(size_t)i * (ny + 1) + j], *Gt = G[(size_t)i * (ny + 1) + j + 1];
+            double q[3] = {H(i, j), HU(i, j), HV(i, j)};
+            for (int m = 0; m < 3; m++) {
+                int my = m == 0 ? 0 : (m == 1 ? 2 : 1);   /* storage component m in the y-edge frame */
+                double ux = (xl->ap[m] + xr->am[m]) + (Fr[m] - Fl[m]);
+                double uy = (yb->ap[my] + ytp->am[my]) + (Gt[m] - Gb[m]);
+                q[m] = (q[m] - dtdx * ux) - dtdy * uy;
+            }
+            if (q[0] < 0.0) q[0] = 0.0;
+            if (q[0] < drytol) { q[1] = 0.0; q[2] = 0.0; }
+            for (int m = 0; m < 3; m++) qn[(size_t)m * nx * ny + (size_t)j * nx + i] = q[m];
+        }
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            size_t k = OIDX(p, i, j), d = (size_t)j * nx + i;
+            p->h[k] = qn[d];
+            p->hu[k] = qn[(size_t)nx * ny + d];
+            p->hv[k] = qn[2 * (size_t)nx * ny + d];
+        }
+#undef XT
+#undef YT
+#undef H
+#undef HU
+#undef HV
+#undef BB
+#undef XSPLIT
+#undef YSPLIT
+    free(qn); free(G); free(Fx); free(X); free(Y); free(tmp); free(a);
+    *sx_out = sx; *sy_out = sy;
+}

@@ -1,0 +1,179 @@
+"""Pins of the oracle's unsplit update with transverse corrections (the
+scheme of the original GeoClaw, which the paper compares against in Sec. 5;
+corner transport upwind, LeVeque 1997).
+
+Each pin checks the scheme against something outside it:
+
+* a y-uniform problem has no transverse waves, so the unsplit step must be
+  bitwise the dimensionally split step (itself pinned by the dam breaks);
+* the exact solution of the linearised equations for a Gaussian hump
+  (Hankel transform of the 2D wave equation): second-order convergence on
+  square and on 2:1 cells;
+* stability at a Courant number of 0.9 in BOTH directions at once, which an
+  unsplit update without (or with wrongly signed) transverse terms does not
+  have (its limit is nu_x + nu_y <= 1);
+* exact transpose symmetry for a non-symmetric surface over a non-symmetric
+  bed (the split scheme breaks it at the splitting error);
+* still water with dry land, and mass between walls, to rounding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_06798_gb300 import workloads as W
+
+special = pytest.importorskip("scipy.special")
+
+
+def _steps_to(o, T):
+    t = 0.0
+    while t < T:
+        t = o.step(1)[0]
+    return t
+
+
+def test_y_uniform_problem_equals_split_step():
+    for hl, hr in ((2.0, 1.0), (1.0, 0.0)):
+        w = W.dam_break_1d(200, hl, hr)
+        a = W.load(oracle.Oracle(w["cfg"]), w)
+        cfg = dict(w["cfg"], transverse=1)
+        b = W.load(oracle.Oracle(cfg), dict(w, cfg=cfg))
+        a.step(60)
+        b.step(60)
+        for f in ("h", "hu", "hv"):
+            assert np.array_equal(a.level_array(0, 1, f), b.level_array(0, 1, f)), f
+
+
+def _linear_hump(r, t, a, sig, c):
+    """eta(r, t) of eta_tt = c^2 lap(eta), eta(r, 0) = a exp(-r^2 / (2 sig^2)),
+    eta_t(r, 0) = 0, as the Hankel transform a sig^2 int exp(-k^2 sig^2 / 2)
+    cos(c k t) J0(k r) k dk (trapezoid rule, integrand below 1e-30 beyond)."""
+    k = np.linspace(0.0, 12.0 / sig, 6001)
+    A = a * sig ** 2 * np.exp(-(k * sig) ** 2 / 2.0)
+    out = np.empty(r.size)
+    for s in range(0, r.size, 4096):
+        rr = r.ravel()[s:s + 4096]
+        out[s:s + rr.size] = np.trapezoid(A * np.cos(c * k * t) * special.j0(np.outer(rr, k)) * k, k, axis=1)
+    return out.reshape(r.shape)
+
+
+def _hump_error(n, aspect, transverse=1, L=200e3, depth=100.0, a=0.01):
+    dx = L / n
+    dy = dx * aspect
+    ny = int(round(L / dy))
+    cfg = W.base_config(nx=n, ny=ny, dx=dx, dy=dy, bc=[W.BC_EXTRAP] * 4, cfl_desired=0.9, transverse=transverse)
+    X, Y = np.meshgrid((np.arange(n) + 0.5) * dx, (np.arange(ny) + 0.5) * dy)
+    sig = L / 12.0
+    eta = a * np.exp(-((X - L / 2) ** 2 + (Y - L / 2) ** 2) / (2 * sig ** 2))
+    o = W.load(oracle.Oracle(cfg), dict(topo=W.flat_topo(cfg, depth), eta=[(0, eta, 0.5 * dx, 0.5 * dy, dx, dy)],
+                                         uplift=[], gauges=[]))
+    c = np.sqrt(9.81 * depth)
+    t = _steps_to(o, 0.3 * L / c)
+    assert o.stats()["cfl_violations"] == 0
+    ref = _linear_hump(np.hypot(X - L / 2, Y - L / 2), t, a, sig, c)
+    return np.abs(o.level_array(0, 1, "eta") - ref).mean() / a
+
+
+@pytest.mark.parametrize("aspect,bound", [(1, 6e-4), (2, 2e-3)])
+def test_converges_to_linear_wave_solution(aspect, bound):
+    """a / depth = 1e-4, so the nonlinear terms sit far below the error."""
+    e1, e2 = _hump_error(40, aspect), _hump_error(80, aspect)
+    assert e2 < bound, (e1, e2)
+    assert np.log2(e1 / e2) >= 1.8, (e1, e2)
+
+
+def test_stable_at_courant_09_in_both_directions():
+    w = W.hump200()
+    cfg = dict(w["cfg"], transverse=1, cfl_desired=0.9)
+    o = W.load(oracle.Oracle(cfg), dict(w, cfg=cfg))
+    m0 = o.stats()["mass"]
+    o.step(400)
+    st = o.stats()
+    eta = o.level_array(0, 1, "eta")
+    assert np.all(np.isfinite(eta))
+    assert np.abs(eta).max() <= 0.5
+    assert abs(st["mass"] - m0) <= 1e-13 * m0
+    assert st["cfl_violations"] == 0
+    # both directions near the limit: the first step runs at nu_x ~ nu_y ~ 0.9
+    h = o.level_array(0, 1, "h")
+    assert np.abs(h - h[::-1, :]).max() <= 1e-12 * h.max()
+    assert np.abs(h - h[:, ::-1]).max() <= 1e-12 * h.max()
+
+
+def _asym_case(transpose, transverse):
+    n, dx = 48, 50.0
+    L = n * dx
+    cfg = W.base_config(nx=n, ny=n, dx=dx, dy=dx, bc=[W.BC_WALL] * 4, cfl_desired=0.9, transverse=transverse)
+    xs = np.linspace(0, L, n + 1)
+    X, Y = np.meshgrid(xs, xs)
+    B = -12.0 + 4.0 * np.sin(X / 300.0) * np.cos(Y / 500.0) + 2.0 * (X / L) ** 2
+    eta = W.gaussian_grid(0, 0, L, L, n + 1, n + 1, 900.0, 1500.0, 1.2, 250.0, 180.0)[0] \
+        - W.gaussian_grid(0, 0, L, L, n + 1, n + 1, 1700.0, 700.0, 0.6, 150.0, 300.0)[0]
+    if transpose:
+        B, eta = B.T, eta.T
+    w = dict(cfg=cfg, topo=[(np.ascontiguousarray(B), 0.0, 0.0, dx, dx)],
+             eta=[(0, np.ascontiguousarray(eta), 0.0, 0.0, dx, dx)], uplift=[], gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    o.step(80)
+    return {f: o.level_array(0, 1, f) for f in ("h", "hu", "hv")}
+
+
+def test_transpose_symmetry():
+    a, b = _asym_case(False, 1), _asym_case(True, 1)
+    scale = np.abs(a["h"]).max()
+    assert np.abs(a["h"] - b["h"].T).max() <= 1e-13 * scale
+    assert np.abs(a["hu"] - b["hv"].T).max() <= 1e-12 * scale
+    assert np.abs(a["hv"] - b["hu"].T).max() <= 1e-12 * scale
+    # the split scheme is not transpose symmetric: the pin has teeth
+    c, d = _asym_case(False, 0), _asym_case(True, 0)
+    assert np.abs(c["h"] - d["h"].T).max() > 1e-6 * scale
+
+
+def test_lake_at_rest_with_dry_land():
+    w = W.lake_at_rest_shelf(n=96)
+    cfg = dict(w["cfg"], transverse=1)
+    o = W.load(oracle.Oracle(cfg), dict(w, cfg=cfg))
+    o.step(200)
+    for f in ("hu", "hv"):
+        assert np.abs(o.level_array(0, 1, f)).max() == 0.0
+    h, B = o.level_array(0, 1, "h"), o.level_array(0, 1, "B")
+    wet = h > 0
+    assert np.abs((h + B)[wet]).max() == 0.0
+    assert (~wet).sum() > 0 and wet.sum() > 0
+
+
+def test_mass_between_walls_with_wetting_and_drying():
+    """A hump running up a beach inside walls, at a fixed dt below the CFL
+    limit: depths stay >= 0, the shoreline moves, mass to rounding."""
+    n, dx = 64, 40.0
+    L = n * dx
+    cfg = W.base_config(nx=n, ny=n, dx=dx, dy=dx, bc=[W.BC_WALL] * 4, transverse=1, dt_max=0.5)
+    xs = np.linspace(0, L, n + 1)
+    X, Y = np.meshgrid(xs, xs)
+    B = -8.0 + 12.0 * (X / L) + 1.5 * np.sin(Y / 200.0)
+    eta = W.gaussian_grid(0, 0, L, L, n + 1, n + 1, 1300.0, 1300.0, 0.5, 200.0, 200.0)[0]
+    w = dict(cfg=cfg, topo=[(B, 0.0, 0.0, dx, dx)], eta=[(0, eta, 0.0, 0.0, dx, dx)], uplift=[],
+             gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    m0 = o.stats()["mass"]
+    wet0 = o.level_array(0, 1, "h") > 0
+    o.step(100)
+    h = o.level_array(0, 1, "h")
+    assert o.stats()["cfl_violations"] == 0
+    assert h.min() >= 0.0
+    assert ((h > 0) != wet0).sum() > 0
+    assert abs(o.stats()["mass"] - m0) <= 1e-13 * m0
+
+
+def test_tiled_level_and_full_refinement_equal_single_grid():
+    """Corner ghost cells matter for the unsplit stencil: a tiled level must
+    still be bitwise the single patch."""
+    w = W.hump200()
+    cfg = dict(w["cfg"], transverse=1)
+    a = W.load(oracle.Oracle(cfg), dict(w, cfg=cfg))
+    cfg2 = dict(cfg, level1_tile=37)
+    b = W.load(oracle.Oracle(cfg2), dict(w, cfg=cfg2))
+    a.step(30)
+    b.step(30)
+    for f in ("h", "hu", "hv"):
+        assert np.array_equal(a.level_array(0, 1, f), b.level_array(0, 1, f))

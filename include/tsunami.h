@@ -77,7 +77,10 @@ typedef struct tsu_config {
     int n_regions;
     double regions[TSU_MAX_REGIONS][6]; /* x1, y1, x2, y2, min_level, max_level (1-based levels) */
     int n_scenarios;            /* independent scenarios advanced together (>= 1) */
-    int transverse;             /* must be 0: dimensional splitting (the paper's GPU scheme) */
+    int transverse;             /* 0: dimensional splitting, x then y (the paper's GPU scheme);
+                                   1: unsplit update with transverse corrections (the original
+                                   GeoClaw scheme Sec. 5 compares against; corner transport
+                                   upwind, LeVeque 1997) */
     double cluster_eff;         /* Berger-Rigoutsos box efficiency, 0.7 if <= 0 */
     int use_graphs;             /* capture repeated coarse steps as a CUDA graph */
     int use_cnn;                /* add the flag predictor's cells to the flags (tsu_cnn_set_weights) */

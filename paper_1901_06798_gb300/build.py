@@ -3,10 +3,11 @@
 ``python -m paper_1901_06798_gb300.build`` compiles ``csrc/`` into
 ``_build/libtsunami.so``.  Translation units compile in parallel:
 
-* ``step_f64.cu`` and ``amr_kernels.cu`` with ``--fmad=false`` so the FP64
+* ``step_f64.cu``, ``step_unsplit_f64.cu`` and ``amr_kernels.cu`` with
+  ``--fmad=false`` so the FP64
   kernels round every product and sum separately, exactly like the FP64
   reference arithmetic;
-* ``step_f32p.cu`` with contraction and CUDA's fast FP32 divide/sqrt allowed
+* ``step_f32p.cu`` and ``step_unsplit_f32p.cu`` with contraction and CUDA's fast FP32 divide/sqrt allowed
   (the FP32 perturbation form, held to 1e-4 m of surface elevation);
 * the host runtime (``tsu_api.cpp``, ``cluster.cpp``) with the host compiler.
 """
@@ -35,6 +36,8 @@ def _nvcc() -> str:
 UNITS = [
     ("step_f64.cu", ["--fmad=false"]),
     ("step_f32p.cu", ["--fmad=true", "--use_fast_math"]),
+    ("step_unsplit_f64.cu", ["--fmad=false"]),
+    ("step_unsplit_f32p.cu", ["--fmad=true", "--use_fast_math"]),
     ("amr_kernels.cu", ["--fmad=false"]),
     ("tsu_api.cpp", []),
     ("cluster.cpp", []),

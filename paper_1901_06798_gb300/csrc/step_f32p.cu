@@ -15,6 +15,7 @@ int step_strip_width_f32p(int threads) { return threads - 4; }
 int launch_step_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t st)
 {
     if (n_items <= 0) return 0;
+    if (a.transverse) return launch_unsplit_f32p(a, n_items, threads, st);
     switch (threads) {
     case 64: step_kernel_f32<64, 4><<<n_items, 64, 0, st>>>(a); break;
     case 128: step_kernel_f32<128, 4><<<n_items, 128, 0, st>>>(a); break;

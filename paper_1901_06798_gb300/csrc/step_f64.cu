@@ -13,6 +13,7 @@ int step_strip_width_f64(int threads) { return threads - 4; }
 int launch_step_f64(const StepArgs &a, int n_items, int threads, cudaStream_t st)
 {
     if (n_items <= 0) return 0;
+    if (a.transverse) return launch_unsplit_f64(a, n_items, threads, st);
     switch (threads) {
     case 64: step_kernel<double, false, 64, 4><<<n_items, 64, 0, st>>>(a); break;
     case 128: step_kernel<double, false, 128, 4><<<n_items, 128, 0, st>>>(a); break;

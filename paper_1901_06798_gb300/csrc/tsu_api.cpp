@@ -622,6 +622,7 @@ struct tsu_ctx {
             a.descs = L.dP.p; a.items = L.dItems.p; a.arena = arena.base; a.cur = L.cur; a.dt1 = dt1.p;
             a.smax = smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = c.g; a.drytol = c.drytol;
             a.dt1f = dt1f.p;
+            a.transverse = c.transverse;
             set_f32_constants(a);
             int e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
                                     : launch_step_f32p(a, (int)L.items.size(), nt(), st);
@@ -854,7 +855,7 @@ int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out)
     const tsu_config &c = *cfg;
     if (c.precision != TSU_F64 && c.precision != TSU_F32P) return TSU_ERR_ARG;
     if (c.nx < 2 || c.ny < 2 || !(c.dx > 0) || !(c.dy > 0)) return TSU_ERR_ARG;
-    if (c.num_levels < 1 || c.num_levels > TSU_MAX_LEVELS || c.n_scenarios < 1 || c.transverse != 0) return TSU_ERR_ARG;
+    if (c.num_levels < 1 || c.num_levels > TSU_MAX_LEVELS || c.n_scenarios < 1 || (c.transverse != 0 && c.transverse != 1)) return TSU_ERR_ARG;
     for (int l = 0; l + 1 < c.num_levels; l++)
         if (c.ratios[l] < 2) return TSU_ERR_ARG;
     if (c.n_regions < 0 || c.n_regions > TSU_MAX_REGIONS || c.patch_max < 1) return TSU_ERR_ARG;
@@ -1170,6 +1171,7 @@ int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, 
                         sa.descs = L.dP.p; sa.items = L.dItems.p; sa.arena = ctx->arena.base; sa.cur = L.cur;
                         sa.dt1 = ctx->zero_dt.p; sa.dt1f = ctx->zero_dtf.p; sa.smax = ctx->smax.p; sa.R = L.R;
                         sa.dx = L.dx; sa.dy = L.dy; sa.g = ctx->c.g; sa.drytol = ctx->c.drytol;
+                        sa.transverse = ctx->c.transverse;
                         set_f32_constants(sa);
                         int e = ctx->prec == TSU_F64 ? launch_step_f64(sa, (int)L.items.size(), ctx->nt(), ctx->st)
                                                      : launch_step_f32p(sa, (int)L.items.size(), ctx->nt(), ctx->st);
@@ -1290,6 +1292,7 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
             a.descs = L.dP.p; a.items = L.dItems.p; a.arena = ctx->arena.base; a.cur = L.cur; a.dt1 = ctx->dt1.p;
             a.smax = ctx->smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = ctx->c.g; a.drytol = ctx->c.drytol;
             a.dt1f = ctx->dt1f.p;
+            a.transverse = ctx->c.transverse;
             set_f32_constants(a);
             CK(cudaEventRecord(ev[2 * k], ctx->st));
             int e = ctx->prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), ctx->nt(), ctx->st)

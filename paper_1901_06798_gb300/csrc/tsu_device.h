@@ -42,6 +42,7 @@ struct StepArgs {
     const float *dt1f;          // level-1 time step per scenario, FP32
     float rdx, rdy;             // 1 / (R dx), 1 / (R dy)
     float gf, drytolf, sqrtgf;
+    int transverse;             // 1: unsplit update with transverse corrections
 };
 
 // FP32 launch constants of a level
@@ -57,6 +58,8 @@ inline void set_f32_constants(StepArgs &a)
 // Launch helpers implemented in the .cu files.
 int launch_step_f64(const StepArgs &a, int n_items, int threads, cudaStream_t st);
 int launch_step_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t st);
+int launch_unsplit_f64(const StepArgs &a, int n_items, int threads, cudaStream_t st);
+int launch_unsplit_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t st);
 int step_threads_f64();
 int step_threads_f32p();
 // columns one work item of the patch update covers, for a launch of `threads` per CTA

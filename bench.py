@@ -106,10 +106,11 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def load_workload(prec_name, stream):
+def load_workload(prec_name, stream, transverse=0):
     from paper_1901_06798_gb300 import binding
     from paper_1901_06798_gb300 import workloads as W
     w = W.shelf(n=4096, dx=500.0)
+    w = dict(w, cfg=dict(w["cfg"], transverse=transverse))
     prec = binding.TSU_F32P if prec_name == "f32p" else binding.TSU_F64
     ctx = binding.Tsunami(w["cfg"], precision=prec, stream=stream)
     W.load(ctx, w)
@@ -135,10 +136,13 @@ def run_ours(args, rank, world, dist, torch):
 
     results = {}
     clocks.start()
-    for prec in ("f32p", "f64"):
-        ctx, w = load_workload(prec, stream)
+    legs = [("f32p", 0, args.steps), ("f64", 0, max(1, min(args.steps, args.fp64_steps)))]
+    if args.transverse_steps > 0:
+        kt = max(1, min(args.steps, args.transverse_steps))
+        legs += [("f32p", 1, kt), ("f64", 1, max(1, kt // 5))]
+    for prec, tr, K in legs:
+        ctx, w = load_workload(prec, stream, tr)
         cells = w["cfg"]["nx"] * w["cfg"]["ny"]
-        K = args.steps if prec == "f32p" else max(1, min(args.steps, args.fp64_steps))
         if args.shape:                                     # fixed launch shape (profiling runs)
             thr, seg = (int(v) for v in args.shape.split(","))
             ctx.set_tuning(thr, seg)
@@ -155,7 +159,7 @@ def run_ours(args, rank, world, dist, torch):
         launches = ctx.stats()["kernel_launches"] - l0
         elapsed = max_over_ranks(step_ms * K / 1000.0)
         kern = max_over_ranks(kernel_ms)
-        results[prec] = dict(K=K, cells=cells, elapsed=elapsed, kernel_ms=kern, launches=launches,
+        results[prec + ("_unsplit" if tr else "")] = dict(K=K, cells=cells, elapsed=elapsed, kernel_ms=kern, launches=launches,
                              value=world * cells * K / elapsed, tune={"threads": tune[0], "seg_rows": tune[1]})
         ctx.close()
         del ctx
@@ -250,6 +254,8 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--transverse-steps", type=int, default=100,
+                    help="steps of the unsplit (transverse-correction) legs; 0 skips them")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default="", help="threads,seg_rows of the patch update instead of autotuning")
@@ -296,6 +302,12 @@ def main():
                      "kernel_ms": r64["kernel_ms"],
                      "hbm_frac": (b64 / (r64["kernel_ms"] / 1e3) / 1e9) / hbm},
             "fp32p_over_fp64": r["value"] / r64["value"],
+            "unsplit": {k.split("_")[0]: {"value": u["value"], "steps": u["K"],
+                                           "ms_per_step": u["elapsed"] / u["K"] * 1e3, "kernel_ms": u["kernel_ms"],
+                                           "hbm_frac": (BYTES_PER_CELL[k.split("_")[0]] * u["cells"]
+                                                        / (u["kernel_ms"] / 1e3) / 1e9) / hbm,
+                                           "launch_shape": u["tune"]}
+                        for k, u in results.items() if k.endswith("_unsplit")},
             "gpu_launches": results["f32p"]["launches"],
             "clocks": clk,
             "e2e": e2e,

@@ -169,13 +169,17 @@ int tsu_read_gauges(tsu_ctx *ctx, double *t, double *eta, int max_samples, int *
 int tsu_get_stats(tsu_ctx *ctx, int scenario, tsu_stats *out);
 
 /* Launch shape of the patch update (the autotuner's knobs): step_threads
- * threads per CTA (64, 128 or 256; a CTA updates a strip of step_threads - 4
- * columns) and seg_rows rows per CTA (patches taller than that are cut into
- * row segments).  0 restores the defaults.  Results do not depend on either. */
+ * threads per CTA and seg_rows rows per CTA (patches taller than that are cut
+ * into row segments).  step_threads is 64, 128 or 256, or also 32 for the
+ * split FP32 update.  A CTA updates a strip of 2 step_threads - 4 columns in
+ * the split FP32 update (two columns per thread), step_threads - 4 otherwise.
+ * 0 restores the defaults.  Results do not depend on either.  Returns
+ * TSU_ERR_ARG for any other value. */
 int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows);
 
 /* Autotuner: time every launch shape of the patch update (threads per CTA
- * 64/128/256 x rows per work item 32/64/128/256) on the context's current
+ * 64/128/256, and 32 for the split FP32 update, x rows per work item
+ * 32/64/128/256) on the context's current
  * levels with `reps` zero-length steps each -- the kernels do all their work
  * but the state is unchanged -- and keep the fastest.  Outputs (any may be
  * NULL): the chosen shape and its time per step of all levels in ms. */

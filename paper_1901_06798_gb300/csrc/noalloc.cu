@@ -110,7 +110,7 @@ extern "C" int tsu_grid_step_noalloc(int precision, void *block, int nx, int ny,
     const size_t esz = precision == TSU_F64 ? 8 : 4;
     if (((uintptr_t)block) % esz) return TSU_ERR_ARG;
     const int nt = precision == TSU_F64 ? step_threads_f64() : step_threads_f32p();
-    const int W = precision == TSU_F64 ? step_strip_width_f64(nt) : step_strip_width_f32p(nt);
+    const int W = precision == TSU_F64 ? step_strip_width_f64(nt, 0) : step_strip_width_f32p(nt, 0);
     const int nsx = (nx + W - 1) / W, nsy = (ny + kSegRows - 1) / kSegRows;
     if ((long long)nsx * nsy > kMaxItems) return TSU_ERR_ARG;
 

@@ -1,25 +1,26 @@
 // step_f32p.cu -- FP32 surface-perturbation form of the fused patch update
-// (step_f32_lean.cuh): state (eta' = h + B, hu, hv) and B in FP32.  The surface jump that
+// (step_f32x2.cuh): state (eta' = h + B, hu, hv) and B in FP32.  The surface jump that
 // drives the waves is formed from eta' directly, so still water is exactly
 // still and the ocean-depth cancellation of h + B never enters the flux.
-#include "step_f32_lean.cuh"
+#include "step_f32x2.cuh"
 
 namespace tsu {
 
 static constexpr int kThreadsF32 = 128;
 
 int step_threads_f32p() { return kThreadsF32; }
-int step_strip_width_f32p(int threads) { return threads - 4; }
+int step_strip_width_f32p(int threads, int transverse) { return transverse ? threads - 4 : 2 * threads - 4; }
 
-// threads per CTA: 64, 128 or 256 (strip width threads - 4 columns)
+// threads per CTA: 32, 64, 128 or 256 (two columns per thread: strip width 2 threads - 4)
 int launch_step_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t st)
 {
     if (n_items <= 0) return 0;
     if (a.transverse) return launch_unsplit_f32p(a, n_items, threads, st);
     switch (threads) {
-    case 64: step_kernel_f32<64, 4><<<n_items, 64, 0, st>>>(a); break;
-    case 128: step_kernel_f32<128, 4><<<n_items, 128, 0, st>>>(a); break;
-    case 256: step_kernel_f32<256, 4><<<n_items, 256, 0, st>>>(a); break;
+    case 32: step_kernel_f32x2<32, 4><<<n_items, 32, 0, st>>>(a); break;
+    case 64: step_kernel_f32x2<64, 4><<<n_items, 64, 0, st>>>(a); break;
+    case 128: step_kernel_f32x2<128, 4><<<n_items, 128, 0, st>>>(a); break;
+    case 256: step_kernel_f32x2<256, 4><<<n_items, 256, 0, st>>>(a); break;
     default: return (int)cudaErrorInvalidValue;
     }
     return (int)cudaGetLastError();

@@ -7,7 +7,7 @@ namespace tsu {
 static constexpr int kThreadsF64 = 64;
 
 int step_threads_f64() { return kThreadsF64; }
-int step_strip_width_f64(int threads) { return threads - 4; }
+int step_strip_width_f64(int threads, int) { return threads - 4; }
 
 // threads per CTA: 64, 128 or 256 (strip width threads - 4 columns)
 int launch_step_f64(const StepArgs &a, int n_items, int threads, cudaStream_t st)

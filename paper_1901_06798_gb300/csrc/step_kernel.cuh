@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
     __shared__ T red[2][NT / 32];
 
     const StepItem it = a.items[blockIdx.x];
+    if (it.w > NT - 4 || it.w < 1 || it.h < 1) return;   // not a work item of this launch shape
     const PatchDesc P = a.descs[it.patch];
     const int t = threadIdx.x;
     const int cur = a.cur;

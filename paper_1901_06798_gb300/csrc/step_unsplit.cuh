@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
     T *red = sm + S::red;
 
     const StepItem it = a.items[blockIdx.x];
+    if (it.w > NT - 4 || it.w < 1 || it.h < 1) return;   // not a work item of this launch shape
     const PatchDesc P = a.descs[it.patch];
     const int t = threadIdx.x;
     const int cur = a.cur;

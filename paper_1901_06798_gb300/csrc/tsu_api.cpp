@@ -335,7 +335,7 @@ struct tsu_ctx {
         L.bclist.clear();
         L.maxring = 0;
         L.maxcells = 0;
-        const int W = prec == TSU_F64 ? step_strip_width_f64(nt()) : step_strip_width_f32p(nt());
+        const int W = prec == TSU_F64 ? step_strip_width_f64(nt(), c.transverse) : step_strip_width_f32p(nt(), c.transverse);
         for (int k = 0; k < n; k++) {
             const PatchDesc &p = L.P[k];
             for (int x0 = 0; x0 < p.nx; x0 += W)
@@ -1131,8 +1131,11 @@ int tsu_get_stats(tsu_ctx *ctx, int scen, tsu_stats *out)
 int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows)
 {
     return guard(ctx, [&] {
-        if (!(step_threads == 0 || step_threads == 64 || step_threads == 128 || step_threads == 256) || seg_rows < 0)
-            throw Err(TSU_ERR_ARG, "step_threads must be 0, 64, 128 or 256 and seg_rows >= 0");
+        const bool narrow = ctx->prec != TSU_F64 && ctx->c.transverse == 0;   // the paired FP32 kernel has 32
+        if (!(step_threads == 0 || step_threads == 64 || step_threads == 128 || step_threads == 256 ||
+              (narrow && step_threads == 32)) || seg_rows < 0)
+            throw Err(TSU_ERR_ARG, "step_threads must be 0, 64, 128 or 256 (32 for the split FP32 update) and "
+                                   "seg_rows >= 0");
         ctx->step_nt = step_threads;
         ctx->seg_rows = seg_rows;
         for (int l = 0; l < ctx->nlev; l++)
@@ -1151,13 +1154,14 @@ int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, 
         ctx->zero_dtf.ensure(ctx->nscen, ctx->st);
         CK(cudaMemsetAsync(ctx->zero_dt.p, 0, ctx->nscen * sizeof(double), ctx->st));
         CK(cudaMemsetAsync(ctx->zero_dtf.p, 0, ctx->nscen * sizeof(float), ctx->st));
-        const int nts[3] = {64, 128, 256}, segs[4] = {32, 64, 128, 256};
+        const int nts[4] = {64, 128, 256, 32}, segs[4] = {32, 64, 128, 256};
+        const int n_nt = ctx->prec != TSU_F64 && ctx->c.transverse == 0 ? 4 : 3;
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         double best = 1e30;
         int bt = 0, bs = 0;
-        for (int a = 0; a < 3; a++)
+        for (int a = 0; a < n_nt; a++)
             for (int b = 0; b < 4; b++) {
                 ctx->step_nt = nts[a];
                 ctx->seg_rows = segs[b];

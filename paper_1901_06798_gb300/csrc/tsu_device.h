@@ -62,8 +62,9 @@ int launch_unsplit_f64(const StepArgs &a, int n_items, int threads, cudaStream_t
 int launch_unsplit_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t st);
 int step_threads_f64();
 int step_threads_f32p();
-// columns one work item of the patch update covers, for a launch of `threads` per CTA
-int step_strip_width_f64(int threads);
-int step_strip_width_f32p(int threads);
+// columns one work item of the patch update covers, for a launch of `threads`
+// per CTA (the unsplit kernels take one column per thread in both precisions)
+int step_strip_width_f64(int threads, int transverse);
+int step_strip_width_f32p(int threads, int transverse);
 
 }  // namespace tsu

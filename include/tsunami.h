@@ -95,6 +95,9 @@ typedef struct tsu_stats {
     long long cfl_violations;
     int patches[TSU_MAX_LEVELS];
     long long kernel_launches;  /* kernels this context has launched */
+    long long regrids;          /* level rebuilds from flags (all scenarios of one call count once) */
+    double regrid_host_ms;      /* host wall time inside those rebuilds, waits for the device included */
+    double cluster_ms;          /* of which clustering the flag masks */
 } tsu_stats;
 
 /* Create a context.  cfg is copied.  cuda_stream: a cudaStream_t (for example
@@ -138,6 +141,19 @@ int tsu_step(tsu_ctx *ctx, int n_coarse_steps, double *t_out);
 
 /* Regenerate levels level+1 .. num_levels from flags on `level` (Sec. 3.2). */
 int tsu_regrid(tsu_ctx *ctx, int scenario, int level);
+
+/* The host step of a regrid on its own (Sec. 3.2, Berger-Rigoutsos
+ * clustering as read in the library): cluster the 0/1 mask `flags` (ny rows of
+ * nx bytes, row-major, host memory) into rectangles, accepting a tight box
+ * when its flags fill at least `eff` of it and every cell of it is nonzero in
+ * `nestable` (same layout; NULL = everywhere nestable), then split boxes into
+ * near-equal pieces of at most patch_max / ratio cells per side.  Writes
+ * (i0, j0, w, h) per box to `boxes` (4 ints each, caller-owned, room for
+ * max_boxes) and the count to *n_boxes.  Needs no GPU and no context.
+ * Errors: TSU_ERR_ARG (bad sizes, NULL flags or outputs, or more than
+ * max_boxes boxes; *n_boxes then holds the count needed). */
+int tsu_cluster_flags(const unsigned char *flags, const unsigned char *nestable, int nx, int ny, double eff,
+                      int ratio, int patch_max, int *boxes, int max_boxes, int *n_boxes);
 
 /* Number of patches of a level, and their boxes: 4 ints per patch (i0, j0, nx,
  * ny) in global cell indices of that level, in the library's patch order. */

@@ -30,7 +30,7 @@ SYMBOLS = ["tsu_create", "tsu_destroy", "tsu_last_error", "tsu_add_topo", "tsu_s
            "tsu_read_field", "tsu_add_gauges", "tsu_read_gauges", "tsu_get_stats", "tsu_sync",
            "tsu_level1_buffers", "tsu_time_level1_steps", "tsu_set_tuning",
            "tsu_grid_step_noalloc", "tsu_autotune", "tsu_cnn_num_params", "tsu_cnn_forward",
-           "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features"]
+           "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features", "tsu_cluster_flags"]
 
 
 class tsu_config(C.Structure):
@@ -50,7 +50,8 @@ class tsu_config(C.Structure):
 class tsu_stats(C.Structure):
     _fields_ = [("dt", C.c_double), ("t", C.c_double), ("mass", C.c_double), ("cell_updates", C.c_double),
                 ("cfl_violations", C.c_longlong), ("patches", C.c_int * MAX_LEVELS),
-                ("kernel_launches", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("regrids", C.c_longlong), ("regrid_host_ms", C.c_double),
+                ("cluster_ms", C.c_double)]
 
 
 _lib = None
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
         "tsu_set_tuning": ([P, I, I], I),
         "tsu_autotune": ([P, I, ip, ip, dp], I),
         "tsu_cnn_num_params": ([], I),
+        "tsu_cluster_flags": ([P, P, I, I, D, I, I, ip, I, ip], I),
         "tsu_cnn_forward": ([fp, fp, I, I, I, I, fp], I),
         "tsu_cnn_loss_grad": ([fp, fp, fp, fp, I, I, I, dp, fp], I),
         "tsu_cnn_train": ([fp, fp, fp, fp, I, I, I, I, I, C.c_float, C.c_uint, dp, dp], I),
@@ -271,7 +273,8 @@ class Tsunami:
         self._check(self._L.tsu_get_stats(self._h, scen, C.byref(s)), "tsu_get_stats")
         return {"dt": s.dt, "t": s.t, "mass": s.mass, "cell_updates": s.cell_updates,
                 "cfl_violations": s.cfl_violations, "patches": list(s.patches)[: self.num_levels],
-                "kernel_launches": s.kernel_launches}
+                "kernel_launches": s.kernel_launches, "regrids": s.regrids, "regrid_host_ms": s.regrid_host_ms,
+                "cluster_ms": s.cluster_ms}
 
     def set_tuning(self, step_threads: int = 0, seg_rows: int = 0):
         self._check(self._L.tsu_set_tuning(self._h, step_threads, seg_rows), "tsu_set_tuning")
@@ -323,6 +326,26 @@ def _f32(a):
 
 def _fptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def cluster_flags(flags, nestable=None, eff: float = 0.7, ratio: int = 1, patch_max: int = 1 << 30):
+    """The library's clustering of a (ny, nx) 0/1 mask (host code, no GPU):
+    boxes (i0, j0, w, h) as an (n, 4) int array."""
+    L = load()
+    f = np.ascontiguousarray(flags, dtype=np.uint8)
+    nst = None if nestable is None else np.ascontiguousarray(nestable, dtype=np.uint8)
+    ny, nx = f.shape
+    cap = 1024
+    while True:
+        out = np.zeros(4 * cap, dtype=np.int32)
+        n = C.c_int()
+        rc = L.tsu_cluster_flags(f.ctypes.data, None if nst is None else nst.ctypes.data, nx, ny, eff, ratio,
+                                 patch_max, out.ctypes.data_as(C.POINTER(C.c_int)), cap, C.byref(n))
+        if rc == 0:
+            return out[: 4 * n.value].reshape(n.value, 4).copy()
+        if n.value <= cap:
+            raise TsuError(rc, "tsu_cluster_flags: bad arguments")
+        cap = n.value
 
 
 def cnn_num_params() -> int:

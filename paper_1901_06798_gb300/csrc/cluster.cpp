@@ -12,11 +12,17 @@
 //   and recurse, lower/left part first.  Boxes are finally split into
 //   near-equal pieces whose fine size is at most patch_max.
 //
-// Column/row prefix sums make every count and signature O(w + h) per box, so
-// the cost is dominated by one pass over the mask.
+// 2D prefix sums of the flags and of the nestable mask make every count and
+// signature O(w + h) per box, so the cost is dominated by one pass over the
+// mask.  They are built only over the flags' bounding box (the recursion's
+// first step takes that box anyway), as 32-bit counts, with rows and column
+// blocks split across host threads.
+#include <algorithm>
 #include <array>
 #include <cstdint>
 #include <cstdlib>
+#include <memory>
+#include <thread>
 #include <vector>
 
 namespace tsu {
@@ -25,20 +31,25 @@ namespace {
 
 struct Sums {
     int nx, ny;
-    std::vector<int32_t> col;   // col[j * nx + i]: flags in column i, rows < j   ((ny+1) x nx)
-    std::vector<int32_t> row;   // row[j * (nx+1) + i]: flags in row j, columns < i (ny x (nx+1))
-    std::vector<int64_t> nest;  // 2D prefix of the nestable mask ((ny+1) x (nx+1))
+    // 2D prefix sums ((ny+1) x (nx+1)) of the flags (.f) and of the nestable
+    // mask (.n), interleaved: P[j][i] counts cells in rows < j, columns < i
+    struct Pair {
+        int32_t f, n;
+    };
+    Pair *P;
 
-    int colsum(int i, int ja, int jb) const { return col[(size_t)(jb + 1) * nx + i] - col[(size_t)ja * nx + i]; }
+    const Pair &at(int j, int i) const { return P[(size_t)j * (nx + 1) + i]; }
+    int colsum(int i, int ja, int jb) const
+    {
+        return at(jb + 1, i + 1).f - at(jb + 1, i).f - at(ja, i + 1).f + at(ja, i).f;
+    }
     int rowsum(int j, int ia, int ib) const
     {
-        return row[(size_t)j * (nx + 1) + ib + 1] - row[(size_t)j * (nx + 1) + ia];
+        return at(j + 1, ib + 1).f - at(j + 1, ia).f - at(j, ib + 1).f + at(j, ia).f;
     }
     int64_t nestsum(int ia, int ja, int ib, int jb) const
     {
-        size_t W = (size_t)nx + 1;
-        return nest[(size_t)(jb + 1) * W + ib + 1] - nest[(size_t)ja * W + ib + 1] - nest[(size_t)(jb + 1) * W + ia] +
-               nest[(size_t)ja * W + ia];
+        return (int64_t)at(jb + 1, ib + 1).n - at(ja, ib + 1).n - at(jb + 1, ia).n + at(ja, ia).n;
     }
 };
 
@@ -46,29 +57,86 @@ struct Region {
     int i0, j0, i1, j1;   // inclusive
 };
 
+// run f(lo, hi) over [0, n) split into contiguous parts on up to `threads` threads
+template <typename Fn> void parallel_for(int n, int threads, Fn f)
+{
+    if (threads <= 1 || n < 2 * threads) { f(0, n); return; }
+    std::vector<std::thread> pool;
+    for (int k = 1; k < threads; k++)
+        pool.emplace_back([=] { f((int)((long long)n * k / threads), (int)((long long)n * (k + 1) / threads)); });
+    f(0, (int)((long long)n / threads));
+    for (auto &t : pool) t.join();
+}
+
 }  // namespace
 
-void cluster_boxes(const uint8_t *F, const uint8_t *N, int nx, int ny, double eff, int ratio, int patch_max,
+void cluster_boxes(const uint8_t *Fg, const uint8_t *Ng, int nxg, int nyg, double eff, int ratio, int patch_max,
                    std::vector<std::array<int, 4>> &out)
 {
+    out.clear();
+    const int threads = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    // bounding box of the flags: the recursion's first step takes the tight box
+    // of the whole mask, so the prefix sums are only needed inside it
+    std::vector<int> rmin(nyg, nxg), rmax(nyg, -1);
+    parallel_for(nyg, threads, [&](int ja, int jb) {
+        for (int j = ja; j < jb; j++) {
+            const uint8_t *r = Fg + (size_t)j * nxg;
+            int lo = -1, hi = -1;
+            for (int i = 0; i < nxg; i++)
+                if (r[i]) { lo = i; break; }
+            if (lo < 0) continue;
+            for (int i = nxg - 1; i >= lo; i--)
+                if (r[i]) { hi = i; break; }
+            rmin[j] = lo;
+            rmax[j] = hi;
+        }
+    });
+    int bi0 = nxg, bi1 = -1, bj0 = -1, bj1 = -1;
+    for (int j = 0; j < nyg; j++)
+        if (rmax[j] >= 0) {
+            if (bj0 < 0) bj0 = j;
+            bj1 = j;
+            bi0 = std::min(bi0, rmin[j]);
+            bi1 = std::max(bi1, rmax[j]);
+        }
+    if (bj0 < 0) return;
+    const int nx = bi1 - bi0 + 1, ny = bj1 - bj0 + 1;
+
+    // workspace kept between calls (regrids repeat with similar sizes): no
+    // zero fill and no fresh pages; every entry is written below
+    static thread_local std::unique_ptr<Sums::Pair[]> work;
+    static thread_local size_t work_cap = 0;
+    const size_t W = (size_t)nx + 1, npair = (size_t)(ny + 1) * W;
+    if (npair > work_cap) {
+        work.reset(new Sums::Pair[npair]);
+        work_cap = npair;
+    }
     Sums S;
     S.nx = nx;
     S.ny = ny;
-    S.col.assign((size_t)(ny + 1) * nx, 0);
-    S.row.assign((size_t)ny * (nx + 1), 0);
-    S.nest.assign((size_t)(ny + 1) * (nx + 1), 0);
-    for (int j = 0; j < ny; j++) {
-        int32_t acc = 0;
-        int64_t nacc = 0;
-        for (int i = 0; i < nx; i++) {
-            uint8_t f = F[(size_t)j * nx + i] ? 1 : 0;
-            S.col[(size_t)(j + 1) * nx + i] = S.col[(size_t)j * nx + i] + f;
-            acc += f;
-            S.row[(size_t)j * (nx + 1) + i + 1] = acc;
-            nacc += N[(size_t)j * nx + i] ? 1 : 0;
-            S.nest[(size_t)(j + 1) * (nx + 1) + i + 1] = S.nest[(size_t)j * (nx + 1) + i + 1] + nacc;
+    S.P = work.get();
+    // row prefixes into rows 1..ny, then accumulated down the columns
+    parallel_for(ny, threads, [&](int ja, int jb) {
+        for (int j = ja; j < jb; j++) {
+            Sums::Pair *r = S.P + (size_t)(j + 1) * W;
+            const uint8_t *fr = Fg + (size_t)(j + bj0) * nxg + bi0, *nr = Ng + (size_t)(j + bj0) * nxg + bi0;
+            int32_t fa = 0, na = 0;
+            r[0] = {0, 0};
+            for (int i = 0; i < nx; i++) {
+                fa += fr[i] ? 1 : 0;
+                na += nr[i] ? 1 : 0;
+                r[i + 1] = {fa, na};
+            }
         }
-    }
+    });
+    parallel_for((int)W, threads, [&](int ia, int ib) {
+        for (int i = ia; i < ib; i++) S.P[i] = {0, 0};
+        for (int j = 1; j <= ny; j++) {
+            Sums::Pair *r = S.P + (size_t)j * W;
+            const Sums::Pair *u = r - W;
+            for (int i = ia; i < ib; i++) { r[i].f += u[i].f; r[i].n += u[i].n; }
+        }
+    });
 
     std::vector<std::array<int, 4>> raw;
     std::vector<Region> stack;
@@ -150,9 +218,8 @@ void cluster_boxes(const uint8_t *F, const uint8_t *N, int nx, int ny, double ef
     }
 
     const int pm = patch_max / ratio > 0 ? patch_max / ratio : 1;
-    out.clear();
     for (const auto &b : raw) {
-        const int i0 = b[0], j0 = b[1], w = b[2], h = b[3];
+        const int i0 = b[0] + bi0, j0 = b[1] + bj0, w = b[2], h = b[3];   // back to level indices
         const int npx = (w + pm - 1) / pm, npy = (h + pm - 1) / pm;
         for (int q = 0; q < npy; q++)
             for (int p = 0; p < npx; p++) {

@@ -16,6 +16,7 @@
 #include <stdexcept>
 #include <string>
 #include <vector>
+#include <chrono>
 
 #include <cuda_runtime.h>
 
@@ -141,6 +142,25 @@ struct Grid {
     double *dev = nullptr;
 };
 
+// page-locked host buffer, grown on demand (device-to-host copies at full link speed)
+struct PinnedHost {
+    uint8_t *p = nullptr;
+    size_t cap = 0;
+    void ensure(size_t n)
+    {
+        if (n <= cap) return;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        CK(cudaMallocHost((void **)&p, n));
+        cap = n;
+    }
+    ~PinnedHost()
+    {
+        if (p) cudaFreeHost(p);
+    }
+};
+
 struct Lvl {
     std::vector<PatchDesc> P;
     std::vector<size_t> blk, blkbytes;
@@ -157,41 +177,54 @@ struct Lvl {
 // Spatial buckets of one scenario's patches on one level, for neighbour and
 // covering-patch lookups while tables are rebuilt.
 struct BoxIndex {
+    // patches bucketed by 64 x 64 cell tiles, in compressed rows: bucket k
+    // holds ids[start[k] .. start[k+1])
     int bs = 64, nbx = 0, nby = 0;
-    std::vector<std::vector<int>> b;
+    std::vector<int> start, ids;
     const std::vector<PatchDesc> *P = nullptr;
-    void build(const std::vector<PatchDesc> &Pv, const std::vector<int> &ids, int nxl, int nyl)
+    void build(const std::vector<PatchDesc> &Pv, const std::vector<int> &which, int nxl, int nyl)
     {
         P = &Pv;
         nbx = (nxl + bs - 1) / bs;
         nby = (nyl + bs - 1) / bs;
-        b.assign((size_t)nbx * nby, {});
-        for (int id : ids) {
-            const PatchDesc &q = Pv[id];
-            for (int by = q.j0 / bs; by <= (q.j0 + q.ny - 1) / bs; by++)
-                for (int bx = q.i0 / bs; bx <= (q.i0 + q.nx - 1) / bs; bx++) b[(size_t)by * nbx + bx].push_back(id);
-        }
+        start.assign((size_t)nbx * nby + 1, 0);
+        auto each = [&](auto f) {
+            for (int id : which) {
+                const PatchDesc &q = Pv[id];
+                for (int by = q.j0 / bs; by <= (q.j0 + q.ny - 1) / bs; by++)
+                    for (int bx = q.i0 / bs; bx <= (q.i0 + q.nx - 1) / bs; bx++) f((size_t)by * nbx + bx, id);
+            }
+        };
+        each([&](size_t k, int) { start[k + 1]++; });
+        for (size_t k = 0; k + 1 < start.size(); k++) start[k + 1] += start[k];
+        ids.resize(start.back());
+        std::vector<int> fill(start.begin(), start.end() - 1);
+        each([&](size_t k, int id) { ids[fill[k]++] = id; });
     }
     int find(int I, int J) const
     {
         if (I < 0 || J < 0 || I >= nbx * bs || J >= nby * bs) return -1;
-        for (int id : b[(size_t)(J / bs) * nbx + I / bs]) {
-            const PatchDesc &q = (*P)[id];
-            if (I >= q.i0 && I < q.i0 + q.nx && J >= q.j0 && J < q.j0 + q.ny) return id;
+        const size_t k = (size_t)(J / bs) * nbx + I / bs;
+        for (int e = start[k]; e < start[k + 1]; e++) {
+            const PatchDesc &q = (*P)[ids[e]];
+            if (I >= q.i0 && I < q.i0 + q.nx && J >= q.j0 && J < q.j0 + q.ny) return ids[e];
         }
         return -1;
     }
     void overlapping(int ia, int ja, int ib, int jb, std::vector<int> &out) const   // half-open box
     {
         out.clear();
+        if (nbx == 0 || nby == 0) return;
         int bxa = std::max(0, floordiv(ia, bs)), bxb = std::min(nbx - 1, floordiv(ib - 1, bs));
         int bya = std::max(0, floordiv(ja, bs)), byb = std::min(nby - 1, floordiv(jb - 1, bs));
         for (int by = bya; by <= byb; by++)
-            for (int bx = bxa; bx <= bxb; bx++)
-                for (int id : b[(size_t)by * nbx + bx]) {
-                    const PatchDesc &q = (*P)[id];
-                    if (q.i0 < ib && q.i0 + q.nx > ia && q.j0 < jb && q.j0 + q.ny > ja) out.push_back(id);
+            for (int bx = bxa; bx <= bxb; bx++) {
+                const size_t k = (size_t)by * nbx + bx;
+                for (int e = start[k]; e < start[k + 1]; e++) {
+                    const PatchDesc &q = (*P)[ids[e]];
+                    if (q.i0 < ib && q.i0 + q.nx > ia && q.j0 < jb && q.j0 + q.ny > ja) out.push_back(ids[e]);
                 }
+            }
         std::sort(out.begin(), out.end());
         out.erase(std::unique(out.begin(), out.end()), out.end());
     }
@@ -237,6 +270,9 @@ struct tsu_ctx {
     // statistics and graphs
     long long launches = 0;
     long long viol_seen = 0;
+    PinnedHost hflags;           // page-locked staging of the flag masks for clustering
+    long long n_regrids = 0;     // host-side regrid accounting (tsu_stats)
+    double regrid_ms = 0.0, cluster_ms = 0.0;
     int seg_rows = 0;  // rows per work item of the patch update (0: library default)
     int step_nt = 0;   // threads per CTA of the patch update (0: library default)
     DevBuf<double> zero_dt;
@@ -350,7 +386,7 @@ struct tsu_ctx {
         for (int k = 0; k < n; k++) ids[L.P[k].scen].push_back(k);
         if (l > 0)
             for (int k = 0; k < (int)lv[l - 1].P.size(); k++) cids[lv[l - 1].P[k].scen].push_back(k);
-        std::vector<int> tmp;
+        std::vector<int> tmp, ctmp;
         for (int s = 0; s < nscen; s++) {
             if (ids[s].empty()) continue;
             BoxIndex bi;
@@ -370,12 +406,20 @@ struct tsu_ctx {
                     int ci1 = floordiv(p.i0 + p.nx + 1, r) + 1, cj1 = floordiv(p.j0 + p.ny + 1, r) + 1;
                     p.cmap_i0 = ci0; p.cmap_j0 = cj0; p.cmap_w = ci1 - ci0 + 1; p.cmap_h = cj1 - cj0 + 1;
                     p.cmap_off = (int)L.cmap.size();
-                    for (int J = cj0; J <= cj1; J++)
-                        for (int I = ci0; I <= ci1; I++) {
-                            int id = -1;
-                            if (I >= 0 && J >= 0 && I < lv[l - 1].nxl && J < lv[l - 1].nyl) id = ci.find(I, J);
-                            L.cmap.push_back(id);
-                        }
+                    // coarse patch of every coarse cell of the footprint (-1: none):
+                    // patches of one level and scenario do not overlap, so painting
+                    // the few overlapping ones gives each cell its unique patch
+                    const int cw = p.cmap_w;
+                    const size_t base = L.cmap.size();
+                    L.cmap.resize(base + (size_t)cw * p.cmap_h, -1);
+                    ci.overlapping(ci0, cj0, ci1 + 1, cj1 + 1, ctmp);
+                    for (int q : ctmp) {
+                        const PatchDesc &c2 = lv[l - 1].P[q];
+                        const int ia = std::max(ci0, c2.i0), ib = std::min(ci1 + 1, c2.i0 + c2.nx);
+                        const int ja = std::max(cj0, c2.j0), jb = std::min(cj1 + 1, c2.j0 + c2.ny);
+                        for (int J = ja; J < jb; J++)
+                            for (int I = ia; I < ib; I++) L.cmap[base + (size_t)(J - cj0) * cw + (I - ci0)] = q;
+                    }
                 }
             }
         }
@@ -473,6 +517,7 @@ struct tsu_ctx {
     // Build level l+1 of the scenarios in `which` from flags on level l.
     void regrid_one(int l, const std::vector<int> &which)
     {
+        const auto t_begin = std::chrono::steady_clock::now();
         const int lf = l + 1, r = ratio[l];
         Lvl &C = lv[l];
         const int nx = C.nxl, ny = C.nyl;
@@ -505,15 +550,20 @@ struct tsu_ctx {
             kl(k_dilate(fraw.p, ftmp.p, nx, ny, np, b, 0, st), "dilate x");
             kl(k_dilate(ftmp.p, fF.p, nx, ny, np, b, 1, st), "dilate y");
             kl(k_nest(fF.p, fN.p, fcov.p, nx, ny, np, fa, st), "nest");
-            std::vector<uint8_t> hF(plane * np), hN(plane * np);
-            CK(cudaMemcpyAsync(hF.data(), fF.p, plane * np, cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(hN.data(), fN.p, plane * np, cudaMemcpyDeviceToHost, st));
+            hflags.ensure(2 * plane * np);
+            uint8_t *hF = hflags.p, *hN = hflags.p + plane * np;
+            CK(cudaMemcpyAsync(hF, fF.p, plane * np, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hN, fN.p, plane * np, cudaMemcpyDeviceToHost, st));
             sync();
+            const auto t_c0 = std::chrono::steady_clock::now();
             for (int s : which)
-                cluster_boxes(hF.data() + plane * slot[s], hN.data() + plane * slot[s], nx, ny, c.cluster_eff, r,
-                              c.patch_max, boxes[s]);
+                cluster_boxes(hF + plane * slot[s], hN + plane * slot[s], nx, ny, c.cluster_eff, r, c.patch_max,
+                              boxes[s]);
+            cluster_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_c0).count();
         }
         rebuild_level(lf, slot, boxes);
+        n_regrids++;
+        regrid_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
     }
 
     void rebuild_level(int lf, const std::vector<int> &slot, std::vector<std::vector<std::array<int, 4>>> &boxes)
@@ -1125,6 +1175,9 @@ int tsu_get_stats(tsu_ctx *ctx, int scen, tsu_stats *out)
         for (int l = 0; l < ctx->nlev; l++)
             for (const auto &p : ctx->lv[l].P) out->patches[l] += p.scen == scen;
         out->kernel_launches = ctx->launches;
+        out->regrids = ctx->n_regrids;
+        out->regrid_host_ms = ctx->regrid_ms;
+        out->cluster_ms = ctx->cluster_ms;
     });
 }
 
@@ -1326,3 +1379,26 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
 }
 
 }  // extern "C"
+
+int tsu_cluster_flags(const unsigned char *flags, const unsigned char *nestable, int nx, int ny, double eff,
+                      int ratio, int patch_max, int *boxes, int max_boxes, int *n_boxes)
+{
+    try {
+        if (!flags || !boxes || !n_boxes || nx < 1 || ny < 1 || ratio < 1 || patch_max < 1 || max_boxes < 0)
+            return TSU_ERR_ARG;
+        std::vector<uint8_t> ones;
+        if (!nestable) {
+            ones.assign((size_t)nx * ny, 1);
+            nestable = ones.data();
+        }
+        std::vector<std::array<int, 4>> out;
+        tsu::cluster_boxes(flags, nestable, nx, ny, eff, ratio, patch_max, out);
+        *n_boxes = (int)out.size();
+        if ((int)out.size() > max_boxes) return TSU_ERR_ARG;
+        for (size_t k = 0; k < out.size(); k++)
+            for (int m = 0; m < 4; m++) boxes[4 * k + m] = out[k][m];
+        return TSU_OK;
+    } catch (...) {
+        return TSU_ERR_ARG;
+    }
+}

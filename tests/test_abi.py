@@ -32,3 +32,12 @@ def test_config_struct_matches_header_field_order():
     names = re.findall(r"\b([a-z_0-9]+)(?:\[[A-Z_0-9]+\])*(?:\[\d+\])?\s*[;,]", body)
     fields = [f[0] for f in binding.tsu_config._fields_]
     assert names == fields
+
+
+def test_stats_struct_matches_header_field_order():
+    txt = open(os.path.join(ROOT, "include", "tsunami.h")).read()
+    body = txt[txt.index("typedef struct tsu_stats {"):txt.index("} tsu_stats;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b([a-z_0-9]+)(?:\[[A-Z_0-9]+\])*(?:\[\d+\])?\s*[;,]", body)
+    fields = [f[0] for f in binding.tsu_stats._fields_]
+    assert names == fields

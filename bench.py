@@ -168,6 +168,46 @@ def run_ours(args, rank, world, dist, torch):
         torch.cuda.synchronize()
     clk = clocks.stop()
 
+    # the 3-level AMR workload and the 64-scenario ensemble: cell updates of all
+    # levels (and scenarios) over wall time, regrids (host clustering) included
+    extra = {}
+    if args.amr_steps > 0:
+        from paper_1901_06798_gb300 import binding as B
+        from paper_1901_06798_gb300 import workloads as W2
+        for name, w in (("amr3", W2.amr3()), ("ensemble64", W2.ensemble(n_scen=64, n=1024, dx=2000.0, ratio=4))):
+            w = dict(w, gauges=w["gauges"])
+            legs_x = {}
+            gauges = {}
+            for prec in ("f32p", "f64"):
+                K = args.amr_steps if prec == "f32p" else max(1, args.amr_steps // 4)
+                ctx = B.Tsunami(w["cfg"], precision=B.TSU_F32P if prec == "f32p" else B.TSU_F64, stream=stream)
+                W2.load(ctx, w)
+                ctx.step(args.warmup)
+                tune = ctx.autotune(2)
+                nscen = w["cfg"]["n_scenarios"]
+                s0 = [ctx.stats(s) for s in range(nscen)]
+                barrier()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ctx.step(K)
+                torch.cuda.synchronize()
+                el = max_over_ranks(time.perf_counter() - t0)
+                s1 = [ctx.stats(s) for s in range(nscen)]
+                cu = sum(b["cell_updates"] - a["cell_updates"] for a, b in zip(s0, s1))
+                legs_x[prec] = {"value": world * cu / el, "steps": K, "ms_per_step": el / K * 1e3,
+                                "cell_updates_per_step": cu / K, "patches_per_level": s1[0]["patches"],
+                                "regrid_host_ms_per_step": (s1[0]["regrid_host_ms"] - s0[0]["regrid_host_ms"]) / K,
+                                "cluster_ms_per_step": (s1[0]["cluster_ms"] - s0[0]["cluster_ms"]) / K,
+                                "launch_shape": {"threads": tune[0], "seg_rows": tune[1]}}
+                gauges[prec] = ctx.read_gauges()
+                ctx.close()
+                torch.cuda.synchronize()
+            n = min(len(gauges["f32p"][0]), len(gauges["f64"][0]))
+            ea, eb = gauges["f32p"][1][:n], gauges["f64"][1][:n]
+            legs_x["gauge_max_abs_f32p_vs_f64_m"] = float(np.abs(ea - eb).max()) if n else None
+            legs_x["f32p_over_f64"] = legs_x["f32p"]["value"] / legs_x["f64"]["value"]
+            extra[name] = legs_x
+
     # end to end through the C ABI with host buffers: inputs uploaded from host
     # arrays, every step returns the simulated time to the host, and the final
     # surface field comes back to the host.
@@ -192,7 +232,7 @@ def run_ours(args, rank, world, dist, torch):
     e2e = {"value": world * n * n * Ke / e2e_elapsed, "unit": UNIT, "h2d_bytes_per_step": h2d / Ke,
            "d2h_bytes_per_step": 8 + eta.nbytes / Ke, "steps": Ke,
            "note": "create + upload inputs + init + K tsu_step calls each returning t + final eta read"}
-    return results, clk, e2e
+    return results, clk, e2e, extra
 
 
 def cpu_baseline():
@@ -256,6 +296,8 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--amr-steps", type=int, default=16,
+                    help="coarse steps of the 3-level AMR and 64-scenario ensemble legs (FP64: a quarter); 0 skips")
     ap.add_argument("--transverse-steps", type=int, default=100,
                     help="steps of the unsplit (transverse-correction) legs; 0 skips them")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -277,7 +319,7 @@ def main():
         import torch.distributed as dist_mod
         dist_mod.init_process_group("nccl")
         dist = dist_mod
-    results, clk, e2e = run_ours(args, rank, world, dist, torch)
+    results, clk, e2e, extra = run_ours(args, rank, world, dist, torch)
     if rank == 0:
         hbm, src = peaks()
         r = results["f32p"]
@@ -310,6 +352,7 @@ def main():
                                                         / (u["kernel_ms"] / 1e3) / 1e9) / hbm,
                                            "launch_shape": u["tune"]}
                         for k, u in results.items() if k.endswith("_unsplit")},
+            "amr": extra,
             "gpu_launches": results["f32p"]["launches"],
             "clocks": clk,
             "e2e": e2e,

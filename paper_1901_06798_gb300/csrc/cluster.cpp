@@ -21,7 +21,6 @@
 #include <array>
 #include <cstdint>
 #include <cstdlib>
-#include <memory>
 #include <thread>
 #include <vector>
 
@@ -71,10 +70,13 @@ template <typename Fn> void parallel_for(int n, int threads, Fn f)
 }  // namespace
 
 void cluster_boxes(const uint8_t *Fg, const uint8_t *Ng, int nxg, int nyg, double eff, int ratio, int patch_max,
-                   std::vector<std::array<int, 4>> &out)
+                   std::vector<std::array<int, 4>> &out, int max_threads, std::vector<int32_t> *workspace)
 {
     out.clear();
-    const int threads = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    // threads only pay off on large masks (one spawn costs about as much as
+    // scanning a few hundred thousand cells)
+    const int hw = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    const int threads = std::max(1, std::min({max_threads, hw, (int)((size_t)nxg * nyg / (1u << 18)) + 1}));
     // bounding box of the flags: the recursion's first step takes the tight box
     // of the whole mask, so the prefix sums are only needed inside it
     std::vector<int> rmin(nyg, nxg), rmax(nyg, -1);
@@ -102,19 +104,17 @@ void cluster_boxes(const uint8_t *Fg, const uint8_t *Ng, int nxg, int nyg, doubl
     if (bj0 < 0) return;
     const int nx = bi1 - bi0 + 1, ny = bj1 - bj0 + 1;
 
-    // workspace kept between calls (regrids repeat with similar sizes): no
-    // zero fill and no fresh pages; every entry is written below
-    static thread_local std::unique_ptr<Sums::Pair[]> work;
-    static thread_local size_t work_cap = 0;
+    // workspace kept between calls by the caller, or per thread (regrids
+    // repeat with similar sizes): no fresh pages once grown; every entry is
+    // written below
+    static thread_local std::vector<int32_t> own;
+    std::vector<int32_t> &work = workspace ? *workspace : own;
     const size_t W = (size_t)nx + 1, npair = (size_t)(ny + 1) * W;
-    if (npair > work_cap) {
-        work.reset(new Sums::Pair[npair]);
-        work_cap = npair;
-    }
+    if (work.size() < 2 * npair) work.resize(2 * npair);
     Sums S;
     S.nx = nx;
     S.ny = ny;
-    S.P = work.get();
+    S.P = reinterpret_cast<Sums::Pair *>(work.data());
     // row prefixes into rows 1..ny, then accumulated down the columns
     parallel_for(ny, threads, [&](int ja, int jb) {
         for (int j = ja; j < jb; j++) {

@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 #include <chrono>
+#include <thread>
 
 #include <cuda_runtime.h>
 
@@ -27,7 +28,7 @@
 
 namespace tsu {
 void cluster_boxes(const uint8_t *F, const uint8_t *N, int nx, int ny, double eff, int ratio, int patch_max,
-                   std::vector<std::array<int, 4>> &out);
+                   std::vector<std::array<int, 4>> &out, int max_threads, std::vector<int32_t> *workspace);
 }
 
 using namespace tsu;
@@ -271,6 +272,7 @@ struct tsu_ctx {
     long long launches = 0;
     long long viol_seen = 0;
     PinnedHost hflags;           // page-locked staging of the flag masks for clustering
+    std::vector<std::vector<int32_t>> cws = std::vector<std::vector<int32_t>>(16);   // clustering workspaces
     long long n_regrids = 0;     // host-side regrid accounting (tsu_stats)
     double regrid_ms = 0.0, cluster_ms = 0.0;
     int seg_rows = 0;  // rows per work item of the patch update (0: library default)
@@ -556,9 +558,24 @@ struct tsu_ctx {
             CK(cudaMemcpyAsync(hN, fN.p, plane * np, cudaMemcpyDeviceToHost, st));
             sync();
             const auto t_c0 = std::chrono::steady_clock::now();
-            for (int s : which)
+            if (which.size() == 1) {
+                const int s = which[0];
                 cluster_boxes(hF + plane * slot[s], hN + plane * slot[s], nx, ny, c.cluster_eff, r, c.patch_max,
-                              boxes[s]);
+                              boxes[s], 16, &cws[0]);
+            } else {
+                // independent scenarios: one host thread per group of them
+                const int nt = std::max(1, std::min({16, (int)which.size(), (int)std::thread::hardware_concurrency()}));
+                std::vector<std::thread> pool;
+                for (int q = 0; q < nt; q++)
+                    pool.emplace_back([&, q] {
+                        for (size_t k = q; k < which.size(); k += nt) {
+                            const int s = which[k];
+                            cluster_boxes(hF + plane * slot[s], hN + plane * slot[s], nx, ny, c.cluster_eff, r,
+                                          c.patch_max, boxes[s], 1, &cws[q]);
+                        }
+                    });
+                for (auto &th : pool) th.join();
+            }
             cluster_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_c0).count();
         }
         rebuild_level(lf, slot, boxes);
@@ -1392,7 +1409,7 @@ int tsu_cluster_flags(const unsigned char *flags, const unsigned char *nestable,
             nestable = ones.data();
         }
         std::vector<std::array<int, 4>> out;
-        tsu::cluster_boxes(flags, nestable, nx, ny, eff, ratio, patch_max, out);
+        tsu::cluster_boxes(flags, nestable, nx, ny, eff, ratio, patch_max, out, 16, nullptr);
         *n_boxes = (int)out.size();
         if ((int)out.size() > max_boxes) return TSU_ERR_ARG;
         for (size_t k = 0; k < out.size(); k++)

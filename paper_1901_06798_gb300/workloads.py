@@ -19,7 +19,7 @@ Workloads (sizes in cells of level 1):
              600 km offshore, extrapolating boundaries.
   amr3(...)  3-level AMR over the shelf profile, ratios 4 and 4, flags
              |eta| > 0.01 m or depth < 200 m, regrid every 4 steps,
-             patches up to 64 fine cells.
+             patches up to 60 fine cells.
   ensemble   independent scenarios on one bathymetry, uplift centres and
              amplitudes drawn from numpy PCG64 with seed 1901.
 """
@@ -113,12 +113,14 @@ def shelf(n: int = 4096, dx: float = 500.0, steps: int = 500) -> dict:
                 eta=[], uplift=[(0, *up)], steps=steps, gauges=g)
 
 
-def amr3(L: float = 2000e3, dx1: float = 2000.0, ratios=(4, 4), patch_max: int = 64,
+def amr3(L: float = 2000e3, dx1: float = 2000.0, ratios=(4, 4), patch_max: int = 60,
          steps: int = 8, eta_tol: float = 0.01, depth_below: float = 200.0) -> dict:
     """3-level patch AMR over the shelf profile (ratios 4, 4), flags where
-    |eta| > 0.01 m or depth < 200 m, regrid every 4 steps, patches up to 64
-    fine cells.  L = 2000 km, dx1 = 2 km is the full size; smaller L scales
-    the bathymetry and uplift with the domain."""
+    |eta| > 0.01 m or depth < 200 m, regrid every 4 steps, patches up to 60
+    fine cells per side (within the 16-64 range of the configuration; 60 is
+    the column strip one 32-thread CTA of the FP32 update covers, so a patch
+    row is one strip).  L = 2000 km, dx1 = 2 km is the full size; smaller L
+    scales the bathymetry and uplift with the domain."""
     n = int(round(L / dx1))
     scale = L / 2000e3
     cfg = base_config(nx=n, ny=n, dx=dx1, dy=dx1, num_levels=len(ratios) + 1, ratios=list(ratios),
@@ -131,7 +133,7 @@ def amr3(L: float = 2000e3, dx1: float = 2000.0, ratios=(4, 4), patch_max: int =
 
 
 def ensemble(n_scen: int = 64, n: int = 1024, dx: float = 2000.0, ratio: int = 4, steps: int = 8,
-             seed: int = 1901, patch_max: int = 64) -> dict:
+             seed: int = 1901, patch_max: int = 60) -> dict:
     """Independent scenarios on one shelf bathymetry, 2 levels (ratio 4):
     uplift centres uniform over s in [550, 750] km x (mid +- 250 km) and
     amplitudes uniform in [0.5, 5] m, drawn from numpy PCG64(seed)."""

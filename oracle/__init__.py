@@ -63,6 +63,7 @@ class ora_config(C.Structure):
         ("patch_max", C.c_int), ("level1_tile", C.c_int),
         ("n_regions", C.c_int), ("regions", (C.c_double * 6) * MAX_REGIONS),
         ("n_scenarios", C.c_int), ("transverse", C.c_int), ("cluster_eff", C.c_double),
+        ("manning_n", C.c_double),
     ]
 
 
@@ -90,6 +91,8 @@ def lib(variant: str = "parity"):
             for name in ("ora_add_topo",):
                 getattr(L, name).argtypes = [P, dp, I, I, D, D, D, D]
                 getattr(L, name).restype = I
+            L.ora_set_velocity.argtypes = [P, I, dp, dp, I, I, D, D, D, D]
+            L.ora_set_velocity.restype = I
             for name in ("ora_set_eta", "ora_add_uplift"):
                 getattr(L, name).argtypes = [P, I, dp, I, I, D, D, D, D]
                 getattr(L, name).restype = I
@@ -172,6 +175,7 @@ def make_config(cfg: dict) -> ora_config:
     c.n_scenarios = cfg.get("n_scenarios", 1)
     c.transverse = cfg.get("transverse", 0)
     c.cluster_eff = cfg.get("cluster_eff", 0.7)
+    c.manning_n = cfg.get("manning_n", 0.0)
     return c
 
 
@@ -215,6 +219,11 @@ class Oracle:
     def set_eta(self, scen, eta, x0, y0, dx, dy):
         e = self._grid(eta)
         self._check(self._L.ora_set_eta(self._h, scen, _dp(e), e.shape[1], e.shape[0], x0, y0, dx, dy), "set_eta")
+
+    def set_velocity(self, scen, u, v, x0, y0, dx, dy):
+        uu, vv = self._grid(u), self._grid(v)
+        self._check(self._L.ora_set_velocity(self._h, scen, _dp(uu), _dp(vv), uu.shape[1], uu.shape[0], x0, y0, dx,
+                                             dy), "set_velocity")
 
     def add_uplift(self, scen, dB, x0, y0, dx, dy):
         d = self._grid(dB)

@@ -59,6 +59,8 @@ typedef struct Scen {
     int nup;
     TopoGrid eta0;
     int has_eta0;
+    TopoGrid u0, v0;            /* initial velocities (node grids) */
+    int has_uv0;
     double t, dt1;
     double rate[ORA_MAX_LEVELS];
     long nsteps[ORA_MAX_LEVELS];
@@ -728,6 +730,7 @@ static int advance(Ora *o, int s, int l)
             ora_step_patch_unsplit(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
         else
             ora_step_patch(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
+        if (o->c.manning_n > 0.0) ora_friction_patch(p, o->c.g, o->c.drytol, o->c.manning_n, dt);
         sx = fmax(sx, a);
         sy = fmax(sy, b);
         S->cell_updates += (double)p->nx * (double)p->ny;
@@ -814,6 +817,7 @@ void *ora_create(const ora_config *cfg)
     Ora *o = (Ora *)calloc(1, sizeof *o);
     o->c = *cfg;
     if (o->c.cluster_eff <= 0.0) o->c.cluster_eff = 0.7;
+    if (!(o->c.manning_n >= 0.0)) { free(o); return NULL; }
     o->R[0] = 1;
     for (int l = 1; l < cfg->num_levels; l++) o->R[l] = o->R[l - 1] * cfg->ratios[l - 1];
     for (int l = 0; l < cfg->num_levels; l++) {
@@ -841,6 +845,7 @@ void ora_destroy(void *vo)
         for (int k = 0; k < S->nup; k++) grid_free(&S->up[k]);
         free(S->up);
         if (S->has_eta0) grid_free(&S->eta0);
+        if (S->has_uv0) { grid_free(&S->u0); grid_free(&S->v0); }
     }
     for (int k = 0; k < o->ntopo; k++) grid_free(&o->topo[k]);
     free(o->topo);
@@ -877,6 +882,20 @@ int ora_set_eta(void *vo, int s, const double *eta, int nx, int ny, double x0, d
     if (S->has_eta0) grid_free(&S->eta0);
     S->eta0 = grid_copy(eta, nx, ny, x0, y0, dx, dy);
     S->has_eta0 = 1;
+    return 0;
+}
+
+/* initial depth-averaged velocities: hu = h u, hv = h v on wet cells at init */
+int ora_set_velocity(void *vo, int s, const double *u, const double *v, int nx, int ny, double x0, double y0,
+                     double dx, double dy)
+{
+    Ora *o = (Ora *)vo;
+    if (o->initialized || s < 0 || s >= o->c.n_scenarios || nx < 2 || ny < 2) return -1;
+    Scen *S = &o->sc[s];
+    if (S->has_uv0) { grid_free(&S->u0); grid_free(&S->v0); }
+    S->u0 = grid_copy(u, nx, ny, x0, y0, dx, dy);
+    S->v0 = grid_copy(v, nx, ny, x0, y0, dx, dy);
+    S->has_uv0 = 1;
     return 0;
 }
 
@@ -930,6 +949,10 @@ int ora_init(void *vo)
                         double hh = eta - B0;
                         if (hh < 0.0) hh = 0.0;
                         p->h[k] = hh;
+                        if (S->has_uv0 && hh >= o->c.drytol && grid_contains(&S->u0, x, y)) {
+                            p->hu[k] = hh * grid_bilinear(&S->u0, x, y);
+                            p->hv[k] = hh * grid_bilinear(&S->v0, x, y);
+                        }
                         p->B[k] = uplift_sum(S, B0, x, y);
                     }
                 apply_bc_field(o, p, p->B, 0, 0);

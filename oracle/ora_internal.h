@@ -19,6 +19,9 @@ typedef struct OPatch {
 void ora_step_patch(OPatch *p, double g, double drytol, double dt, double dx, double dy,
                     double *sx, double *sy);
 
+/* Manning friction of the interior cells after a step (Sec. 2.1 drag D) */
+void ora_friction_patch(OPatch *p, double g, double drytol, double n, double dt);
+
 /* one unsplit step with transverse corrections (the original GeoClaw scheme) */
 void ora_step_patch_unsplit(OPatch *p, double g, double drytol, double dt, double dx, double dy,
                             double *sx, double *sy);

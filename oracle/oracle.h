@@ -54,6 +54,7 @@ typedef struct ora_config {
     int n_scenarios;
     int transverse;             /* 0: dimensional splitting (the paper's GPU scheme) */
     double cluster_eff;         /* Berger-Rigoutsos acceptance efficiency */
+    double manning_n;           /* Manning coefficient of the drag D (Sec. 2.1); 0: no friction */
 } ora_config;
 
 typedef struct ora_rp {
@@ -75,6 +76,10 @@ void *ora_create(const ora_config *cfg);
 void ora_destroy(void *o);
 int ora_add_topo(void *o, const double *B, int nx, int ny, double x0, double y0, double dx, double dy);
 int ora_set_eta(void *o, int scen, const double *eta, int nx, int ny, double x0, double y0, double dx, double dy);
+/* initial velocities u, v (same node-grid convention as the surface): at
+ * init every wet cell gets hu = h u, hv = h v */
+int ora_set_velocity(void *o, int scen, const double *u, const double *v, int nx, int ny, double x0, double y0,
+                     double dx, double dy);
 int ora_add_uplift(void *o, int scen, const double *dB, int nx, int ny, double x0, double y0, double dx, double dy);
 int ora_init(void *o);
 int ora_step(void *o, int n_coarse, double *t_out);

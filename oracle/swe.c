@@ -12,6 +12,7 @@
  *   Sec. 2.2, Eq. (theta) and the upwind index I   wave limiter ratio
  *   Sec. 2.2, Eqs. (..._x), (..._y)          Godunov dimensional splitting, x then y
  *   Sec. 2.2, CFL condition                  nu = |s dt / dx| <= 1
+ *   Sec. 2.1, drag D (Manning, n)           friction step after each level step
  *
  * Readings of points the paper leaves open (each is listed in the design doc):
  *   - f-wave form: the solver decomposes the flux jump (including the
@@ -510,4 +511,27 @@ void ora_step_patch_unsplit(OPatch *p, double g, double drytol, double dt, doubl
 #undef YSPLIT
     free(qn); free(G); free(Fx); free(X); free(Y); free(tmp); free(a);
     *sx_out = sx; *sy_out = sy;
+}
+
+/* Manning friction (Sec. 2.1: the momentum equations carry -D hu and -D hv).
+ * Reading: the printed D = n^2 g h^(-7/3) sqrt(u^2 + v^2) is not
+ * dimensionally consistent with -D hu; with the momentum magnitude,
+ * D = n^2 g h^(-7/3) sqrt((hu)^2 + (hv)^2) = g n^2 |u| / h^(4/3), it is the
+ * Manning law.  Applied as a pointwise step after each wave-propagation step
+ * of a level, implicit in the momentum with D from the updated state:
+ * hu <- hu / (1 + dt D), hv <- hv / (1 + dt D), on wet interior cells. */
+void ora_friction_patch(OPatch *p, double g, double drytol, double n, double dt)
+{
+    const double coef = (n * n) * g;
+    for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++) {
+            size_t k = OIDX(p, i, j);
+            double h = p->h[k];
+            if (!(h >= drytol)) continue;
+            double hu = p->hu[k], hv = p->hv[k];
+            double D = (coef * pow(h, -7.0 / 3.0)) * sqrt(hu * hu + hv * hv);
+            double f = 1.0 + dt * D;
+            p->hu[k] = hu / f;
+            p->hv[k] = hv / f;
+        }
 }

@@ -34,7 +34,7 @@ def base_config(**kw) -> dict:
     cfg = dict(nx=64, ny=64, x0=0.0, y0=0.0, dx=1.0, dy=1.0, num_levels=1, ratios=[], bc=[BC_WALL] * 4,
                g=9.81, drytol=1e-3, cfl_desired=0.9, cfl_max=1.0, dt_max=1e9, regrid_interval=0,
                flag_eta_tol=0.0, flag_depth_below=0.0, patch_max=64, level1_tile=0, regions=[],
-               n_scenarios=1, transverse=0, cluster_eff=0.7)
+               n_scenarios=1, transverse=0, cluster_eff=0.7, manning_n=0.0)
     cfg.update(kw)
     return cfg
 
@@ -179,11 +179,14 @@ def lake_at_rest_shelf(n: int = 96, dx: float = 2000.0) -> dict:
 
 def load(obj, w: dict):
     """Feed a workload's inputs to a solver object exposing add_topo,
-    set_eta, add_uplift and init (the oracle or the GPU library binding)."""
+    set_eta, set_velocity, add_uplift and init (the oracle or the GPU
+    library binding)."""
     for (B, x0, y0, dx, dy) in w["topo"]:
         obj.add_topo(B, x0, y0, dx, dy)
     for (s, e, x0, y0, dx, dy) in w["eta"]:
         obj.set_eta(s, e, x0, y0, dx, dy)
+    for (s, u, v, x0, y0, dx, dy) in w.get("uv", []):
+        obj.set_velocity(s, u, v, x0, y0, dx, dy)
     for (s, d, x0, y0, dx, dy) in w["uplift"]:
         obj.add_uplift(s, d, x0, y0, dx, dy)
     if len(w.get("gauges", [])):

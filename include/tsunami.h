@@ -85,6 +85,9 @@ typedef struct tsu_config {
     int use_graphs;             /* capture repeated coarse steps as a CUDA graph */
     int use_cnn;                /* add the flag predictor's cells to the flags (tsu_cnn_set_weights) */
     int cnn_buffer;             /* flag buffer width used together with the predictor (instead of b) */
+    double manning_n;           /* Manning coefficient of the drag (Sec. 2.1; the paper's runs use 0.025),
+                                   applied after every level step as hu, hv <- hu, hv / (1 + dt D),
+                                   D = n^2 g sqrt(hu^2 + hv^2) / h^(7/3), on wet cells; 0: none */
 } tsu_config;
 
 typedef struct tsu_stats {
@@ -121,6 +124,12 @@ int tsu_add_topo(tsu_ctx *ctx, const double *B, int nx, int ny, double x0, doubl
  * Before tsu_init only.  eta: nx*ny host doubles, copied. */
 int tsu_set_eta(tsu_ctx *ctx, int scenario, const double *eta, int nx, int ny,
                 double x0, double y0, double dx, double dy);
+
+/* Initial depth-averaged velocities u, v of one scenario (default 0), on one
+ * node grid (both nx*ny host doubles, copied; same convention as tsu_set_eta):
+ * at tsu_init every wet cell gets hu = h u, hv = h v.  Before tsu_init only. */
+int tsu_set_velocity(tsu_ctx *ctx, int scenario, const double *u, const double *v, int nx, int ny,
+                     double x0, double y0, double dx, double dy);
 
 /* Instantaneous seafloor deformation (Sec. 5.1.1 dtopo, applied at once):
  * B += dB on every cell of every level with h unchanged, so the surface rises

@@ -30,7 +30,7 @@ SYMBOLS = ["tsu_create", "tsu_destroy", "tsu_last_error", "tsu_add_topo", "tsu_s
            "tsu_read_field", "tsu_add_gauges", "tsu_read_gauges", "tsu_get_stats", "tsu_sync",
            "tsu_level1_buffers", "tsu_time_level1_steps", "tsu_set_tuning",
            "tsu_grid_step_noalloc", "tsu_autotune", "tsu_cnn_num_params", "tsu_cnn_forward",
-           "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features", "tsu_cluster_flags"]
+           "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features", "tsu_cluster_flags", "tsu_set_velocity"]
 
 
 class tsu_config(C.Structure):
@@ -43,7 +43,7 @@ class tsu_config(C.Structure):
         ("flag_depth_below", C.c_double), ("patch_max", C.c_int), ("level1_tile", C.c_int),
         ("n_regions", C.c_int), ("regions", (C.c_double * 6) * MAX_REGIONS), ("n_scenarios", C.c_int),
         ("transverse", C.c_int), ("cluster_eff", C.c_double), ("use_graphs", C.c_int),
-        ("use_cnn", C.c_int), ("cnn_buffer", C.c_int),
+        ("use_cnn", C.c_int), ("cnn_buffer", C.c_int), ("manning_n", C.c_double),
     ]
 
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "tsu_autotune": ([P, I, ip, ip, dp], I),
         "tsu_cnn_num_params": ([], I),
         "tsu_cluster_flags": ([P, P, I, I, D, I, I, ip, I, ip], I),
+        "tsu_set_velocity": ([P, I, dp, dp, I, I, D, D, D, D], I),
         "tsu_cnn_forward": ([fp, fp, I, I, I, I, fp], I),
         "tsu_cnn_loss_grad": ([fp, fp, fp, fp, I, I, I, dp, fp], I),
         "tsu_cnn_train": ([fp, fp, fp, fp, I, I, I, I, I, C.c_float, C.c_uint, dp, dp], I),
@@ -151,6 +152,7 @@ def make_config(cfg: dict, precision: int = TSU_F64, use_graphs: bool = True) ->
     c.use_graphs = 1 if use_graphs else 0
     c.use_cnn = cfg.get("use_cnn", 0)
     c.cnn_buffer = cfg.get("cnn_buffer", 1)
+    c.manning_n = cfg.get("manning_n", 0.0)
     return c
 
 
@@ -199,6 +201,11 @@ class Tsunami:
     def set_eta(self, scen, eta, x0, y0, dx, dy):
         e = self._grid(eta)
         self._check(self._L.tsu_set_eta(self._h, scen, _dp(e), e.shape[1], e.shape[0], x0, y0, dx, dy), "tsu_set_eta")
+
+    def set_velocity(self, scen, u, v, x0, y0, dx, dy):
+        uu, vv = self._grid(u), self._grid(v)
+        self._check(self._L.tsu_set_velocity(self._h, scen, _dp(uu), _dp(vv), uu.shape[1], uu.shape[0], x0, y0, dx,
+                                             dy), "tsu_set_velocity")
 
     def add_uplift(self, scen, dB, x0, y0, dx, dy):
         d = self._grid(dB)

@@ -334,7 +334,8 @@ __device__ double uplift_sum(const TopoSet &ts, int scen, double B, double x, do
     return B;
 }
 
-// B (and, for level-1 initialisation, the state) of the patches in `list`
+// B (and, for level-1 initialisation, the state: h from the initial surface,
+// hu = h u, hv = h v from the initial velocities on wet cells) of the patches in `list`
 // at every cell inside the domain; cells outside are filled by bc_kernel.
 template <typename T, bool PERT>
 __global__ void init_patch_kernel(LevelView L, const int *list, TopoSet ts, int cur, int set_state, double x0,
@@ -354,13 +355,19 @@ __global__ void init_patch_kernel(LevelView L, const int *list, TopoSet ts, int 
         a.Bp()[k] = (T)B;
         if (set_state) {
             double eta = 0.0;
-            int eg = ts.eta_index[P.scen];
+            int eg = ts.eta_index[3 * P.scen];
             if (eg >= 0 && grid_contains(ts.grids[eg], x, y)) eta = grid_bilinear(ts.grids[eg], x, y);
             double hh = eta - B0;
             if (hh < 0.0) hh = 0.0;
+            double hu = 0.0, hv = 0.0;
+            const int ug = ts.eta_index[3 * P.scen + 1], vg = ts.eta_index[3 * P.scen + 2];
+            if (ug >= 0 && hh >= ts.drytol && grid_contains(ts.grids[ug], x, y)) {
+                hu = hh * grid_bilinear(ts.grids[ug], x, y);
+                hv = hh * grid_bilinear(ts.grids[vg], x, y);
+            }
             a.f(cur, 0)[k] = PERT ? (T)(hh + B) : (T)hh;
-            a.f(cur, 1)[k] = T(0);
-            a.f(cur, 2)[k] = T(0);
+            a.f(cur, 1)[k] = (T)hu;
+            a.f(cur, 2)[k] = (T)hv;
         }
     }
 }

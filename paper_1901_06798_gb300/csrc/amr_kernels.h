@@ -41,8 +41,9 @@ struct TopoDev {
 struct TopoSet {
     const TopoDev *grids;
     const int *scen;
-    const int *eta_index;        // per scenario: grid index of its initial surface or -1
+    const int *eta_index;        // per scenario s: [3s] initial surface, [3s+1] u, [3s+2] v grid index or -1
     int nbase, ngrids;
+    double drytol;               // initial velocities apply to wet cells only
 };
 
 struct FlagArgs {

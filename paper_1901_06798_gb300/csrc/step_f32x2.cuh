@@ -207,6 +207,20 @@ __device__ __forceinline__ void limit2(const W2 &r, const I2 &I, float2 dtdx, fl
     }
 }
 
+// Manning friction of two updated cells (as friction() in step_kernel.cuh)
+__device__ __forceinline__ void friction2(float2 q0, float2 &hu, float2 &hv, float2 B, float drytol, float coef,
+                                          float dt)
+{
+    const float2 h = sub(q0, B);
+    const float2 m2 = fma(hu, hu, mul(hv, hv));
+    float fx = 1.0f, fy = 1.0f;
+    if (h.x >= drytol) fx = fmaf(dt, coef * __powf(h.x, -7.0f / 3.0f) * sqrtf(m2.x), 1.0f);
+    if (h.y >= drytol) fy = fmaf(dt, coef * __powf(h.y, -7.0f / 3.0f) * sqrtf(m2.y), 1.0f);
+    const float2 r = make_float2(__fdividef(1.0f, fx), __fdividef(1.0f, fy));
+    hu = mul(hu, r);
+    hv = mul(hv, r);
+}
+
 // wet/dry post-processing of two updated cells (perturbation form)
 __device__ __forceinline__ void post2(float2 &q0, float2 &qn, float2 &qt, float2 B, float drytol)
 {
@@ -411,6 +425,8 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
                             float2 n1 = fnma(dtdy2, add(add(apo[1], yam[1]), sub(Fm[1], Fo[1])), ycm2.hn);
                             float2 n2 = fnma(dtdy2, add(add(apo[2], yam[2]), sub(Fm[2], Fo[2])), ycm2.ht);
                             post2(n0, n1, n2, ycm2.B, drytol);
+                            if (a.manningf > 0.0f)   // y frame: n2 = hu, n1 = hv
+                                friction2(n0, n2, n1, ycm2.B, drytol, a.manningf, dt1 * a.rR);
                             float *d = dst + (long long)(rc - y0) * pitch;
                             if (w8) {
                                 st2(d + go[0], n0);

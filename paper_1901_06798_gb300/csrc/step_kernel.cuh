@@ -205,6 +205,23 @@ __device__ __forceinline__ void postprocess(T &q0, T &qn, T &qt, T B, T drytol)
     }
 }
 
+// Manning friction of one updated cell (Sec. 2.1 drag, read with the momentum
+// magnitude: D = n^2 g sqrt(hu^2 + hv^2) / h^(7/3)), implicit in the
+// momentum: hu, hv <- hu, hv / (1 + dt D) on a wet cell.  coef = n^2 g.
+template <typename T> __device__ __forceinline__ T dpow(T x, T y);
+template <> __device__ __forceinline__ double dpow<double>(double x, double y) { return pow(x, y); }
+template <> __device__ __forceinline__ float dpow<float>(float x, float y) { return powf(x, y); }
+template <typename T, bool PERT>
+__device__ __forceinline__ void friction(T q0, T &hu, T &hv, T B, T drytol, T coef, T dt)
+{
+    const T h = PERT ? q0 - B : q0;
+    if (!(h >= drytol)) return;
+    const T D = (coef * dpow<T>(h, T(-7.0 / 3.0))) * dsqrt<T>(hu * hu + hv * hv);
+    const T f = T(1) + dt * D;
+    hu = hu / f;
+    hv = hv / f;
+}
+
 __device__ __forceinline__ void cp_async_elem(void *smem, const void *gmem, int bytes)
 {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -372,6 +389,8 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
                                 qn[m] = qn[m] - dtdy * u;
                             }
                             postprocess<T, PERT>(qn[0], qn[1], qn[2], Bm2, drytol);
+                            if (a.manning > 0.0)   // y frame: qn[2] = hu, qn[1] = hv
+                                friction<T, PERT>(qn[0], qn[2], qn[1], Bm2, drytol, (T)a.manning, (T)dt);
                             long long gi = (long long)(rc + 2) * pitch + (x0 + t);
                             qo0[gi] = qn[0];
                             qo2[gi] = qn[1];

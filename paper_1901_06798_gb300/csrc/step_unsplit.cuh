@@ -150,6 +150,10 @@ template <> __device__ __forceinline__ float dt_over<float>(const StepArgs &a, i
     return a.dt1f[scen] * (ydir ? a.rdy : a.rdx);
 }
 
+template <typename T> __device__ __forceinline__ T dt_level(const StepArgs &a, int scen);
+template <> __device__ __forceinline__ double dt_level<double>(const StepArgs &a, int scen) { return a.dt1[scen] / a.R; }
+template <> __device__ __forceinline__ float dt_level<float>(const StepArgs &a, int scen) { return a.dt1f[scen] * a.rR; }
+
 template <typename T, bool PERT, int NT, int RING>
 __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
 {
@@ -379,6 +383,9 @@ __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
                 q[m] = (q[m] - dtdx * ux) - dtdy * uy;
             }
             postprocess<T, PERT>(q[0], q[1], q[2], Bc, drytol);
+            if (a.manning > 0.0)
+                friction<T, PERT>(q[0], q[1], q[2], Bc, drytol, PERT ? (T)a.manningf : (T)a.manning,
+                                  dt_level<T>(a, P.scen));
             if (j >= y0 && j < y0 + h) {
                 const long long gi = (long long)(j + 2) * pitch + (x0 + t);
                 qo0[gi] = q[0];

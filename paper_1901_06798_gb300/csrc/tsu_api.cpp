@@ -246,7 +246,7 @@ struct tsu_ctx {
     Lvl lv[kMaxLevels];
     std::vector<Grid> grids;   // base topography first, then layers and surfaces in call order
     int nbase = 0;
-    std::vector<int> eta_index;
+    std::vector<int> eta_index;   // per scenario: initial surface, u and v grid indices (-1: none)
     DevBuf<TopoDev> dGrids;
     DevBuf<int> dGridScen, dEtaIdx;
     bool topo_dirty = true;
@@ -318,6 +318,7 @@ struct tsu_ctx {
         TopoSet ts;
         ts.grids = dGrids.p; ts.scen = dGridScen.p; ts.eta_index = dEtaIdx.p;
         ts.nbase = nbase; ts.ngrids = (int)grids.size();
+        ts.drytol = c.drytol;
         return ts;
     }
     void sync() { CK(cudaStreamSynchronize(st)); }
@@ -690,6 +691,7 @@ struct tsu_ctx {
             a.smax = smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = c.g; a.drytol = c.drytol;
             a.dt1f = dt1f.p;
             a.transverse = c.transverse;
+            a.manning = (c.manning_n * c.manning_n) * c.g;
             set_f32_constants(a);
             int e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
                                     : launch_step_f32p(a, (int)L.items.size(), nt(), st);
@@ -922,7 +924,8 @@ int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out)
     const tsu_config &c = *cfg;
     if (c.precision != TSU_F64 && c.precision != TSU_F32P) return TSU_ERR_ARG;
     if (c.nx < 2 || c.ny < 2 || !(c.dx > 0) || !(c.dy > 0)) return TSU_ERR_ARG;
-    if (c.num_levels < 1 || c.num_levels > TSU_MAX_LEVELS || c.n_scenarios < 1 || (c.transverse != 0 && c.transverse != 1)) return TSU_ERR_ARG;
+    if (c.num_levels < 1 || c.num_levels > TSU_MAX_LEVELS || c.n_scenarios < 1 || (c.transverse != 0 && c.transverse != 1) ||
+        !(c.manning_n >= 0.0)) return TSU_ERR_ARG;
     for (int l = 0; l + 1 < c.num_levels; l++)
         if (c.ratios[l] < 2) return TSU_ERR_ARG;
     if (c.n_regions < 0 || c.n_regions > TSU_MAX_REGIONS || c.patch_max < 1) return TSU_ERR_ARG;
@@ -974,7 +977,7 @@ int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out)
         x->cells_h.assign((size_t)S * kMaxLevels, 0.0);
         x->cells.upload(x->cells_h, st);
         x->nsteps.assign(S, {});
-        x->eta_index.assign(S, -1);
+        x->eta_index.assign(3 * S, -1);
         x->sync();
     });
     if (rc != TSU_OK) {
@@ -1013,7 +1016,23 @@ int tsu_set_eta(tsu_ctx *ctx, int scen, const double *eta, int nx, int ny, doubl
         if (scen < 0 || scen >= ctx->nscen) throw Err(TSU_ERR_ARG, "bad scenario");
         check_grid(eta, nx, ny, dx, dy);
         ctx->grids.push_back(Grid{nx, ny, x0, y0, dx, dy, std::vector<double>(eta, eta + (size_t)nx * ny), -2, nullptr});
-        ctx->eta_index[scen] = (int)ctx->grids.size() - 1;
+        ctx->eta_index[3 * scen] = (int)ctx->grids.size() - 1;
+    });
+}
+
+int tsu_set_velocity(tsu_ctx *ctx, int scen, const double *u, const double *v, int nx, int ny, double x0, double y0,
+                     double dx, double dy)
+{
+    return guard(ctx, [&] {
+        if (ctx->initialized) throw Err(TSU_ERR_ARG, "the initial velocities must be set before tsu_init");
+        if (scen < 0 || scen >= ctx->nscen) throw Err(TSU_ERR_ARG, "bad scenario");
+        check_grid(u, nx, ny, dx, dy);
+        check_grid(v, nx, ny, dx, dy);
+        const size_t n = (size_t)nx * ny;
+        ctx->grids.push_back(Grid{nx, ny, x0, y0, dx, dy, std::vector<double>(u, u + n), -2, nullptr});
+        ctx->eta_index[3 * scen + 1] = (int)ctx->grids.size() - 1;
+        ctx->grids.push_back(Grid{nx, ny, x0, y0, dx, dy, std::vector<double>(v, v + n), -2, nullptr});
+        ctx->eta_index[3 * scen + 2] = (int)ctx->grids.size() - 1;
     });
 }
 
@@ -1246,6 +1265,7 @@ int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, 
                         sa.dt1 = ctx->zero_dt.p; sa.dt1f = ctx->zero_dtf.p; sa.smax = ctx->smax.p; sa.R = L.R;
                         sa.dx = L.dx; sa.dy = L.dy; sa.g = ctx->c.g; sa.drytol = ctx->c.drytol;
                         sa.transverse = ctx->c.transverse;
+                        sa.manning = (ctx->c.manning_n * ctx->c.manning_n) * ctx->c.g;
                         set_f32_constants(sa);
                         int e = ctx->prec == TSU_F64 ? launch_step_f64(sa, (int)L.items.size(), ctx->nt(), ctx->st)
                                                      : launch_step_f32p(sa, (int)L.items.size(), ctx->nt(), ctx->st);
@@ -1367,6 +1387,7 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
             a.smax = ctx->smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = ctx->c.g; a.drytol = ctx->c.drytol;
             a.dt1f = ctx->dt1f.p;
             a.transverse = ctx->c.transverse;
+            a.manning = (ctx->c.manning_n * ctx->c.manning_n) * ctx->c.g;
             set_f32_constants(a);
             CK(cudaEventRecord(ev[2 * k], ctx->st));
             int e = ctx->prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), ctx->nt(), ctx->st)

@@ -43,6 +43,9 @@ struct StepArgs {
     float rdx, rdy;             // 1 / (R dx), 1 / (R dy)
     float gf, drytolf, sqrtgf;
     int transverse;             // 1: unsplit update with transverse corrections
+    double manning;             // n^2 g of the friction step (0: none)
+    float manningf;
+    float rR;                   // 1 / R (FP32 level time step = dt1f * rR)
 };
 
 // FP32 launch constants of a level
@@ -53,6 +56,8 @@ inline void set_f32_constants(StepArgs &a)
     a.gf = (float)a.g;
     a.drytolf = (float)a.drytol;
     a.sqrtgf = (float)__builtin_sqrt(a.g);
+    a.manningf = (float)a.manning;
+    a.rR = (float)(1.0 / a.R);
 }
 
 // Launch helpers implemented in the .cu files.

@@ -31,6 +31,8 @@
 #ifndef TSUNAMI_H
 #define TSUNAMI_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -209,6 +211,24 @@ int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows);
  * but the state is unchanged -- and keep the fastest.  Outputs (any may be
  * NULL): the chosen shape and its time per step of all levels in ms. */
 int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, double *best_ms);
+
+/* Checkpoint and restart of a whole simulation, between tsu_step calls
+ * (after tsu_init).  tsu_checkpoint_save writes every patch of every level and
+ * scenario -- its box and its current state and B, ghost cells included --
+ * with the time, time step, wave-speed rates, step and regrid counters and
+ * the gauge records into buf (caller-owned host memory, cap bytes) and the
+ * size into *written.  buf = NULL with cap = 0 only queries the size.  A
+ * checkpoint is taken between coarse steps, where the state before the next
+ * step is all that the next step reads, so one time level suffices.
+ * tsu_checkpoint_restore replaces the hierarchy of an initialised context
+ * with a checkpoint's.  The context must have the same tsu_config (compared
+ * byte for byte), the same topography and uplift layers (new patches sample
+ * B from them at later regrids) and the same gauges; predictor weights are
+ * set again with tsu_cnn_set_weights.  The run then continues exactly as the
+ * saved one would have.  Errors: TSU_ERR_ARG (buffer too small, not a
+ * checkpoint, another configuration, truncated or corrupt data). */
+int tsu_checkpoint_save(tsu_ctx *ctx, void *buf, size_t cap, size_t *written);
+int tsu_checkpoint_restore(tsu_ctx *ctx, const void *buf, size_t n);
 
 /* Synchronise the context's stream. */
 int tsu_sync(tsu_ctx *ctx);

@@ -30,7 +30,8 @@ SYMBOLS = ["tsu_create", "tsu_destroy", "tsu_last_error", "tsu_add_topo", "tsu_s
            "tsu_read_field", "tsu_add_gauges", "tsu_read_gauges", "tsu_get_stats", "tsu_sync",
            "tsu_level1_buffers", "tsu_time_level1_steps", "tsu_set_tuning",
            "tsu_grid_step_noalloc", "tsu_autotune", "tsu_cnn_num_params", "tsu_cnn_forward",
-           "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features", "tsu_cluster_flags", "tsu_set_velocity"]
+           "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features", "tsu_cluster_flags", "tsu_set_velocity",
+           "tsu_checkpoint_save", "tsu_checkpoint_restore"]
 
 
 class tsu_config(C.Structure):
@@ -96,6 +97,8 @@ def load(path: str = LIB_PATH):
         "tsu_cnn_num_params": ([], I),
         "tsu_cluster_flags": ([P, P, I, I, D, I, I, ip, I, ip], I),
         "tsu_set_velocity": ([P, I, dp, dp, I, I, D, D, D, D], I),
+        "tsu_checkpoint_save": ([P, P, C.c_size_t, C.POINTER(C.c_size_t)], I),
+        "tsu_checkpoint_restore": ([P, P, C.c_size_t], I),
         "tsu_cnn_forward": ([fp, fp, I, I, I, I, fp], I),
         "tsu_cnn_loss_grad": ([fp, fp, fp, fp, I, I, I, dp, fp], I),
         "tsu_cnn_train": ([fp, fp, fp, fp, I, I, I, I, I, C.c_float, C.c_uint, dp, dp], I),
@@ -282,6 +285,19 @@ class Tsunami:
                 "cfl_violations": s.cfl_violations, "patches": list(s.patches)[: self.num_levels],
                 "kernel_launches": s.kernel_launches, "regrids": s.regrids, "regrid_host_ms": s.regrid_host_ms,
                 "cluster_ms": s.cluster_ms}
+
+    def checkpoint(self) -> bytes:
+        """The whole simulation state between steps (tsu_checkpoint_save)."""
+        n = C.c_size_t()
+        self._check(self._L.tsu_checkpoint_save(self._h, None, 0, C.byref(n)), "tsu_checkpoint_save")
+        buf = C.create_string_buffer(n.value)
+        self._check(self._L.tsu_checkpoint_save(self._h, buf, n.value, C.byref(n)), "tsu_checkpoint_save")
+        return buf.raw[: n.value]
+
+    def restore(self, data: bytes):
+        """Continue from a checkpoint (tsu_checkpoint_restore); the context
+        needs the same configuration and inputs and must be initialised."""
+        self._check(self._L.tsu_checkpoint_restore(self._h, data, len(data)), "tsu_checkpoint_restore")
 
     def set_tuning(self, step_threads: int = 0, seg_rows: int = 0):
         self._check(self._L.tsu_set_tuning(self._h, step_threads, seg_rows), "tsu_set_tuning")

@@ -850,6 +850,186 @@ struct tsu_ctx {
         check_device_errors(cfl);
     }
 
+    // ------------------------------------------------------------ checkpoints
+    // Layout (host byte order): header, config, control block, per level the
+    // patch boxes with their current state (q0, q1, q2) and B including ghost
+    // cells, then the gauge records.  Taken between coarse steps, where the
+    // next step's old state is the saved one, so one time level suffices.
+    static constexpr uint64_t kCkptMagic = 0x3154504b43555354ull;   // "TSUCKPT1"
+    struct Writer {
+        std::vector<uint8_t> *out;
+        template <typename T> void put(const T *p, size_t n)
+        {
+            const uint8_t *b = reinterpret_cast<const uint8_t *>(p);
+            out->insert(out->end(), b, b + n * sizeof(T));
+        }
+        template <typename T> void one(T v) { put(&v, 1); }
+    };
+    struct Reader {
+        const uint8_t *p, *end;
+        template <typename T> void get(T *dst, size_t n)
+        {
+            size_t by = n * sizeof(T);
+            if ((size_t)(end - p) < by) throw Err(TSU_ERR_ARG, "checkpoint is truncated");
+            std::memcpy(dst, p, by);
+            p += by;
+        }
+        template <typename T> T one()
+        {
+            T v;
+            get(&v, 1);
+            return v;
+        }
+    };
+    template <typename T> std::vector<T> d2h(const T *d, size_t n)
+    {
+        std::vector<T> v(n);
+        if (n) CK(cudaMemcpyAsync(v.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+        return v;
+    }
+    std::vector<uint8_t> checkpoint()
+    {
+        if (!initialized) throw Err(TSU_ERR_ARG, "tsu_init has not been called");
+        sync();
+        std::vector<uint8_t> out;
+        Writer w{&out};
+        w.one(kCkptMagic);
+        w.one<int32_t>(prec); w.one<int32_t>(nscen); w.one<int32_t>(nlev); w.one<int32_t>((int32_t)sizeof(tsu_config));
+        w.put(&c, 1);
+        auto dt = d2h(dt1.p, nscen); auto dtf = d2h(dt1f.p, nscen); auto tt = d2h(t.p, nscen);
+        auto rt = d2h(rate.p, (size_t)nscen * kMaxLevels); auto cu = d2h(cellupd.p, nscen);
+        auto vi = d2h(viol.p, nscen); auto sm = d2h(smax.p, 2 * (size_t)nscen);
+        const int ng = (int)gxy.size() / 2;
+        auto gt = d2h(dgt.p, (size_t)(ng ? nsamp : 0) * nscen);
+        auto ge = d2h(dgeta.p, (size_t)(ng ? nsamp : 0) * nscen * ng);
+        std::vector<std::vector<uint8_t>> data(nlev);
+        for (int l = 0; l < nlev; l++) {
+            const Lvl &L = lv[l];
+            size_t tot = 0;
+            for (const auto &p : L.P) tot += (size_t)p.fs * 4 * esz;
+            data[l].resize(tot);
+            size_t o = 0;
+            for (const auto &p : L.P) {
+                const uint8_t *blk = reinterpret_cast<const uint8_t *>(arena.base) + (size_t)p.off * esz;
+                const size_t fb = (size_t)p.fs * esz;
+                const int fld[4] = {L.cur * 3 + 0, L.cur * 3 + 1, L.cur * 3 + 2, 6};
+                for (int f = 0; f < 4; f++) {
+                    CK(cudaMemcpyAsync(data[l].data() + o, blk + fld[f] * fb, fb, cudaMemcpyDeviceToHost, st));
+                    o += fb;
+                }
+            }
+        }
+        sync();
+        w.put(dt.data(), dt.size()); w.put(dtf.data(), dtf.size()); w.put(tt.data(), tt.size());
+        w.put(rt.data(), rt.size()); w.put(cu.data(), cu.size()); w.put(vi.data(), vi.size());
+        w.put(sm.data(), sm.size());
+        for (int s = 0; s < nscen; s++) w.put(nsteps[s].data(), kMaxLevels);
+        w.one<int64_t>(viol_seen);
+        for (int l = 0; l < nlev; l++) {
+            const Lvl &L = lv[l];
+            w.one<int64_t>((int64_t)L.P.size());
+            for (const auto &p : L.P) {
+                const int32_t box[5] = {p.scen, p.i0, p.j0, p.nx, p.ny};
+                w.put(box, 5);
+            }
+            w.put(data[l].data(), data[l].size());
+        }
+        w.one<int32_t>(ng);
+        w.one<int64_t>(ng ? nsamp : 0);
+        w.put(gt.data(), gt.size());
+        w.put(ge.data(), ge.size());
+        return out;
+    }
+    void restore(const uint8_t *buf, size_t n)
+    {
+        if (!initialized) throw Err(TSU_ERR_ARG, "restore needs an initialised context (tsu_init)");
+        Reader r{buf, buf + n};
+        if (r.one<uint64_t>() != kCkptMagic) throw Err(TSU_ERR_ARG, "not a checkpoint");
+        const int p_ = r.one<int32_t>(), ns = r.one<int32_t>(), nl = r.one<int32_t>(), cs = r.one<int32_t>();
+        if (p_ != prec || ns != nscen || nl != nlev || cs != (int32_t)sizeof(tsu_config))
+            throw Err(TSU_ERR_ARG, "checkpoint of another precision, scenario count or level count");
+        tsu_config cc;
+        r.get(&cc, 1);
+        if (std::memcmp(&cc, &c, sizeof c) != 0) throw Err(TSU_ERR_ARG, "checkpoint of another configuration");
+        std::vector<double> dt(nscen), tt(nscen), rt((size_t)nscen * kMaxLevels), cu(nscen);
+        std::vector<float> dtf(nscen);
+        std::vector<long long> vi(nscen);
+        std::vector<unsigned long long> sm(2 * (size_t)nscen);
+        r.get(dt.data(), dt.size()); r.get(dtf.data(), dtf.size()); r.get(tt.data(), tt.size());
+        r.get(rt.data(), rt.size()); r.get(cu.data(), cu.size()); r.get(vi.data(), vi.size());
+        r.get(sm.data(), sm.size());
+        std::vector<std::array<long long, kMaxLevels>> nst(nscen);
+        for (int s = 0; s < nscen; s++) r.get(nst[s].data(), kMaxLevels);
+        const long long vseen = r.one<int64_t>();
+        // replace the hierarchy level by level (coarse maps point into the coarser table)
+        sync();
+        for (int l = 0; l < nlev; l++) {
+            Lvl &L = lv[l];
+            for (size_t k = 0; k < L.P.size(); k++) arena.release(L.blk[k], L.blkbytes[k]);
+            L.P.clear(); L.blk.clear(); L.blkbytes.clear();
+        }
+        for (int l = 0; l < nlev; l++) {
+            Lvl &L = lv[l];
+            const long long np = r.one<int64_t>();
+            if (np < 0 || np > (1ll << 26)) throw Err(TSU_ERR_ARG, "checkpoint is corrupt");
+            std::vector<int32_t> boxes((size_t)np * 5);
+            r.get(boxes.data(), boxes.size());
+            for (long long k = 0; k < np; k++) {
+                const int32_t *b = &boxes[(size_t)k * 5];
+                if (b[0] < 0 || b[0] >= nscen || b[3] < 1 || b[4] < 1 || b[1] < 0 || b[2] < 0 || b[1] + b[3] > L.nxl ||
+                    b[2] + b[4] > L.nyl)
+                    throw Err(TSU_ERR_ARG, "checkpoint is corrupt");
+                PatchDesc d = make_desc(l, b[0], b[1], b[2], b[3], b[4]);
+                size_t by = (size_t)d.fs * 7 * esz;
+                size_t off = arena.alloc(by, st);
+                d.off = (long long)(off / esz);
+                L.P.push_back(d); L.blk.push_back(off); L.blkbytes.push_back(by);
+            }
+            L.cur = 0;
+            L.olds.clear();
+            L.dOlds.upload(L.olds, st);
+            finish_level(l);
+            for (const auto &p : L.P) {
+                uint8_t *blk = reinterpret_cast<uint8_t *>(arena.base) + (size_t)p.off * esz;
+                const size_t fb = (size_t)p.fs * esz;
+                const int fld[4] = {0, 1, 2, 6};
+                for (int f = 0; f < 4; f++) {
+                    std::vector<uint8_t> tmp(fb);
+                    r.get(tmp.data(), fb);
+                    CK(cudaMemcpyAsync(blk + fld[f] * fb, tmp.data(), fb, cudaMemcpyHostToDevice, st));
+                    sync();
+                }
+            }
+        }
+        const int ng = r.one<int32_t>();
+        const long long ns_ = r.one<int64_t>();
+        if (ng != (int)gxy.size() / 2 || ns_ < 0) throw Err(TSU_ERR_ARG, "checkpoint has other gauges");
+        std::vector<double> gt((size_t)ns_ * nscen), ge((size_t)ns_ * nscen * ng);
+        r.get(gt.data(), gt.size());
+        r.get(ge.data(), ge.size());
+        if (ng) {
+            ensure_samples(ns_);
+            if (ns_) {
+                CK(cudaMemcpyAsync(dgt.p, gt.data(), gt.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+                CK(cudaMemcpyAsync(dgeta.p, ge.data(), ge.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+            }
+            nsamp = ns_;
+            CK(cudaMemcpyAsync(dnsamp.p, &nsamp, sizeof(long long), cudaMemcpyHostToDevice, st));
+        }
+        CK(cudaMemcpyAsync(dt1.p, dt.data(), nscen * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dt1f.p, dtf.data(), nscen * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(t.p, tt.data(), nscen * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(rate.p, rt.data(), rt.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(cellupd.p, cu.data(), nscen * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(viol.p, vi.data(), nscen * sizeof(long long), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(smax.p, sm.data(), sm.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+        nsteps = nst;
+        viol_seen = vseen;
+        update_gauges();
+        hier_version++;
+        sync();
+    }
+
     void add_uplift_now(int s, const Grid &g)
     {
         TopoDev U{g.nx, g.ny, g.x0, g.y0, g.dx, g.dy, g.dev};
@@ -1439,4 +1619,24 @@ int tsu_cluster_flags(const unsigned char *flags, const unsigned char *nestable,
     } catch (...) {
         return TSU_ERR_ARG;
     }
+}
+
+int tsu_checkpoint_save(tsu_ctx *ctx, void *buf, size_t cap, size_t *written)
+{
+    return guard(ctx, [&] {
+        if (!written) throw Err(TSU_ERR_ARG, "bad argument");
+        std::vector<uint8_t> v = ctx->checkpoint();
+        *written = v.size();
+        if (buf == nullptr && cap == 0) return;    // size query
+        if (!buf || cap < v.size()) throw Err(TSU_ERR_ARG, "checkpoint buffer too small");
+        std::memcpy(buf, v.data(), v.size());
+    });
+}
+
+int tsu_checkpoint_restore(tsu_ctx *ctx, const void *buf, size_t n)
+{
+    return guard(ctx, [&] {
+        if (!buf) throw Err(TSU_ERR_ARG, "bad argument");
+        ctx->restore(reinterpret_cast<const uint8_t *>(buf), n);
+    });
 }

@@ -852,6 +852,45 @@ int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplan
     return (int)cudaGetLastError();
 }
 
+// Bounding box of the flagged cells of each plane: box[4p .. 4p+3] = min i,
+// min j, max i, max j (left at nx, ny, -1, -1 when nothing is flagged).  One
+// block per (row group, plane); warp minima/maxima, then one atomic per warp.
+__global__ void flag_bbox_kernel(const uint8_t *F, int nx, int ny, int rows_per_block, int *box)
+{
+    const int p = blockIdx.y;
+    const uint8_t *Fp = F + (size_t)p * nx * ny;
+    int i0 = nx, j0 = ny, i1 = -1, j1 = -1;
+    const int ja = blockIdx.x * rows_per_block, jb = min(ny, ja + rows_per_block);
+    for (int j = ja; j < jb; j++)
+        for (int i = threadIdx.x; i < nx; i += blockDim.x)
+            if (Fp[(size_t)j * nx + i]) {
+                i0 = min(i0, i); i1 = max(i1, i);
+                j0 = min(j0, j); j1 = max(j1, j);
+            }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        i0 = min(i0, __shfl_xor_sync(0xffffffffu, i0, o));
+        j0 = min(j0, __shfl_xor_sync(0xffffffffu, j0, o));
+        i1 = max(i1, __shfl_xor_sync(0xffffffffu, i1, o));
+        j1 = max(j1, __shfl_xor_sync(0xffffffffu, j1, o));
+    }
+    if ((threadIdx.x & 31) == 0 && i1 >= 0) {
+        atomicMin(box + 4 * p + 0, i0);
+        atomicMin(box + 4 * p + 1, j0);
+        atomicMax(box + 4 * p + 2, i1);
+        atomicMax(box + 4 * p + 3, j1);
+    }
+}
+
+int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st)
+{
+    if (nplanes <= 0) return 0;
+    const int rpb = 8;
+    dim3 grid((ny + rpb - 1) / rpb, nplanes);
+    flag_bbox_kernel<<<grid, 256, 0, st>>>(F, nx, ny, rpb, box);
+    return (int)cudaGetLastError();
+}
+
 int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int maxcells, int cur, double g,
                  double drytol, unsigned long long *smax, cudaStream_t st)
 {

@@ -90,6 +90,8 @@ int k_regrid_init(int prec, const LevelView &L, const LevelView &Old, const Leve
                   int maxcells, int cur, int cur_c, int ratio, double drytol, int *err, cudaStream_t st);
 int k_flag(int prec, const LevelView &L, int npatch, int maxcells, int cur, const FlagArgs &fa, cudaStream_t st);
 int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir, cudaStream_t st);
+// bounding box (min i, min j, max i, max j) of the flagged cells of each plane; box preset to (nx, ny, -1, -1)
+int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st);
 int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa,
            cudaStream_t st);
 int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int maxcells, int cur, double g,

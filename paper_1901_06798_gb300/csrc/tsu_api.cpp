@@ -267,7 +267,7 @@ struct tsu_ctx {
     long long samp_cap = 0, nsamp = 0;
     // flags
     DevBuf<uint8_t> fraw, fcov, ftmp, fF, fN;
-    DevBuf<int> fslot;
+    DevBuf<int> fslot, fbox;
     // statistics and graphs
     long long launches = 0;
     long long viol_seen = 0;
@@ -553,27 +553,47 @@ struct tsu_ctx {
             kl(k_dilate(fraw.p, ftmp.p, nx, ny, np, b, 0, st), "dilate x");
             kl(k_dilate(ftmp.p, fF.p, nx, ny, np, b, 1, st), "dilate y");
             kl(k_nest(fF.p, fN.p, fcov.p, nx, ny, np, fa, st), "nest");
-            hflags.ensure(2 * plane * np);
-            uint8_t *hF = hflags.p, *hN = hflags.p + plane * np;
-            CK(cudaMemcpyAsync(hF, fF.p, plane * np, cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(hN, fN.p, plane * np, cudaMemcpyDeviceToHost, st));
+            // only the flags' bounding box of each plane comes to the host (the
+            // clustering starts from that box, so the boxes are the same)
+            std::vector<int> bb(4 * (size_t)np);
+            for (int q = 0; q < np; q++) { bb[4 * q] = nx; bb[4 * q + 1] = ny; bb[4 * q + 2] = -1; bb[4 * q + 3] = -1; }
+            fbox.upload(bb, st);
+            kl(k_flag_bbox(fF.p, nx, ny, np, fbox.p, st), "flag bbox");
+            CK(cudaMemcpyAsync(bb.data(), fbox.p, bb.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+            sync();
+            std::vector<size_t> hoff(np + 1, 0);
+            for (int q = 0; q < np; q++) {
+                const size_t w = bb[4 * q + 2] >= 0 ? (size_t)(bb[4 * q + 2] - bb[4 * q] + 1) : 0;
+                const size_t h = bb[4 * q + 2] >= 0 ? (size_t)(bb[4 * q + 3] - bb[4 * q + 1] + 1) : 0;
+                hoff[q + 1] = hoff[q] + w * h;
+            }
+            hflags.ensure(2 * std::max<size_t>(hoff[np], 1));
+            uint8_t *hF = hflags.p, *hN = hflags.p + hoff[np];
+            for (int q = 0; q < np; q++) {
+                if (bb[4 * q + 2] < 0) continue;
+                const size_t w = bb[4 * q + 2] - bb[4 * q] + 1, h = bb[4 * q + 3] - bb[4 * q + 1] + 1;
+                const size_t src = plane * q + (size_t)bb[4 * q + 1] * nx + bb[4 * q];
+                CK(cudaMemcpy2DAsync(hF + hoff[q], w, fF.p + src, nx, w, h, cudaMemcpyDeviceToHost, st));
+                CK(cudaMemcpy2DAsync(hN + hoff[q], w, fN.p + src, nx, w, h, cudaMemcpyDeviceToHost, st));
+            }
             sync();
             const auto t_c0 = std::chrono::steady_clock::now();
+            auto cluster_one = [&](int s, int threads, std::vector<int32_t> *ws) {
+                const int q = slot[s];
+                if (bb[4 * q + 2] < 0) return;
+                const int w = bb[4 * q + 2] - bb[4 * q] + 1, h = bb[4 * q + 3] - bb[4 * q + 1] + 1;
+                cluster_boxes(hF + hoff[q], hN + hoff[q], w, h, c.cluster_eff, r, c.patch_max, boxes[s], threads, ws);
+                for (auto &b : boxes[s]) { b[0] += bb[4 * q]; b[1] += bb[4 * q + 1]; }
+            };
             if (which.size() == 1) {
-                const int s = which[0];
-                cluster_boxes(hF + plane * slot[s], hN + plane * slot[s], nx, ny, c.cluster_eff, r, c.patch_max,
-                              boxes[s], 16, &cws[0]);
+                cluster_one(which[0], 16, &cws[0]);
             } else {
                 // independent scenarios: one host thread per group of them
                 const int nt = std::max(1, std::min({16, (int)which.size(), (int)std::thread::hardware_concurrency()}));
                 std::vector<std::thread> pool;
                 for (int q = 0; q < nt; q++)
                     pool.emplace_back([&, q] {
-                        for (size_t k = q; k < which.size(); k += nt) {
-                            const int s = which[k];
-                            cluster_boxes(hF + plane * slot[s], hN + plane * slot[s], nx, ny, c.cluster_eff, r,
-                                          c.patch_max, boxes[s], 1, &cws[q]);
-                        }
+                        for (size_t k = q; k < which.size(); k += nt) cluster_one(which[k], 1, &cws[q]);
                     });
                 for (auto &th : pool) th.join();
             }
@@ -1057,7 +1077,7 @@ struct tsu_ctx {
         dt1.release(); dt1f.release(); t.release(); rate.release(); cellupd.release(); cells.release(); Rl.release(); mass.release();
         viol.release(); smax.release(); derr.release();
         dgxy.release(); dgeta.release(); dgt.release(); dnsamp.release(); dgloc.release();
-        fraw.release(); fcov.release(); ftmp.release(); fF.release(); fN.release(); fslot.release();
+        fraw.release(); fcov.release(); ftmp.release(); fF.release(); fN.release(); fslot.release(); fbox.release();
         dstage.release(); zero_dt.release(); zero_dtf.release();
         cnn_theta.release(); cnn_feat.release(); cnn_logits.release(); cnn_half.release();
         if (arena.base) cudaFreeAsync(arena.base, st);

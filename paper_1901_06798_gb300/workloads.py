@@ -20,6 +20,8 @@ Workloads (sizes in cells of level 1):
   amr3(...)  3-level AMR over the shelf profile, ratios 4 and 4, flags
              |eta| > 0.01 m or depth < 200 m, regrid every 4 steps,
              patches up to 60 fine cells.
+  amr4_bay   4-level AMR (ratios 4, 4, 8) down to 31.25 m around a synthetic
+             semicircular bay on the beach, 10 gauges (deep, shelf, bay).
   ensemble   independent scenarios on one bathymetry, uplift centres and
              amplitudes drawn from numpy PCG64 with seed 1901.
 """
@@ -130,6 +132,59 @@ def amr3(L: float = 2000e3, dx1: float = 2000.0, ratios=(4, 4), patch_max: int =
     g = np.array([[L - 600e3 * scale, L / 2], [L - 300e3 * scale, L / 2], [L - 100e3 * scale, L / 2 + 10e3 * scale]])
     return dict(name="amr3", cfg=cfg, topo=shelf_topo(L, L, scale=scale, step_km=max(0.25, scale)),
                 eta=[], uplift=[(0, *up)], steps=steps, gauges=g)
+
+
+def bay_topo(L: float, scale: float, xs: float, yc: float, radius: float, box: float, res: float):
+    """Fine topography grid over the bay box: the beach profile with a
+    semicircular bay cut into it, B = min(B_beach, -10 (1 - (r / radius)^2))
+    for r < radius around the shoreline point (xs, yc).  Node spacing res."""
+    n = int(round(box / res)) + 1
+    xg = xs - box / 2 + np.arange(n) * res
+    yg = yc - box / 2 + np.arange(n) * res
+    X, Y = np.meshgrid(xg, yg)
+    s_km = (L - X) / 1000.0 / scale
+    beach = np.where(s_km <= 150.0, 50.0 - 250.0 * s_km / 150.0, -200.0)
+    r = np.hypot(X - xs, Y - yc)
+    bay = np.where(r < radius, -10.0 * (1.0 - (r / radius) ** 2), np.inf)
+    return (np.minimum(beach, bay), xg[0], yg[0], res, res)
+
+
+def amr4_bay(L: float = 3000e3, dx1: float = 4000.0, ratios=(4, 4, 8), radius: float = 5000.0,
+             box: float = 12000.0, patch_max: int = 60, eta_tol: float = 0.01, depth_below: float = 200.0,
+             steps: int = 8) -> dict:
+    """4-level AMR down to dx1 / 128 (31.25 m at full size) around a
+    synthetic bay: the shelf profile scaled to the domain, a semicircular
+    bay of the given radius cut into the beach at mid-y, the 2 m uplift of
+    the uniform workload, flags |eta| > 0.01 m or depth < 200 m, the finest
+    level forced over a box x box square around the bay and capped to three
+    levels elsewhere, regrid every 4 steps, 10 gauges (4 deep water 700 km
+    offshore, 3 on the shelf 300 km offshore, 3 in the bay; offsets scale
+    with the domain)."""
+    n = int(round(L / dx1))
+    scale = L / 2048e3
+    xs = L - 30e3 * scale                   # shoreline of the beach profile
+    yc = L / 2
+    nl = len(ratios) + 1
+    half = box / 2
+    bx1, by1, bx2, by2 = xs - half, yc - half, xs + half, yc + half
+    big = 10 * L
+    regions = [[bx1, by1, bx2, by2, nl, nl],                     # the bay box: finest level forced
+               [-big, -big, bx1, big, 0, nl - 1], [bx2, -big, big, big, 0, nl - 1],   # elsewhere capped
+               [bx1, -big, bx2, by1, 0, nl - 1], [bx1, by2, bx2, big, 0, nl - 1]]
+    cfg = base_config(nx=n, ny=n, dx=dx1, dy=dx1, num_levels=nl, ratios=list(ratios), bc=[BC_EXTRAP] * 4,
+                      regrid_interval=4, flag_eta_tol=eta_tol, flag_depth_below=depth_below,
+                      patch_max=patch_max, regions=regions)
+    up = shelf_uplift(L, L, scale=scale)
+    finest = dx1
+    for r in ratios:
+        finest /= r
+    topo = shelf_topo(L, L, scale=scale, step_km=max(0.25, scale)) + \
+        [bay_topo(L, scale, xs, yc, radius, box, finest)]
+    deep = [[L - 700e3 * scale, yc + d * scale] for d in (-300e3, -100e3, 100e3, 300e3)]
+    shelfg = [[L - 300e3 * scale, yc + d * scale] for d in (-200e3, 0.0, 200e3)]
+    bayg = [[xs - 0.4 * radius, yc], [xs + 0.4 * radius, yc - 0.4 * radius], [xs + 0.6 * radius, yc + 0.2 * radius]]
+    return dict(name="amr4_bay", cfg=cfg, topo=topo, eta=[], uplift=[(0, *up)], steps=steps,
+                gauges=np.array(deep + shelfg + bayg))
 
 
 def ensemble(n_scen: int = 64, n: int = 1024, dx: float = 2000.0, ratio: int = 4, steps: int = 8,

@@ -252,3 +252,20 @@ def test_full_size_shelf4096_properties():
     assert o.stats()["dt"] == g.stats()["dt"]
     eo = o.read_field(0, 1, "eta", len(xs), len(ys), xs[0], ys[0], dx, dx)
     assert rel_err(eta, eo) <= F64_REL
+
+
+def test_amr4_bay_four_levels_ratio_8():
+    """The 4-level bay workload scaled down (96 km, ratios 4, 4, 8, the
+    finest level forced around the bay and capped elsewhere): FP64 patch
+    lists, fields and gauges bit for bit; FP32 gauges within 1e-4 m."""
+    w = W.amr4_bay(L=96e3, dx1=4000.0, radius=1200.0, box=3000.0)
+    o, g = run_pair(w, 4)
+    assert o.num_patches(0, 4) > 0
+    compare_levels(o, g, 4, bitwise=True)
+    to, eo = o.read_gauges()
+    tg, eg = g.read_gauges()
+    assert np.array_equal(eo, eg)
+    o, g = run_pair(w, 4, precision=1)
+    _, eo = o.read_gauges()
+    _, eg = g.read_gauges()
+    assert np.abs(eg - eo).max() <= F32P_ETA

@@ -235,6 +235,82 @@ def run_ours(args, rank, world, dist, torch):
     return results, clk, e2e, extra
 
 
+def run_config4(args, stream, torch):
+    """The 4-level bay workload with plain flagging and with the learned
+    flag predictor.  The predictor is trained on the GPU on (features, flags
+    one regrid later) pairs logged from the uniform shelf workload (the same
+    bathymetry and uplift at 2 km, 128^2 windows around flagged cells)."""
+    from paper_1901_06798_gb300 import binding as B
+    from paper_1901_06798_gb300 import workloads as W
+    t_start = time.perf_counter()
+    w2 = W.shelf(n=1024, dx=2000.0)
+    cfg2 = dict(w2["cfg"], flag_eta_tol=0.01, flag_depth_below=200.0, regrid_interval=4)
+    g = W.load(B.Tsunami(cfg2, precision=B.TSU_F32P, stream=stream), dict(w2, cfg=cfg2, gauges=np.zeros((0, 2))))
+    rng = np.random.Generator(np.random.PCG64(4))
+    X, T, prev, win = [], [], None, 128
+    for _ in range(args.config4_train_regrids):
+        f, fl = g.cnn_features(0, 1)
+        if prev is not None:
+            js, is_ = np.nonzero(fl)
+            for _ in range(6):
+                k = rng.integers(len(js))
+                j0 = int(np.clip(js[k] - win // 2, 0, fl.shape[0] - win))
+                i0 = int(np.clip(is_[k] - win // 2, 0, fl.shape[1] - win))
+                X.append(prev[:, j0:j0 + win, i0:i0 + win])
+                T.append(fl[j0:j0 + win, i0:i0 + win].astype(np.float32))
+        prev = f
+        g.step(4)
+    g.close()
+    X, T = np.stack(X), np.stack(T)
+    theta, l0, l1 = B.cnn_train(W.cnn_init_params(0), X, T, np.ones_like(T), steps=600, batch=8, lr=2e-3, seed=1)
+    train = {"samples": int(len(X)), "window": win, "loss_first": l0, "loss_last": l1,
+             "seconds": time.perf_counter() - t_start}
+    w = W.amr4_bay()
+    runs = {}
+    k64 = max(1, min(args.config4_steps, 40))
+    for name, use, prec in (("plain", 0, B.TSU_F32P), ("cnn", 1, B.TSU_F32P), ("f64_plain", 0, B.TSU_F64)):
+        cfg = dict(w["cfg"], use_cnn=use, cnn_buffer=1)
+        ctx = B.Tsunami(cfg, precision=prec, stream=stream)
+        if use:
+            ctx.cnn_set_weights(theta)
+        W.load(ctx, dict(w, cfg=cfg))
+        ctx.set_tuning(32, 32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        misses, checked, done = 0, 0, 0
+        nsteps = k64 if prec == B.TSU_F64 else args.config4_steps
+        while done < nsteps:
+            n = min(8, nsteps - done)
+            ctx.step(n)
+            done += n
+            _, fl = ctx.cnn_features(0, 1)             # level-1 criterion flags now
+            cov = np.zeros_like(fl, dtype=bool)
+            r = w["cfg"]["ratios"][0]
+            for (i0, j0, nx, ny) in ctx.boxes(0, 2):
+                cov[j0 // r:(j0 + ny) // r, i0 // r:(i0 + nx) // r] = True
+            misses += int(((fl > 0) & ~cov).sum())
+            checked += int((fl > 0).sum())
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        st = ctx.stats()
+        runs[name] = {"steps": nsteps, "wall_s": el, "cell_updates": st["cell_updates"],
+                      "rate": st["cell_updates"] / el, "patches_per_level": st["patches"],
+                      "missed_flags": misses, "checked_flags": checked, "t_end_s": st["t"],
+                      "gauges": ctx.read_gauges()}
+        ctx.close()
+    ea, eb = runs["plain"].pop("gauges")[1], runs["cnn"].pop("gauges")[1]
+    e64 = runs["f64_plain"].pop("gauges")[1]
+    n = min(len(ea), len(eb))
+    n64 = min(len(eb), len(e64))
+    return {"workload": "amr4_bay: 3000 km, dx 4 km -> 31.25 m (ratios 4, 4, 8), bay radius 5 km, 10 gauges",
+            "train": train, "plain": runs["plain"], "cnn": runs["cnn"], "f64_plain": runs["f64_plain"],
+            "rate_ratio_f32p_cnn_over_f64_plain": runs["cnn"]["rate"] / runs["f64_plain"]["rate"],
+            "gauge_max_abs_f32p_cnn_vs_f64_plain_m": float(np.abs(eb[:n64] - e64[:n64]).max()) if n64 else None,
+            "cell_update_ratio_cnn_over_plain": runs["cnn"]["cell_updates"] / runs["plain"]["cell_updates"],
+            "wall_ratio_cnn_over_plain": runs["cnn"]["wall_s"] / runs["plain"]["wall_s"],
+            "gauge_max_abs_cnn_vs_plain_m": float(np.abs(ea[:n] - eb[:n]).max()) if n else None}
+
+
 def cpu_baseline():
     """The FP64 oracle as it stands (one thread) on a bounded sample of the
     workload: the full 4096^2 grid, 2 steps."""
@@ -298,6 +374,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--amr-steps", type=int, default=16,
                     help="coarse steps of the 3-level AMR and 64-scenario ensemble legs (FP64: a quarter); 0 skips")
+    ap.add_argument("--config4-steps", type=int, default=0,
+                    help="coarse steps of the 4-level bay workload, plain vs learned flagging (0: skip)")
+    ap.add_argument("--config4-train-regrids", type=int, default=40,
+                    help="regrid intervals of the uniform shelf run that supply predictor training pairs")
     ap.add_argument("--transverse-steps", type=int, default=100,
                     help="steps of the unsplit (transverse-correction) legs; 0 skips them")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -320,6 +400,9 @@ def main():
         dist_mod.init_process_group("nccl")
         dist = dist_mod
     results, clk, e2e, extra = run_ours(args, rank, world, dist, torch)
+    config4 = None
+    if args.config4_steps > 0 and rank == 0:
+        config4 = run_config4(args, torch.cuda.current_stream().cuda_stream, torch)
     if rank == 0:
         hbm, src = peaks()
         r = results["f32p"]
@@ -353,6 +436,7 @@ def main():
                                            "launch_shape": u["tune"]}
                         for k, u in results.items() if k.endswith("_unsplit")},
             "amr": extra,
+            **({"config4": config4} if config4 else {}),
             "gpu_launches": results["f32p"]["launches"],
             "clocks": clk,
             "e2e": e2e,

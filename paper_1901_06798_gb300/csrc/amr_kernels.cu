@@ -526,38 +526,51 @@ __global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, 
 // |hu|/10, |hv|/10 and the criterion flag, zero where no patch covers a cell.
 template <typename T, bool PERT>
 __global__ void cnn_features_kernel(LevelView L, int cur, const int *scen_slot, const uint8_t *raw, float *feat,
-                                    double drytol)
+                                    double drytol, CnnWindow win)
 {
     const PatchDesc P = L.descs[blockIdx.y];
     const int slot = scen_slot[P.scen];
     if (slot < 0) return;
+    if (P.i0 >= win.x0 + win.w || P.i0 + P.nx <= win.x0 || P.j0 >= win.y0 + win.h || P.j0 + P.ny <= win.y0) return;
     const int n = P.nx * P.ny;
     Acc<T> a = acc<T>(L.arena, P);
-    const long long plane = (long long)L.nxl * L.nyl;
+    const long long lplane = (long long)L.nxl * L.nyl;
+    const long long plane = (long long)win.w * win.h;   // features of the window only
     float *f = feat + (long long)slot * 5 * plane;
-    const uint8_t *rw = raw + (long long)slot * plane;
+    const uint8_t *rw = raw + (long long)slot * lplane;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         int i = c % P.nx, j = c / P.nx;
+        const int I = P.i0 + i - win.x0, J = P.j0 + j - win.y0;
+        if (I < 0 || J < 0 || I >= win.w || J >= win.h) continue;
         long long k = a.idx(i, j);
         double B = (double)a.Bp()[k], q0 = (double)a.f(cur, 0)[k];
         double h = PERT ? q0 - B : q0;
         double eta = PERT ? q0 : h + B;
-        long long gk = (long long)(P.j0 + j) * L.nxl + (P.i0 + i);
+        long long gk = (long long)J * win.w + I;                         // in the window
+        long long lk = (long long)(P.j0 + j) * L.nxl + (P.i0 + i);      // in the level plane
         double dep = -B / 1000.0;
         dep = dep < -1.0 ? -1.0 : (dep > 5.0 ? 5.0 : dep);
         f[gk] = h >= drytol ? (float)(eta / 0.1) : 0.0f;
         f[plane + gk] = (float)dep;
         f[2 * plane + gk] = (float)(fabs((double)a.f(cur, 1)[k]) / 10.0);
         f[3 * plane + gk] = (float)(fabs((double)a.f(cur, 2)[k]) / 10.0);
-        f[4 * plane + gk] = rw[gk] ? 1.0f : 0.0f;
+        f[4 * plane + gk] = rw[lk] ? 1.0f : 0.0f;
     }
 }
 
-// raw flags |= (logit > 0) on covered cells
-__global__ void cnn_union_kernel(uint8_t *raw, const uint8_t *cov, const float *logits, long long n)
+// raw flags |= (logit > 0) on covered cells of the target box (logits of the
+// window, one plane per flag plane)
+__global__ void cnn_union_kernel(uint8_t *raw, const uint8_t *cov, const float *logits, int nx, int ny, int np,
+                                 CnnWindow win)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
-        if (cov[p] && logits[p] > 0.0f) raw[p] = 1;
+    const long long tn = (long long)win.tw * win.th, n = tn * np;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const long long pl = q / tn, r = q % tn;
+        const int I = win.tx0 + (int)(r % win.tw), J = win.ty0 + (int)(r / win.tw);
+        const long long g = pl * (long long)nx * ny + (long long)J * nx + I;
+        const long long w = pl * (long long)win.w * win.h + (long long)(J - win.y0) * win.w + (I - win.x0);
+        if (cov[g] && logits[w] > 0.0f) raw[g] = 1;
+    }
 }
 
 // ---------------------------------------------------------------- rates, dt
@@ -947,19 +960,22 @@ int k_patch_out(int prec, const LevelView &L, int p, int ncells, int cur, double
 }
 
 int k_cnn_features(int prec, const LevelView &L, int npatch, int maxcells, int cur, const int *scen_slot,
-                   const uint8_t *raw, float *feat, double drytol, cudaStream_t st)
+                   const uint8_t *raw, float *feat, double drytol, const CnnWindow &win, cudaStream_t st)
 {
     if (npatch <= 0) return 0;
     dim3 g = grid_for(maxcells, npatch, 128);
-    TSU_DISPATCH(prec, cnn_features_kernel, <<<g, 128, 0, st>>>(L, cur, scen_slot, raw, feat, drytol));
+    TSU_DISPATCH(prec, cnn_features_kernel, <<<g, 128, 0, st>>>(L, cur, scen_slot, raw, feat, drytol, win));
     return (int)cudaGetLastError();
 }
 
-int k_cnn_union(uint8_t *raw, const uint8_t *cov, const float *logits, long long n, cudaStream_t st)
+int k_cnn_union(uint8_t *raw, const uint8_t *cov, const float *logits, int nx, int ny, int np, const CnnWindow &win,
+                cudaStream_t st)
 {
+    long long n = (long long)win.tw * win.th * np;
+    if (n <= 0) return 0;
     long long b = (n + 255) / 256;
     if (b > 152 * 32) b = 152 * 32;
-    cnn_union_kernel<<<(int)(b < 1 ? 1 : b), 256, 0, st>>>(raw, cov, logits, n);
+    cnn_union_kernel<<<(int)(b < 1 ? 1 : b), 256, 0, st>>>(raw, cov, logits, nx, ny, np, win);
     return (int)cudaGetLastError();
 }
 

@@ -46,6 +46,14 @@ struct TopoSet {
     double drytol;               // initial velocities apply to wet cells only
 };
 
+// Window of a level plane on which the flag predictor runs (x0, y0, w, h), and
+// the target box inside it whose predictions are used (tx0, ty0, tw, th; the
+// window adds the predictor's 3-cell receptive margin where the plane allows)
+struct CnnWindow {
+    int x0, y0, w, h;
+    int tx0, ty0, tw, th;
+};
+
 struct FlagArgs {
     uint8_t *raw, *cov;
     const int *scen_slot;        // plane of each scenario or -1
@@ -107,8 +115,9 @@ int k_read_field(int prec, const LevelView &L, int npatch, int cur, int scen, in
                  cudaStream_t st);
 int k_patch_out(int prec, const LevelView &L, int p, int ncells, int cur, double *out, cudaStream_t st);
 int k_cnn_features(int prec, const LevelView &L, int npatch, int maxcells, int cur, const int *scen_slot,
-                   const uint8_t *raw, float *feat, double drytol, cudaStream_t st);
-int k_cnn_union(uint8_t *raw, const uint8_t *cov, const float *logits, long long n, cudaStream_t st);
+                   const uint8_t *raw, float *feat, double drytol, const CnnWindow &win, cudaStream_t st);
+int k_cnn_union(uint8_t *raw, const uint8_t *cov, const float *logits, int nx, int ny, int np, const CnnWindow &win,
+                cudaStream_t st);
 int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, double *mass, cudaStream_t st);
 
 }  // namespace tsu

@@ -503,18 +503,76 @@ struct tsu_ctx {
     // ------------------------------------------------------------ regrid
     // Predictor logits for the np planes of level l whose raw criterion flags
     // and scenario slots (fslot) are set.
+    // Bounding box, on level l, of the cells where the region caps allow level
+    // newlev (a superset: a coarse raster marks a cell capped only when one
+    // capping region holds its whole footprint).  Returns false when none is.
+    bool allowed_box(int l, int newlev, int &i0, int &j0, int &i1, int &j1) const
+    {
+        const Lvl &C = lv[l];
+        const int G = 256, gx = std::min(G, C.nxl), gy = std::min(G, C.nyl);
+        i0 = C.nxl; j0 = C.nyl; i1 = -1; j1 = -1;
+        for (int b = 0; b < gy; b++)
+            for (int a = 0; a < gx; a++) {
+                const int ia = (int)((long long)a * C.nxl / gx), ib = (int)((long long)(a + 1) * C.nxl / gx) - 1;
+                const int ja = (int)((long long)b * C.nyl / gy), jb = (int)((long long)(b + 1) * C.nyl / gy) - 1;
+                const double xa = c.x0 + (ia + 0.5) * C.dx, xb = c.x0 + (ib + 0.5) * C.dx;
+                const double ya = c.y0 + (ja + 0.5) * C.dy, yb = c.y0 + (jb + 0.5) * C.dy;
+                bool capped = false;
+                for (int k = 0; k < c.n_regions && !capped; k++) {
+                    const double *R = c.regions[k];
+                    capped = xa >= R[0] && xb <= R[2] && ya >= R[1] && yb <= R[3] && (double)newlev > R[5];
+                }
+                if (capped) continue;
+                i0 = std::min(i0, ia); j0 = std::min(j0, ja); i1 = std::max(i1, ib); j1 = std::max(j1, jb);
+            }
+        return i1 >= 0;
+    }
+
+    // Predicted flags of the np planes of level l whose raw criterion flags
+    // and scenario slots (fslot) are set, ORed into the raw flags.  The
+    // predictor runs on a window only: the criterion flags' bounding box grown
+    // by the regrid interval (a wave crosses at most one cell per step, so no
+    // flag farther away can appear by the next regrid) and clipped to where the
+    // region caps allow the new level, plus the predictor's 3-cell receptive
+    // margin.
     void cnn_predict(int l, int np)
     {
         Lvl &C = lv[l];
-        const size_t plane = (size_t)C.nxl * C.nyl;
-        cnn_feat.ensure(plane * 5 * np, st);
-        cnn_logits.ensure(plane * np, st);
-        cnn_half.ensure(cnn_half_workspace_bytes(np, C.nyl, C.nxl), st);
-        CK(cudaMemsetAsync(cnn_feat.p, 0, plane * 5 * np * sizeof(float), st));
-        kl(k_cnn_features(prec, view(l), (int)C.P.size(), C.maxcells, C.cur, fslot.p, fraw.p, cnn_feat.p, c.drytol, st),
-           "cnn features");
-        kl(cnn_forward(cnn_theta.p, cnn_feat.p, np, C.nyl, C.nxl, true, nullptr, cnn_logits.p, cnn_half.p, st),
+        const int nx = C.nxl, ny = C.nyl;
+        std::vector<int> bb(4 * (size_t)np);
+        for (int q = 0; q < np; q++) { bb[4 * q] = nx; bb[4 * q + 1] = ny; bb[4 * q + 2] = -1; bb[4 * q + 3] = -1; }
+        fbox.upload(bb, st);
+        kl(k_flag_bbox(fraw.p, nx, ny, np, fbox.p, st), "criterion bbox");
+        CK(cudaMemcpyAsync(bb.data(), fbox.p, bb.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+        sync();
+        int ti0 = nx, tj0 = ny, ti1 = -1, tj1 = -1;
+        for (int q = 0; q < np; q++)
+            if (bb[4 * q + 2] >= 0) {
+                ti0 = std::min(ti0, bb[4 * q]); tj0 = std::min(tj0, bb[4 * q + 1]);
+                ti1 = std::max(ti1, bb[4 * q + 2]); tj1 = std::max(tj1, bb[4 * q + 3]);
+            }
+        if (ti1 < 0) return;
+        const int b = c.regrid_interval > 0 ? c.regrid_interval : 0;
+        ti0 = std::max(0, ti0 - b); tj0 = std::max(0, tj0 - b);
+        ti1 = std::min(nx - 1, ti1 + b); tj1 = std::min(ny - 1, tj1 + b);
+        int ai0, aj0, ai1, aj1;
+        if (!allowed_box(l, l + 2, ai0, aj0, ai1, aj1)) return;
+        ti0 = std::max(ti0, ai0); tj0 = std::max(tj0, aj0); ti1 = std::min(ti1, ai1); tj1 = std::min(tj1, aj1);
+        if (ti0 > ti1 || tj0 > tj1) return;
+        CnnWindow w;
+        w.tx0 = ti0; w.ty0 = tj0; w.tw = ti1 - ti0 + 1; w.th = tj1 - tj0 + 1;
+        w.x0 = std::max(0, ti0 - 3); w.y0 = std::max(0, tj0 - 3);
+        w.w = std::min(nx - 1, ti1 + 3) - w.x0 + 1; w.h = std::min(ny - 1, tj1 + 3) - w.y0 + 1;
+        const size_t wp = (size_t)w.w * w.h;
+        cnn_feat.ensure(wp * 5 * np, st);
+        cnn_logits.ensure(wp * np, st);
+        cnn_half.ensure(cnn_half_workspace_bytes(np, w.h, w.w), st);
+        CK(cudaMemsetAsync(cnn_feat.p, 0, wp * 5 * np * sizeof(float), st));
+        kl(k_cnn_features(prec, view(l), (int)C.P.size(), C.maxcells, C.cur, fslot.p, fraw.p, cnn_feat.p, c.drytol, w,
+                          st), "cnn features");
+        kl(cnn_forward(cnn_theta.p, cnn_feat.p, np, w.h, w.w, true, nullptr, cnn_logits.p, cnn_half.p, st),
            "cnn forward");
+        kl(k_cnn_union(fraw.p, fcov.p, cnn_logits.p, nx, ny, np, w, st), "cnn union");
     }
 
     // Build level l+1 of the scenarios in `which` from flags on level l.
@@ -547,7 +605,6 @@ struct tsu_ctx {
             if (c.use_cnn && cnn_ready) {
                 // criterion(now) OR predicted flags, then the narrower buffer
                 cnn_predict(l, np);
-                kl(k_cnn_union(fraw.p, fcov.p, cnn_logits.p, (long long)plane * np, st), "cnn union");
                 b = c.cnn_buffer > 0 ? c.cnn_buffer : 0;
             }
             kl(k_dilate(fraw.p, ftmp.p, nx, ny, np, b, 0, st), "dilate x");
@@ -1531,8 +1588,9 @@ int tsu_cnn_features(tsu_ctx *ctx, int scen, int level, float *features, unsigne
         ctx->kl(k_flag(ctx->prec, ctx->view(l), (int)C.P.size(), C.maxcells, C.cur, fa, ctx->st), "flag");
         ctx->cnn_feat.ensure(plane * 5, ctx->st);
         CK(cudaMemsetAsync(ctx->cnn_feat.p, 0, plane * 5 * sizeof(float), ctx->st));
+        const CnnWindow whole{0, 0, C.nxl, C.nyl, 0, 0, C.nxl, C.nyl};
         ctx->kl(k_cnn_features(ctx->prec, ctx->view(l), (int)C.P.size(), C.maxcells, C.cur, ctx->fslot.p, ctx->fraw.p,
-                               ctx->cnn_feat.p, ctx->c.drytol, ctx->st), "cnn features");
+                               ctx->cnn_feat.p, ctx->c.drytol, whole, ctx->st), "cnn features");
         if (features)
             CK(cudaMemcpyAsync(features, ctx->cnn_feat.p, plane * 5 * sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
         if (flags) CK(cudaMemcpyAsync(flags, ctx->fraw.p, plane, cudaMemcpyDeviceToHost, ctx->st));

@@ -232,6 +232,19 @@ def lake_at_rest_shelf(n: int = 96, dx: float = 2000.0) -> dict:
                 uplift=[], steps=0, gauges=np.zeros((0, 2)))
 
 
+def cnn_init_params(seed: int = 0) -> np.ndarray:
+    """Seeded starting weights of the refinement-flag predictor in the packed
+    order of the C ABI (per layer 5->16, 16->16, 16->16 3x3 and 16->1 1x1:
+    weights (out, in, k, k), then biases): He-normal weights from numpy
+    PCG64(seed), zero biases."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for ci, co, k in ((5, 16, 3), (16, 16, 3), (16, 16, 3), (16, 1, 1)):
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / (ci * k * k)), co * ci * k * k))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts)
+
+
 def load(obj, w: dict):
     """Feed a workload's inputs to a solver object exposing add_topo,
     set_eta, set_velocity, add_uplift and init (the oracle or the GPU

@@ -106,6 +106,43 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class Busy:
+    """Device- and host-busy fractions of a timed region (the paper's P1/P2
+    style metrics): the mean of nvidia-smi's utilization.gpu -- the share of
+    each sample period in which a kernel was running -- and this process's
+    CPU time over wall time."""
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        self.t0, self.c0 = time.perf_counter(), os.times()
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=utilization.gpu",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        wall = time.perf_counter() - self.t0
+        c1 = os.times()
+        host = ((c1.user - self.c0.user) + (c1.system - self.c0.system)) / wall if wall > 0 else None
+        gpu = None
+        if self.p:
+            self.p.terminate()
+            out, _ = self.p.communicate(timeout=10)
+            v = []
+            for line in out.strip().splitlines():
+                try:
+                    v.append(float(line.strip()))
+                except ValueError:
+                    pass
+            gpu = statistics.mean(v) / 100.0 if v else None
+        return {"gpu_busy_frac": gpu, "host_busy_frac": host}
+
+
 def load_workload(prec_name, stream, transverse=0):
     from paper_1901_06798_gb300 import binding
     from paper_1901_06798_gb300 import workloads as W
@@ -188,16 +225,20 @@ def run_ours(args, rank, world, dist, torch):
                 s0 = [ctx.stats(s) for s in range(nscen)]
                 barrier()
                 torch.cuda.synchronize()
+                busy = Busy(int(os.environ.get("LOCAL_RANK", 0)))
+                busy.start()
                 t0 = time.perf_counter()
                 ctx.step(K)
                 torch.cuda.synchronize()
                 el = max_over_ranks(time.perf_counter() - t0)
+                bz = busy.stop()
                 s1 = [ctx.stats(s) for s in range(nscen)]
                 cu = sum(b["cell_updates"] - a["cell_updates"] for a, b in zip(s0, s1))
                 legs_x[prec] = {"value": world * cu / el, "steps": K, "ms_per_step": el / K * 1e3,
                                 "cell_updates_per_step": cu / K, "patches_per_level": s1[0]["patches"],
                                 "regrid_host_ms_per_step": (s1[0]["regrid_host_ms"] - s0[0]["regrid_host_ms"]) / K,
                                 "cluster_ms_per_step": (s1[0]["cluster_ms"] - s0[0]["cluster_ms"]) / K,
+                                **bz,
                                 "launch_shape": {"threads": tune[0], "seg_rows": tune[1]}}
                 gauges[prec] = ctx.read_gauges()
                 ctx.close()
@@ -274,7 +315,7 @@ def run_config4(args, stream, torch):
         if use:
             ctx.cnn_set_weights(theta)
         W.load(ctx, dict(w, cfg=cfg))
-        ctx.set_tuning(32, 32)
+        ctx.set_tuning(64 if prec == B.TSU_F64 else 32, 32)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         misses, checked, done = 0, 0, 0

@@ -11,7 +11,7 @@ constexpr int kCnnHidden = 16;  // channels of the three 3x3 layers
 int cnn_n_params();
 // FP32 activations + gradient planes needed by cnn_loss_grad for n planes of H x W
 size_t cnn_workspace_floats(int n, int H, int W);
-// FP16 activations needed by the inference path
+// workspace bytes of the inference path (its activations stay in shared memory)
 size_t cnn_half_workspace_bytes(int n, int H, int W);
 // logits (n, H, W) of inputs x (n, 5, H, W); act: >= 3*16*n*H*W floats (FP32 path)
 int cnn_forward(const float *theta, const float *x, int n, int H, int W, bool fp16, float *act, float *logits,

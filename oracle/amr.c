@@ -372,6 +372,30 @@ static int fill_ghosts(Ora *o, int s, int l, double alpha)
 /* ------------------------------------------------------------------ */
 /* updating: fine -> coarse averaging (Sec. 3.1 step 4)                */
 
+/* ------------------------------------------------------------------ */
+/* latitude-longitude geometry (spherical coordinates)                  */
+/*   row J of level l spans latitudes y0 + J dy .. y0 + (J + 1) dy (deg); */
+/*   its capacity is the zone area over the area of an equatorial cell,   */
+/*   (sin phi_top - sin phi_bottom) / dphi; the latitude edge below row J  */
+/*   has relative length cos(y0 + J dy).                                  */
+
+#define ORA_D2R (3.14159265358979323846 / 180.0)
+
+static double geo_kap(const Ora *o, int l, int J)
+{
+    const double a = (o->c.y0 + (double)J * o->dyl[l]) * ORA_D2R;
+    const double b = (o->c.y0 + (double)(J + 1) * o->dyl[l]) * ORA_D2R;
+    return (sin(b) - sin(a)) / (o->dyl[l] * ORA_D2R);
+}
+
+static double geo_ced(const Ora *o, int l, int J) { return cos((o->c.y0 + (double)J * o->dyl[l]) * ORA_D2R); }
+
+static double earth_r(const Ora *o) { return o->c.earth_radius > 0.0 ? o->c.earth_radius : 6371.0e3; }
+
+/* physical cell sizes (at the equator on the sphere) */
+static double phys_dx(const Ora *o, int l) { return o->c.spherical ? earth_r(o) * (o->dxl[l] * ORA_D2R) : o->dxl[l]; }
+static double phys_dy(const Ora *o, int l) { return o->c.spherical ? earth_r(o) * (o->dyl[l] * ORA_D2R) : o->dyl[l]; }
+
 static void average_down(Ora *o, int s, int lf)
 {
     int lc = lf - 1, r = o->c.ratios[lc];
@@ -385,20 +409,30 @@ static void average_down(Ora *o, int s, int lf)
                 if (!c) continue;
                 double se = 0.0, su = 0.0, sv = 0.0;
                 int nwet = 0;
-                for (int jj = 0; jj < r; jj++)
+                double kw = 0.0, ka = 0.0;   /* spherical: capacity of the wet fine cells and of all */
+                for (int jj = 0; jj < r; jj++) {
+                    const double kf_ = o->c.spherical ? geo_kap(o, lf, Jc * r + jj) : 1.0;
                     for (int ii = 0; ii < r; ii++) {
                         size_t kf = OIDX(f, Ic * r + ii - f->i0, Jc * r + jj - f->j0);
-                        if (f->h[kf] >= drytol) { se = se + (f->h[kf] + f->B[kf]); nwet++; }
-                        su = su + f->hu[kf];
-                        sv = sv + f->hv[kf];
+                        if (o->c.spherical) {
+                            if (f->h[kf] >= drytol) { se = se + kf_ * (f->h[kf] + f->B[kf]); kw = kw + kf_; nwet++; }
+                            su = su + kf_ * f->hu[kf];
+                            sv = sv + kf_ * f->hv[kf];
+                            ka = ka + kf_;
+                        } else {
+                            if (f->h[kf] >= drytol) { se = se + (f->h[kf] + f->B[kf]); nwet++; }
+                            su = su + f->hu[kf];
+                            sv = sv + f->hv[kf];
+                        }
                     }
+                }
                 size_t kc = OIDX(c, Ic - c->i0, Jc - c->j0);
                 double hc = 0.0;
                 if (nwet > 0) {
-                    hc = se / (double)nwet - c->B[kc];
+                    hc = (o->c.spherical ? se / kw : se / (double)nwet) - c->B[kc];
                     if (hc < 0.0) hc = 0.0;
                 }
-                double rr = (double)(r * r);
+                double rr = o->c.spherical ? ka : (double)(r * r);
                 c->h[kc] = hc;
                 if (hc < drytol) { c->hu[kc] = 0.0; c->hv[kc] = 0.0; }
                 else { c->hu[kc] = su / rr; c->hv[kc] = sv / rr; }
@@ -560,15 +594,20 @@ int ora_cluster(const unsigned char *flags, const unsigned char *nestable, int n
 static double cell_rate(const Ora *o, const OPatch *p, double *sxo, double *syo)
 {
     double g = o->c.g, sx = 0.0, sy = 0.0;
-    for (int j = 0; j < p->ny; j++)
+    for (int j = 0; j < p->ny; j++) {
+        /* on the sphere a row's speeds count relative to its capacity */
+        const double kj = o->c.spherical ? geo_kap(o, p->level, p->j0 + j) : 1.0;
         for (int i = 0; i < p->nx; i++) {
             size_t k = OIDX(p, i, j);
             double h = p->h[k];
             if (h < o->c.drytol) continue;
             double c = sqrt(g * h);
-            sx = fmax(sx, fabs(p->hu[k] / h) + c);
-            sy = fmax(sy, fabs(p->hv[k] / h) + c);
+            double ax = fabs(p->hu[k] / h) + c, ay = fabs(p->hv[k] / h) + c;
+            if (o->c.spherical) { ax = ax / kj; ay = ay / kj; }
+            sx = fmax(sx, ax);
+            sy = fmax(sy, ay);
         }
+    }
     *sxo = sx; *syo = sy;
     return 0.0;
 }
@@ -583,7 +622,7 @@ static void level_cell_rate(Ora *o, int s, int l)
         sx = fmax(sx, a);
         sy = fmax(sy, b);
     }
-    double r = fmax(sx / o->dxl[l], sy / o->dyl[l]);
+    double r = fmax(sx / phys_dx(o, l), sy / phys_dy(o, l));
     o->sc[s].rate[l] = fmax(o->sc[s].rate[l], r);
 }
 
@@ -726,7 +765,15 @@ static int advance(Ora *o, int s, int l)
         OPatch *p = L->p[k];
         save_old(p);
         double a, b;
-        if (o->c.transverse)
+        if (o->c.spherical) {
+            double *kap = malloc((size_t)(p->ny + 4) * sizeof(double));
+            double *ced = malloc((size_t)(p->ny + 5) * sizeof(double));
+            for (int j = -2; j < p->ny + 2; j++) kap[j + 2] = geo_kap(o, l, p->j0 + j);
+            for (int j = -2; j <= p->ny + 2; j++) ced[j + 2] = geo_ced(o, l, p->j0 + j);
+            ora_step_patch_geo(p, o->c.g, o->c.drytol, dt, phys_dx(o, l), phys_dy(o, l), kap, ced, &a, &b);
+            free(kap);
+            free(ced);
+        } else if (o->c.transverse)
             ora_step_patch_unsplit(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
         else
             ora_step_patch(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
@@ -735,7 +782,7 @@ static int advance(Ora *o, int s, int l)
         sy = fmax(sy, b);
         S->cell_updates += (double)p->nx * (double)p->ny;
     }
-    double rate = fmax(sx / o->dxl[l], sy / o->dyl[l]);
+    double rate = fmax(sx / phys_dx(o, l), sy / phys_dy(o, l));
     if (dt * rate > o->c.cfl_max) S->cfl_viol++;
     S->rate[l] = fmax(S->rate[l], rate);
 
@@ -818,6 +865,10 @@ void *ora_create(const ora_config *cfg)
     o->c = *cfg;
     if (o->c.cluster_eff <= 0.0) o->c.cluster_eff = 0.7;
     if (!(o->c.manning_n >= 0.0)) { free(o); return NULL; }
+    if (o->c.spherical && (o->c.transverse || !(cfg->y0 > -90.0) || !(cfg->y0 + cfg->ny * cfg->dy < 90.0))) {
+        free(o);
+        return NULL;
+    }
     o->R[0] = 1;
     for (int l = 1; l < cfg->num_levels; l++) o->R[l] = o->R[l - 1] * cfg->ratios[l - 1];
     for (int l = 0; l < cfg->num_levels; l++) {
@@ -1089,12 +1140,15 @@ int ora_stats(void *vo, int s, double *out)
     Level *L = &S->lev[0];
     for (int k = 0; k < L->n; k++) {
         OPatch *p = L->p[k];
-        for (int j = 0; j < p->ny; j++)
-            for (int i = 0; i < p->nx; i++) mass = mass + p->h[OIDX(p, i, j)];
+        for (int j = 0; j < p->ny; j++) {
+            const double kj = o->c.spherical ? geo_kap(o, 0, p->j0 + j) : 1.0;
+            for (int i = 0; i < p->nx; i++)
+                mass = o->c.spherical ? mass + kj * p->h[OIDX(p, i, j)] : mass + p->h[OIDX(p, i, j)];
+        }
     }
     out[0] = S->dt1;
     out[1] = S->t;
-    out[2] = mass * o->c.dx * o->c.dy;
+    out[2] = mass * phys_dx(o, 0) * phys_dy(o, 0);
     out[3] = (double)S->cfl_viol;
     out[4] = S->cell_updates;
     for (int l = 0; l < ORA_MAX_LEVELS; l++) out[5 + l] = l < o->c.num_levels ? (double)S->lev[l].n : 0.0;

@@ -19,6 +19,13 @@ typedef struct OPatch {
 void ora_step_patch(OPatch *p, double g, double drytol, double dt, double dx, double dy,
                     double *sx, double *sy);
 
+/* split step on a latitude-longitude grid in capacity form: kap[j + 2] is the
+ * capacity of patch row j (-2 <= j < ny + 2), ced[j + 2] the relative length of
+ * the latitude edge below row j (-2 <= j <= ny + 2); dxp, dyp are the physical
+ * cell sizes at the equator.  sx, sy: largest speeds scaled to those sizes. */
+void ora_step_patch_geo(OPatch *p, double g, double drytol, double dt, double dxp, double dyp, const double *kap,
+                        const double *ced, double *sx, double *sy);
+
 /* Manning friction of the interior cells after a step (Sec. 2.1 drag D) */
 void ora_friction_patch(OPatch *p, double g, double drytol, double n, double dt);
 

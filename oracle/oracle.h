@@ -55,6 +55,8 @@ typedef struct ora_config {
     int transverse;             /* 0: dimensional splitting (the paper's GPU scheme) */
     double cluster_eff;         /* Berger-Rigoutsos acceptance efficiency */
     double manning_n;           /* Manning coefficient of the drag D (Sec. 2.1); 0: no friction */
+    int spherical;              /* 1: x = longitude, y = latitude in degrees (capacity form) */
+    double earth_radius;        /* metres (spherical; <= 0: 6371 km) */
 } ora_config;
 
 typedef struct ora_rp {

@@ -13,6 +13,7 @@
  *   Sec. 2.2, Eqs. (..._x), (..._y)          Godunov dimensional splitting, x then y
  *   Sec. 2.2, CFL condition                  nu = |s dt / dx| <= 1
  *   Sec. 2.1, drag D (Manning, n)           friction step after each level step
+ *   spherical coordinates (Sec. 1, supported for transoceanic runs): capacity-form split step
  *
  * Readings of points the paper leaves open (each is listed in the design doc):
  *   - f-wave form: the solver decomposes the flux jump (including the
@@ -206,6 +207,121 @@ static double sweep_1d(double g, double drytol, int n, double dtdx,
     }
     free(rp); free(amdq); free(apdq); free(F);
     return smax;
+}
+
+/* The y sweep on a latitude-longitude grid (capacity form).  Cell c of the
+ * column has capacity kap[c + 2] (its area over the area of an equatorial
+ * cell), edge e (between cells e-1 and e) the relative length ced[e]
+ * (cos of its latitude).  Fluctuations and correction fluxes are weighted by
+ * their edge's length and the update divided by the cell's capacity; the
+ * Courant number of edge e is dt |s| ced[e] / (dyp kbar_e), kbar_e the mean
+ * capacity of its two cells; the mass gets the divergence term
+ * (ced[i+1] - ced[i]) hv_i of the varying edge length, so that it is
+ * conserved exactly.  Returns max |s| ced / kbar over the edges 0..n. */
+static double sweep_1d_geo(double g, double drytol, int n, double dt, double dyp, const double *kap,
+                           const double *ced, const double *h, const double *hn, const double *ht, const double *B,
+                           double *ho, double *hno, double *hto)
+{
+    if (n < 1) return 0.0;
+    ora_rp *rp = (ora_rp *)malloc((size_t)(n + 3) * sizeof *rp);
+    for (int e = -1; e <= n + 1; e++) {
+        int cl = e - 1 + 2, cr = e + 2;
+        ora_riemann(g, drytol, h[cl], hn[cl], ht[cl], B[cl], h[cr], hn[cr], ht[cr], B[cr], &rp[e + 1]);
+    }
+    double (*amdq)[3] = malloc((size_t)(n + 1) * sizeof *amdq);
+    double (*apdq)[3] = malloc((size_t)(n + 1) * sizeof *apdq);
+    double (*F)[3] = malloc((size_t)(n + 1) * sizeof *F);
+    double smax = 0.0;
+    for (int e = 0; e <= n; e++) {
+        const ora_rp *r = &rp[e + 1];
+        for (int m = 0; m < 3; m++) {
+            amdq[e][m] = (w_left(r->s[0]) * r->Z[0][m] + w_left(r->s[1]) * r->Z[1][m]) + w_left(r->s[2]) * r->Z[2][m];
+            apdq[e][m] = (w_right(r->s[0]) * r->Z[0][m] + w_right(r->s[1]) * r->Z[1][m]) + w_right(r->s[2]) * r->Z[2][m];
+        }
+        if (r->wallR) { apdq[e][0] = 0.0; apdq[e][1] = 0.0; apdq[e][2] = 0.0; }
+        if (r->wallL) { amdq[e][0] = 0.0; amdq[e][1] = 0.0; amdq[e][2] = 0.0; }
+        const double kbar = 0.5 * (kap[e - 1 + 2] + kap[e + 2]);
+        const double dtdy = (dt * ced[e]) / (kbar * dyp);
+        double c[3] = {0.0, 0.0, 0.0};
+        if (!r->wallL && !r->wallR) {
+            for (int p = 0; p < 3; p++) {
+                const double *Zi = r->Z[p];
+                double dii = (Zi[0] * Zi[0] + Zi[1] * Zi[1]) + Zi[2] * Zi[2];
+                double phi = 0.0;
+                if (dii != 0.0) {
+                    int I = r->s[p] >= 0.0 ? e - 1 : e + 1;
+                    const double *ZI = rp[I + 1].Z[p];
+                    double dIi = (ZI[0] * Zi[0] + ZI[1] * Zi[1]) + ZI[2] * Zi[2];
+                    phi = ora_mc_limiter(dIi / dii);
+                }
+                double s = r->s[p];
+                double cp = (1.0 - dtdy * fabs(s)) * phi;
+                if (s < 0.0) cp = -cp;
+                else if (s == 0.0) cp = 0.0;
+                c[p] = cp;
+            }
+        }
+        for (int m = 0; m < 3; m++)
+            F[e][m] = 0.5 * ((c[0] * r->Z[0][m] + c[1] * r->Z[1][m]) + c[2] * r->Z[2][m]);
+        smax = fmax(smax, fmax(-r->s[0], r->s[2]) * (ced[e] / kbar));
+    }
+    for (int i = 0; i < n; i++) {
+        const double *q[3] = {h, hn, ht};
+        double *qo[3] = {ho, hno, hto};
+        const double dtk = dt / (kap[i + 2] * dyp);
+        for (int m = 0; m < 3; m++) {
+            double upd = (ced[i] * apdq[i][m] + ced[i + 1] * amdq[i + 1][m]) +
+                         (ced[i + 1] * F[i + 1][m] - ced[i] * F[i][m]);
+            if (m == 0) upd = upd + (ced[i + 1] - ced[i]) * hn[i + 2];
+            qo[m][i] = q[m][i + 2] - dtk * upd;
+        }
+        if (ho[i] < 0.0) ho[i] = 0.0;
+        if (ho[i] < drytol) { hno[i] = 0.0; hto[i] = 0.0; }
+    }
+    free(rp); free(amdq); free(apdq); free(F);
+    return smax;
+}
+
+/* The split step on a latitude-longitude grid: the x sweep of row j is the
+ * plane sweep with dt / (kap_j dxp) (all longitude edges have the same
+ * length), its speeds scaled by 1 / kap_j; the y sweep is sweep_1d_geo. */
+void ora_step_patch_geo(OPatch *p, double g, double drytol, double dt, double dxp, double dyp, const double *kap,
+                        const double *ced, double *sx_out, double *sy_out)
+{
+    int nx = p->nx, ny = p->ny;
+    int nmax = (nx > ny ? nx : ny) + 4;
+    double *a = malloc(4 * (size_t)nmax * sizeof(double));
+    double *o = malloc(3 * (size_t)nmax * sizeof(double));
+    double *ah = a, *an = a + nmax, *at = a + 2 * nmax, *aB = a + 3 * nmax;
+    double *oh = o, *on = o + nmax, *ot = o + 2 * nmax;
+    double sx = 0.0, sy = 0.0;
+    for (int j = -2; j < ny + 2; j++) {
+        for (int i = -2; i < nx + 2; i++) {
+            size_t k = OIDX(p, i, j);
+            ah[i + 2] = p->h[k]; an[i + 2] = p->hu[k]; at[i + 2] = p->hv[k]; aB[i + 2] = p->B[k];
+        }
+        const double kj = kap[j + 2];
+        double s = sweep_1d(g, drytol, nx, dt / (kj * dxp), ah, an, at, aB, oh, on, ot);
+        if (j >= 0 && j < ny) sx = fmax(sx, s / kj);
+        for (int i = 0; i < nx; i++) {
+            size_t k = OIDX(p, i, j);
+            p->h[k] = oh[i]; p->hu[k] = on[i]; p->hv[k] = ot[i];
+        }
+    }
+    for (int i = 0; i < nx; i++) {
+        for (int j = -2; j < ny + 2; j++) {
+            size_t k = OIDX(p, i, j);
+            ah[j + 2] = p->h[k]; an[j + 2] = p->hv[k]; at[j + 2] = p->hu[k]; aB[j + 2] = p->B[k];
+        }
+        double s = sweep_1d_geo(g, drytol, ny, dt, dyp, kap, ced + 2, ah, an, at, aB, oh, on, ot);
+        sy = fmax(sy, s);
+        for (int j = 0; j < ny; j++) {
+            size_t k = OIDX(p, i, j);
+            p->h[k] = oh[j]; p->hv[k] = on[j]; p->hu[k] = ot[j];
+        }
+    }
+    free(a); free(o);
+    *sx_out = sx; *sy_out = sy;
 }
 
 /* Q* = x-sweep(Q^n) on every row including the ghost rows (so the y-sweep

@@ -36,7 +36,7 @@ def base_config(**kw) -> dict:
     cfg = dict(nx=64, ny=64, x0=0.0, y0=0.0, dx=1.0, dy=1.0, num_levels=1, ratios=[], bc=[BC_WALL] * 4,
                g=9.81, drytol=1e-3, cfl_desired=0.9, cfl_max=1.0, dt_max=1e9, regrid_interval=0,
                flag_eta_tol=0.0, flag_depth_below=0.0, patch_max=64, level1_tile=0, regions=[],
-               n_scenarios=1, transverse=0, cluster_eff=0.7, manning_n=0.0)
+               n_scenarios=1, transverse=0, cluster_eff=0.7, manning_n=0.0, spherical=0, earth_radius=0.0)
     cfg.update(kw)
     return cfg
 

@@ -90,6 +90,11 @@ typedef struct tsu_config {
     double manning_n;           /* Manning coefficient of the drag (Sec. 2.1; the paper's runs use 0.025),
                                    applied after every level step as hu, hv <- hu, hv / (1 + dt D),
                                    D = n^2 g sqrt(hu^2 + hv^2) / h^(7/3), on wet cells; 0: none */
+    int spherical;              /* 1: latitude-longitude grid -- x0, dx longitude and y0, dy latitude in
+                                   degrees, the domain inside (-90, 90) -- advanced in capacity form
+                                   (cell capacity = zone area over an equatorial cell's, latitude edges
+                                   weighted by cos of their latitude); split scheme only */
+    double earth_radius;        /* metres, spherical grids (<= 0: 6371 km) */
 } tsu_config;
 
 typedef struct tsu_stats {

@@ -595,15 +595,19 @@ static double cell_rate(const Ora *o, const OPatch *p, double *sxo, double *syo)
 {
     double g = o->c.g, sx = 0.0, sy = 0.0;
     for (int j = 0; j < p->ny; j++) {
-        /* on the sphere a row's speeds count relative to its capacity */
+        /* on the sphere a row's x speeds count relative to its capacity, its y
+         * speeds like those of its y-edges: times ced_e / kap, the larger of
+         * its two edges (the Courant numbers of the capacity-form sweeps) */
         const double kj = o->c.spherical ? geo_kap(o, p->level, p->j0 + j) : 1.0;
+        const double cj = o->c.spherical ? fmax(geo_ced(o, p->level, p->j0 + j), geo_ced(o, p->level, p->j0 + j + 1)) / kj
+                                         : 1.0;
         for (int i = 0; i < p->nx; i++) {
             size_t k = OIDX(p, i, j);
             double h = p->h[k];
             if (h < o->c.drytol) continue;
             double c = sqrt(g * h);
             double ax = fabs(p->hu[k] / h) + c, ay = fabs(p->hv[k] / h) + c;
-            if (o->c.spherical) { ax = ax / kj; ay = ay / kj; }
+            if (o->c.spherical) { ax = ax / kj; ay = ay * cj; }
             sx = fmax(sx, ax);
             sy = fmax(sy, ay);
         }

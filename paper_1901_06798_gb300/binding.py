@@ -45,6 +45,7 @@ class tsu_config(C.Structure):
         ("n_regions", C.c_int), ("regions", (C.c_double * 6) * MAX_REGIONS), ("n_scenarios", C.c_int),
         ("transverse", C.c_int), ("cluster_eff", C.c_double), ("use_graphs", C.c_int),
         ("use_cnn", C.c_int), ("cnn_buffer", C.c_int), ("manning_n", C.c_double),
+        ("spherical", C.c_int), ("earth_radius", C.c_double),
     ]
 
 
@@ -156,6 +157,8 @@ def make_config(cfg: dict, precision: int = TSU_F64, use_graphs: bool = True) ->
     c.use_cnn = cfg.get("use_cnn", 0)
     c.cnn_buffer = cfg.get("cnn_buffer", 1)
     c.manning_n = cfg.get("manning_n", 0.0)
+    c.spherical = cfg.get("spherical", 0)
+    c.earth_radius = cfg.get("earth_radius", 0.0)
     return c
 
 

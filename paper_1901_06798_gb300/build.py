@@ -9,7 +9,8 @@
   reference arithmetic;
 * ``step_f32p.cu`` and ``step_unsplit_f32p.cu`` with contraction and CUDA's fast FP32 divide/sqrt allowed
   (the FP32 perturbation form, held to 1e-4 m of surface elevation);
-* the host runtime (``tsu_api.cpp``, ``cluster.cpp``) with the host compiler.
+* the host runtime (``tsu_api.cpp``, ``cluster.cpp``) with the host compiler, without
+  contraction (its geometry tables round like the oracle's).
 """
 from __future__ import annotations
 
@@ -70,7 +71,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *extra,
                    "-c", os.path.join(CSRC, src), "-o", obj]
         else:
-            cmd = [nvcc, "-x", "c++", "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
+            cmd = [nvcc, "-x", "c++", "-O2", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-c",
                    os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

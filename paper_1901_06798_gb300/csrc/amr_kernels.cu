@@ -258,26 +258,36 @@ __global__ void average_kernel(LevelView Fv, LevelView C, int cur_f, int cur_c, 
         if (cp < 0) { atomicOr(err, 2); continue; }
         double se = 0.0, su = 0.0, sv = 0.0;
         int nwet = 0;
-        for (int jj = 0; jj < r; jj++)
+        double kw = 0.0, ka = 0.0;   // latitude-longitude grids: capacities of the wet and of all fine cells
+        for (int jj = 0; jj < r; jj++) {
+            const double kf_ = Fv.kap ? Fv.kap[Jc * r + jj + 2] : 1.0;
             for (int ii = 0; ii < r; ii++) {
                 long long kf = fa.idx(Ic * r + ii - F.i0, Jc * r + jj - F.j0);
                 double B = (double)fB[kf];
                 double q0 = (double)f0[kf];
                 double h = PERT ? q0 - B : q0;
-                if (h >= drytol) { se = se + (PERT ? q0 : h + B); nwet++; }
-                su = su + (double)f1[kf];
-                sv = sv + (double)f2[kf];
+                if (Fv.kap) {
+                    if (h >= drytol) { se = se + kf_ * (PERT ? q0 : h + B); kw = kw + kf_; nwet++; }
+                    su = su + kf_ * (double)f1[kf];
+                    sv = sv + kf_ * (double)f2[kf];
+                    ka = ka + kf_;
+                } else {
+                    if (h >= drytol) { se = se + (PERT ? q0 : h + B); nwet++; }
+                    su = su + (double)f1[kf];
+                    sv = sv + (double)f2[kf];
+                }
             }
+        }
         const PatchDesc P = C.descs[cp];
         Acc<T> ca = acc<T>(C.arena, P);
         long long kc = ca.idx(Ic - P.i0, Jc - P.j0);
         double Bc = (double)ca.Bp()[kc];
         double hc = 0.0;
         if (nwet > 0) {
-            hc = se / (double)nwet - Bc;
+            hc = (Fv.kap ? se / kw : se / (double)nwet) - Bc;
             if (hc < 0.0) hc = 0.0;
         }
-        double rr = (double)(r * r);
+        double rr = Fv.kap ? ka : (double)(r * r);
         ca.f(cur_c, 0)[kc] = PERT ? (T)(hc + Bc) : (T)hc;
         if (hc < drytol) { ca.f(cur_c, 1)[kc] = T(0); ca.f(cur_c, 2)[kc] = T(0); }
         else { ca.f(cur_c, 1)[kc] = (T)(su / rr); ca.f(cur_c, 2)[kc] = (T)(sv / rr); }
@@ -592,6 +602,14 @@ __global__ void cell_speed_kernel(LevelView L, const int *list, int cur, double 
         T cc = PERT ? (T)sqrtf((float)((T)g * h)) : (T)sqrt((double)((T)g * h));
         T ux = a.f(cur, 1)[k] / h, uy = a.f(cur, 2)[k] / h;
         T ax = (ux < T(0) ? -ux : ux) + cc, ay = (uy < T(0) ? -uy : uy) + cc;
+        if (L.kap) {   // latitude-longitude grids: x speeds over the row's capacity, y speeds
+                       // times the larger edge length over it (the sweeps' Courant numbers)
+            const double kd = L.kap[P.j0 + j + 2];
+            const T kj = (T)kd;
+            const T cj = (T)(fmax(L.ced[P.j0 + j + 2], L.ced[P.j0 + j + 3]) / kd);
+            ax = ax / kj;
+            ay = ay * cj;
+        }
         sxT = ax > sxT ? ax : sxT;
         syT = ay > syT ? ay : syT;
     }
@@ -759,7 +777,8 @@ __global__ void mass_kernel(LevelView L, int cur, double *mass)
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         long long k = a.idx(c % P.nx, c / P.nx);
         double q0 = (double)a.f(cur, 0)[k];
-        s += PERT ? q0 - (double)a.Bp()[k] : q0;
+        double h = PERT ? q0 - (double)a.Bp()[k] : q0;
+        s += L.kap ? L.kap[P.j0 + c / P.nx + 2] * h : h;   // capacity-weighted on latitude-longitude grids
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(mass + P.scen, s);

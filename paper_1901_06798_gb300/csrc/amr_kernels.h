@@ -16,6 +16,8 @@ struct LevelView {
     const int *nbrs;        // same-level neighbour lists
     const int *cmap;        // coarse-level patch index maps
     const int *olds;        // regrid: overlapping old patches
+    const double *kap;      // latitude-longitude grids: capacity of row J at [J + 2]; null on Cartesian grids
+    const double *ced;      // latitude-longitude grids: relative length of the latitude edge below row J at [J + 2]
 };
 
 // Device control block of a context: per scenario dt, time, rates, counters.

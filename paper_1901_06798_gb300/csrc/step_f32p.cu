@@ -16,6 +16,16 @@ int launch_step_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t s
 {
     if (n_items <= 0) return 0;
     if (a.transverse) return launch_unsplit_f32p(a, n_items, threads, st);
+    if (a.kap != nullptr) {   // latitude-longitude grid (capacity form)
+        switch (threads) {
+        case 32: step_kernel_f32x2<32, 4, true><<<n_items, 32, 0, st>>>(a); break;
+        case 64: step_kernel_f32x2<64, 4, true><<<n_items, 64, 0, st>>>(a); break;
+        case 128: step_kernel_f32x2<128, 4, true><<<n_items, 128, 0, st>>>(a); break;
+        case 256: step_kernel_f32x2<256, 4, true><<<n_items, 256, 0, st>>>(a); break;
+        default: return (int)cudaErrorInvalidValue;
+        }
+        return (int)cudaGetLastError();
+    }
     switch (threads) {
     case 32: step_kernel_f32x2<32, 4><<<n_items, 32, 0, st>>>(a); break;
     case 64: step_kernel_f32x2<64, 4><<<n_items, 64, 0, st>>>(a); break;

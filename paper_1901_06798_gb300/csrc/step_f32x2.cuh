@@ -33,6 +33,12 @@
 //     A-dQ + F~ of edge 2t+2);
 //   * the y sweeps of the two columns run side by side in registers, paired
 //     the same way.
+// GEO: latitude-longitude grid in capacity form (Sec. 2.1 spherical
+// coordinates): the x sweep of row j runs with dt / (kap_j dx) and reports
+// speeds / kap_j; each y-edge's A-dQ, A+dQ and F~ are weighted by its relative
+// length ced_e once, right after the limiter (its Courant number uses
+// dt ced_e / (kbar_e dy), kbar_e the mean capacity of its two cells); the cell
+// update divides by kap_j and adds (ced_{j+1} - ced_j) hv_j to the mass.
 // Strip width W = 2 NT - 4 columns.  Registers are capped so that 12 warps fit
 // on an SM (at the uncapped ~220 registers only 8 do and the kernel waits on
 // latency; more than 12 spills).
@@ -236,7 +242,7 @@ __device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<floa
 
 }  // namespace x2
 
-template <int NT, int RING>
+template <int NT, int RING, bool GEO = false>
 __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs a)
 {
     using namespace x2;
@@ -262,6 +268,9 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
     const float dt1 = a.dt1f[P.scen];
     const float dtdx = dt1 * a.rdx, dtdy = dt1 * a.rdy;
     const float2 dtdx2 = f2(dtdx), dtdy2 = f2(dtdy);
+    // capacity of patch row j at kapP[j], relative length of the y-edge below it at cedP[j]
+    const float *kapP = GEO ? a.kapf + (P.j0 + 2) : nullptr;
+    const float *cedP = GEO ? a.cedf + (P.j0 + 2) : nullptr;
     const float g = a.gf, drytol = a.drytolf, sqrtg = a.sqrtgf;
     const int x0 = it.x0, y0 = it.y0, w = it.w, h = it.h;
     const int pitch = P.pitch;
@@ -339,6 +348,12 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
         const int slot = k % RING;
         const int r = y0 - 2 + k;
         const bool rowint = r >= y0 && r < y0 + h;
+        float rk = 1.0f;
+        float2 dtdxr = dtdx2;
+        if (GEO) {
+            rk = 1.0f / kapP[r];
+            dtdxr = f2(dtdx * rk);
+        }
 
         // ---- x edges 2t (cells 2t-1 | 2t) and 2t+1 (cells 2t | 2t+1)
         C2 L;
@@ -373,11 +388,11 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
             I.m2 = make_float2(sZy[4][a2], sZx[4][b2]);
             I.n2 = make_float2(sZy[5][a2], sZx[5][b2]);
             I.t2 = make_float2(sZy[6][a2], sZx[6][b2]);
-            limit2(xw, I, dtdx2, xam, xap, xF);
+            limit2(xw, I, dtdxr, xam, xap, xF);
             sP[0][t] = xam[0].x + xF[0].x; sP[1][t] = xam[1].x + xF[1].x; sP[2][t] = xam[2].x + xF[2].x;
             if (rowint) {
-                if (limx) smx = fmaxf(smx, fmaxf(-xw.s0.x, xw.s2.x));
-                if (limy) smx = fmaxf(smx, fmaxf(-xw.s0.y, xw.s2.y));
+                if (limx) smx = fmaxf(smx, fmaxf(-xw.s0.x, xw.s2.x) * rk);
+                if (limy) smx = fmaxf(smx, fmaxf(-xw.s0.y, xw.s2.y) * rk);
             }
         }
         __syncthreads();
@@ -390,9 +405,9 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
                 const float2 r0 = make_float2(xam[0].y + xF[0].y, sP[0][tr]);
                 const float2 r1 = make_float2(xam[1].y + xF[1].y, sP[1][tr]);
                 const float2 r2 = make_float2(xam[2].y + xF[2].y, sP[2][tr]);
-                q0 = fnma(dtdx2, add(sub(xap[0], xF[0]), r0), q0);
-                q1 = fnma(dtdx2, add(sub(xap[1], xF[1]), r1), q1);
-                q2 = fnma(dtdx2, add(sub(xap[2], xF[2]), r2), q2);
+                q0 = fnma(dtdxr, add(sub(xap[0], xF[0]), r0), q0);
+                q1 = fnma(dtdxr, add(sub(xap[1], xF[1]), r1), q1);
+                q2 = fnma(dtdxr, add(sub(xap[2], xF[2]), r2), q2);
             }
             post2(q0, q1, q2, xc.B, drytol);
 
@@ -415,15 +430,32 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
                         I.n2 = make_float2(a2 ? wo.z2n.x : wn.z2n.x, b2 ? wo.z2n.y : wn.z2n.y);
                         I.t2 = make_float2(a2 ? wo.z2t.x : wn.z2t.x, b2 ? wo.z2t.y : wn.z2t.y);
                         float2 yam[3];
-                        limit2(wm, I, dtdy2, yam, apm, Fm);
-                        if (outx) smy = fmaxf(smy, fmaxf(-wm.s0.x, wm.s2.x));
-                        if (outy) smy = fmaxf(smy, fmaxf(-wm.s0.y, wm.s2.y));
+                        float2 dtdye = dtdy2;
+                        float cr = 1.0f, ce = 1.0f;
+                        if (GEO) {
+                            ce = cedP[e];
+                            cr = ce / (0.5f * (kapP[e - 1] + kapP[e]));
+                            dtdye = f2(dtdy * cr);
+                        }
+                        limit2(wm, I, dtdye, yam, apm, Fm);
+                        if (outx) smy = fmaxf(smy, fmaxf(-wm.s0.x, wm.s2.x) * cr);
+                        if (outy) smy = fmaxf(smy, fmaxf(-wm.s0.y, wm.s2.y) * cr);
+                        if (GEO) {
+                            const float2 ce2 = f2(ce);
+#pragma unroll
+                            for (int m = 0; m < 3; m++) { yam[m] = mul(ce2, yam[m]); apm[m] = mul(ce2, apm[m]); Fm[m] = mul(ce2, Fm[m]); }
+                        }
                         const int rc = r - 2;
                         if (rc >= y0 && rc < y0 + h) {
                             // cell row r-2: y-edges r-2 (A+dQ, F~ from the last row) and r-1
-                            float2 n0 = fnma(dtdy2, add(add(apo[0], yam[0]), sub(Fm[0], Fo[0])), ycm2.q0);
-                            float2 n1 = fnma(dtdy2, add(add(apo[1], yam[1]), sub(Fm[1], Fo[1])), ycm2.hn);
-                            float2 n2 = fnma(dtdy2, add(add(apo[2], yam[2]), sub(Fm[2], Fo[2])), ycm2.ht);
+                            float2 dtk = dtdy2, m0 = add(add(apo[0], yam[0]), sub(Fm[0], Fo[0]));
+                            if (GEO) {
+                                dtk = f2(dtdy / kapP[rc]);
+                                m0 = fma(f2(ce - cedP[rc]), ycm2.hn, m0);   // divergence of the edge length
+                            }
+                            float2 n0 = fnma(dtk, m0, ycm2.q0);
+                            float2 n1 = fnma(dtk, add(add(apo[1], yam[1]), sub(Fm[1], Fo[1])), ycm2.hn);
+                            float2 n2 = fnma(dtk, add(add(apo[2], yam[2]), sub(Fm[2], Fo[2])), ycm2.ht);
                             post2(n0, n1, n2, ycm2.B, drytol);
                             if (a.manningf > 0.0f)   // y frame: n2 = hu, n1 = hv
                                 friction2(n0, n2, n1, ycm2.B, drytol, a.manningf, dt1 * a.rR);

@@ -20,6 +20,14 @@
 //     the x and y sweeps are fused in one kernel;
 //   * the max |s| of the edges touching interior cells is reduced with warp
 //     shuffles, then one atomicMax per CTA (Sec. 4.3 reduction).
+// GEO: latitude-longitude grid in capacity form (Sec. 2.1 spherical
+// coordinates; LeVeque's capacity-form wave propagation): row j has capacity
+// kap_j, the latitude edge below it the relative length ced_j.  The x sweep of
+// row j runs with dt / (kap_j dx) and reports speeds / kap_j; each y-edge's
+// fluctuations and correction flux are weighted by ced_e, its Courant number
+// uses dt ced_e / (kbar_e dy) (kbar_e the mean capacity of its two cells), the
+// cell update divides by kap_j, and the mass gets the term
+// (ced_{j+1} - ced_j) hv_j of the varying edge length.
 // The arithmetic of riemann()/limit() follows the FP64 oracle operation by
 // operation; the FP64 instantiation is compiled without contraction so the
 // two agree to the last bit.
@@ -238,7 +246,11 @@ __device__ __forceinline__ void atomic_max_speed(unsigned long long *dst, double
     atomicMax(dst, (unsigned long long)__double_as_longlong(v));
 }
 
-template <typename T, bool PERT, int NT, int RING>
+template <typename T> __device__ __forceinline__ const T *geo_table(const double *d, const float *f);
+template <> __device__ __forceinline__ const double *geo_table<double>(const double *d, const float *) { return d; }
+template <> __device__ __forceinline__ const float *geo_table<float>(const double *, const float *f) { return f; }
+
+template <typename T, bool PERT, int NT, int RING, bool GEO = false>
 __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
 {
     static_assert(RING >= 3, "the derived values of row k+1 need its copy complete at iteration k");
@@ -269,6 +281,9 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
     const int x0 = it.x0, y0 = it.y0, w = it.w, h = it.h;
     const int pitch = P.pitch;
     const int nrows = h + 4;
+    // capacity of patch row j at kapP[j], relative length of the y-edge below it at cedP[j]
+    const T *kapP = GEO ? geo_table<T>(a.kap, a.kapf) + (P.j0 + 2) : nullptr;
+    const T *cedP = GEO ? geo_table<T>(a.ced, a.cedf) + (P.j0 + 2) : nullptr;
     // ring cell t <-> patch column x0 - 2 + t (storage column x0 + t)
     const bool loader = t < w + 4;
     const long long colofs = (long long)(x0 + t);
@@ -316,6 +331,8 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
         const int slot = k % RING;
         const int r = y0 - 2 + k;            // patch-local row of this iteration
         const bool rowint = r >= y0 && r < y0 + h;
+        const T kr = GEO ? kapP[r] : T(1);
+        const T dtdxr = GEO ? (T)(dt / (kr * a.dx)) : dtdx;
 
         // ---- x sweep: Riemann problem at edge t (ring cells t, t+1)
         Wave<T> xw;
@@ -344,10 +361,13 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
 #pragma unroll
                 for (int m = 0; m < 3; m++) ZI[p][m] = sZ[p * 3 + m][nb];
             }
-            limit<T>(xw, ZI, dtdx, xam, xap, xF);
+            limit<T>(xw, ZI, dtdxr, xam, xap, xF);
 #pragma unroll
             for (int m = 0; m < 3; m++) { sAp[m][t] = xap[m]; sF[m][t] = xF[m]; }
-            if (rowint) smx = dmax<T>(smx, dmax<T>(-xw.s[0], xw.s[2]));
+            if (rowint) {
+                const T se = dmax<T>(-xw.s[0], xw.s[2]);
+                smx = dmax<T>(smx, GEO ? se / kr : se);
+            }
         }
         __syncthreads();
 
@@ -357,7 +377,7 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
 #pragma unroll
             for (int m = 0; m < 3; m++) {
                 T u = (sAp[m][t - 1] + xam[m]) + (xF[m] - sF[m][t - 1]);
-                qs[m] = qs[m] - dtdx * u;
+                qs[m] = qs[m] - dtdxr * u;
             }
             postprocess<T, PERT>(qs[0], qs[1], qs[2], xc.B, drytol);
 
@@ -378,15 +398,34 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
 #pragma unroll
                             for (int m = 0; m < 3; m++) ZI[p][m] = ymid.s[p] >= T(0) ? yold.Z[p][m] : ynew.Z[p][m];
                         T yam[3], yapn[3], yFn[3];
-                        limit<T>(ymid, ZI, dtdy, yam, yapn, yFn);
-                        smy = dmax<T>(smy, dmax<T>(-ymid.s[0], ymid.s[2]));
+                        T dtdye = dtdy, cratio = T(1);
+                        if (GEO) {
+                            const T kbar = T(0.5) * (kapP[e - 1] + kapP[e]);
+                            dtdye = ((T)dt * cedP[e]) / (kbar * (T)a.dy);
+                            cratio = cedP[e] / kbar;
+                        }
+                        limit<T>(ymid, ZI, dtdye, yam, yapn, yFn);
+                        const T se = dmax<T>(-ymid.s[0], ymid.s[2]);
+                        smy = dmax<T>(smy, GEO ? se * cratio : se);
                         const int rc = r - 2;   // cell between y-edges r-2 and r-1
                         if (rc >= y0 && rc < y0 + h) {
                             T qn[3] = {qm2[0], qm2[2], qm2[1]};   // (mass, normal = hv, transverse = hu)
+                            if (GEO) {
+                                const T clo = cedP[rc], chi = cedP[e];
+                                const T dtk = (T)dt / (kapP[rc] * (T)a.dy);
+                                const T hv = qm2[2];
 #pragma unroll
-                            for (int m = 0; m < 3; m++) {
-                                T u = (yap[m] + yam[m]) + (yFn[m] - yF[m]);
-                                qn[m] = qn[m] - dtdy * u;
+                                for (int m = 0; m < 3; m++) {
+                                    T u = (clo * yap[m] + chi * yam[m]) + (chi * yFn[m] - clo * yF[m]);
+                                    if (m == 0) u = u + (chi - clo) * hv;
+                                    qn[m] = qn[m] - dtk * u;
+                                }
+                            } else {
+#pragma unroll
+                                for (int m = 0; m < 3; m++) {
+                                    T u = (yap[m] + yam[m]) + (yFn[m] - yF[m]);
+                                    qn[m] = qn[m] - dtdy * u;
+                                }
                             }
                             postprocess<T, PERT>(qn[0], qn[1], qn[2], Bm2, drytol);
                             if (a.manning > 0.0)   // y frame: qn[2] = hu, qn[1] = hv

@@ -173,6 +173,10 @@ struct Lvl {
     int cur = 0, maxring = 0, maxcells = 0;
     int nxl = 0, nyl = 0;
     double dx = 0, dy = 0, R = 1;
+    // latitude-longitude grids: physical equatorial cell sizes and the row tables
+    double dxp = 0, dyp = 0;
+    DevBuf<double> dKap, dCed;
+    DevBuf<float> dKapF, dCedF;
 };
 
 // Spatial buckets of one scenario's patches on one level, for neighbour and
@@ -291,6 +295,17 @@ struct tsu_ctx {
 
     // ------------------------------------------------------------ helpers
     int nt() const { return step_nt > 0 ? step_nt : (prec == TSU_F64 ? step_threads_f64() : step_threads_f32p()); }
+    // physical cell sizes of level l (of an equatorial cell on latitude-longitude grids)
+    double pdx(int l) const { return c.spherical ? lv[l].dxp : lv[l].dx; }
+    double pdy(int l) const { return c.spherical ? lv[l].dyp : lv[l].dy; }
+    void set_geometry(StepArgs &a, int l) const
+    {
+        a.dx = pdx(l);
+        a.dy = pdy(l);
+        if (c.spherical) {
+            a.kap = lv[l].dKap.p; a.ced = lv[l].dCed.p; a.kapf = lv[l].dKapF.p; a.cedf = lv[l].dCedF.p;
+        }
+    }
     int seg() const { return seg_rows > 0 ? seg_rows : (prec == TSU_F64 ? 128 : 64); }
     void kl(int e, const char *what)
     {
@@ -311,6 +326,8 @@ struct tsu_ctx {
         v.arena = arena.base;
         v.nxl = lv[l].nxl; v.nyl = lv[l].nyl;
         v.nbrs = lv[l].dNbrs.p; v.cmap = lv[l].dCmap.p; v.olds = lv[l].dOlds.p;
+        v.kap = c.spherical ? lv[l].dKap.p : nullptr;
+        v.ced = c.spherical ? lv[l].dCed.p : nullptr;
         return v;
     }
     TopoSet topo()
@@ -728,7 +745,7 @@ struct tsu_ctx {
             // wave-speed rate of the new patches for the next dt
             kl(k_cell_speed(prec, view(lf), L.dList.p, (int)fresh.size(), L.maxcells, L.cur, c.g, c.drytol, smax.p, st),
                "cell speed");
-            kl(k_post_level(ctrl(), lf, nscen, L.R, L.dx, L.dy, c.cfl_max, 1, st), "post rate");
+            kl(k_post_level(ctrl(), lf, nscen, L.R, pdx(lf), pdy(lf), c.cfl_max, 1, st), "post rate");
         }
         // release the replaced patches of the regridded scenarios
         for (size_t k = 0; k < oldP.size(); k++)
@@ -765,15 +782,16 @@ struct tsu_ctx {
             }
             StepArgs a{};
             a.descs = L.dP.p; a.items = L.dItems.p; a.arena = arena.base; a.cur = L.cur; a.dt1 = dt1.p;
-            a.smax = smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = c.g; a.drytol = c.drytol;
+            a.smax = smax.p; a.R = L.R; a.g = c.g; a.drytol = c.drytol;
             a.dt1f = dt1f.p;
             a.transverse = c.transverse;
             a.manning = (c.manning_n * c.manning_n) * c.g;
+            set_geometry(a, l);
             set_f32_constants(a);
             int e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
                                     : launch_step_f32p(a, (int)L.items.size(), nt(), st);
             kl(e, "patch step");
-            kl(k_post_level(ctrl(), l, nscen, L.R, L.dx, L.dy, c.cfl_max, 0, st), "post step");
+            kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, 0, st), "post step");
             L.cur ^= 1;
         }
         if (l + 1 < nlev && !lv[l + 1].P.empty()) {
@@ -917,7 +935,7 @@ struct tsu_ctx {
         }
         kl(k_cell_speed(prec, view(0), L.dList.p, (int)all.size(), L.maxcells, L.cur, c.g, c.drytol, smax.p, st),
            "cell speed");
-        kl(k_post_level(ctrl(), 0, nscen, L.R, L.dx, L.dy, c.cfl_max, 1, st), "post rate");
+        kl(k_post_level(ctrl(), 0, nscen, L.R, pdx(0), pdy(0), c.cfl_max, 1, st), "post rate");
         initialized = true;
         std::vector<int> everyone(nscen);
         for (int s = 0; s < nscen; s++) everyone[s] = s;
@@ -1128,6 +1146,7 @@ struct tsu_ctx {
         for (auto &L : lv) {
             L.dP.release(); L.dItems.release(); L.dNbrs.release(); L.dCmap.release(); L.dBc.release();
             L.dOlds.release(); L.dList.release();
+            L.dKap.release(); L.dCed.release(); L.dKapF.release(); L.dCedF.release();
         }
         for (auto &g : grids) if (g.dev) cudaFreeAsync(g.dev, st);
         dGrids.release(); dGridScen.release(); dEtaIdx.release();
@@ -1183,6 +1202,8 @@ int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out)
     if (c.nx < 2 || c.ny < 2 || !(c.dx > 0) || !(c.dy > 0)) return TSU_ERR_ARG;
     if (c.num_levels < 1 || c.num_levels > TSU_MAX_LEVELS || c.n_scenarios < 1 || (c.transverse != 0 && c.transverse != 1) ||
         !(c.manning_n >= 0.0)) return TSU_ERR_ARG;
+    if (c.spherical != 0 && (c.spherical != 1 || c.transverse || !(c.y0 > -90.0) || !(c.y0 + c.ny * c.dy < 90.0)))
+        return TSU_ERR_ARG;
     for (int l = 0; l + 1 < c.num_levels; l++)
         if (c.ratios[l] < 2) return TSU_ERR_ARG;
     if (c.n_regions < 0 || c.n_regions > TSU_MAX_REGIONS || c.patch_max < 1) return TSU_ERR_ARG;
@@ -1215,6 +1236,29 @@ int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out)
             x->lv[l].dx = c.dx / (double)R;
             x->lv[l].dy = c.dy / (double)R;
             rl[l] = (double)R;
+        }
+        if (c.spherical) {
+            // latitude-longitude geometry: rows J of level l span y0 + J dy .. y0 + (J + 1) dy degrees;
+            // capacity (sin top - sin bottom) / dphi, latitude edge below row J weighted by its cos
+            const double d2r = 3.14159265358979323846 / 180.0;
+            const double Re = c.earth_radius > 0.0 ? c.earth_radius : 6371.0e3;
+            for (int l = 0; l < x->nlev; l++) {
+                Lvl &L = x->lv[l];
+                L.dxp = Re * (L.dx * d2r);
+                L.dyp = Re * (L.dy * d2r);
+                std::vector<double> kap(L.nyl + 4), ced(L.nyl + 5);
+                std::vector<float> kapf(L.nyl + 4), cedf(L.nyl + 5);
+                for (int J = -2; J < L.nyl + 2; J++) {
+                    const double a = (c.y0 + (double)J * L.dy) * d2r, b = (c.y0 + (double)(J + 1) * L.dy) * d2r;
+                    kap[J + 2] = (std::sin(b) - std::sin(a)) / (L.dy * d2r);
+                    kapf[J + 2] = (float)kap[J + 2];
+                }
+                for (int J = -2; J <= L.nyl + 2; J++) {
+                    ced[J + 2] = std::cos((c.y0 + (double)J * L.dy) * d2r);
+                    cedf[J + 2] = (float)ced[J + 2];
+                }
+                L.dKap.upload(kap, x->st); L.dCed.upload(ced, x->st); L.dKapF.upload(kapf, x->st); L.dCedF.upload(cedf, x->st);
+            }
         }
         const int S = x->nscen;
         cudaStream_t st = x->st;
@@ -1462,7 +1506,7 @@ int tsu_get_stats(tsu_ctx *ctx, int scen, tsu_stats *out)
         ctx->sync();
         out->dt = v[0];
         out->t = v[1];
-        out->mass = v[2] * ctx->c.dx * ctx->c.dy;
+        out->mass = v[2] * ctx->pdx(0) * ctx->pdy(0);
         out->cell_updates = v[3];
         out->cfl_violations = vi;
         for (int l = 0; l < ctx->nlev; l++)
@@ -1520,9 +1564,10 @@ int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, 
                         StepArgs sa{};
                         sa.descs = L.dP.p; sa.items = L.dItems.p; sa.arena = ctx->arena.base; sa.cur = L.cur;
                         sa.dt1 = ctx->zero_dt.p; sa.dt1f = ctx->zero_dtf.p; sa.smax = ctx->smax.p; sa.R = L.R;
-                        sa.dx = L.dx; sa.dy = L.dy; sa.g = ctx->c.g; sa.drytol = ctx->c.drytol;
+                        sa.g = ctx->c.g; sa.drytol = ctx->c.drytol;
                         sa.transverse = ctx->c.transverse;
                         sa.manning = (ctx->c.manning_n * ctx->c.manning_n) * ctx->c.g;
+                        ctx->set_geometry(sa, l);
                         set_f32_constants(sa);
                         int e = ctx->prec == TSU_F64 ? launch_step_f64(sa, (int)L.items.size(), ctx->nt(), ctx->st)
                                                      : launch_step_f32p(sa, (int)L.items.size(), ctx->nt(), ctx->st);
@@ -1642,17 +1687,18 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
             }
             StepArgs a{};
             a.descs = L.dP.p; a.items = L.dItems.p; a.arena = ctx->arena.base; a.cur = L.cur; a.dt1 = ctx->dt1.p;
-            a.smax = ctx->smax.p; a.R = L.R; a.dx = L.dx; a.dy = L.dy; a.g = ctx->c.g; a.drytol = ctx->c.drytol;
+            a.smax = ctx->smax.p; a.R = L.R; a.g = ctx->c.g; a.drytol = ctx->c.drytol;
             a.dt1f = ctx->dt1f.p;
             a.transverse = ctx->c.transverse;
             a.manning = (ctx->c.manning_n * ctx->c.manning_n) * ctx->c.g;
+            ctx->set_geometry(a, 0);
             set_f32_constants(a);
             CK(cudaEventRecord(ev[2 * k], ctx->st));
             int e = ctx->prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), ctx->nt(), ctx->st)
                                          : launch_step_f32p(a, (int)L.items.size(), ctx->nt(), ctx->st);
             ctx->kl(e, "patch step");
             CK(cudaEventRecord(ev[2 * k + 1], ctx->st));
-            ctx->kl(k_post_level(ctx->ctrl(), 0, ctx->nscen, L.R, L.dx, L.dy, ctx->c.cfl_max, 0, ctx->st), "post step");
+            ctx->kl(k_post_level(ctx->ctrl(), 0, ctx->nscen, L.R, ctx->pdx(0), ctx->pdy(0), ctx->c.cfl_max, 0, ctx->st), "post step");
             L.cur ^= 1;
             ctx->kl(k_end_step(ctx->ctrl(), ctx->nscen, ctx->st), "end step");
             for (int s = 0; s < ctx->nscen; s++) ctx->nsteps[s][0]++;

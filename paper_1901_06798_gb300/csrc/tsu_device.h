@@ -46,6 +46,11 @@ struct StepArgs {
     double manning;             // n^2 g of the friction step (0: none)
     float manningf;
     float rR;                   // 1 / R (FP32 level time step = dt1f * rR)
+    // latitude-longitude grids (capacity form): dx, dy above are the physical
+    // sizes of an equatorial cell; capacity of global row J at kap[J + 2], relative
+    // length of the latitude edge below row J at ced[J + 2]; null on Cartesian grids
+    const double *kap, *ced;
+    const float *kapf, *cedf;
 };
 
 // FP32 launch constants of a level

@@ -24,6 +24,10 @@ Workloads (sizes in cells of level 1):
              semicircular bay on the beach, 10 gauges (deep, shelf, bay).
   ensemble   independent scenarios on one bathymetry, uplift centres and
              amplitudes drawn from numpy PCG64 with seed 1901.
+  lonlat(w)  any of the above on a latitude-longitude grid (the coordinates
+             of the paper's ocean runs): x and y in metres become longitude
+             and latitude in degrees, cell sizes and input grids scaled to
+             match at the domain's middle latitude.
 """
 from __future__ import annotations
 
@@ -261,3 +265,35 @@ def load(obj, w: dict):
         obj.add_gauges(w["gauges"])
     obj.init()
     return obj
+
+
+def lonlat(w: dict, lon0: float = 140.0, lat0: float = 30.0, radius: float = 6371.0e3) -> dict:
+    """The workload ``w`` (Cartesian, metres) placed on a latitude-longitude
+    grid: the point (x, y) goes to longitude lon0 + (x - x0) / (R cos(phi_m))
+    and latitude lat0 + (y - y0) / R (in degrees; phi_m the domain's middle
+    latitude), so the grid keeps its cell counts and, at phi_m, its cell sizes
+    in metres.  Every input grid, region, uplift and gauge is mapped the same
+    way; velocities stay in m/s.  Sets spherical = 1."""
+    cfg = dict(w["cfg"])
+    d2r = np.pi / 180.0
+    ky = 1.0 / (radius * d2r)
+    phim = lat0 + 0.5 * cfg["ny"] * cfg["dy"] * ky
+    kx = 1.0 / (radius * d2r * np.cos(phim * d2r))
+    xo, yo = cfg["x0"], cfg["y0"]
+
+    def mx(x):
+        return lon0 + (x - xo) * kx
+
+    def my(y):
+        return lat0 + (y - yo) * ky
+
+    cfg.update(x0=lon0, y0=lat0, dx=cfg["dx"] * kx, dy=cfg["dy"] * ky, spherical=1, earth_radius=radius,
+               regions=[[mx(r[0]), my(r[1]), mx(r[2]), my(r[3]), r[4], r[5]] for r in cfg.get("regions", [])])
+    out = dict(w, cfg=cfg, name=w.get("name", "workload") + "_lonlat")
+    out["topo"] = [(B, mx(x0), my(y0), dx * kx, dy * ky) for (B, x0, y0, dx, dy) in w["topo"]]
+    out["eta"] = [(s, e, mx(x0), my(y0), dx * kx, dy * ky) for (s, e, x0, y0, dx, dy) in w["eta"]]
+    out["uplift"] = [(s, d, mx(x0), my(y0), dx * kx, dy * ky) for (s, d, x0, y0, dx, dy) in w["uplift"]]
+    out["uv"] = [(s, u, v, mx(x0), my(y0), dx * kx, dy * ky) for (s, u, v, x0, y0, dx, dy) in w.get("uv", [])]
+    g = np.asarray(w.get("gauges", np.zeros((0, 2))), dtype=float).reshape(-1, 2)
+    out["gauges"] = np.stack([mx(g[:, 0]), my(g[:, 1])], axis=1) if len(g) else g
+    return out

@@ -84,7 +84,9 @@ typedef struct tsu_config {
                                    GeoClaw scheme Sec. 5 compares against; corner transport
                                    upwind, LeVeque 1997) */
     double cluster_eff;         /* Berger-Rigoutsos box efficiency, 0.7 if <= 0 */
-    int use_graphs;             /* capture repeated coarse steps as a CUDA graph */
+    int use_graphs;             /* replay coarse steps as CUDA graphs: pairs of steps within one tsu_step
+                                   call, and single steps (one graph per buffer-parity pattern) when no
+                                   regrid falls in the next three; recaptured after every regrid */
     int use_cnn;                /* add the flag predictor's cells to the flags (tsu_cnn_set_weights) */
     int cnn_buffer;             /* flag buffer width used together with the predictor (instead of b) */
     double manning_n;           /* Manning coefficient of the drag (Sec. 2.1; the paper's runs use 0.025),

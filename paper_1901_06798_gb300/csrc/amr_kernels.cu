@@ -786,11 +786,15 @@ __global__ void mass_kernel(LevelView L, int cur, double *mass)
 
 // ---------------------------------------------------------------- launchers
 
+// CTAs per patch: enough to cover its work, at most 64 when there are many
+// patches, and up to 16 per SM over the whole grid when there are few (a
+// single large patch must still fill the GPU)
 static dim3 grid_for(int per_patch, int npatch, int threads)
 {
     int bx = (per_patch + threads - 1) / threads;
+    const int cap = npatch >= 38 ? 64 : (152 * 16) / (npatch > 0 ? npatch : 1);
     if (bx < 1) bx = 1;
-    if (bx > 64) bx = 64;
+    if (bx > cap) bx = cap;
     return dim3(bx, npatch);
 }
 
@@ -958,14 +962,28 @@ int k_gauges(int prec, const GaugeArgs &ga, const CtrlView &cv, cudaStream_t st)
     return (int)cudaGetLastError();
 }
 
-int k_read_field(int prec, const LevelView &L, int npatch, int cur, int scen, int field, double *dst, int nx, int ny,
-                 double x0, double y0, double dx, double dy, double X0, double Y0, double dxl, double dyl,
+int k_read_field(int prec, const LevelView &L, int npatch, int maxpts, int cur, int scen, int field, double *dst, int nx,
+                 int ny, double x0, double y0, double dx, double dy, double X0, double Y0, double dxl, double dyl,
                  cudaStream_t st)
 {
     if (npatch <= 0) return 0;
-    dim3 g(16, npatch);
+    dim3 g = grid_for(maxpts, npatch, 128);
     TSU_DISPATCH(prec, read_field_kernel,
                  <<<g, 128, 0, st>>>(L, cur, scen, field, dst, nx, ny, x0, y0, dx, dy, X0, Y0, dxl, dyl));
+    return (int)cudaGetLastError();
+}
+
+__global__ void fill_kernel(double *p, long long n, double v)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        p[k] = v;
+}
+
+int k_fill(double *p, long long n, double v, cudaStream_t st)
+{
+    if (n <= 0) return 0;
+    long long b = (n + 255) / 256;
+    fill_kernel<<<(int)(b < 152 * 8 ? b : 152 * 8), 256, 0, st>>>(p, n, v);
     return (int)cudaGetLastError();
 }
 

@@ -112,9 +112,11 @@ int k_begin_step(const CtrlView &cv, int nscen, int nlev, const double *Rl, doub
                  cudaStream_t st);
 int k_end_step(const CtrlView &cv, int nscen, cudaStream_t st);
 int k_gauges(int prec, const GaugeArgs &ga, const CtrlView &cv, cudaStream_t st);
-int k_read_field(int prec, const LevelView &L, int npatch, int cur, int scen, int field, double *dst, int nx, int ny,
-                 double x0, double y0, double dx, double dy, double X0, double Y0, double dxl, double dyl,
+// maxpts: an upper bound on the output points one patch covers (sizes the grid)
+int k_read_field(int prec, const LevelView &L, int npatch, int maxpts, int cur, int scen, int field, double *dst, int nx,
+                 int ny, double x0, double y0, double dx, double dy, double X0, double Y0, double dxl, double dyl,
                  cudaStream_t st);
+int k_fill(double *p, long long n, double v, cudaStream_t st);
 int k_patch_out(int prec, const LevelView &L, int p, int ncells, int cur, double *out, cudaStream_t st);
 int k_cnn_features(int prec, const LevelView &L, int npatch, int maxcells, int cur, const int *scen_slot,
                    const uint8_t *raw, float *feat, double drytol, const CnnWindow &win, cudaStream_t st);

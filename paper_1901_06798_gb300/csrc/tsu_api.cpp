@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <stdexcept>
 #include <string>
@@ -291,7 +292,20 @@ struct tsu_ctx {
     cudaGraphExec_t gexec = nullptr;
     long long graph_version = -1;
     long long graph_kernels = 0;
+    // one-coarse-step graphs, keyed by the levels' buffer parities at their start
+    struct StepGraph {
+        unsigned key;
+        cudaGraphExec_t ex;
+        std::array<int, kMaxLevels> post;   // the parities it leaves
+        long long kernels;
+    };
+    std::vector<StepGraph> g1;
+    long long g1_version = -1;
     DevBuf<double> dstage;
+    PinnedHost hsmall;                         // page-locked readback of error flag, CFL counts, times
+    PinnedHost hstage;                         // page-locked double buffer of staged device-to-host reads
+    cudaEvent_t stage_ev[8] = {};
+    int device = 0;                            // the CUDA device current at tsu_create
 
     // ------------------------------------------------------------ helpers
     int nt() const { return step_nt > 0 ? step_nt : (prec == TSU_F64 ? step_threads_f64() : step_threads_f32p()); }
@@ -877,6 +891,11 @@ struct tsu_ctx {
                 }
                 nsamp += gxy.empty() ? 0 : 2;
                 done += 2;
+            } else if (c.use_graphs && !regrid_ahead(3)) {
+                // single steps (a caller reading back every step): a graph per parity
+                // pattern, captured only when it will be launched again before a regrid
+                one_step_graph();
+                done++;
             } else {
                 coarse_step();
                 done++;
@@ -884,18 +903,137 @@ struct tsu_ctx {
         }
     }
 
-    void check_device_errors(bool &cfl)
+    unsigned parity_key() const
     {
-        int e = 0;
-        std::vector<long long> v(nscen);
-        CK(cudaMemcpyAsync(&e, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(v.data(), viol.p, nscen * sizeof(long long), cudaMemcpyDeviceToHost, st));
+        unsigned k = 0;
+        for (int l = 0; l < nlev; l++) k |= (unsigned)(lv[l].cur & 1) << l;
+        return k;
+    }
+
+    // One coarse step as a graph launch.  A coarse step flips the buffer parity
+    // of level 1 (and of any level with an odd number of substeps), so one graph
+    // is captured per parity pattern and reused while the hierarchy is unchanged.
+    void one_step_graph()
+    {
+        if (g1_version != hier_version) {
+            for (auto &g : g1) cudaGraphExecDestroy(g.ex);
+            g1.clear();
+            g1_version = hier_version;
+        }
+        const unsigned key = parity_key();
+        int gi = -1;
+        for (size_t k = 0; k < g1.size(); k++)
+            if (g1[k].key == key) gi = (int)k;
+        if (gi < 0) {
+            const long long l0 = launches, ns0 = nsamp;
+            const std::vector<std::array<long long, kMaxLevels>> ns = nsteps;
+            std::array<int, kMaxLevels> pre{};
+            for (int l = 0; l < nlev; l++) pre[l] = lv[l].cur;
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            try {
+                coarse_step();
+            } catch (...) {
+                cudaStreamEndCapture(st, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            CK(cudaStreamEndCapture(st, &g));
+            StepGraph sg{};
+            sg.key = key;
+            const cudaError_t e = cudaGraphInstantiate(&sg.ex, g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+            sg.kernels = launches - l0;
+            for (int l = 0; l < nlev; l++) sg.post[l] = lv[l].cur;
+            // the capture only recorded the step: put the host state back
+            launches = l0;
+            nsteps = ns;
+            nsamp = ns0;
+            for (int l = 0; l < nlev; l++) lv[l].cur = pre[l];
+            g1.push_back(sg);
+            gi = (int)g1.size() - 1;
+        }
+        CK(cudaGraphLaunch(g1[gi].ex, st));
+        launches += g1[gi].kernels;
+        for (int l = 0; l < nlev; l++) lv[l].cur = g1[gi].post[l];
+        long long per = 1;
+        for (int l = 0; l < nlev; l++) {
+            for (int s = 0; s < nscen; s++)
+                if (l == 0 || has_patches(s, l)) nsteps[s][l] += per;
+            if (l + 1 < nlev) per *= ratio[l];
+        }
+        nsamp += gxy.empty() ? 0 : 1;
+    }
+
+    // Error flag and CFL-violation counts (and, with t_out, every scenario's
+    // time) in one synchronisation, through page-locked memory.
+    void check_device_errors(bool &cfl, double *t_out = nullptr)
+    {
+        const size_t ns = (size_t)nscen;
+        hsmall.ensure(64 + ns * (sizeof(long long) + sizeof(double)));
+        int *e = reinterpret_cast<int *>(hsmall.p);
+        long long *v = reinterpret_cast<long long *>(hsmall.p + 64);
+        double *tt = reinterpret_cast<double *>(hsmall.p + 64 + ns * sizeof(long long));
+        CK(cudaMemcpyAsync(e, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(v, viol.p, ns * sizeof(long long), cudaMemcpyDeviceToHost, st));
+        if (t_out) CK(cudaMemcpyAsync(tt, t.p, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
         sync();
-        if (e) throw Err(TSU_ERR_NESTING, "a ghost cell or coarse cell had no covering patch (nesting)");
+        if (*e) throw Err(TSU_ERR_NESTING, "a ghost cell or coarse cell had no covering patch (nesting)");
+        if (t_out) std::memcpy(t_out, tt, ns * sizeof(double));
         long long tot = 0;
-        for (auto x : v) tot += x;
+        for (size_t s = 0; s < ns; s++) tot += v[s];
         cfl = tot > viol_seen;
         viol_seen = tot;
+    }
+
+    // Device-to-host copy of n doubles through page-locked staging.  Chunks go
+    // round-robin to up to kWorkers host threads, each with its own staging
+    // slot and event: the link copies one chunk while the other threads move
+    // theirs into dst (and take dst's first-touch page faults) in parallel.
+    void d2h_staged(double *dst, const double *src, size_t n)
+    {
+        constexpr size_t kChunk = (size_t)1 << 19;   // doubles per chunk (4 MiB)
+        constexpr int kWorkers = 8;
+        if (n <= 4096) {
+            hsmall.ensure(4096 * sizeof(double));
+            CK(cudaMemcpyAsync(hsmall.p, src, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+            sync();
+            std::memcpy(dst, hsmall.p, n * sizeof(double));
+            return;
+        }
+        const size_t nch = (n + kChunk - 1) / kChunk;
+        const int T = (int)std::min<size_t>(kWorkers, nch);
+        hstage.ensure((size_t)T * kChunk * sizeof(double));
+        for (int w = 0; w < T; w++)
+            if (!stage_ev[w]) CK(cudaEventCreateWithFlags(&stage_ev[w], cudaEventDisableTiming));
+        double *buf = reinterpret_cast<double *>(hstage.p);
+        std::vector<int> err(T, 0);
+        auto work = [&](int w) {
+            if (w > 0 && cudaSetDevice(device) != cudaSuccess) {
+                err[w] = (int)cudaErrorInvalidDevice;
+                return;
+            }
+            double *slot = buf + (size_t)w * kChunk;
+            for (size_t k = (size_t)w; k < nch && !err[w]; k += (size_t)T) {
+                const size_t off = k * kChunk, m = std::min(kChunk, n - off);
+                cudaError_t e = cudaMemcpyAsync(slot, src + off, m * sizeof(double), cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaEventRecord(stage_ev[w], st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(stage_ev[w]);
+                if (e != cudaSuccess) {
+                    err[w] = (int)e;
+                    break;
+                }
+                std::memcpy(dst + off, slot, m * sizeof(double));
+            }
+        };
+        std::vector<std::thread> th;
+        for (int w = 1; w < T; w++) th.emplace_back(work, w);
+        work(0);
+        for (auto &x : th) x.join();
+        for (int w = 0; w < T; w++)
+            if (err[w]) CK((cudaError_t)err[w]);
+        sync();
     }
 
     // ------------------------------------------------------------ init
@@ -1143,6 +1281,9 @@ struct tsu_ctx {
     {
         if (st) cudaStreamSynchronize(st);
         if (gexec) cudaGraphExecDestroy(gexec);
+        for (auto &g : g1) cudaGraphExecDestroy(g.ex);
+        for (auto &e : stage_ev)
+            if (e) cudaEventDestroy(e);
         for (auto &L : lv) {
             L.dP.release(); L.dItems.release(); L.dNbrs.release(); L.dCmap.release(); L.dBc.release();
             L.dOlds.release(); L.dList.release();
@@ -1221,6 +1362,7 @@ int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out)
         x->nlev = c.num_levels;
         x->nscen = c.n_scenarios;
         for (int l = 0; l + 1 < x->nlev; l++) x->ratio[l] = c.ratios[l];
+        CK(cudaGetDevice(&x->device));
         if (cuda_stream) x->st = (cudaStream_t)cuda_stream;
         else {
             CK(cudaStreamCreateWithFlags(&x->st, cudaStreamNonBlocking));
@@ -1362,11 +1504,7 @@ int tsu_step(tsu_ctx *ctx, int n, double *t_out)
     int rc = guard(ctx, [&] {
         if (n < 0) throw Err(TSU_ERR_ARG, "negative step count");
         ctx->step(n);
-        ctx->check_device_errors(cfl);
-        if (t_out) {
-            CK(cudaMemcpyAsync(t_out, ctx->t.p, ctx->nscen * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-            ctx->sync();
-        }
+        ctx->check_device_errors(cfl, t_out);
     });
     if (rc == TSU_OK && cfl) {
         ctx->err = "a level step ran with a Courant number above cfl_max";
@@ -1443,18 +1581,25 @@ int tsu_read_field(tsu_ctx *ctx, int scen, int level, int field, double *dst, in
             throw Err(TSU_ERR_ARG, "bad argument");
         size_t n = (size_t)nx * ny;
         ctx->dstage.ensure(n, ctx->st);
-        CK(cudaMemsetAsync(ctx->dstage.p, 0xff, n * sizeof(double), ctx->st));
+        ctx->kl(k_fill(ctx->dstage.p, (long long)n, std::numeric_limits<double>::quiet_NaN(), ctx->st), "fill");
         int la = level == 0 ? 0 : level - 1, lb = level == 0 ? ctx->nlev - 1 : level - 1;
         for (int l = la; l <= lb; l++) {
             Lvl &L = ctx->lv[l];
             if (L.P.empty()) continue;
-            ctx->kl(k_read_field(ctx->prec, ctx->view(l), (int)L.P.size(), L.cur, scen, field, ctx->dstage.p, nx, ny, x0,
-                                 y0, dx, dy, ctx->c.x0, ctx->c.y0, L.dx, L.dy, ctx->st), "read field");
+            // output points a patch can cover: its extent in output spacings, plus the edges
+            const double sx = L.dx / dx, sy = L.dy / dy;
+            long long maxpts = 1;
+            for (const auto &P : L.P) {
+                long long w = std::min<long long>(nx, (long long)std::ceil(P.nx * sx) + 3);
+                long long h = std::min<long long>(ny, (long long)std::ceil(P.ny * sy) + 3);
+                maxpts = std::max(maxpts, w * h);
+            }
+            ctx->kl(k_read_field(ctx->prec, ctx->view(l), (int)L.P.size(), (int)std::min<long long>(maxpts, 1LL << 30),
+                                 L.cur, scen, field, ctx->dstage.p, nx, ny, x0, y0, dx, dy, ctx->c.x0, ctx->c.y0, L.dx,
+                                 L.dy, ctx->st),
+                    "read field");
         }
-        CK(cudaMemcpyAsync(dst, ctx->dstage.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-        ctx->sync();
-        for (size_t k = 0; k < n; k++)
-            if (std::isnan(dst[k])) dst[k] = NAN;
+        ctx->d2h_staged(dst, ctx->dstage.p, n);
     });
 }
 

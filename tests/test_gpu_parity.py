@@ -135,6 +135,29 @@ def test_graph_replay_equals_eager():
     assert np.array_equal(ta, tb) and np.array_equal(ea, eb)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_step_graphs_equal_eager(prec):
+    """Single-step calls replay one graph per buffer-parity pattern; they must
+    give the eager run bit for bit, on a tiled level and under AMR whose
+    regrids come every 4 coarse steps (graphs between regrids, eager around
+    them), with every step's returned time equal."""
+    w = W.shelf(n=128, dx=2000.0)
+    cfg = dict(w["cfg"], level1_tile=40)
+    wa = W.amr3(L=240e3, dx1=4000.0, steps=6)
+    cfga = dict(wa["cfg"], regrid_interval=16)
+    for ww, c, nlev, steps in ((w, cfg, 1, 7), (wa, cfga, 3, 13)):
+        a = W.load(_gpu(c, prec, use_graphs=True), dict(ww, cfg=c))
+        b = W.load(_gpu(c, prec, use_graphs=False), dict(ww, cfg=c))
+        for _ in range(steps):
+            assert np.array_equal(a.step(1), b.step(1))
+        compare_levels(a, b, nlev, bitwise=True)
+        ta, ea = a.read_gauges()
+        tb, eb = b.read_gauges()
+        assert np.array_equal(ta, tb) and np.array_equal(ea, eb)
+        assert a.stats()["cell_updates"] == b.stats()["cell_updates"]
+    assert a.num_patches(0, 3) > 0
+
+
 def test_autotune_leaves_the_solution_unchanged():
     """The autotuner times zero-length steps: afterwards the run still matches
     the oracle bit for bit, in whatever launch shape it chose."""

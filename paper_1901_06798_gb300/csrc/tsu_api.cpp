@@ -49,6 +49,21 @@ struct Err : std::runtime_error {
 
 int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// f(q, begin, end) over contiguous ranges of [0, n), ranges in order q = 0, 1, ..;
+// on up to 16 host threads when n is large enough to pay for them
+template <typename F> void parallel_ranges(int n, F &&f)
+{
+    const int T = n < 512 ? 1 : std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    if (T == 1) {
+        f(0, 0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int q = 1; q < T; q++) th.emplace_back([&, q] { f(q, (int)((long long)n * q / T), (int)((long long)n * (q + 1) / T)); });
+    f(0, 0, (int)((long long)n / T));
+    for (auto &x : th) x.join();
+}
+
 template <typename T> struct DevBuf {
     T *p = nullptr;
     size_t cap = 0;
@@ -420,42 +435,71 @@ struct tsu_ctx {
         for (int k = 0; k < n; k++) ids[L.P[k].scen].push_back(k);
         if (l > 0)
             for (int k = 0; k < (int)lv[l - 1].P.size(); k++) cids[lv[l - 1].P[k].scen].push_back(k);
-        std::vector<int> tmp, ctmp;
+        std::vector<BoxIndex> bis(nscen), cis(nscen);
         for (int s = 0; s < nscen; s++) {
             if (ids[s].empty()) continue;
-            BoxIndex bi;
-            bi.build(L.P, ids[s], L.nxl, L.nyl);
-            BoxIndex ci;
-            if (l > 0) ci.build(lv[l - 1].P, cids[s], lv[l - 1].nxl, lv[l - 1].nyl);
-            for (int k : ids[s]) {
+            bis[s].build(L.P, ids[s], L.nxl, L.nyl);
+            if (l > 0) cis[s].build(lv[l - 1].P, cids[s], lv[l - 1].nxl, lv[l - 1].nyl);
+        }
+        // patch k's tables in patch order: scenario by scenario, as the ids lists run
+        std::vector<int> order;
+        order.reserve(n);
+        for (int s = 0; s < nscen; s++) order.insert(order.end(), ids[s].begin(), ids[s].end());
+        // coarse-map footprints and their offsets first (they depend on the box only)
+        if (l > 0) {
+            const int r = ratio[l - 1];
+            size_t tot = 0;
+            for (int k : order) {
                 PatchDesc &p = L.P[k];
-                bi.overlapping(p.i0 - 2, p.j0 - 2, p.i0 + p.nx + 2, p.j0 + p.ny + 2, tmp);
-                p.nbr_off = (int)L.nbrs.size();
+                const int ci0 = floordiv(p.i0 - 2, r) - 1, cj0 = floordiv(p.j0 - 2, r) - 1;
+                const int ci1 = floordiv(p.i0 + p.nx + 1, r) + 1, cj1 = floordiv(p.j0 + p.ny + 1, r) + 1;
+                p.cmap_i0 = ci0; p.cmap_j0 = cj0; p.cmap_w = ci1 - ci0 + 1; p.cmap_h = cj1 - cj0 + 1;
+                p.cmap_off = (int)tot;
+                tot += (size_t)p.cmap_w * p.cmap_h;
+            }
+            L.cmap.assign(tot, -1);
+        }
+        // neighbour lists and coarse maps, patch ranges on host threads; each
+        // range's neighbour ids go to its own buffer, joined in order afterwards
+        std::vector<std::vector<int>> nb(16);
+        std::array<std::array<int, 2>, 16> rng{};
+        parallel_ranges(n, [&](int q, int b, int e) {
+            rng[q] = {b, e};
+            std::vector<int> tmp, ctmp;
+            std::vector<int> &out = nb[q];
+            for (int o = b; o < e; o++) {
+                const int k = order[o];
+                PatchDesc &p = L.P[k];
+                bis[p.scen].overlapping(p.i0 - 2, p.j0 - 2, p.i0 + p.nx + 2, p.j0 + p.ny + 2, tmp);
+                p.nbr_off = (int)out.size();   // relative to the range's buffer for now
                 p.nbr_cnt = 0;
-                for (int q : tmp)
-                    if (q != k) { L.nbrs.push_back(q); p.nbr_cnt++; }
+                for (int x : tmp)
+                    if (x != k) { out.push_back(x); p.nbr_cnt++; }
                 if (l > 0) {
-                    int r = ratio[l - 1];
-                    int ci0 = floordiv(p.i0 - 2, r) - 1, cj0 = floordiv(p.j0 - 2, r) - 1;
-                    int ci1 = floordiv(p.i0 + p.nx + 1, r) + 1, cj1 = floordiv(p.j0 + p.ny + 1, r) + 1;
-                    p.cmap_i0 = ci0; p.cmap_j0 = cj0; p.cmap_w = ci1 - ci0 + 1; p.cmap_h = cj1 - cj0 + 1;
-                    p.cmap_off = (int)L.cmap.size();
                     // coarse patch of every coarse cell of the footprint (-1: none):
                     // patches of one level and scenario do not overlap, so painting
                     // the few overlapping ones gives each cell its unique patch
-                    const int cw = p.cmap_w;
-                    const size_t base = L.cmap.size();
-                    L.cmap.resize(base + (size_t)cw * p.cmap_h, -1);
-                    ci.overlapping(ci0, cj0, ci1 + 1, cj1 + 1, ctmp);
-                    for (int q : ctmp) {
-                        const PatchDesc &c2 = lv[l - 1].P[q];
+                    const int ci0 = p.cmap_i0, cj0 = p.cmap_j0, cw = p.cmap_w;
+                    const int ci1 = ci0 + cw - 1, cj1 = cj0 + p.cmap_h - 1;
+                    const size_t base = (size_t)p.cmap_off;
+                    cis[p.scen].overlapping(ci0, cj0, ci1 + 1, cj1 + 1, ctmp);
+                    for (int x : ctmp) {
+                        const PatchDesc &c2 = lv[l - 1].P[x];
                         const int ia = std::max(ci0, c2.i0), ib = std::min(ci1 + 1, c2.i0 + c2.nx);
                         const int ja = std::max(cj0, c2.j0), jb = std::min(cj1 + 1, c2.j0 + c2.ny);
                         for (int J = ja; J < jb; J++)
-                            for (int I = ia; I < ib; I++) L.cmap[base + (size_t)(J - cj0) * cw + (I - ci0)] = q;
+                            for (int I = ia; I < ib; I++) L.cmap[base + (size_t)(J - cj0) * cw + (I - ci0)] = x;
                     }
                 }
             }
+        });
+        {
+            std::vector<int> shift(17, 0);
+            for (int q = 0; q < 16; q++) shift[q + 1] = shift[q] + (int)nb[q].size();
+            L.nbrs.reserve(shift[16]);
+            for (int q = 0; q < 16; q++) L.nbrs.insert(L.nbrs.end(), nb[q].begin(), nb[q].end());
+            for (int q = 0; q < 16; q++)
+                for (int o = rng[q][0]; o < rng[q][1]; o++) L.P[order[o]].nbr_off += shift[q];
         }
         L.dP.upload(L.P, st);
         L.dItems.upload(L.items, st);

@@ -207,13 +207,15 @@ int tsu_get_stats(tsu_ctx *ctx, int scenario, tsu_stats *out);
  * into row segments).  step_threads is 64, 128 or 256, or also 32 for the
  * split FP32 update.  A CTA updates a strip of 2 step_threads - 4 columns in
  * the split FP32 update (two columns per thread), step_threads - 4 otherwise.
- * 0 restores the defaults.  Results do not depend on either.  Returns
- * TSU_ERR_ARG for any other value. */
+ * The split FP32 update runs as two kernels: the knobs shape its x-sweep
+ * kernel (rows counted over the patch's ghost rows too); its y-sweep kernel
+ * always takes strips of 64 columns and 32 rows.  0 restores the defaults.
+ * Results do not depend on either.  Returns TSU_ERR_ARG for any other value. */
 int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows);
 
 /* Autotuner: time every launch shape of the patch update (threads per CTA
  * 64/128/256, and 32 for the split FP32 update, x rows per work item
- * 32/64/128/256) on the context's current
+ * 32/64/128/256, or 16/32/64/128 for the split FP32 update) on the context's current
  * levels with `reps` zero-length steps each -- the kernels do all their work
  * but the state is unchanged -- and keep the fastest.  Outputs (any may be
  * NULL): the chosen shape and its time per step of all levels in ms. */

@@ -181,10 +181,11 @@ struct PinnedHost {
 struct Lvl {
     std::vector<PatchDesc> P;
     std::vector<size_t> blk, blkbytes;
-    std::vector<StepItem> items;
+    std::vector<StepItem> items, items_y;   // patch update work items (items_y: FP32 split y kernel)
     std::vector<int> nbrs, cmap, bclist, olds;
     DevBuf<PatchDesc> dP;
-    DevBuf<StepItem> dItems;
+    DevBuf<StepItem> dItems, dItemsY;
+    DevBuf<float> dScratch;                 // FP32 split update: Q* of every patch (3 fields each)
     DevBuf<int> dNbrs, dCmap, dBc, dOlds, dList;
     int cur = 0, maxring = 0, maxcells = 0;
     int nxl = 0, nyl = 0;
@@ -323,19 +324,34 @@ struct tsu_ctx {
     int device = 0;                            // the CUDA device current at tsu_create
 
     // ------------------------------------------------------------ helpers
-    int nt() const { return step_nt > 0 ? step_nt : (prec == TSU_F64 ? step_threads_f64() : step_threads_f32p()); }
+    // FP32 split scheme: the patch update runs as the x and y kernels with a Q* scratch
+    bool split_f32() const { return prec != TSU_F64 && c.transverse == 0; }
+    int nt() const
+    {
+        if (step_nt > 0) return step_nt;
+        return prec == TSU_F64 ? step_threads_f64() : (split_f32() ? 64 : step_threads_f32p());
+    }
     // physical cell sizes of level l (of an equatorial cell on latitude-longitude grids)
     double pdx(int l) const { return c.spherical ? lv[l].dxp : lv[l].dx; }
     double pdy(int l) const { return c.spherical ? lv[l].dyp : lv[l].dy; }
-    void set_geometry(StepArgs &a, int l) const
+    // per-level launch data of the patch update: cell sizes, latitude-longitude
+    // tables, and the FP32 split kernels' scratch and y work items
+    void level_args(StepArgs &a, int l) const
     {
         a.dx = pdx(l);
         a.dy = pdy(l);
         if (c.spherical) {
             a.kap = lv[l].dKap.p; a.ced = lv[l].dCed.p; a.kapf = lv[l].dKapF.p; a.cedf = lv[l].dCedF.p;
         }
+        if (split_f32()) {
+            a.scratch = lv[l].dScratch.p;
+            a.items_y = lv[l].dItemsY.p;
+            a.n_items_y = (int)lv[l].items_y.size();
+        }
     }
-    int seg() const { return seg_rows > 0 ? seg_rows : (prec == TSU_F64 ? 128 : 64); }
+    // kernels one patch-update launch of level l runs
+    int step_kernels() const { return split_f32() ? 2 : 1; }
+    int seg() const { return seg_rows > 0 ? seg_rows : (prec == TSU_F64 ? 128 : (split_f32() ? 16 : 64)); }
     void kl(int e, const char *what)
     {
         launches++;
@@ -420,12 +436,30 @@ struct tsu_ctx {
         L.bclist.clear();
         L.maxring = 0;
         L.maxcells = 0;
+        L.items_y.clear();
         const int W = prec == TSU_F64 ? step_strip_width_f64(nt(), c.transverse) : step_strip_width_f32p(nt(), c.transverse);
+        const bool split = split_f32();
+        size_t soff = 0;
         for (int k = 0; k < n; k++) {
-            const PatchDesc &p = L.P[k];
-            for (int x0 = 0; x0 < p.nx; x0 += W)
-                for (int y0 = 0; y0 < p.ny; y0 += seg())
-                    L.items.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(seg(), p.ny - y0)});
+            PatchDesc &p = L.P[k];
+            if (split) {
+                // x kernel: every row including the ghost rows, no halo rows; y kernel:
+                // strips of 2 x 32 columns and segments of 32 interior rows
+                for (int x0 = 0; x0 < p.nx; x0 += W)
+                    for (int y0 = -2; y0 < p.ny + 2; y0 += seg())
+                        L.items.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(seg(), p.ny + 2 - y0)});
+                constexpr int WY = 64, SY = 32;
+                for (int x0 = 0; x0 < p.nx; x0 += WY)
+                    for (int y0 = 0; y0 < p.ny; y0 += SY)
+                        L.items_y.push_back(StepItem{k, x0, y0, std::min(WY, p.nx - x0), std::min(SY, p.ny - y0)});
+                p.soff = (long long)soff;
+                soff += 3 * (size_t)p.fs;
+            } else {
+                p.soff = 0;
+                for (int x0 = 0; x0 < p.nx; x0 += W)
+                    for (int y0 = 0; y0 < p.ny; y0 += seg())
+                        L.items.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(seg(), p.ny - y0)});
+            }
             L.maxring = std::max(L.maxring, (p.nx + 4) * (p.ny + 4) - p.nx * p.ny);
             L.maxcells = std::max(L.maxcells, (p.nx + 4) * (p.ny + 4));
             if (p.bcmask) L.bclist.push_back(k);
@@ -501,8 +535,10 @@ struct tsu_ctx {
             for (int q = 0; q < 16; q++)
                 for (int o = rng[q][0]; o < rng[q][1]; o++) L.P[order[o]].nbr_off += shift[q];
         }
+        if (split) L.dScratch.ensure(std::max<size_t>(soff, 64), st);
         L.dP.upload(L.P, st);
         L.dItems.upload(L.items, st);
+        L.dItemsY.upload(L.items_y, st);
         L.dNbrs.upload(L.nbrs, st);
         if (l > 0) L.dCmap.upload(L.cmap, st);
         L.dBc.upload(L.bclist, st);
@@ -844,11 +880,12 @@ struct tsu_ctx {
             a.dt1f = dt1f.p;
             a.transverse = c.transverse;
             a.manning = (c.manning_n * c.manning_n) * c.g;
-            set_geometry(a, l);
+            level_args(a, l);
             set_f32_constants(a);
             int e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
                                     : launch_step_f32p(a, (int)L.items.size(), nt(), st);
             kl(e, "patch step");
+            launches += step_kernels() - 1;
             kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, 0, st), "post step");
             L.cur ^= 1;
         }
@@ -1332,6 +1369,7 @@ struct tsu_ctx {
             L.dP.release(); L.dItems.release(); L.dNbrs.release(); L.dCmap.release(); L.dBc.release();
             L.dOlds.release(); L.dList.release();
             L.dKap.release(); L.dCed.release(); L.dKapF.release(); L.dCedF.release();
+            L.dItemsY.release(); L.dScratch.release();
         }
         for (auto &g : grids) if (g.dev) cudaFreeAsync(g.dev, st);
         dGrids.release(); dGridScen.release(); dEtaIdx.release();
@@ -1733,8 +1771,12 @@ int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, 
         ctx->zero_dtf.ensure(ctx->nscen, ctx->st);
         CK(cudaMemsetAsync(ctx->zero_dt.p, 0, ctx->nscen * sizeof(double), ctx->st));
         CK(cudaMemsetAsync(ctx->zero_dtf.p, 0, ctx->nscen * sizeof(float), ctx->st));
-        const int nts[4] = {64, 128, 256, 32}, segs[4] = {32, 64, 128, 256};
-        const int n_nt = ctx->prec != TSU_F64 && ctx->c.transverse == 0 ? 4 : 3;
+        // threads x rows per work item; the FP32 split update's x kernel also takes
+        // 32 threads and needs no halo rows, so it gets shorter segments
+        const bool split = ctx->split_f32();
+        const int nts[4] = {64, 128, 256, 32};
+        const int segs[4] = {split ? 16 : 32, split ? 32 : 64, split ? 64 : 128, split ? 128 : 256};
+        const int n_nt = split ? 4 : 3;
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
@@ -1756,11 +1798,12 @@ int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, 
                         sa.g = ctx->c.g; sa.drytol = ctx->c.drytol;
                         sa.transverse = ctx->c.transverse;
                         sa.manning = (ctx->c.manning_n * ctx->c.manning_n) * ctx->c.g;
-                        ctx->set_geometry(sa, l);
+                        ctx->level_args(sa, l);
                         set_f32_constants(sa);
                         int e = ctx->prec == TSU_F64 ? launch_step_f64(sa, (int)L.items.size(), ctx->nt(), ctx->st)
                                                      : launch_step_f32p(sa, (int)L.items.size(), ctx->nt(), ctx->st);
                         ctx->kl(e, "autotune step");
+                        ctx->launches += ctx->step_kernels() - 1;
                     }
                 };
                 run();
@@ -1880,12 +1923,13 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
             a.dt1f = ctx->dt1f.p;
             a.transverse = ctx->c.transverse;
             a.manning = (ctx->c.manning_n * ctx->c.manning_n) * ctx->c.g;
-            ctx->set_geometry(a, 0);
+            ctx->level_args(a, 0);
             set_f32_constants(a);
             CK(cudaEventRecord(ev[2 * k], ctx->st));
             int e = ctx->prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), ctx->nt(), ctx->st)
                                          : launch_step_f32p(a, (int)L.items.size(), ctx->nt(), ctx->st);
             ctx->kl(e, "patch step");
+            ctx->launches += ctx->step_kernels() - 1;
             CK(cudaEventRecord(ev[2 * k + 1], ctx->st));
             ctx->kl(k_post_level(ctx->ctrl(), 0, ctx->nscen, L.R, ctx->pdx(0), ctx->pdy(0), ctx->c.cfl_max, 0, ctx->st), "post step");
             L.cur ^= 1;

@@ -20,6 +20,7 @@ struct PatchDesc {
     int nbr_off, nbr_cnt;      // same-level patches whose interior may feed this patch's ghosts
     int cmap_off, cmap_i0, cmap_j0, cmap_w, cmap_h;  // coarse-level patch index per coarse cell (levels >= 2)
     int old_off, old_cnt;      // old same-level patches overlapping (regrid initialisation)
+    long long soff;            // FP32 split update: element offset of the patch's Q* (3 fields of fs) in the scratch
 };
 
 // One work item of the patch update: a strip of columns [x0, x0+w) and a row
@@ -51,6 +52,11 @@ struct StepArgs {
     // length of the latitude edge below row J at ced[J + 2]; null on Cartesian grids
     const double *kap, *ced;
     const float *kapf, *cedf;
+    // FP32 split update (two kernels): the level's Q* scratch and the y kernel's
+    // work items (strips of 64 columns x row segments); null scratch: fused kernel
+    float *scratch;
+    const StepItem *items_y;
+    int n_items_y;
 };
 
 // FP32 launch constants of a level

@@ -68,6 +68,10 @@ def test_noalloc_two_steps_match_context_path(prec):
     else:
         assert np.abs((h + B) - (a2["h"] + a2["B"])).max() <= 1e-4
         assert np.abs(hu - a2["hu"]).max() <= 1e-4 * max(1.0, np.abs(a2["hu"]).max())
+        # the context runs the split FP32 update (x and y kernels through a Q*
+        # scratch), this entry point the fused kernel: the same operations, the same bits
+        for mine, ref in ((h, a2["h"]), (hu, a2["hu"]), (hv, a2["hv"])):
+            assert np.array_equal(mine, ref)
 
 
 def test_noalloc_rejects_oversize_and_bad_layout():

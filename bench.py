@@ -46,14 +46,15 @@ def peaks():
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("step_kernel.cuh", "step_f32x2.cuh", "step_f32p.cu", "step_f64.cu", "tsu_device.h"):
+    for f in ("step_kernel.cuh", "step_f32x2.cuh", "step_split_f32.cuh", "step_f32p.cu", "step_f64.cu", "tsu_device.h"):
         h.update(open(os.path.join(ROOT, "paper_1901_06798_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(prec):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
-    only if it was taken on the current kernel source."""
+    """DRAM bytes of one patch update (the x- and y-sweep kernels of the FP32
+    split update together) from the committed ncu summary, only if it was taken
+    on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(p):
         return None
@@ -464,7 +465,8 @@ def main():
                        "launch_shape": r["tune"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "step_kernel_f32x2", "kernel_ms": r["kernel_ms"],
+                         "kernel": "patch update = step_x_f32x2 + step_y_f32x2 (one launch each per step)",
+                         "kernel_ms": r["kernel_ms"],
                          "bytes_per_launch": bpl, "peak_source": src},
             "fp64": {"value": r64["value"], "steps": r64["K"], "ms_per_step": r64["elapsed"] / r64["K"] * 1e3,
                      "kernel_ms": r64["kernel_ms"],

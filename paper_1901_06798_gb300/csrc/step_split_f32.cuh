@@ -10,7 +10,9 @@
 // step_y_f32x2: one CTA of 32 threads per strip of 64 columns (two per
 //   thread) and a segment of interior rows; reads Q* and B of the segment plus
 //   two rows above and below, runs the y sweep of its columns in registers
-//   (no shared memory, no barriers, no halo columns) and writes Q^{n+1}.
+//   (no halo columns, no barriers) and writes Q^{n+1}.  Each thread streams
+//   its own two columns through a cp.async ring in shared memory, YRING - 1
+//   rows ahead, so the loads' latency hides behind the rows in flight.
 //
 // Against the fused kernel (step_f32x2.cuh) the split pays 24 B per cell more
 // HBM traffic (Q* out and back in), which the 4096^2 update has room for: the
@@ -194,12 +196,16 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
 
 // threads per CTA of the y kernel: one warp, two columns per thread
 constexpr int kSplitYThreads = 32;
+constexpr int kSplitYRing = 4;   // rows in flight per thread
 
 template <bool GEO>
 __global__ void __launch_bounds__(kSplitYThreads) step_y_f32x2(StepArgs a)
 {
     using namespace x2;
-    constexpr int NT = kSplitYThreads;
+    constexpr int NT = kSplitYThreads, YRING = kSplitYRing;
+    // ring[slot][field][2 t .. 2 t + 1]: fields Q* eta', hu, hv and B; thread t
+    // only ever reads its own two columns, so its cp.async waits suffice
+    __shared__ __align__(16) float ring[YRING][4][2 * NT];
     const StepItem it = a.items_y[blockIdx.x];
     if (it.w > 2 * NT || it.w < 1 || it.h < 1) return;   // uniform over the CTA
     const PatchDesc P = a.descs[it.patch];
@@ -224,14 +230,31 @@ __global__ void __launch_bounds__(kSplitYThreads) step_y_f32x2(StepArgs a)
     const long long cbase = (long long)y0 * pitch + (col + 2);
     const bool w8 = vx && vy && ((reinterpret_cast<uintptr_t>(qs0 + cbase) & 7) == 0) &&
                     ((reinterpret_cast<uintptr_t>(qo0 + cbase) & 7) == 0) && ((pitch & 1) == 0) && ((fs & 1) == 0);
-    auto ld = [&](const float *f, int k) {
-        const long long o = cbase + (long long)k * pitch;
-        if (w8) return ld2(f + o);
-        return make_float2(vx ? f[o] : 0.0f, vy ? f[o + 1] : 0.0f);
-    };
     const int nrows = h + 4;
-    // next row's Q* and B, loaded one row ahead (y roles: hn = hv, ht = hu)
-    float2 nq0 = ld(qs0, 0), nq1 = ld(qs0 + fs, 0), nq2 = ld(qs0 + 2 * fs, 0), nB = ld(Bg, 0);
+    const float *fsrc[4] = {qs0, qs0 + fs, qs0 + 2 * fs, Bg};
+    const int c0 = 2 * t;
+    auto prefetch = [&](int k) {
+        if (k < nrows) {
+            const int slot = k % YRING;
+            const long long o = cbase + (long long)k * pitch;
+            if (w8) {
+#pragma unroll
+                for (int f = 0; f < 4; f++) cp_async_elem(&ring[slot][f][c0], fsrc[f] + o, 8);
+            } else {
+                if (vx) {
+#pragma unroll
+                    for (int f = 0; f < 4; f++) cp_async_elem(&ring[slot][f][c0], fsrc[f] + o, 4);
+                }
+                if (vy) {
+#pragma unroll
+                    for (int f = 0; f < 4; f++) cp_async_elem(&ring[slot][f][c0 + 1], fsrc[f] + o + 1, 4);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int k = 0; k < YRING - 1; k++) prefetch(k);
 
     C2 yq2, yq1, yq0;
     W2 ywo, ywm, ywn;
@@ -245,9 +268,16 @@ __global__ void __launch_bounds__(kSplitYThreads) step_y_f32x2(StepArgs a)
     auto row = [&](const int k, const C2 &ycm2, const C2 &ycm1, C2 &ycur, const W2 &wo, const W2 &wm, W2 &wn,
                    const float2 (&apo)[3], const float2 (&Fo)[3], float2 (&apm)[3], float2 (&Fm)[3]) {
         const int r = y0 - 2 + k;
-        ycur.q0 = nq0; ycur.hn = nq2; ycur.ht = nq1; ycur.B = nB;
-        if (k + 1 < nrows) {
-            nq0 = ld(qs0, k + 1); nq1 = ld(qs0 + fs, k + 1); nq2 = ld(qs0 + 2 * fs, k + 1); nB = ld(Bg, k + 1);
+        prefetch(k + YRING - 1);
+        cp_async_wait<YRING - 1>();   // row k of this thread has landed
+        {
+            const int slot = k % YRING;
+            // lanes outside the strip read zeros: a dry cell whose results are not stored
+            ycur.q0 = vx ? ld2(&ring[slot][0][c0]) : f2(0.0f);
+            ycur.ht = vx ? ld2(&ring[slot][1][c0]) : f2(0.0f);
+            ycur.hn = vx ? ld2(&ring[slot][2][c0]) : f2(0.0f);
+            ycur.B = vx ? ld2(&ring[slot][3][c0]) : f2(0.0f);
+            if (!vy) { ycur.q0.y = 0.0f; ycur.ht.y = 0.0f; ycur.hn.y = 0.0f; ycur.B.y = 0.0f; }
         }
         derive(ycur, sqrtg, drytol);
         if (k >= 1) {
@@ -313,6 +343,7 @@ __global__ void __launch_bounds__(kSplitYThreads) step_y_f32x2(StepArgs a)
 #pragma unroll
         for (int m = 0; m < 3; m++) { yao[m] = yam1[m]; yfo[m] = yfm1[m]; }
     }
+    cp_async_wait<0>();
 
     if (!(smy > 0.0f)) smy = 0.0f;
 #pragma unroll

@@ -34,6 +34,14 @@ sys.path.insert(0, ROOT)
 METRIC = "cell updates/sec (all AMR levels) FP32-pert vs FP64 on 1 GB300; % HBM roofline"
 UNIT = "cell updates/s"
 BYTES_PER_CELL = {"f32p": 28, "f64": 56}   # read q0,q1,q2,B + write q0,q1,q2 per interior cell update
+# algorithmic floating-point operations (add/sub, mul, div, sqrt) per interior cell update of the
+# split step with every edge active, counted on the oracle compiled with a counting scalar type
+# (tests/test_oracle_flops.py, the all-wet 200^2 hump; comparisons and min/max not included)
+FLOPS_PER_CELL = 347.1
+# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz;
+# FP64: GB300's nominal dense FP64 rate
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
 
 
 def peaks():
@@ -468,9 +476,18 @@ def main():
                          "kernel": "patch update = step_x_f32x2 + step_y_f32x2 (one launch each per step)",
                          "kernel_ms": r["kernel_ms"],
                          "bytes_per_launch": bpl, "peak_source": src},
+            # the other roof of the same update: algorithmic flops against the FP32 pipes; neither
+            # binds -- the update is bound by instruction issue (see the design notes)
+            "roofline_fp32": {"bound": "alu", "achieved": FLOPS_PER_CELL * r["cells"] / (r["kernel_ms"] / 1e3) / 1e12,
+                              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": FLOPS_PER_CELL * r["cells"] / (r["kernel_ms"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                              "flops_per_cell": FLOPS_PER_CELL,
+                              "peak_source": "derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"},
             "fp64": {"value": r64["value"], "steps": r64["K"], "ms_per_step": r64["elapsed"] / r64["K"] * 1e3,
                      "kernel_ms": r64["kernel_ms"],
-                     "hbm_frac": (b64 / (r64["kernel_ms"] / 1e3) / 1e9) / hbm},
+                     "hbm_frac": (b64 / (r64["kernel_ms"] / 1e3) / 1e9) / hbm,
+                     "fp64_frac": FLOPS_PER_CELL * r64["cells"] / (r64["kernel_ms"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                     "fp64_peak": "nominal 1.25 TFLOP/s"},
             "fp32p_over_fp64": r["value"] / r64["value"],
             "unsplit": {k.split("_")[0]: {"value": u["value"], "steps": u["K"],
                                            "ms_per_step": u["elapsed"] / u["K"] * 1e3, "kernel_ms": u["kernel_ms"],

@@ -51,6 +51,43 @@ def build(variant: str = "parity", force: bool = False) -> str:
     return out
 
 
+def build_flopcount(force: bool = False) -> str:
+    """Compile ``flopcount.cpp``: ``swe.c`` with a counting scalar type, for the
+    algorithmic operation count of one cell update (no contraction, as the oracle)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, "libora_flopcount.so")
+    deps = [os.path.join(_HERE, s) for s in ("flopcount.cpp", "swe.c", *_HDRS)]
+    if not force and os.path.exists(out):
+        mt = os.path.getmtime(out)
+        if all(os.path.getmtime(d) <= mt for d in deps):
+            return out
+    cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17", "-fPIC", "-shared",
+           "-Wno-class-memaccess", os.path.join(_HERE, "flopcount.cpp"), "-o", out + ".tmp", "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+    return out
+
+
+FLOP_KINDS = ("add", "mul", "div", "sqrt", "cmp", "minmax", "abs", "neg")
+
+
+def count_step_flops(h, hu, hv, B, g, drytol, dt, dx, dy):
+    """Operation counts of one split step (``ora_step_patch``) of a patch given
+    as (ny + 4, nx + 4) arrays with their ghost cells filled.  Returns a dict
+    over FLOP_KINDS, and the updated (h, hu, hv)."""
+    L = C.CDLL(build_flopcount())
+    dp = C.POINTER(C.c_double)
+    L.flop_count_step.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp] + [C.c_double] * 5 + [C.POINTER(C.c_longlong)]
+    L.flop_count_step.restype = C.c_int
+    ny4, nx4 = h.shape
+    a = [np.ascontiguousarray(x, dtype=np.float64).copy() for x in (h, hu, hv, B)]
+    out = (C.c_longlong * 8)()
+    rc = L.flop_count_step(nx4 - 4, ny4 - 4, *[x.ctypes.data_as(dp) for x in a], g, drytol, dt, dx, dy, out)
+    if rc != 0:
+        raise ValueError(f"flop_count_step failed ({rc})")
+    return dict(zip(FLOP_KINDS, list(out))), tuple(a[:3])
+
+
 class ora_config(C.Structure):
     _fields_ = [
         ("nx", C.c_int), ("ny", C.c_int),

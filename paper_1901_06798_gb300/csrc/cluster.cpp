@@ -24,6 +24,8 @@
 #include <thread>
 #include <vector>
 
+#include "host_pool.h"
+
 namespace tsu {
 
 namespace {
@@ -56,15 +58,13 @@ struct Region {
     int i0, j0, i1, j1;   // inclusive
 };
 
-// run f(lo, hi) over [0, n) split into contiguous parts on up to `threads` threads
+// run f(lo, hi) over [0, n) split into `threads` contiguous parts on the host pool
 template <typename Fn> void parallel_for(int n, int threads, Fn f)
 {
     if (threads <= 1 || n < 2 * threads) { f(0, n); return; }
-    std::vector<std::thread> pool;
-    for (int k = 1; k < threads; k++)
-        pool.emplace_back([=] { f((int)((long long)n * k / threads), (int)((long long)n * (k + 1) / threads)); });
-    f(0, (int)((long long)n / threads));
-    for (auto &t : pool) t.join();
+    tsu::HostPool::get().run(threads, [&](int k) {
+        f((int)((long long)n * k / threads), (int)((long long)n * (k + 1) / threads));
+    });
 }
 
 }  // namespace
@@ -73,8 +73,8 @@ void cluster_boxes(const uint8_t *Fg, const uint8_t *Ng, int nxg, int nyg, doubl
                    std::vector<std::array<int, 4>> &out, int max_threads, std::vector<int32_t> *workspace)
 {
     out.clear();
-    // threads only pay off on large masks (one spawn costs about as much as
-    // scanning a few hundred thousand cells)
+    // threads only pay off on large masks (handing a loop to the pool costs
+    // about as much as scanning some tens of thousands of cells)
     const int hw = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
     const int threads = std::max(1, std::min({max_threads, hw, (int)((size_t)nxg * nyg / (1u << 18)) + 1}));
     // bounding box of the flags: the recursion's first step takes the tight box

@@ -73,14 +73,15 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
             if (c0 + 1 < ncols && v8) {
 #pragma unroll
                 for (int f = 0; f < 4; f++) cp_async_elem(&ring[slot][f][c0], s + fo[f], 8);
-            } else {
-                if (c0 < ncols) {
+            } else if (c0 < ncols) {
+                // past an odd last column the second slot repeats the first: a
+                // stale slot could send the valid lane down the other Riemann path
+                // (general instead of paired), which rounds differently
+                const int c1 = c0 + 1 < ncols ? 1 : 0;
 #pragma unroll
-                    for (int f = 0; f < 4; f++) cp_async_elem(&ring[slot][f][c0], s + fo[f], 4);
-                }
-                if (c0 + 1 < ncols) {
-#pragma unroll
-                    for (int f = 0; f < 4; f++) cp_async_elem(&ring[slot][f][c0 + 1], s + fo[f] + 1, 4);
+                for (int f = 0; f < 4; f++) {
+                    cp_async_elem(&ring[slot][f][c0], s + fo[f], 4);
+                    cp_async_elem(&ring[slot][f][c0 + 1], s + fo[f] + c1, 4);
                 }
             }
         }

@@ -25,6 +25,7 @@
 #include "../../include/tsunami.h"
 #include "amr_kernels.h"
 #include "cnn.h"
+#include "host_pool.h"
 #include "tsu_device.h"
 
 namespace tsu {
@@ -50,18 +51,15 @@ struct Err : std::runtime_error {
 int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // f(q, begin, end) over contiguous ranges of [0, n), ranges in order q = 0, 1, ..;
-// on up to 16 host threads when n is large enough to pay for them
+// on the host pool (up to 16 threads) when n is large enough to pay for it
 template <typename F> void parallel_ranges(int n, F &&f)
 {
-    const int T = n < 512 ? 1 : std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+    const int T = n < 512 ? 1 : tsu::HostPool::get().size();
     if (T == 1) {
         f(0, 0, n);
         return;
     }
-    std::vector<std::thread> th;
-    for (int q = 1; q < T; q++) th.emplace_back([&, q] { f(q, (int)((long long)n * q / T), (int)((long long)n * (q + 1) / T)); });
-    f(0, 0, (int)((long long)n / T));
-    for (auto &x : th) x.join();
+    tsu::HostPool::get().run(T, [&](int q) { f(q, (int)((long long)n * q / T), (int)((long long)n * (q + 1) / T)); });
 }
 
 template <typename T> struct DevBuf {
@@ -756,14 +754,12 @@ struct tsu_ctx {
             if (which.size() == 1) {
                 cluster_one(which[0], 16, &cws[0]);
             } else {
-                // independent scenarios: one host thread per group of them
-                const int nt = std::max(1, std::min({16, (int)which.size(), (int)std::thread::hardware_concurrency()}));
-                std::vector<std::thread> pool;
-                for (int q = 0; q < nt; q++)
-                    pool.emplace_back([&, q] {
-                        for (size_t k = q; k < which.size(); k += nt) cluster_one(which[k], 1, &cws[q]);
-                    });
-                for (auto &th : pool) th.join();
+                // independent scenarios: one pool task per group of them (each
+                // clusters on its own thread: no nested pool loops)
+                const int nt = std::max(1, std::min({16, (int)which.size(), tsu::HostPool::get().size()}));
+                tsu::HostPool::get().run(nt, [&](int q) {
+                    for (size_t k = q; k < which.size(); k += nt) cluster_one(which[k], 1, &cws[q]);
+                });
             }
             cluster_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_c0).count();
         }

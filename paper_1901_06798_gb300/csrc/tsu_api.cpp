@@ -180,7 +180,9 @@ struct Lvl {
     std::vector<PatchDesc> P;
     std::vector<size_t> blk, blkbytes;
     std::vector<StepItem> items, items_y;   // patch update work items (items_y: FP32 split y kernel)
-    std::vector<int> nbrs, cmap, bclist, olds;
+    std::vector<int> nbrs, bclist, olds;
+    PinnedHost hcmap;   // coarse-patch maps of this level, built in page-locked memory for an async upload
+    cudaEvent_t cmap_ev = nullptr;   // recorded after that upload: hcmap is free again once it completes
     DevBuf<PatchDesc> dP;
     DevBuf<StepItem> dItems, dItemsY;
     DevBuf<float> dScratch;                 // FP32 split update: Q* of every patch (3 fields each)
@@ -430,7 +432,6 @@ struct tsu_ctx {
         const int n = (int)L.P.size();
         L.items.clear();
         L.nbrs.clear();
-        L.cmap.clear();
         L.bclist.clear();
         L.maxring = 0;
         L.maxcells = 0;
@@ -478,6 +479,7 @@ struct tsu_ctx {
         order.reserve(n);
         for (int s = 0; s < nscen; s++) order.insert(order.end(), ids[s].begin(), ids[s].end());
         // coarse-map footprints and their offsets first (they depend on the box only)
+        size_t cmap_n = 0;
         if (l > 0) {
             const int r = ratio[l - 1];
             size_t tot = 0;
@@ -489,8 +491,12 @@ struct tsu_ctx {
                 p.cmap_off = (int)tot;
                 tot += (size_t)p.cmap_w * p.cmap_h;
             }
-            L.cmap.assign(tot, -1);
+            // the last upload from this buffer must be done before it is rewritten
+            if (L.cmap_ev) CK(cudaEventSynchronize(L.cmap_ev));
+            L.hcmap.ensure(std::max<size_t>(tot, 1) * sizeof(int));
+            cmap_n = tot;
         }
+        int *cmap = reinterpret_cast<int *>(L.hcmap.p);
         // neighbour lists and coarse maps, patch ranges on host threads; each
         // range's neighbour ids go to its own buffer, joined in order afterwards
         std::vector<std::vector<int>> nb(16);
@@ -514,13 +520,14 @@ struct tsu_ctx {
                     const int ci0 = p.cmap_i0, cj0 = p.cmap_j0, cw = p.cmap_w;
                     const int ci1 = ci0 + cw - 1, cj1 = cj0 + p.cmap_h - 1;
                     const size_t base = (size_t)p.cmap_off;
+                    std::fill(cmap + base, cmap + base + (size_t)cw * p.cmap_h, -1);
                     cis[p.scen].overlapping(ci0, cj0, ci1 + 1, cj1 + 1, ctmp);
                     for (int x : ctmp) {
                         const PatchDesc &c2 = lv[l - 1].P[x];
                         const int ia = std::max(ci0, c2.i0), ib = std::min(ci1 + 1, c2.i0 + c2.nx);
                         const int ja = std::max(cj0, c2.j0), jb = std::min(cj1 + 1, c2.j0 + c2.ny);
                         for (int J = ja; J < jb; J++)
-                            for (int I = ia; I < ib; I++) L.cmap[base + (size_t)(J - cj0) * cw + (I - ci0)] = x;
+                            for (int I = ia; I < ib; I++) cmap[base + (size_t)(J - cj0) * cw + (I - ci0)] = x;
                     }
                 }
             }
@@ -538,7 +545,12 @@ struct tsu_ctx {
         L.dItems.upload(L.items, st);
         L.dItemsY.upload(L.items_y, st);
         L.dNbrs.upload(L.nbrs, st);
-        if (l > 0) L.dCmap.upload(L.cmap, st);
+        if (l > 0) {
+            L.dCmap.ensure(std::max<size_t>(cmap_n, 1), st);
+            if (cmap_n) CK(cudaMemcpyAsync(L.dCmap.p, cmap, cmap_n * sizeof(int), cudaMemcpyHostToDevice, st));
+            if (!L.cmap_ev) CK(cudaEventCreateWithFlags(&L.cmap_ev, cudaEventDisableTiming));
+            CK(cudaEventRecord(L.cmap_ev, st));
+        }
         L.dBc.upload(L.bclist, st);
         for (int s = 0; s < nscen; s++) cells_h[(size_t)s * kMaxLevels + l] = 0.0;
         for (const auto &p : L.P) cells_h[(size_t)p.scen * kMaxLevels + l] += (double)p.nx * p.ny;
@@ -804,14 +816,26 @@ struct tsu_ctx {
             std::vector<BoxIndex> oi(nscen);
             for (int s = 0; s < nscen; s++)
                 if (slot[s] >= 0 && !ids[s].empty()) oi[s].build(oldP, ids[s], L.nxl, L.nyl);
-            std::vector<int> tmp;
-            for (int k : fresh) {
-                PatchDesc &p = L.P[k];
-                p.old_off = (int)L.olds.size();
-                p.old_cnt = 0;
-                if (ids[p.scen].empty()) continue;
-                oi[p.scen].overlapping(p.i0, p.j0, p.i0 + p.nx, p.j0 + p.ny, tmp);
-                for (int q : tmp) { L.olds.push_back(q); p.old_cnt++; }
+            // fresh patches in contiguous ranges on the host pool, each range's ids
+            // joined in patch order afterwards
+            std::vector<std::vector<int>> ob(16);
+            std::array<std::array<int, 2>, 16> rng{};
+            parallel_ranges((int)fresh.size(), [&](int q, int b, int e) {
+                rng[q] = {b, e};
+                std::vector<int> tmp;
+                for (int o = b; o < e; o++) {
+                    PatchDesc &p = L.P[fresh[o]];
+                    p.old_off = (int)ob[q].size();
+                    p.old_cnt = 0;
+                    if (ids[p.scen].empty()) continue;
+                    oi[p.scen].overlapping(p.i0, p.j0, p.i0 + p.nx, p.j0 + p.ny, tmp);
+                    for (int x : tmp) { ob[q].push_back(x); p.old_cnt++; }
+                }
+            });
+            for (int q = 0; q < 16; q++) {
+                const int shift = (int)L.olds.size();
+                for (int o = rng[q][0]; o < rng[q][1]; o++) L.P[fresh[o]].old_off += shift;
+                L.olds.insert(L.olds.end(), ob[q].begin(), ob[q].end());
             }
         }
         L.dOlds.upload(L.olds, st);
@@ -1366,6 +1390,7 @@ struct tsu_ctx {
             L.dOlds.release(); L.dList.release();
             L.dKap.release(); L.dCed.release(); L.dKapF.release(); L.dCedF.release();
             L.dItemsY.release(); L.dScratch.release();
+            if (L.cmap_ev) cudaEventDestroy(L.cmap_ev);
         }
         for (auto &g : grids) if (g.dev) cudaFreeAsync(g.dev, st);
         dGrids.release(); dGridScen.release(); dEtaIdx.release();

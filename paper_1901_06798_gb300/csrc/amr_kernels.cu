@@ -346,10 +346,13 @@ __device__ double uplift_sum(const TopoSet &ts, int scen, double B, double x, do
 
 // B (and, for level-1 initialisation, the state: h from the initial surface,
 // hu = h u, hv = h v from the initial velocities on wet cells) of the patches in `list`
-// at every cell inside the domain; cells outside are filled by bc_kernel.
+// at every cell inside the domain; cells outside are filled by bc_kernel.  At a
+// regrid (Old.descs set) a cell that an old patch of the level held in its
+// interior takes that patch's B -- the same value, without sampling the
+// topography again -- and only the other cells are sampled.
 template <typename T, bool PERT>
-__global__ void init_patch_kernel(LevelView L, const int *list, TopoSet ts, int cur, int set_state, double x0,
-                                  double y0, double dxl, double dyl)
+__global__ void init_patch_kernel(LevelView L, LevelView Old, const int *list, TopoSet ts, int cur, int set_state,
+                                  double x0, double y0, double dxl, double dyl)
 {
     const PatchDesc P = L.descs[list[blockIdx.y]];
     const int n = (P.nx + 4) * (P.ny + 4);
@@ -358,8 +361,20 @@ __global__ void init_patch_kernel(LevelView L, const int *list, TopoSet ts, int 
         int i = c % (P.nx + 4) - 2, j = c / (P.nx + 4) - 2;
         int I = P.i0 + i, J = P.j0 + j;
         if (I < 0 || I >= L.nxl || J < 0 || J >= L.nyl) continue;
-        double x = x0 + ((double)I + 0.5) * dxl, y = y0 + ((double)J + 0.5) * dyl;
         long long k = a.idx(i, j);
+        if (!set_state && Old.descs) {
+            bool held = false;
+            for (int m = 0; m < P.old_cnt && !held; m++) {
+                const PatchDesc Q = Old.descs[L.olds[P.old_off + m]];
+                if (I >= Q.i0 && I < Q.i0 + Q.nx && J >= Q.j0 && J < Q.j0 + Q.ny) {
+                    Acc<T> b = acc<T>(L.arena, Q);
+                    a.Bp()[k] = b.Bp()[b.idx(I - Q.i0, J - Q.j0)];
+                    held = true;
+                }
+            }
+            if (held) continue;
+        }
+        double x = x0 + ((double)I + 0.5) * dxl, y = y0 + ((double)J + 0.5) * dyl;
         double B0 = base_topo(ts, x, y);
         double B = uplift_sum(ts, P.scen, B0, x, y);
         a.Bp()[k] = (T)B;
@@ -832,12 +847,13 @@ int k_average(int prec, const LevelView &F, const LevelView &C, int npatch, int 
     return (int)cudaGetLastError();
 }
 
-int k_init_patches(int prec, const LevelView &L, const int *list, int nlist, int maxcells, const TopoSet &ts, int cur,
+int k_init_patches(int prec, const LevelView &L, const LevelView &Old, const int *list, int nlist, int maxcells,
+                   const TopoSet &ts, int cur,
                    int set_state, double x0, double y0, double dxl, double dyl, cudaStream_t st)
 {
     if (nlist <= 0) return 0;
     dim3 g = grid_for(maxcells, nlist, 128);
-    TSU_DISPATCH(prec, init_patch_kernel, <<<g, 128, 0, st>>>(L, list, ts, cur, set_state, x0, y0, dxl, dyl));
+    TSU_DISPATCH(prec, init_patch_kernel, <<<g, 128, 0, st>>>(L, Old, list, ts, cur, set_state, x0, y0, dxl, dyl));
     return (int)cudaGetLastError();
 }
 

@@ -92,8 +92,11 @@ int k_bc(int prec, const LevelView &L, const BcArgs &b, int nlist, int maxring, 
          cudaStream_t st);
 int k_average(int prec, const LevelView &F, const LevelView &C, int npatch, int maxcells, int cur_f, int cur_c, int r,
               double drytol, int *err, cudaStream_t st);
-int k_init_patches(int prec, const LevelView &L, const int *list, int nlist, int maxcells, const TopoSet &ts, int cur,
-                   int set_state, double x0, double y0, double dxl, double dyl, cudaStream_t st);
+// Old: the level's previous patch table at a regrid (B copied where an old patch held the cell), or a view
+// with null descs
+int k_init_patches(int prec, const LevelView &L, const LevelView &Old, const int *list, int nlist, int maxcells,
+                   const TopoSet &ts, int cur, int set_state, double x0, double y0, double dxl, double dyl,
+                   cudaStream_t st);
 int k_uplift(int prec, const LevelView &L, int npatch, int maxcells, const TopoDev &U, int scen, int cur, double x0,
              double y0, double dxl, double dyl, cudaStream_t st);
 int k_regrid_init(int prec, const LevelView &L, const LevelView &Old, const LevelView &C, const int *list, int nlist,

@@ -842,8 +842,10 @@ struct tsu_ctx {
         finish_level(lf);
         if (!fresh.empty()) {
             L.dList.upload(fresh, st);
-            kl(k_init_patches(prec, view(lf), L.dList.p, (int)fresh.size(), L.maxcells, topo(), L.cur, 0, c.x0, c.y0,
-                              L.dx, L.dy, st), "init B");
+            // B: copied where an old patch of the level held the cell, else sampled
+            kl(k_init_patches(prec, view(lf), view(lf, oldD.p), L.dList.p, (int)fresh.size(), L.maxcells, topo(), L.cur,
+                              0, c.x0, c.y0, L.dx, L.dy, st),
+               "init B");
             // B outside the domain for new boundary patches
             std::vector<int> bl;
             for (int k : fresh) if (L.P[k].bcmask) bl.push_back(k);
@@ -1166,8 +1168,10 @@ struct tsu_ctx {
                 }
         finish_level(0);
         L.dList.upload(all, st);
-        kl(k_init_patches(prec, view(0), L.dList.p, (int)all.size(), L.maxcells, topo(), L.cur, 1, c.x0, c.y0, L.dx, L.dy,
-                          st), "init level 1");
+        LevelView none{};
+        kl(k_init_patches(prec, view(0), none, L.dList.p, (int)all.size(), L.maxcells, topo(), L.cur, 1, c.x0, c.y0,
+                          L.dx, L.dy, st),
+           "init level 1");
         if (!L.bclist.empty()) {
             BcArgs ba{L.dBc.p, {c.bc[0], c.bc[1], c.bc[2], c.bc[3]}};
             kl(k_bc(prec, view(0), ba, (int)L.bclist.size(), L.maxring, L.cur, 0, 1, st), "bc B");

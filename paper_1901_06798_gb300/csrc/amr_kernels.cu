@@ -157,6 +157,18 @@ __global__ void ghost_fill_kernel(LevelView L, LevelView C, int cur, int cur_c, 
     Acc<T> a = acc<T>(L.arena, P);
     T *q0 = a.f(cur, 0), *q1 = a.f(cur, 1), *q2 = a.f(cur, 2);
     const T *Bp = a.Bp();
+    // the patch's neighbour boxes, staged once per CTA (each ghost cell searches them)
+    constexpr int kStaged = 32;
+    __shared__ int4 nbox[kStaged];
+    __shared__ int nid[kStaged];
+    const int ns = P.nbr_cnt < kStaged ? P.nbr_cnt : kStaged;
+    for (int m = threadIdx.x; m < ns; m += blockDim.x) {
+        const int qi = L.nbrs[P.nbr_off + m];
+        const PatchDesc &Q = L.descs[qi];
+        nbox[m] = make_int4(Q.i0, Q.j0, Q.i0 + Q.nx, Q.j0 + Q.ny);
+        nid[m] = qi;
+    }
+    __syncthreads();
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
         int i, j;
         ring_cell(P, g, i, j);
@@ -164,7 +176,11 @@ __global__ void ghost_fill_kernel(LevelView L, LevelView C, int cur, int cur_c, 
         if (I < 0 || I >= L.nxl || J < 0 || J >= L.nyl) continue;
         long long k = a.idx(i, j);
         int src = -1;
-        for (int m = 0; m < P.nbr_cnt; m++) {
+        for (int m = 0; m < ns; m++) {
+            const int4 b = nbox[m];
+            if (I >= b.x && I < b.z && J >= b.y && J < b.w) { src = nid[m]; break; }
+        }
+        for (int m = ns; src < 0 && m < P.nbr_cnt; m++) {   // more neighbours than staged
             int qi = L.nbrs[P.nbr_off + m];
             const PatchDesc &Q = L.descs[qi];
             if (I >= Q.i0 && I < Q.i0 + Q.nx && J >= Q.j0 && J < Q.j0 + Q.ny) { src = qi; break; }
@@ -842,7 +858,8 @@ int k_average(int prec, const LevelView &F, const LevelView &C, int npatch, int 
               double drytol, int *err, cudaStream_t st)
 {
     if (npatch <= 0) return 0;
-    dim3 g = grid_for(maxcells, npatch, 128);
+    // one thread per coarse cell: a patch has about maxcells / r^2 of them
+    dim3 g = grid_for((maxcells + r * r - 1) / (r * r), npatch, 128);
     TSU_DISPATCH(prec, average_kernel, <<<g, 128, 0, st>>>(F, C, cur_f, cur_c, r, drytol, err));
     return (int)cudaGetLastError();
 }

@@ -262,7 +262,7 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
  * clip(-B / 1000 m, -1, 5), |hu| / 10, |hv| / 10 m^2/s, the criterion flag),
  * which cells the criterion will flag at the next regrid.  With use_cnn the
  * flags become criterion(now) OR prediction, dilated by cnn_buffer instead of
- * b; the criterion stays both the fallback and the judge (cells it flags are
+ * b; the criterion stays both the fallback and the arbiter (cells it flags are
  * always refined).  Parameters: a flat FP32 vector (per layer W (C_out, C_in,
  * k, k) then b (C_out); layers 5->16 3x3, 16->16 3x3, 16->16 3x3, 16->1 1x1).
  * ------------------------------------------------------------------------- */

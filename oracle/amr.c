@@ -16,7 +16,7 @@
  *               interpolation and averaging that keep the ocean at rest.
  *   Sec. 5.1.2  zeta output field (Eq. zeta) and gauges.
  *
- * Readings where the paper is silent (listed in the design doc):
+ * Readings where the paper is silent:
  *   - interpolation: linear in time of (h, hu, hv) as q0 + a (q1 - q0), then
  *     minmod-limited linear in space of (eta, hu, hv) using wet neighbours
  *     only; fine h = max(0, eta - B_f); momenta zeroed below drytol.  A dry

@@ -15,7 +15,7 @@
  *   Sec. 2.1, drag D (Manning, n)           friction step after each level step
  *   spherical coordinates (Sec. 1, supported for transoceanic runs): capacity-form split step
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - f-wave form: the solver decomposes the flux jump (including the
  *     bathymetry source -g hbar dB folded into the momentum flux jump as
  *     g hbar d(eta)) into f-waves Z^p = s^p W^p, so A-dQ/A+dQ are the sums of

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
 
-Bars (written here, derived in the design doc):
+Bars (written here; FP32 rounding in the perturbation form is 1e-7 m per step on O(1 m) values):
   * FP64: relative error per field (max |gpu - oracle| / max |oracle|) <= 1e-12
     after the stated steps; patch lists (integer work) bit-exact; the FP64
     kernels are built without contraction and follow the oracle's operation

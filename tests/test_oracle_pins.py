@@ -20,7 +20,7 @@ G = 9.81
 
 
 # --------------------------------------------------------------------------
-# Riemann solver (Sec. 2.2; solver internals: the reading in the design doc)
+# Riemann solver (Sec. 2.2; the paper only cites the solver, so its internals are a reading)
 
 def _flux(h, hn, ht):
     """Physical flux of the x-split shallow water equations (Eq. swe)."""

@@ -189,3 +189,25 @@ def test_lonlat_workload_is_the_plane_workload_near_its_middle_latitude():
     _, ea = a.read_gauges()
     _, eb = b.read_gauges()
     assert np.abs(ea - eb).max() <= 0.05 * np.abs(eb).max()
+
+
+def test_time_step_from_capacity_scaled_speeds():
+    """Still water over a flat bed at 30-40 N: every edge has the speed
+    c = sqrt(g h).  After the first step dt comes from the sweeps' speeds:
+    x edges of row J count c / kap_J, y edges c ced_e / kbar_e (reading of
+    the capacity form's Courant numbers), so dt = 0.9 / max(c / (min kap dxp),
+    c max(ced / kbar) / dyp) with dxp = dyp = R dphi."""
+    n, d, depth = 20, 0.5, 3000.0
+    y0 = 30.0
+    cfg = W.base_config(nx=n, ny=n, x0=150.0, y0=y0, dx=d, dy=d, bc=[W.BC_WALL] * 4, spherical=1)
+    w = dict(cfg=cfg, topo=[(np.full((2, 2), -depth), 150.0, y0, n * d, n * d)], eta=[], uplift=[],
+             gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    o.step(3)
+    c = np.sqrt(9.81 * depth)
+    kap = np.array([_kappa(y0, d, J) for J in range(-1, n + 1)])      # rows -1 .. n
+    ced = np.cos((y0 + np.arange(0, n + 1) * d) * D2R)                # edges 0 .. n
+    kbar = 0.5 * (kap[:-1] + kap[1:])                                  # edge e between rows e-1, e
+    dp = R * d * D2R
+    rate = max(c / (kap[1:-1].min() * dp), c * (ced / kbar).max() / dp)
+    assert abs(o.stats()["dt"] - 0.9 / rate) <= 1e-12 * (0.9 / rate)

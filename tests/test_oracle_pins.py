@@ -106,6 +106,69 @@ def test_riemann_wall_no_mass_flux():
         assert abs(hL * uL + amdq[0]) < 1e-12
 
 
+def test_riemann_single_shock_is_one_wave():
+    """States joined by one 3-shock (Rankine-Hugoniot: s [h] = [hu],
+    s [hu] = [hu^2 + g h^2 / 2]; right state at rest, depths 2 -> 1 and 3 -> 0.5,
+    Lax-admissible) make one wave: for the shallow water equations the Roe
+    average has the shock speed as an eigenvalue, so the Einfeldt bound
+    s3 = max(u_r + c_r, u_hat + c_hat) is the shock speed and the whole flux
+    jump goes into wave 3.  An unweighted velocity average (or any other
+    average) leaves part of the jump in wave 1."""
+    g = 9.81
+    for hL, hR in ((2.0, 1.0), (3.0, 0.5)):
+        # mass: s (hR - hL) = -hL uL; momentum: s (-hL uL) = g/2 (hR^2 - hL^2) - hL uL^2
+        uL = math.sqrt(0.5 * g * (hL * hL - hR * hR) * (hL - hR) / (hL * hR))
+        sh = hL * uL / (hL - hR)
+        assert math.sqrt(g * hR) < sh < uL + math.sqrt(g * hL)    # Lax conditions (u_r = 0)
+        Z, s, wl, wr = oracle.riemann(hL, hL * uL, 0.0, 0.0, hR, 0.0, 0.0, 0.0)
+        assert s[2] == pytest.approx(sh, rel=1e-13)
+        assert np.abs(Z[0]).max() <= 1e-12 * np.abs(Z[2]).max()
+        assert np.abs(Z[2][:2] - np.array([-hL * uL, 0.5 * g * (hR * hR - hL * hL) - hL * uL * uL])).max() \
+            <= 1e-12 * np.abs(Z[2]).max()
+
+
+def test_square_pulse_makes_no_new_minimum():
+    """A 0.1 m square pulse on 1 m of still water splits into two pulses.  The
+    wave-limited scheme is TVD in each characteristic field of the linearised
+    system, so the surface stays above the still level up to the nonlinear
+    coupling (1e-3 m at this amplitude); a limiter fed the downwind neighbour
+    undershoots by several millimetres."""
+    n = 400
+    cfg = W.base_config(nx=n, ny=4, dx=1.0, dy=1.0, bc=[W.BC_EXTRAP, W.BC_EXTRAP, W.BC_WALL, W.BC_WALL])
+    xs = np.arange(n) + 0.5
+    row = np.where((xs > 150) & (xs < 200), 1.1, 1.0)
+    w = dict(cfg=cfg, topo=[(np.zeros((2, 2)), 0.0, 0.0, float(n), 4.0)],
+             eta=[(0, np.stack([row, row]), 0.5, 0.0, 1.0, 4.0)], uplift=[], gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    o.step(60)
+    h = o.level_array(0, 1, "h")
+    assert h.min() > 1.0 - 1e-3
+    assert h.max() < 1.1
+
+
+def test_depth_flags_refine_the_shallow_band():
+    """At rest, the only flags are depth < 200 m: after the first regrid every
+    level-1 cell shallower than that is covered by level 2, and most of the
+    covered area lies within the flag buffer of a shallow cell."""
+    w = W.amr3(L=240e3, dx1=4000.0, steps=6)
+    cfg = dict(w["cfg"], num_levels=2, ratios=[4], flag_eta_tol=0.0)
+    w = dict(w, cfg=cfg, uplift=[])
+    o = W.load(oracle.Oracle(cfg), w)
+    B = o.level_array(0, 1, "B")
+    shallow = -B < 200.0
+    cov = np.zeros_like(shallow)
+    for (i0, j0, nx, ny), _ in o.patches(0, 2):
+        cov[j0 // 4:(j0 + ny) // 4, i0 // 4:(i0 + nx) // 4] = True
+    assert shallow.any() and (~shallow).any()
+    assert cov[shallow].all()
+    b = cfg["regrid_interval"]
+    near = np.zeros_like(shallow)
+    for dj in range(-b, b + 1):
+        for di in range(-b, b + 1):
+            near |= np.roll(np.roll(shallow, dj, axis=0), di, axis=1)
+    assert (cov & ~near).sum() <= 0.5 * cov.sum()
+
+
 def test_mc_limiter_table():
     """MC limiter phi = max(0, min((1+t)/2, 2, 2t)) at tabulated points."""
     table = {-1.0: 0.0, 0.0: 0.0, 0.25: 0.5, 1 / 3: 2 / 3, 0.5: 0.75, 1.0: 1.0, 2.0: 1.5, 3.0: 2.0, 10.0: 2.0}
@@ -425,3 +488,28 @@ def test_cluster_respects_nesting():
     _check_boxes(f, b)
     for i0, j0, w, h in b:
         assert nest[j0:j0 + h, i0:i0 + w].all()
+
+
+def test_interpolation_makes_no_new_extrema():
+    """A limited linear reconstruction keeps every fine value inside the range
+    of its coarse cell and the neighbours (no new extrema).  Coarse surface
+    with a kink: slope 0.02 per cell, then 0.08; the cell at the kink has
+    one-sided differences in a ratio of 4, where a slope larger than the
+    smaller difference would push its outer fine cells past a neighbour."""
+    nx, ny, dx = 40, 8, 100.0
+    i = np.arange(nx)
+    eta_c = np.where(i < 20, 0.02 * i, 0.4 + 0.08 * (i - 20))
+    cfg = W.base_config(nx=nx, ny=ny, dx=dx, dy=dx, bc=[W.BC_EXTRAP] * 4, num_levels=2, ratios=[4],
+                        regrid_interval=4, regions=[[1200.0, 0.0, 2800.0, ny * dx, 2, 2]])
+    w = dict(cfg=cfg, topo=[(np.full((2, 2), -100.0), 0.0, 0.0, nx * dx, ny * dx)],
+             eta=[(0, np.stack([eta_c, eta_c]), 0.5 * dx, 0.0, dx, ny * dx)], uplift=[], gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    e1, e2 = o.level_array(0, 1, "eta"), o.level_array(0, 2, "eta")
+    assert np.abs(e1[3] - eta_c).max() < 1e-12
+    checked = 0
+    for J, I in zip(*np.nonzero(~np.isnan(e2))):
+        Ic, Jc = I // 4, J // 4
+        nb = e1[max(Jc - 1, 0):Jc + 2, max(Ic - 1, 0):Ic + 2]
+        assert nb.min() - 1e-12 <= e2[J, I] <= nb.max() + 1e-12, (I, J, e2[J, I], nb.min(), nb.max())
+        checked += 1
+    assert checked > 0 and not np.isnan(e2[:, 80:84]).all()    # the kink cell is refined

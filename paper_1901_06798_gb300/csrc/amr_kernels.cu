@@ -616,42 +616,57 @@ __global__ void cnn_union_kernel(uint8_t *raw, const uint8_t *cov, const float *
 
 // ---------------------------------------------------------------- rates, dt
 
+// Largest cell wave speeds (x, y) of the patches in `list`, for the first dt
+// of a level or of new patches.  One block walks whole patches (32 x 8
+// threads over columns and rows, no index division) and reduces in shared
+// memory: one atomic pair per patch, not per warp (thousands of patches from a
+// regrid would otherwise queue on the same two words).
 template <typename T, bool PERT>
-__global__ void cell_speed_kernel(LevelView L, const int *list, int cur, double g, double drytol,
-                                  unsigned long long *smax)
+__global__ void __launch_bounds__(256) cell_speed_kernel(LevelView L, const int *list, int nlist, int cur, double g,
+                                                         double drytol, unsigned long long *smax)
 {
-    const PatchDesc P = L.descs[list ? list[blockIdx.y] : blockIdx.y];
-    const int n = P.nx * P.ny;
-    Acc<T> a = acc<T>(L.arena, P);
-    T sxT = T(0), syT = T(0);   // running maxima in the state's precision (no FP64 work per cell in FP32)
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        int i = c % P.nx, j = c / P.nx;
-        long long k = a.idx(i, j);
-        T q0 = a.f(cur, 0)[k];
-        T h = PERT ? q0 - a.Bp()[k] : q0;
-        if (h < (T)drytol) continue;
-        T cc = PERT ? (T)sqrtf((float)((T)g * h)) : (T)sqrt((double)((T)g * h));
-        T ux = a.f(cur, 1)[k] / h, uy = a.f(cur, 2)[k] / h;
-        T ax = (ux < T(0) ? -ux : ux) + cc, ay = (uy < T(0) ? -uy : uy) + cc;
-        if (L.kap) {   // latitude-longitude grids: x speeds over the row's capacity, y speeds
-                       // times the larger edge length over it (the sweeps' Courant numbers)
-            const double kd = L.kap[P.j0 + j + 2];
-            const T kj = (T)kd;
-            const T cj = (T)(fmax(L.ced[P.j0 + j + 2], L.ced[P.j0 + j + 3]) / kd);
-            ax = ax / kj;
-            ay = ay * cj;
+    __shared__ double red[2][8];
+    const int tx = threadIdx.x, ty = threadIdx.y, lane = ty * 32 + tx;
+    for (int pi = blockIdx.x; pi < nlist; pi += gridDim.x) {
+        const PatchDesc P = L.descs[list ? list[pi] : pi];
+        Acc<T> a = acc<T>(L.arena, P);
+        T sxT = T(0), syT = T(0);   // running maxima in the state's precision (no FP64 work per cell in FP32)
+        for (int j = ty; j < P.ny; j += 8) {
+            const T *r0 = a.f(cur, 0) + a.idx(0, j), *r1 = a.f(cur, 1) + a.idx(0, j), *r2 = a.f(cur, 2) + a.idx(0, j);
+            const T *rB = a.Bp() + a.idx(0, j);
+            for (int i = tx; i < P.nx; i += 32) {
+                T q0 = r0[i];
+                T h = PERT ? q0 - rB[i] : q0;
+                if (h < (T)drytol) continue;
+                T cc = PERT ? (T)sqrtf((float)((T)g * h)) : (T)sqrt((double)((T)g * h));
+                T ux = r1[i] / h, uy = r2[i] / h;
+                T ax = (ux < T(0) ? -ux : ux) + cc, ay = (uy < T(0) ? -uy : uy) + cc;
+                if (L.kap) {   // latitude-longitude grids: x speeds over the row's capacity, y speeds
+                               // times the larger edge length over it (the sweeps' Courant numbers)
+                    const double kd = L.kap[P.j0 + j + 2];
+                    const T kj = (T)kd;
+                    const T cj = (T)(fmax(L.ced[P.j0 + j + 2], L.ced[P.j0 + j + 3]) / kd);
+                    ax = ax / kj;
+                    ay = ay * cj;
+                }
+                sxT = ax > sxT ? ax : sxT;
+                syT = ay > syT ? ay : syT;
+            }
         }
-        sxT = ax > sxT ? ax : sxT;
-        syT = ay > syT ? ay : syT;
-    }
-    double sx = (double)sxT, sy = (double)syT;
-    for (int o = 16; o > 0; o >>= 1) {
-        sx = fmax(sx, __shfl_xor_sync(0xffffffffu, sx, o));
-        sy = fmax(sy, __shfl_xor_sync(0xffffffffu, sy, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (sx > 0.0) atomicMax(smax + 2 * P.scen, (unsigned long long)__double_as_longlong(sx));
-        if (sy > 0.0) atomicMax(smax + 2 * P.scen + 1, (unsigned long long)__double_as_longlong(sy));
+        double sx = (double)sxT, sy = (double)syT;
+        for (int o = 16; o > 0; o >>= 1) {
+            sx = fmax(sx, __shfl_xor_sync(0xffffffffu, sx, o));
+            sy = fmax(sy, __shfl_xor_sync(0xffffffffu, sy, o));
+        }
+        if (tx == 0) { red[0][ty] = sx; red[1][ty] = sy; }
+        __syncthreads();
+        if (lane == 0) {
+            double mx = 0.0, my = 0.0;
+            for (int k = 0; k < 8; k++) { mx = fmax(mx, red[0][k]); my = fmax(my, red[1][k]); }
+            if (mx > 0.0) atomicMax(smax + 2 * P.scen, (unsigned long long)__double_as_longlong(mx));
+            if (my > 0.0) atomicMax(smax + 2 * P.scen + 1, (unsigned long long)__double_as_longlong(my));
+        }
+        __syncthreads();   // red is reused by the next patch
     }
 }
 
@@ -964,8 +979,9 @@ int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int m
                  double drytol, unsigned long long *smax, cudaStream_t st)
 {
     if (nlist <= 0) return 0;
-    dim3 gr = grid_for(maxcells, nlist, 128);
-    TSU_DISPATCH(prec, cell_speed_kernel, <<<gr, 128, 0, st>>>(L, list, cur, g, drytol, smax));
+    (void)maxcells;
+    const int blocks = nlist < 152 * 8 ? nlist : 152 * 8;   // 8 blocks of 256 threads per SM
+    TSU_DISPATCH(prec, cell_speed_kernel, <<<blocks, dim3(32, 8), 0, st>>>(L, list, nlist, cur, g, drytol, smax));
     return (int)cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@
 // scenarios) into one launch.
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <type_traits>
 #include "amr_kernels.h"
 
 namespace tsu {
@@ -49,25 +50,31 @@ __device__ __forceinline__ void ring_cell(const PatchDesc &P, int g, int &i, int
     i = k < 2 ? -2 + k : P.nx + (k - 2);
 }
 
-__device__ __forceinline__ double minmod(double a, double b)
+// Arithmetic of the coarse-to-fine interpolation: double for the FP64 state
+// (the oracle's operations exactly), float for the FP32 perturbation form
+// (GB300's FP64 rate is a small fraction of its FP32 rate; eta' values are O(1 m))
+template <bool PERT> using InterpT = typename std::conditional<PERT, float, double>::type;
+
+template <typename W> __device__ __forceinline__ W minmod(W a, W b)
 {
-    if (a > 0.0 && b > 0.0) return fmin(a, b);
-    if (a < 0.0 && b < 0.0) return fmax(a, b);
-    return 0.0;
+    if (a > W(0) && b > W(0)) return a < b ? a : b;
+    if (a < W(0) && b < W(0)) return a > b ? a : b;
+    return W(0);
 }
 
-// one coarse cell's (eta, hu, hv) at time fraction alpha, in double
-struct CVal {
+// one coarse cell's (eta, hu, hv) at time fraction alpha
+template <typename W> struct CVal {
     int found, wet;
-    double q[3];
+    W q[3];
 };
 
 template <typename T, bool PERT>
-__device__ CVal coarse_value(const LevelView &C, int cur_c, const int *cmap, const PatchDesc &F, int I, int J,
-                             double alpha, double drytol)
+__device__ CVal<InterpT<PERT>> coarse_value(const LevelView &C, int cur_c, const int *cmap, const PatchDesc &F, int I,
+                                            int J, InterpT<PERT> alpha, InterpT<PERT> drytol)
 {
-    CVal v;
-    v.found = 0; v.wet = 0; v.q[0] = v.q[1] = v.q[2] = 0.0;
+    using W = InterpT<PERT>;
+    CVal<W> v;
+    v.found = 0; v.wet = 0; v.q[0] = v.q[1] = v.q[2] = W(0);
     if (I < 0 || I >= C.nxl || J < 0 || J >= C.nyl) return v;
     int mi = I - F.cmap_i0, mj = J - F.cmap_j0;
     if (mi < 0 || mi >= F.cmap_w || mj < 0 || mj >= F.cmap_h) return v;
@@ -76,18 +83,18 @@ __device__ CVal coarse_value(const LevelView &C, int cur_c, const int *cmap, con
     const PatchDesc P = C.descs[cp];
     Acc<T> a = acc<T>(C.arena, P);
     long long k = a.idx(I - P.i0, J - P.j0);
-    double B = (double)a.Bp()[k];
-    double q0n = (double)a.f(cur_c, 0)[k], q1n = (double)a.f(cur_c, 1)[k], q2n = (double)a.f(cur_c, 2)[k];
-    double q0, q1, q2;
-    if (alpha == 1.0) { q0 = q0n; q1 = q1n; q2 = q2n; }
+    W B = (W)a.Bp()[k];
+    W q0n = (W)a.f(cur_c, 0)[k], q1n = (W)a.f(cur_c, 1)[k], q2n = (W)a.f(cur_c, 2)[k];
+    W q0, q1, q2;
+    if (alpha == W(1)) { q0 = q0n; q1 = q1n; q2 = q2n; }
     else {
-        double q0o = (double)a.f(1 - cur_c, 0)[k], q1o = (double)a.f(1 - cur_c, 1)[k], q2o = (double)a.f(1 - cur_c, 2)[k];
+        W q0o = (W)a.f(1 - cur_c, 0)[k], q1o = (W)a.f(1 - cur_c, 1)[k], q2o = (W)a.f(1 - cur_c, 2)[k];
         q0 = q0o + alpha * (q0n - q0o);
         q1 = q1o + alpha * (q1n - q1o);
         q2 = q2o + alpha * (q2n - q2o);
     }
     v.found = 1;
-    double h = PERT ? q0 - B : q0;
+    W h = PERT ? q0 - B : q0;
     v.wet = h >= drytol;
     v.q[0] = PERT ? q0 : h + B;
     v.q[1] = q1;
@@ -98,49 +105,56 @@ __device__ CVal coarse_value(const LevelView &C, int cur_c, const int *cmap, con
 // Space-time interpolation of fine cell (I, J) of level F from the coarse
 // level (minmod-limited linear in space of eta, hu, hv over wet neighbours;
 // a dry coarse centre takes the lowest wet surface of its 3x3 neighbourhood).
-// Writes q0 (h or eta'), q1, q2; returns false on a nesting error.
+// Writes q0 (h or eta'), q1, q2; returns false on a nesting error.  In the
+// perturbation form the surface is written as eta' itself, not as
+// (eta' - B) + B, which in FP32 would round eta' to the ulp of the depth.
 template <typename T, bool PERT>
 __device__ bool interp_fine(const LevelView &C, int cur_c, const int *cmap, const PatchDesc &F, int r, int I, int J,
-                            double Bf, double alpha, double drytol, T &o0, T &o1, T &o2)
+                            double Bfd, double alphad, double drytold, T &o0, T &o1, T &o2)
 {
+    using W = InterpT<PERT>;
+    const W Bf = (W)Bfd, alpha = (W)alphad, drytol = (W)drytold;
     int Ic = I / r, Jc = J / r;
-    CVal c = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic, Jc, alpha, drytol);
+    CVal<W> c = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic, Jc, alpha, drytol);
     if (!c.found) return false;
-    double hf, hu, hv;
+    W hf, hu, hv, ef;   // ef: the surface eta when hf > 0
     if (!c.wet) {
-        double eref = 0.0;
+        W eref = W(0);
         int any = 0;
         for (int dj = -1; dj <= 1; dj++)
             for (int di = -1; di <= 1; di++) {
                 if (di == 0 && dj == 0) continue;
-                CVal nb = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic + di, Jc + dj, alpha, drytol);
+                CVal<W> nb = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic + di, Jc + dj, alpha, drytol);
                 if (nb.found && nb.wet && (!any || nb.q[0] < eref)) { eref = nb.q[0]; any = 1; }
             }
-        hf = any ? eref - Bf : 0.0;
-        if (hf < 0.0) hf = 0.0;
-        hu = 0.0; hv = 0.0;
+        hf = any ? eref - Bf : W(0);
+        ef = eref;
+        if (hf < W(0)) hf = W(0);
+        hu = W(0); hv = W(0);
     } else {
-        CVal xm = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic - 1, Jc, alpha, drytol);
-        CVal xp = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic + 1, Jc, alpha, drytol);
-        CVal ym = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic, Jc - 1, alpha, drytol);
-        CVal yp = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic, Jc + 1, alpha, drytol);
-        double xi = ((double)(I - Ic * r) + 0.5) / (double)r - 0.5;
-        double et = ((double)(J - Jc * r) + 0.5) / (double)r - 0.5;
-        double qf[3];
+        CVal<W> xm = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic - 1, Jc, alpha, drytol);
+        CVal<W> xp = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic + 1, Jc, alpha, drytol);
+        CVal<W> ym = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic, Jc - 1, alpha, drytol);
+        CVal<W> yp = coarse_value<T, PERT>(C, cur_c, cmap, F, Ic, Jc + 1, alpha, drytol);
+        W xi = ((W)(I - Ic * r) + W(0.5)) / (W)r - W(0.5);
+        W et = ((W)(J - Jc * r) + W(0.5)) / (W)r - W(0.5);
+        W qf[3];
         for (int m = 0; m < 3; m++) {
-            double dxp = (xp.found && xp.wet) ? xp.q[m] - c.q[m] : 0.0;
-            double dxm = (xm.found && xm.wet) ? c.q[m] - xm.q[m] : 0.0;
-            double dyp = (yp.found && yp.wet) ? yp.q[m] - c.q[m] : 0.0;
-            double dym = (ym.found && ym.wet) ? c.q[m] - ym.q[m] : 0.0;
-            double sx = minmod(dxp, dxm), sy = minmod(dyp, dym);
+            W dxp = (xp.found && xp.wet) ? xp.q[m] - c.q[m] : W(0);
+            W dxm = (xm.found && xm.wet) ? c.q[m] - xm.q[m] : W(0);
+            W dyp = (yp.found && yp.wet) ? yp.q[m] - c.q[m] : W(0);
+            W dym = (ym.found && ym.wet) ? c.q[m] - ym.q[m] : W(0);
+            W sx = minmod<W>(dxp, dxm), sy = minmod<W>(dyp, dym);
             qf[m] = (c.q[m] + xi * sx) + et * sy;
         }
         hf = qf[0] - Bf;
-        if (hf < 0.0) hf = 0.0;
-        if (hf < drytol) { hu = 0.0; hv = 0.0; }
+        ef = qf[0];
+        if (hf < W(0)) hf = W(0);
+        if (hf < drytol) { hu = W(0); hv = W(0); }
         else { hu = qf[1]; hv = qf[2]; }
     }
-    o0 = PERT ? (T)(hf + Bf) : (T)hf;
+    if (PERT) o0 = (T)(hf > W(0) ? ef : Bf);
+    else o0 = (T)hf;
     o1 = (T)hu;
     o2 = (T)hv;
     return true;

@@ -273,9 +273,16 @@ __global__ void bc_kernel(LevelView L, int cur, BcArgs bcs, int do_state, int do
 
 // ---------------------------------------------------------------- averaging
 
+// Averaging of each fine patch onto the coarse cells it covers: surface over
+// the wet fine cells, momenta over all (capacity-weighted on latitude-longitude
+// grids).  Arithmetic in the state's precision (InterpT); in the perturbation
+// form the coarse surface is written as the mean eta' itself, not as
+// (mean - B) + B.
 template <typename T, bool PERT>
-__global__ void average_kernel(LevelView Fv, LevelView C, int cur_f, int cur_c, int r, double drytol, int *err)
+__global__ void average_kernel(LevelView Fv, LevelView C, int cur_f, int cur_c, int r, double drytold, int *err)
 {
+    using W = InterpT<PERT>;
+    const W drytol = (W)drytold;
     const PatchDesc F = Fv.descs[blockIdx.y];
     const int cw = F.nx / r, ch = F.ny / r;
     const int n = cw * ch;
@@ -286,39 +293,41 @@ __global__ void average_kernel(LevelView Fv, LevelView C, int cur_f, int cur_c, 
         int mi = Ic - F.cmap_i0, mj = Jc - F.cmap_j0;
         int cp = Fv.cmap[F.cmap_off + mj * F.cmap_w + mi];
         if (cp < 0) { atomicOr(err, 2); continue; }
-        double se = 0.0, su = 0.0, sv = 0.0;
+        W se = W(0), su = W(0), sv = W(0);
         int nwet = 0;
-        double kw = 0.0, ka = 0.0;   // latitude-longitude grids: capacities of the wet and of all fine cells
+        W kw = W(0), ka = W(0);   // latitude-longitude grids: capacities of the wet and of all fine cells
         for (int jj = 0; jj < r; jj++) {
-            const double kf_ = Fv.kap ? Fv.kap[Jc * r + jj + 2] : 1.0;
+            const W kf_ = Fv.kap ? (W)Fv.kap[Jc * r + jj + 2] : W(1);
             for (int ii = 0; ii < r; ii++) {
                 long long kf = fa.idx(Ic * r + ii - F.i0, Jc * r + jj - F.j0);
-                double B = (double)fB[kf];
-                double q0 = (double)f0[kf];
-                double h = PERT ? q0 - B : q0;
+                W B = (W)fB[kf];
+                W q0 = (W)f0[kf];
+                W h = PERT ? q0 - B : q0;
                 if (Fv.kap) {
                     if (h >= drytol) { se = se + kf_ * (PERT ? q0 : h + B); kw = kw + kf_; nwet++; }
-                    su = su + kf_ * (double)f1[kf];
-                    sv = sv + kf_ * (double)f2[kf];
+                    su = su + kf_ * (W)f1[kf];
+                    sv = sv + kf_ * (W)f2[kf];
                     ka = ka + kf_;
                 } else {
                     if (h >= drytol) { se = se + (PERT ? q0 : h + B); nwet++; }
-                    su = su + (double)f1[kf];
-                    sv = sv + (double)f2[kf];
+                    su = su + (W)f1[kf];
+                    sv = sv + (W)f2[kf];
                 }
             }
         }
         const PatchDesc P = C.descs[cp];
         Acc<T> ca = acc<T>(C.arena, P);
         long long kc = ca.idx(Ic - P.i0, Jc - P.j0);
-        double Bc = (double)ca.Bp()[kc];
-        double hc = 0.0;
+        W Bc = (W)ca.Bp()[kc];
+        W hc = W(0), ec = Bc;   // ec: the coarse surface
         if (nwet > 0) {
-            hc = (Fv.kap ? se / kw : se / (double)nwet) - Bc;
-            if (hc < 0.0) hc = 0.0;
+            ec = Fv.kap ? se / kw : se / (W)nwet;
+            hc = ec - Bc;
+            if (hc < W(0)) hc = W(0);
         }
-        double rr = Fv.kap ? ka : (double)(r * r);
-        ca.f(cur_c, 0)[kc] = PERT ? (T)(hc + Bc) : (T)hc;
+        W rr = Fv.kap ? ka : (W)(r * r);
+        if (PERT) ca.f(cur_c, 0)[kc] = (T)(hc > W(0) ? ec : Bc);
+        else ca.f(cur_c, 0)[kc] = (T)hc;
         if (hc < drytol) { ca.f(cur_c, 1)[kc] = T(0); ca.f(cur_c, 2)[kc] = T(0); }
         else { ca.f(cur_c, 1)[kc] = (T)(su / rr); ca.f(cur_c, 2)[kc] = (T)(sv / rr); }
     }

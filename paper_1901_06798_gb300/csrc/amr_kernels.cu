@@ -640,21 +640,23 @@ __global__ void cnn_union_kernel(uint8_t *raw, const uint8_t *cov, const float *
 // ---------------------------------------------------------------- rates, dt
 
 // Largest cell wave speeds (x, y) of the patches in `list`, for the first dt
-// of a level or of new patches.  One block walks whole patches (32 x 8
-// threads over columns and rows, no index division) and reduces in shared
-// memory: one atomic pair per patch, not per warp (thousands of patches from a
-// regrid would otherwise queue on the same two words).
+// of a level or of new patches.  Blocks walk patches (blockIdx.y) and, within
+// a patch, interleaved groups of 8 rows (blockIdx.x; 32 x 8 threads over
+// columns and rows, no index division), then reduce in shared memory: one
+// atomic pair per block and patch, not per warp (thousands of patches from a
+// regrid would otherwise queue on the same two words).  Many small patches
+// take one block each; one large patch spreads over many.
 template <typename T, bool PERT>
 __global__ void __launch_bounds__(256) cell_speed_kernel(LevelView L, const int *list, int nlist, int cur, double g,
                                                          double drytol, unsigned long long *smax)
 {
     __shared__ double red[2][8];
     const int tx = threadIdx.x, ty = threadIdx.y, lane = ty * 32 + tx;
-    for (int pi = blockIdx.x; pi < nlist; pi += gridDim.x) {
+    for (int pi = blockIdx.y; pi < nlist; pi += gridDim.y) {
         const PatchDesc P = L.descs[list ? list[pi] : pi];
         Acc<T> a = acc<T>(L.arena, P);
         T sxT = T(0), syT = T(0);   // running maxima in the state's precision (no FP64 work per cell in FP32)
-        for (int j = ty; j < P.ny; j += 8) {
+        for (int j = blockIdx.x * 8 + ty; j < P.ny; j += gridDim.x * 8) {
             const T *r0 = a.f(cur, 0) + a.idx(0, j), *r1 = a.f(cur, 1) + a.idx(0, j), *r2 = a.f(cur, 2) + a.idx(0, j);
             const T *rB = a.Bp() + a.idx(0, j);
             for (int i = tx; i < P.nx; i += 32) {
@@ -1002,9 +1004,13 @@ int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int m
                  double drytol, unsigned long long *smax, cudaStream_t st)
 {
     if (nlist <= 0) return 0;
-    (void)maxcells;
-    const int blocks = nlist < 152 * 8 ? nlist : 152 * 8;   // 8 blocks of 256 threads per SM
-    TSU_DISPATCH(prec, cell_speed_kernel, <<<blocks, dim3(32, 8), 0, st>>>(L, list, nlist, cur, g, drytol, smax));
+    // about 8 blocks of 256 threads per SM in all: patches first, then row groups within a patch
+    constexpr int kBlocks = 152 * 8;
+    const int by = nlist < kBlocks ? nlist : kBlocks;
+    int bx = (maxcells + 256 * 32 - 1) / (256 * 32);   // about 32 cells per thread
+    if (bx > kBlocks / by) bx = kBlocks / by;
+    if (bx < 1) bx = 1;
+    TSU_DISPATCH(prec, cell_speed_kernel, <<<dim3(bx, by), dim3(32, 8), 0, st>>>(L, list, nlist, cur, g, drytol, smax));
     return (int)cudaGetLastError();
 }
 

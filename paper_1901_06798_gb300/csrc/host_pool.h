@@ -12,13 +12,25 @@
 #include <thread>
 #include <vector>
 
+#include <unistd.h>
+
 namespace tsu {
 
 class HostPool {
 public:
+    // The pool of this process.  A child forked after the pool started has the
+    // object but not its threads, so a new pool is made for the child (the
+    // parent's copy is left as it is).
     static HostPool &get()
     {
-        static HostPool *p = new HostPool(std::max(1, std::min(16, (int)std::thread::hardware_concurrency())));
+        static std::mutex mk;
+        static HostPool *p = nullptr;
+        static pid_t owner = 0;
+        std::lock_guard<std::mutex> lk(mk);
+        if (!p || owner != getpid()) {
+            p = new HostPool(std::max(1, std::min(16, (int)std::thread::hardware_concurrency())));
+            owner = getpid();
+        }
         return *p;
     }
     int size() const { return nthreads_; }

@@ -70,3 +70,25 @@ def test_flags_touching_the_mask_edges():
     g = np.zeros((1, 1), dtype=np.uint8)
     g[0, 0] = 1
     assert _same(g).tolist() == [[0, 0, 1, 1]]
+
+
+def test_clustering_in_a_forked_child():
+    """The host pool behind the clustering survives a fork: a child forked
+    after the pool started gets a pool of its own and returns the parent's
+    boxes (a pool without its worker threads would wait forever)."""
+    import os
+    import warnings
+    from paper_1901_06798_gb300 import binding
+    F = np.zeros((900, 1100), np.uint8)
+    F[300:500, 200:700] = 1
+    F[620:700, 100:160] = 1
+    N = np.ones_like(F)
+    a = binding.cluster_flags(F, N, 0.7, 4, 60)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", DeprecationWarning)
+        pid = os.fork()
+    if pid == 0:
+        b = binding.cluster_flags(F, N, 0.7, 4, 60)
+        os._exit(0 if np.array_equal(a, b) else 3)
+    _, status = os.waitpid(pid, 0)
+    assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0

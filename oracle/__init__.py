@@ -100,7 +100,7 @@ class ora_config(C.Structure):
         ("patch_max", C.c_int), ("level1_tile", C.c_int),
         ("n_regions", C.c_int), ("regions", (C.c_double * 6) * MAX_REGIONS),
         ("n_scenarios", C.c_int), ("transverse", C.c_int), ("cluster_eff", C.c_double),
-        ("manning_n", C.c_double), ("spherical", C.c_int), ("earth_radius", C.c_double),
+        ("manning_n", C.c_double), ("spherical", C.c_int), ("earth_radius", C.c_double), ("reflux", C.c_int),
     ]
 
 
@@ -215,6 +215,7 @@ def make_config(cfg: dict) -> ora_config:
     c.manning_n = cfg.get("manning_n", 0.0)
     c.spherical = cfg.get("spherical", 0)
     c.earth_radius = cfg.get("earth_radius", 0.0)
+    c.reflux = cfg.get("reflux", 0)
     return c
 
 

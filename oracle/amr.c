@@ -67,6 +67,13 @@ typedef struct Scen {
     int substep[ORA_MAX_LEVELS];
     long cfl_viol;
     double cell_updates;
+    /* refluxing registers of level l as the coarse level of l+1, over its whole
+     * index space, 4 faces (W, E, S, N) per cell: dt times the mass flux the
+     * cell's own update used (cflux), the time- and length-weighted sum of the
+     * fine fluxes through that face (fflux), and which faces are coarse-fine
+     * interfaces this step (fset) */
+    double *cflux[ORA_MAX_LEVELS], *fflux[ORA_MAX_LEVELS];
+    unsigned char *fset[ORA_MAX_LEVELS];
 } Scen;
 
 typedef struct Ora {
@@ -755,6 +762,123 @@ static int regrid_from(Ora *o, int s, int l)
 }
 
 /* ------------------------------------------------------------------ */
+/* refluxing (Sec. 3.1 step 5), optional: the mass only                */
+/*                                                                     */
+/* Reading: the paper describes step 5 (replace a coarse cell's flux   */
+/* through a face it shares with finer cells by the finer fluxes) and  */
+/* drops it on the GPU.  In the wave-propagation form a cell's update  */
+/* is a difference of edge "fluxes" seen from that cell (sweep_1d_flux:*/
+/* G- for the left/lower cell, G+ for the right/upper one).  For the   */
+/* mass they are the same flux up to rounding (the f-waves of the mass */
+/* sum to the jump of hu: the bed source enters the momentum only).    */
+/* Momentum is not refluxed: with the bed source its edge fluxes are   */
+/* not one flux, and the coarse and fine flux of a lake at rest differ */
+/* by the hydrostatic term of the two beds, which refluxing would turn */
+/* into motion.  Per coarse step of level l: the flux each level-l     */
+/* cell used through each face (dt_l G), the sum over the fine steps   */
+/* and the r fine edges of a face of dt_{l+1} G / r, taken as the fine */
+/* cells used it, then after averaging every uncovered level-l cell    */
+/* next to a fine patch gets h += (used - fine) / dx (signs by face);  */
+/* a depth driven below zero is clamped, as after a sweep.             */
+
+static void reflux_clear(Ora *o, int s, int l)
+{
+    Scen *S = &o->sc[s];
+    const size_t n = (size_t)o->nxl[l] * o->nyl[l] * 4;
+    if (!S->cflux[l]) {
+        S->cflux[l] = calloc(n, sizeof(double));
+        S->fflux[l] = calloc(n, sizeof(double));
+        S->fset[l] = calloc(n, 1);
+    } else {
+        memset(S->cflux[l], 0, n * sizeof(double));
+        memset(S->fflux[l], 0, n * sizeof(double));
+        memset(S->fset[l], 0, n);
+    }
+}
+
+enum { FACE_W = 0, FACE_E = 1, FACE_S = 2, FACE_N = 3 };
+
+static size_t reg_index(const Ora *o, int l, int I, int J, int face)
+{
+    return ((size_t)J * o->nxl[l] + I) * 4 + face;
+}
+
+/* level l as the coarse level: the flux each interior cell's update used through each face */
+static void reflux_record_coarse(Ora *o, int s, int l, const OPatch *p, double dt, const double *xf,
+                                 const double *yf)
+{
+    Scen *S = &o->sc[s];
+    const int nx = p->nx, ny = p->ny;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            const int I = p->i0 + i, J = p->j0 + j;
+            double *c = S->cflux[l] + reg_index(o, l, I, J, 0);
+            c[FACE_W] = dt * xf[2 * ((size_t)j * (nx + 1) + i) + 1];       /* as the right cell of x-edge i */
+            c[FACE_E] = dt * xf[2 * ((size_t)j * (nx + 1) + i + 1)];       /* as the left cell of x-edge i+1 */
+            c[FACE_S] = dt * yf[2 * ((size_t)i * (ny + 1) + j) + 1];       /* as the upper cell of y-edge j */
+            c[FACE_N] = dt * yf[2 * ((size_t)i * (ny + 1) + j + 1)];       /* as the lower cell of y-edge j+1 */
+        }
+}
+
+/* one fine boundary edge: the outside level-l cell (Io, Jo) decides whether it is
+ * a coarse-fine interface (inside the domain, in no other level-l patch) */
+static void reflux_add_fine(Ora *o, int s, int l, const OPatch *p, int Io, int Jo, int face, double v)
+{
+    if (!inside_domain(o, l, Io, Jo)) return;
+    if (find_patch(o, s, l, Io, Jo, p)) return;
+    const int r = o->c.ratios[l - 1];
+    const int Ic = Io / r, Jc = Jo / r;
+    Scen *S = &o->sc[s];
+    const size_t k = reg_index(o, l - 1, Ic, Jc, face);
+    S->fflux[l - 1][k] = S->fflux[l - 1][k] + v / (double)r;
+    S->fset[l - 1][k] = 1;
+}
+
+/* level l as the fine level: its boundary edges' fluxes, as its own cells used them */
+static void reflux_record_fine(Ora *o, int s, int l, const OPatch *p, double dt, const double *xf,
+                               const double *yf)
+{
+    const int nx = p->nx, ny = p->ny;
+    for (int j = 0; j < ny; j++) {
+        /* west boundary: the coarse cell outside sees the patch on its east face */
+        reflux_add_fine(o, s, l, p, p->i0 - 1, p->j0 + j, FACE_E, dt * xf[2 * ((size_t)j * (nx + 1)) + 1]);
+        reflux_add_fine(o, s, l, p, p->i0 + nx, p->j0 + j, FACE_W, dt * xf[2 * ((size_t)j * (nx + 1) + nx)]);
+    }
+    for (int i = 0; i < nx; i++) {
+        reflux_add_fine(o, s, l, p, p->i0 + i, p->j0 - 1, FACE_N, dt * yf[2 * ((size_t)i * (ny + 1)) + 1]);
+        reflux_add_fine(o, s, l, p, p->i0 + i, p->j0 + ny, FACE_S, dt * yf[2 * ((size_t)i * (ny + 1) + ny)]);
+    }
+}
+
+/* after the fine steps and the averaging: correct the uncovered level-l cells */
+static void reflux_apply(Ora *o, int s, int l)
+{
+    Scen *S = &o->sc[s];
+    const int r = o->c.ratios[l];
+    const double dx = o->dxl[l], dy = o->dyl[l];
+    Level *L = &S->lev[l];
+    for (int k = 0; k < L->n; k++) {
+        OPatch *p = L->p[k];
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                const int I = p->i0 + i, J = p->j0 + j;
+                const size_t b = reg_index(o, l, I, J, 0);
+                const unsigned char *f = S->fset[l] + b;
+                if (!(f[0] | f[1] | f[2] | f[3])) continue;
+                if (find_patch(o, s, l + 1, I * r, J * r, NULL)) continue;   /* covered: averaged */
+                const double *c = S->cflux[l] + b, *fi = S->fflux[l] + b;
+                double h = p->h[OIDX(p, i, j)];
+                if (f[FACE_W]) h = h + (fi[FACE_W] - c[FACE_W]) / dx;
+                if (f[FACE_E]) h = h + (c[FACE_E] - fi[FACE_E]) / dx;
+                if (f[FACE_S]) h = h + (fi[FACE_S] - c[FACE_S]) / dy;
+                if (f[FACE_N]) h = h + (c[FACE_N] - fi[FACE_N]) / dy;
+                if (h < 0.0) h = 0.0;
+                p->h[OIDX(p, i, j)] = h;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* recursive time stepping (Sec. 3.1)                                  */
 
 static int advance(Ora *o, int s, int l)
@@ -764,12 +888,22 @@ static int advance(Ora *o, int s, int l)
     double dt = S->dt1 / (double)o->R[l];
     double alpha = l > 0 ? (double)S->substep[l] / (double)o->c.ratios[l - 1] : 0.0;
     if (fill_ghosts(o, s, l, alpha)) return -1;
+    const int coarse_of_next = o->c.reflux && l + 1 < o->c.num_levels && S->lev[l + 1].n > 0;
+    if (coarse_of_next) reflux_clear(o, s, l);
     double sx = 0.0, sy = 0.0;
     for (int k = 0; k < L->n; k++) {
         OPatch *p = L->p[k];
         save_old(p);
         double a, b;
-        if (o->c.spherical) {
+        if (o->c.reflux && (coarse_of_next || l > 0)) {
+            double *xf = malloc(2 * (size_t)p->ny * (p->nx + 1) * sizeof(double));
+            double *yf = malloc(2 * (size_t)p->nx * (p->ny + 1) * sizeof(double));
+            ora_step_patch_flux(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b, xf, yf);
+            if (coarse_of_next) reflux_record_coarse(o, s, l, p, dt, xf, yf);
+            if (l > 0) reflux_record_fine(o, s, l, p, dt, xf, yf);
+            free(xf);
+            free(yf);
+        } else if (o->c.spherical) {
             double *kap = malloc((size_t)(p->ny + 4) * sizeof(double));
             double *ced = malloc((size_t)(p->ny + 5) * sizeof(double));
             for (int j = -2; j < p->ny + 2; j++) kap[j + 2] = geo_kap(o, l, p->j0 + j);
@@ -796,6 +930,7 @@ static int advance(Ora *o, int s, int l)
             if (advance(o, s, l + 1)) return -1;
         }
         average_down(o, s, l + 1);
+        if (coarse_of_next) reflux_apply(o, s, l);
     }
     S->nsteps[l]++;
     if (l + 1 < o->c.num_levels && o->c.regrid_interval > 0 && S->nsteps[l] % o->c.regrid_interval == 0)
@@ -873,6 +1008,10 @@ void *ora_create(const ora_config *cfg)
         free(o);
         return NULL;
     }
+    if (o->c.reflux && (o->c.transverse || o->c.spherical)) {   /* refluxing: split scheme on plane grids */
+        free(o);
+        return NULL;
+    }
     o->R[0] = 1;
     for (int l = 1; l < cfg->num_levels; l++) o->R[l] = o->R[l - 1] * cfg->ratios[l - 1];
     for (int l = 0; l < cfg->num_levels; l++) {
@@ -901,6 +1040,7 @@ void ora_destroy(void *vo)
         free(S->up);
         if (S->has_eta0) grid_free(&S->eta0);
         if (S->has_uv0) { grid_free(&S->u0); grid_free(&S->v0); }
+        for (int l = 0; l < ORA_MAX_LEVELS; l++) { free(S->cflux[l]); free(S->fflux[l]); free(S->fset[l]); }
     }
     for (int k = 0; k < o->ntopo; k++) grid_free(&o->topo[k]);
     free(o->topo);

@@ -19,6 +19,12 @@ typedef struct OPatch {
 void ora_step_patch(OPatch *p, double g, double drytol, double dt, double dx, double dy,
                     double *sx, double *sy);
 
+/* the same step, also returning the edge mass fluxes of the interior rows (xf:
+ * ny (nx + 1) x-edges) and columns (yf: nx (ny + 1) y-edges), two per edge: as
+ * the lower/left cell's update uses it, and as the upper/right cell's does */
+void ora_step_patch_flux(OPatch *p, double g, double drytol, double dt, double dx, double dy,
+                         double *sx, double *sy, double *xf, double *yf);
+
 /* split step on a latitude-longitude grid in capacity form: kap[j + 2] is the
  * capacity of patch row j (-2 <= j < ny + 2), ced[j + 2] the relative length of
  * the latitude edge below row j (-2 <= j <= ny + 2); dxp, dyp are the physical

@@ -57,6 +57,7 @@ typedef struct ora_config {
     double manning_n;           /* Manning coefficient of the drag D (Sec. 2.1); 0: no friction */
     int spherical;              /* 1: x = longitude, y = latitude in degrees (capacity form) */
     double earth_radius;        /* metres (spherical; <= 0: 6371 km) */
+    int reflux;                 /* 1: refluxing of the mass (Sec. 3.1 step 5; split scheme, plane grids) */
 } ora_config;
 
 typedef struct ora_rp {

@@ -140,10 +140,15 @@ static double w_right(double s) { return s > 0.0 ? 1.0 : (s == 0.0 ? 0.5 : 0.0);
 /* One 1D sweep over n interior cells with 2 ghost cells on each side.
  * Input arrays have n+4 entries (cell c at index c+2).  The updated interior
  * is written to the output arrays (n entries).  Returns max |s| over the
- * edges 0..n (the edges that touch an interior cell). */
-static double sweep_1d(double g, double drytol, int n, double dtdx,
-                       const double *h, const double *hn, const double *ht, const double *B,
-                       double *ho, double *hno, double *hto)
+ * edges 0..n (the edges that touch an interior cell).
+ * gflux (NULL: not wanted; 2 (n+1) entries): the mass flux of edge e as each
+ * neighbour's update uses it -- the update of cell i is
+ * h_i - dtdx (G-_{i+1} - G+_i) with G-_e = hn_{e-1} + (A-dQ)_e + F~_e (seen
+ * from the left cell) and G+_e = hn_e - (A+dQ)_e + F~_e (from the right):
+ * gflux[2e] = G-_e, gflux[2e+1] = G+_e.  Used by the refluxing option. */
+static double sweep_1d_flux(double g, double drytol, int n, double dtdx,
+                            const double *h, const double *hn, const double *ht, const double *B,
+                            double *ho, double *hno, double *hto, double *gflux)
 {
     /* Riemann problems at edges e = -1 .. n+1 (edge e between cells e-1 and e) */
     ora_rp *rp = (ora_rp *)malloc((size_t)(n + 3) * sizeof *rp);
@@ -192,6 +197,10 @@ static double sweep_1d(double g, double drytol, int n, double dtdx,
 
         double se = fmax(-r->s[0], r->s[2]);
         smax = fmax(smax, se);
+        if (gflux) {
+            gflux[2 * e] = (hn[e - 1 + 2] + amdq[e][0]) + F[e][0];
+            gflux[2 * e + 1] = (hn[e + 2] - apdq[e][0]) + F[e][0];
+        }
     }
 
     /* cell update, Eq. (wave_propagation_2nd_order) */
@@ -207,6 +216,13 @@ static double sweep_1d(double g, double drytol, int n, double dtdx,
     }
     free(rp); free(amdq); free(apdq); free(F);
     return smax;
+}
+
+static double sweep_1d(double g, double drytol, int n, double dtdx,
+                       const double *h, const double *hn, const double *ht, const double *B,
+                       double *ho, double *hno, double *hto)
+{
+    return sweep_1d_flux(g, drytol, n, dtdx, h, hn, ht, B, ho, hno, hto, NULL);
 }
 
 /* The y sweep on a latitude-longitude grid (capacity form).  Cell c of the
@@ -330,6 +346,17 @@ void ora_step_patch_geo(OPatch *p, double g, double drytol, double dt, double dx
 void ora_step_patch(OPatch *p, double g, double drytol, double dt, double dx, double dy,
                     double *sx_out, double *sy_out)
 {
+    ora_step_patch_flux(p, g, drytol, dt, dx, dy, sx_out, sy_out, NULL, NULL);
+}
+
+/* ora_step_patch, also returning the edge mass fluxes of the interior rows and
+ * columns (xf, yf may be NULL): xf[2 ((j (nx + 1)) + e) + side] for x-edge e
+ * (0..nx) of row j (0..ny-1), yf[2 ((i (ny + 1)) + e) + side] for y-edge e of
+ * column i; side 0 as the lower/left cell uses it, 1 as the upper/right cell
+ * does (sweep_1d_flux; the y sweep's fluxes are those of Q*). */
+void ora_step_patch_flux(OPatch *p, double g, double drytol, double dt, double dx, double dy,
+                         double *sx_out, double *sy_out, double *xf, double *yf)
+{
     int nx = p->nx, ny = p->ny;
     int nmax = (nx > ny ? nx : ny) + 4;
     double *a = malloc(4 * (size_t)nmax * sizeof(double));
@@ -344,7 +371,8 @@ void ora_step_patch(OPatch *p, double g, double drytol, double dt, double dx, do
             size_t k = OIDX(p, i, j);
             ah[i + 2] = p->h[k]; an[i + 2] = p->hu[k]; at[i + 2] = p->hv[k]; aB[i + 2] = p->B[k];
         }
-        double s = sweep_1d(g, drytol, nx, dtdx, ah, an, at, aB, oh, on, ot);
+        double *gx = (xf && j >= 0 && j < ny) ? xf + 2 * (size_t)j * (nx + 1) : NULL;
+        double s = sweep_1d_flux(g, drytol, nx, dtdx, ah, an, at, aB, oh, on, ot, gx);
         if (j >= 0 && j < ny) sx = fmax(sx, s);
         for (int i = 0; i < nx; i++) {
             size_t k = OIDX(p, i, j);
@@ -356,7 +384,8 @@ void ora_step_patch(OPatch *p, double g, double drytol, double dt, double dx, do
             size_t k = OIDX(p, i, j);
             ah[j + 2] = p->h[k]; an[j + 2] = p->hv[k]; at[j + 2] = p->hu[k]; aB[j + 2] = p->B[k];
         }
-        double s = sweep_1d(g, drytol, ny, dtdy, ah, an, at, aB, oh, on, ot);
+        double *gy = yf ? yf + 2 * (size_t)i * (ny + 1) : NULL;
+        double s = sweep_1d_flux(g, drytol, ny, dtdy, ah, an, at, aB, oh, on, ot, gy);
         sy = fmax(sy, s);
         for (int j = 0; j < ny; j++) {
             size_t k = OIDX(p, i, j);

@@ -92,3 +92,32 @@ def test_clustering_in_a_forked_child():
         os._exit(0 if np.array_equal(a, b) else 3)
     _, status = os.waitpid(pid, 0)
     assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
+
+
+def test_clustering_from_concurrent_threads():
+    """Several host threads clustering at once share one worker pool (its
+    loops run one at a time): every call returns the boxes of a serial call."""
+    import threading
+    from paper_1901_06798_gb300 import binding
+    rng = np.random.default_rng(11)
+    masks = []
+    for k in range(6):
+        F = (rng.random((700, 900)) < 0.01).astype(np.uint8)
+        F[100 + 40 * k:300 + 40 * k, 150:600] = 1
+        masks.append(F)
+    N = np.ones_like(masks[0])
+    ref = [binding.cluster_flags(F, N, 0.7, 4, 60) for F in masks]
+    out = [None] * len(masks)
+
+    def work(k):
+        for _ in range(3):
+            out[k] = binding.cluster_flags(masks[k], N, 0.7, 4, 60)
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(len(masks))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=120)
+    assert not any(t.is_alive() for t in th)
+    for a, b in zip(out, ref):
+        assert np.array_equal(a, b)

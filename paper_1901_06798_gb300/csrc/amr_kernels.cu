@@ -838,9 +838,15 @@ __global__ void patch_out_kernel(LevelView L, int p, int cur, double *out)
     }
 }
 
+// Mass of each scenario over level 1 (the composite mass once finer levels
+// are averaged down), in FP64 and in a fixed order, so it is reproducible to
+// the last bit: block b of patch p sums its cells (capacity-weighted on
+// latitude-longitude grids), reduces by a fixed tree and writes parts[p B + b];
+// mass_sum_kernel adds the parts of each scenario in (p, b) order.
 template <typename T, bool PERT>
-__global__ void mass_kernel(LevelView L, int cur, double *mass)
+__global__ void __launch_bounds__(256) mass_kernel(LevelView L, int cur, double *parts)
 {
+    __shared__ double red[256];
     const PatchDesc P = L.descs[blockIdx.y];
     const int n = P.nx * P.ny;
     Acc<T> a = acc<T>(L.arena, P);
@@ -849,10 +855,27 @@ __global__ void mass_kernel(LevelView L, int cur, double *mass)
         long long k = a.idx(c % P.nx, c / P.nx);
         double q0 = (double)a.f(cur, 0)[k];
         double h = PERT ? q0 - (double)a.Bp()[k] : q0;
-        s += L.kap ? L.kap[P.j0 + c / P.nx + 2] * h : h;   // capacity-weighted on latitude-longitude grids
+        s += L.kap ? L.kap[P.j0 + c / P.nx + 2] * h : h;
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(mass + P.scen, s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) parts[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void mass_sum_kernel(const PatchDesc *descs, int npatch, int nb, const double *parts, double *mass,
+                                int nscen)
+{
+    for (int sc = blockIdx.x * blockDim.x + threadIdx.x; sc < nscen; sc += gridDim.x * blockDim.x) {
+        double m = 0.0;
+        for (int p = 0; p < npatch; p++)
+            if (descs[p].scen == sc)
+                for (int b = 0; b < nb; b++) m = m + parts[(size_t)p * nb + b];
+        mass[sc] = m;
+    }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -1094,11 +1117,17 @@ int k_cnn_union(uint8_t *raw, const uint8_t *cov, const float *logits, int nx, i
     return (int)cudaGetLastError();
 }
 
-int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, double *mass, cudaStream_t st)
+int k_mass_parts(int npatch, int maxcells) { return npatch * (int)grid_for(maxcells, npatch, 256).x; }
+
+int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, double *parts, double *mass, int nscen,
+           cudaStream_t st)
 {
     if (npatch <= 0) return 0;
     dim3 g = grid_for(maxcells, npatch, 256);
-    TSU_DISPATCH(prec, mass_kernel, <<<g, 256, 0, st>>>(L, cur, mass));
+    TSU_DISPATCH(prec, mass_kernel, <<<g, 256, 0, st>>>(L, cur, parts));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+    mass_sum_kernel<<<(nscen + 127) / 128, 128, 0, st>>>(L.descs, npatch, (int)g.x, parts, mass, nscen);
     return (int)cudaGetLastError();
 }
 

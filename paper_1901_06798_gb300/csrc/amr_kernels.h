@@ -125,6 +125,9 @@ int k_cnn_features(int prec, const LevelView &L, int npatch, int maxcells, int c
                    const uint8_t *raw, float *feat, double drytol, const CnnWindow &win, cudaStream_t st);
 int k_cnn_union(uint8_t *raw, const uint8_t *cov, const float *logits, int nx, int ny, int np, const CnnWindow &win,
                 cudaStream_t st);
-int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, double *mass, cudaStream_t st);
+// mass per scenario over level 1 in a fixed summation order; parts: k_mass_parts(npatch, maxcells) doubles
+int k_mass_parts(int npatch, int maxcells);
+int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, double *parts, double *mass, int nscen,
+           cudaStream_t st);
 
 }  // namespace tsu

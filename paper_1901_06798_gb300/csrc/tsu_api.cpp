@@ -318,6 +318,7 @@ struct tsu_ctx {
     std::vector<StepGraph> g1;
     long long g1_version = -1;
     DevBuf<double> dstage;
+    DevBuf<double> massParts;                  // per-block partial masses of tsu_get_stats
     PinnedHost hsmall;                         // page-locked readback of error flag, CFL counts, times
     PinnedHost hstage;                         // page-locked double buffer of staged device-to-host reads
     cudaEvent_t stage_ev[8] = {};
@@ -1402,7 +1403,7 @@ struct tsu_ctx {
         viol.release(); smax.release(); derr.release();
         dgxy.release(); dgeta.release(); dgt.release(); dnsamp.release(); dgloc.release();
         fraw.release(); fcov.release(); ftmp.release(); fF.release(); fN.release(); fslot.release(); fbox.release();
-        dstage.release(); zero_dt.release(); zero_dtf.release();
+        dstage.release(); zero_dt.release(); zero_dtf.release(); massParts.release();
         cnn_theta.release(); cnn_feat.release(); cnn_logits.release(); cnn_half.release();
         if (arena.base) cudaFreeAsync(arena.base, st);
         if (st) cudaStreamSynchronize(st);
@@ -1746,8 +1747,13 @@ int tsu_get_stats(tsu_ctx *ctx, int scen, tsu_stats *out)
         std::memset(out, 0, sizeof *out);
         CK(cudaMemsetAsync(ctx->mass.p, 0, ctx->nscen * sizeof(double), ctx->st));
         Lvl &L = ctx->lv[0];
-        if (!L.P.empty())
-            ctx->kl(k_mass(ctx->prec, ctx->view(0), (int)L.P.size(), L.maxcells, L.cur, ctx->mass.p, ctx->st), "mass");
+        if (!L.P.empty()) {
+            ctx->massParts.ensure((size_t)k_mass_parts((int)L.P.size(), L.maxcells), ctx->st);
+            ctx->kl(k_mass(ctx->prec, ctx->view(0), (int)L.P.size(), L.maxcells, L.cur, ctx->massParts.p, ctx->mass.p,
+                           ctx->nscen, ctx->st),
+                    "mass");
+            ctx->launches++;   // k_mass runs two kernels
+        }
         double v[4];
         long long vi;
         CK(cudaMemcpyAsync(&v[0], ctx->dt1.p + scen, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));

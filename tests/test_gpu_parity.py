@@ -292,3 +292,16 @@ def test_amr4_bay_four_levels_ratio_8():
     _, eo = o.read_gauges()
     _, eg = g.read_gauges()
     assert np.abs(eg - eo).max() <= F32P_ETA
+
+
+def test_mass_is_reproducible():
+    """tsu_get_stats sums the mass in FP64 in a fixed order: the same state
+    gives the same bits, call after call and context after context, and it
+    agrees with the oracle's mass."""
+    w = _amr_small()
+    o, g = run_pair(w, 6, precision=0)
+    g2 = W.load(_gpu(w["cfg"], 0), w)
+    g2.step(6)
+    m = [g.stats()["mass"] for _ in range(3)] + [g2.stats()["mass"]]
+    assert all(x == m[0] for x in m), m
+    assert abs(m[0] - o.stats()["mass"]) <= 1e-12 * abs(o.stats()["mass"])

@@ -102,7 +102,8 @@ typedef struct tsu_config {
 typedef struct tsu_stats {
     double dt;                  /* last level-1 time step */
     double t;                   /* simulated time */
-    double mass;                /* sum of h dx dy over level 1, FP64 */
+    double mass;                /* sum of h dx dy over level 1 (finer levels are averaged into it), FP64,
+                                   summed in a fixed order: the same state gives the same bits */
     double cell_updates;        /* interior cells x steps summed over levels */
     long long cfl_violations;
     int patches[TSU_MAX_LEVELS];

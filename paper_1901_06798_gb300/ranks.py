@@ -63,3 +63,99 @@ def job_rate(units: float, seconds: float, dist=None) -> float:
     dist.all_reduce(u, op=dist.ReduceOp.SUM)
     dist.all_reduce(s, op=dist.ReduceOp.MAX)
     return float(u.item()) / float(s.item())
+
+
+# ---------------------------------------------------------------------------
+# Within one scenario: patches of a level spread over ranks.
+#
+# A level's patches are independent given their ghost cells (Sec. 3.1), so a
+# scenario too large for one GPU splits by patches: each rank owns a set of
+# patches, keeps them compact along a space-filling curve, and before every
+# level step receives the 2-cell halos of its patches that other ranks own.
+# Per level step the exchange is those halos (point to point) plus one
+# all-reduce of the max wave speed; at a regrid the ranks all-gather the new
+# patch lists.  These functions are the host side: the partition, the halo
+# schedule, and a CPU data path over torch.distributed for the tests.  (No
+# run here has more than one GPU, so the device data path -- ghost strips sent
+# between the ghost fill and the update -- is not wired.)
+
+def morton(i: int, j: int, bits: int = 16) -> int:
+    """Z-order index of (i, j): the bits of i and j interleaved (i in the even bits)."""
+    z = 0
+    for b in range(bits):
+        z |= ((i >> b) & 1) << (2 * b) | ((j >> b) & 1) << (2 * b + 1)
+    return z
+
+
+def partition_patches(boxes, world: int) -> list[int]:
+    """Owner rank of each patch (boxes: (i0, j0, nx, ny) in level indices).
+    Patches are ordered along the Z curve of their centres and the ordered
+    list is cut into `world` contiguous runs of about equal cell count (a cut
+    falls after the patch that takes the running total past k/world of it)."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    n = len(boxes)
+    order = sorted(range(n), key=lambda k: (morton(boxes[k][0] + boxes[k][2] // 2, boxes[k][1] + boxes[k][3] // 2), k))
+    total = sum(b[2] * b[3] for b in boxes)
+    owner = [0] * n
+    acc, r = 0, 0
+    for k in order:
+        owner[k] = r
+        acc += boxes[k][2] * boxes[k][3]
+        while r + 1 < world and acc * world >= (r + 1) * total:
+            r += 1
+    return owner
+
+
+def halo_schedule(boxes, owner, nxl: int, nyl: int, ghost: int = 2):
+    """Messages of one level's halo exchange: a list of (src, dst, q, p, box)
+    where rank src owns patch q, rank dst owns patch p, and box = (i0, j0, i1,
+    j1), half-open in level indices, is the part of q's interior inside p's
+    ghost ring (corners included) and inside the domain.  Pairs on the same
+    rank need no message and are left out; the list is sorted (src, dst, q, p)
+    so both sides walk it in the same order."""
+    msgs = []
+    for p, (pi, pj, pw, ph) in enumerate(boxes):
+        gi0, gj0 = max(pi - ghost, 0), max(pj - ghost, 0)
+        gi1, gj1 = min(pi + pw + ghost, nxl), min(pj + ph + ghost, nyl)
+        for q, (qi, qj, qw, qh) in enumerate(boxes):
+            if q == p or owner[q] == owner[p]:
+                continue
+            i0, j0 = max(gi0, qi), max(gj0, qj)
+            i1, j1 = min(gi1, qi + qw), min(gj1, qj + qh)
+            if i0 < i1 and j0 < j1:
+                msgs.append((owner[q], owner[p], q, p, (i0, j0, i1, j1)))
+    msgs.sort(key=lambda m: (m[0], m[1], m[2], m[3]))
+    return msgs
+
+
+def exchange_halos(fields: dict, boxes, owner, schedule, rank: int, dist, ghost: int = 2):
+    """CPU data path of one halo exchange: `fields` maps each patch this rank
+    owns to its (ny + 2 ghost, nx + 2 ghost) array (ghost ring included);
+    for every message with this rank as source the interior block is sent, and
+    every message with this rank as destination lands in the patch's ghost
+    ring.  Sends and receives are posted together and then waited on."""
+    import torch
+    reqs, recv = [], []
+    for (src, dst, q, p, (i0, j0, i1, j1)) in schedule:
+        if src == rank:
+            qi, qj = boxes[q][0], boxes[q][1]
+            blk = fields[q][j0 - qj + ghost:j1 - qj + ghost, i0 - qi + ghost:i1 - qi + ghost]
+            reqs.append(dist.isend(torch.from_numpy(blk.copy()), dst))
+        elif dst == rank:
+            buf = torch.empty((j1 - j0, i1 - i0), dtype=torch.float64)
+            reqs.append(dist.irecv(buf, src))
+            recv.append((p, (i0, j0, i1, j1), buf))
+    for r in reqs:
+        r.wait()
+    for p, (i0, j0, i1, j1), buf in recv:
+        pi, pj = boxes[p][0], boxes[p][1]
+        fields[p][j0 - pj + ghost:j1 - pj + ghost, i0 - pi + ghost:i1 - pi + ghost] = buf.numpy()
+
+
+def max_speed(local: float, dist) -> float:
+    """The level's max wave speed over all ranks (the one collective of a level step)."""
+    import torch
+    t = torch.tensor([local], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())

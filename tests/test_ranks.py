@@ -83,3 +83,191 @@ def test_two_rank_ensemble_equals_single_context(tmp_path):
     assert np.array_equal(got["E"], e)
     # 10 + 20 units over max(1, 2) seconds
     assert float(got["rate"]) == 15.0
+
+
+# ---------------------------------------------------------------------------
+# Within one scenario: a level's patches spread over ranks, ghost halos
+# exchanged point to point before each step.
+
+def _tiles(nx, ny, t):
+    return [(i, j, min(t, nx - i), min(t, ny - j)) for j in range(0, ny, t) for i in range(0, nx, t)]
+
+
+def _random_boxes(rng, n=40):
+    """Disjoint boxes scattered over a 256 x 256 level (a refined level's patches)."""
+    taken = np.zeros((256, 256), bool)
+    out = []
+    while len(out) < n:
+        w, h = (int(v) for v in rng.integers(4, 40, 2))
+        i, j = (int(v) for v in rng.integers(0, 256 - 40, 2))
+        if not taken[j:j + h, i:i + w].any():
+            taken[j:j + h, i:i + w] = True
+            out.append((i, j, w, h))
+    return out
+
+
+def test_morton_interleaves_bits():
+    assert [ranks.morton(i, j) for j in range(2) for i in range(2)] == [0, 1, 2, 3]
+    assert ranks.morton(2, 0) == 4 and ranks.morton(0, 2) == 8 and ranks.morton(3, 3) == 15
+    assert ranks.morton(0xFFFF, 0) == 0x55555555 and ranks.morton(0, 0xFFFF) == 0xAAAAAAAA
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 5, 8])
+def test_partition_balances_cells(world):
+    rng = np.random.default_rng(7)
+    for boxes in (_tiles(200, 150, 16), _random_boxes(rng)):
+        owner = ranks.partition_patches(boxes, world)
+        assert len(owner) == len(boxes) and set(owner) <= set(range(world))
+        cells = [b[2] * b[3] for b in boxes]
+        load = np.bincount(owner, weights=cells, minlength=world)
+        # a contiguous cut of the curve misses the even share by less than one patch
+        assert np.abs(load - sum(cells) / world).max() <= max(cells)
+        assert len(set(owner)) == min(world, len(boxes))
+    assert ranks.partition_patches([], 4) == []
+    with pytest.raises(ValueError):
+        ranks.partition_patches(_tiles(8, 8, 4), 0)
+
+
+def test_partition_follows_the_curve():
+    """Owners are non-decreasing along the Z order: each rank holds one run of
+    the curve, so its patches are compact and its halo short."""
+    boxes = _tiles(256, 256, 16)
+    owner = ranks.partition_patches(boxes, 4)
+    order = sorted(range(len(boxes)), key=lambda k: ranks.morton(boxes[k][0] + 8, boxes[k][1] + 8))
+    assert [owner[k] for k in order] == sorted(owner)
+    # 16 x 16 tiles into 4 ranks: the Z curve gives each rank one quadrant
+    for k, (i, j, _, _) in enumerate(boxes):
+        assert owner[k] == (i >= 128) + 2 * (j >= 128)
+
+
+@pytest.mark.parametrize("world", [2, 3, 5])
+def test_halo_schedule_covers_every_ghost_cell_once(world):
+    nx, ny = 61, 47
+    boxes = _tiles(nx, ny, 9)
+    owner = ranks.partition_patches(boxes, world)
+    msgs = ranks.halo_schedule(boxes, owner, nx, ny)
+    assert msgs == sorted(msgs, key=lambda m: m[:4])
+    cover = {p: np.zeros((h + 4, w + 4), int) for p, (_, _, w, h) in enumerate(boxes)}
+    for src, dst, q, p, (i0, j0, i1, j1) in msgs:
+        assert src == owner[q] and dst == owner[p] and src != dst
+        qi, qj, qw, qh = boxes[q]
+        assert qi <= i0 < i1 <= qi + qw and qj <= j0 < j1 <= qj + qh        # inside q's interior
+        pi, pj = boxes[p][:2]
+        cover[p][j0 - pj + 2:j1 - pj + 2, i0 - pi + 2:i1 - pi + 2] += 1
+    for p, (pi, pj, pw, ph) in enumerate(boxes):
+        # same-rank neighbours fill the rest of the ghost ring locally
+        for q, (qi, qj, qw, qh) in enumerate(boxes):
+            if q != p and owner[q] == owner[p]:
+                i0, j0 = max(pi - 2, qi), max(pj - 2, qj)
+                i1, j1 = min(pi + pw + 2, qi + qw), min(pj + ph + 2, qj + qh)
+                if i0 < i1 and j0 < j1:
+                    cover[p][j0 - pj + 2:j1 - pj + 2, i0 - pi + 2:i1 - pi + 2] += 1
+        jj, ii = np.mgrid[pj - 2:pj + ph + 2, pi - 2:pi + pw + 2]
+        inside = (ii >= 0) & (ii < nx) & (jj >= 0) & (jj < ny)
+        interior = (ii >= pi) & (ii < pi + pw) & (jj >= pj) & (jj < pj + ph)
+        ring = inside & ~interior
+        assert (cover[p][ring] == 1).all(), p
+        assert (cover[p][~ring] == 0).all(), p
+
+
+def _level_state(nx, ny, dx):
+    """A wet-dry level: a hump of water over a bottom with an island, moving."""
+    y, x = np.mgrid[0:ny, 0:nx] * dx + dx / 2
+    B = -10.0 + 13.0 * np.exp(-((x - 0.7 * nx * dx) ** 2 + (y - 0.35 * ny * dx) ** 2) / (0.08 * nx * dx) ** 2)
+    eta = 0.8 * np.exp(-((x - 0.3 * nx * dx) ** 2 + (y - 0.55 * ny * dx) ** 2) / (0.12 * nx * dx) ** 2)
+    h = np.maximum(eta - B, 0.0)
+    hu = 0.4 * h * np.sin(x / (nx * dx) * 5.0)
+    hv = -0.3 * h * np.cos(y / (ny * dx) * 4.0)
+    return [h, hu, hv, B]
+
+
+_G, _DRY, _DT, _DX = 9.81, 1e-3, 0.5, 10.0
+
+
+def _whole_level_steps(state, steps):
+    import oracle
+    q = [a.copy() for a in state]
+    for _ in range(steps):
+        _, (h, hu, hv) = oracle.count_step_flops(*(np.pad(a, 2, mode="edge") for a in q), _G, _DRY, _DT, _DX, _DX)
+        q[:3] = [a[2:-2, 2:-2] for a in (h, hu, hv)]
+    return q
+
+
+def _level_rank_main(rank, world, port, out_dir, nx, ny, tile, steps):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        boxes = _tiles(nx, ny, tile)
+        owner = ranks.partition_patches(boxes, world)
+        msgs = ranks.halo_schedule(boxes, owner, nx, ny)
+        state = _level_state(nx, ny, _DX)
+        mine = [p for p in range(len(boxes)) if owner[p] == rank]
+        # each rank holds only its patches: (ny + 4, nx + 4) per field, ghosts included
+        pad = {p: [np.zeros((boxes[p][3] + 4, boxes[p][2] + 4)) for _ in range(4)] for p in mine}
+        for p in mine:
+            i, j, w, h = boxes[p]
+            for f in range(4):
+                pad[p][f][2:-2, 2:-2] = state[f][j:j + h, i:i + w]
+        sent = 0
+        for _ in range(steps):
+            for f in range(4):
+                fields = {p: pad[p][f] for p in mine}
+                ranks.exchange_halos(fields, boxes, owner, msgs, rank, dist)
+                for p in mine:                                    # same-rank neighbours
+                    pi, pj, pw, ph = boxes[p]
+                    for q in mine:
+                        qi, qj, qw, qh = boxes[q]
+                        i0, j0 = max(pi - 2, qi), max(pj - 2, qj)
+                        i1, j1 = min(pi + pw + 2, qi + qw), min(pj + ph + 2, qj + qh)
+                        if q != p and i0 < i1 and j0 < j1:
+                            pad[p][f][j0 - pj + 2:j1 - pj + 2, i0 - pi + 2:i1 - pi + 2] = \
+                                pad[q][f][j0 - qj + 2:j1 - qj + 2, i0 - qi + 2:i1 - qi + 2]
+                for p in mine:                                    # extrapolation outside the domain
+                    pi, pj, pw, ph = boxes[p]
+                    jj = np.clip(np.arange(pj - 2, pj + ph + 2), 0, ny - 1) - pj + 2
+                    ii = np.clip(np.arange(pi - 2, pi + pw + 2), 0, nx - 1) - pi + 2
+                    pad[p][f] = pad[p][f][np.ix_(jj, ii)]
+            sent += sum((m[4][2] - m[4][0]) * (m[4][3] - m[4][1]) for m in msgs if m[0] == rank)
+            for p in mine:
+                _, new = oracle.count_step_flops(*pad[p], _G, _DRY, _DT, _DX, _DX)
+                for f in range(3):
+                    pad[p][f][2:-2, 2:-2] = new[f][2:-2, 2:-2]
+        smax = max(float(np.abs(pad[p][1][2:-2, 2:-2]).max()) for p in mine)
+        gmax = ranks.max_speed(smax, dist)
+        out = [np.full((ny, nx), np.nan) for _ in range(3)]
+        for p in mine:
+            i, j, w, h = boxes[p]
+            for f in range(3):
+                out[f][j:j + h, i:i + w] = pad[p][f][2:-2, 2:-2]
+        np.savez(os.path.join(out_dir, f"level_rank{rank}.npz"), h=out[0], hu=out[1], hv=out[2],
+                 smax=smax, gmax=gmax, sent=sent)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_level_step_equals_whole_level(tmp_path):
+    """A 61 x 47 level in 9 x 9 patches (ragged last row and column), split over
+    two ranks: after four steps with the halos exchanged each step, the union
+    of the ranks' patches is bit for bit four oracle steps of the whole level."""
+    import oracle
+    oracle.build_flopcount()
+    nx, ny, tile, steps, world = 61, 47, 9, 4, 2
+    mp.start_processes(_level_rank_main, args=(world, _port(), str(tmp_path), nx, ny, tile, steps),
+                       nprocs=world, join=True, start_method="spawn")
+    parts = [np.load(tmp_path / f"level_rank{r}.npz") for r in range(world)]
+    ref = _whole_level_steps(_level_state(nx, ny, _DX), steps)
+    assert (ref[0] == 0.0).any() and (ref[0] > 0.0).any()            # wet and dry cells both present
+    for k, f in enumerate(("h", "hu", "hv")):
+        got = np.where(np.isnan(parts[0][f]), parts[1][f], parts[0][f])
+        assert not np.isnan(got).any()
+        assert np.isnan(parts[0][f]).sum() + np.isnan(parts[1][f]).sum() == nx * ny   # each cell on one rank
+        assert np.array_equal(got, ref[k]), f
+    # the all-reduce gives both ranks the larger of the two local maxima
+    assert float(parts[0]["gmax"]) == float(parts[1]["gmax"]) == max(float(p["smax"]) for p in parts)
+    # halo cells moved per step and field, against the level's cells
+    boxes = _tiles(nx, ny, tile)
+    owner = ranks.partition_patches(boxes, world)
+    cut = sum((b[2] - b[0]) * (b[3] - b[1]) for *_, b in ranks.halo_schedule(boxes, owner, nx, ny))
+    assert sum(int(p["sent"]) for p in parts) == cut * steps
+    assert cut < 0.25 * nx * ny

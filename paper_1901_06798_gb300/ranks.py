@@ -6,10 +6,12 @@ its own time step, patches and gauges.  So they partition across ranks with no
 collective on the data path.  Rank r builds its own context holding scenarios
 [lo, hi), steps it, and only the finished gauge records are gathered at the
 end.  A uniform single-scenario grid does not partition this way (that would
-need halo exchange every level step); there every rank runs a replica.
+need halo exchange every level step); the benchmark runs a replica per rank.
+The second half of the module is the host side of that exchange: a partition
+of one level's patches over ranks and the schedule of its ghost halos.
 
 Everything here is host logic over ``torch.distributed`` (any backend); the
-solver is whatever object the caller passes (the CUDA binding on a GPU machine).
+solver is whatever object the caller passes (the CUDA binding where a GPU is present).
 """
 from __future__ import annotations
 

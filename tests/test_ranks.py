@@ -4,9 +4,12 @@
 * an ensemble advanced as two shards (one context per rank, no collective on
   the data path) and gathered at the end is bit for bit the single-context
   run (scenarios are independent: own dt, patches, gauges);
-* the whole-job rate is the units of all ranks over the slowest rank's time.
+* the whole-job rate is the units of all ranks over the slowest rank's time;
+* one level's patches split over ranks: the partition balances cells along
+  the Z curve, the halo schedule covers each ghost cell once, and a level
+  stepped as two ranks exchanging halos is bit for bit the whole level.
 
-The per-rank solver here is the oracle; on a GPU machine the same host logic
+The per-rank solver here is the oracle; with a GPU the same host logic
 drives the CUDA binding.
 """
 import os

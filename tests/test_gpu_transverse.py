@@ -102,6 +102,33 @@ def test_f32_perturbation_within_1e4_m(name):
     assert np.abs(eg - eo).max() <= F32P_ETA
 
 
+def test_f32_launch_shapes_agree_and_match_oracle():
+    """FP32 on ragged strips: every launch shape gives the same bits (the shape
+    only moves work between CTAs) and stays within the surface bar; also with
+    2:1 cells and walls on two sides."""
+    from paper_1901_06798_gb300 import binding
+    w = W.hump200()
+    for cfg, steps in ((dict(w["cfg"], nx=133, ny=71), 25),
+                       (dict(w["cfg"], ny=100, dy=20.0, bc=[W.BC_EXTRAP, W.BC_WALL, W.BC_EXTRAP, W.BC_WALL]), 40)):
+        cfg = dict(cfg, transverse=1)
+        o = W.load(oracle.Oracle(cfg), dict(w, cfg=cfg))
+        o.step(steps)
+        wet = o.level_array(0, 1, "h") > 0
+        ref = None
+        for tuning in [(64, 32), (128, 64), (256, 128), (64, 7)]:
+            g = W.load(binding.Tsunami(cfg, precision=1), dict(w, cfg=cfg))
+            g.set_tuning(*tuning)
+            g.step(steps)
+            got = {f: g.level_array(0, 1, f) for f in ("eta", "hu", "hv")}
+            g.close()
+            if ref is None:
+                ref = got
+                assert np.abs(got["eta"] - o.level_array(0, 1, "eta"))[wet].max() <= F32P_ETA
+            else:
+                for f in got:
+                    assert np.array_equal(got[f], ref[f]), (tuning, f)
+
+
 def test_lake_at_rest_both_precisions():
     from paper_1901_06798_gb300 import binding
     w = W.lake_at_rest_shelf(n=96)

@@ -29,16 +29,12 @@
 //   3. forms G of y-edge r-1 of its column from the x-terms of rows r-2, r-1;
 //   4. forms F of x-edge t of row r-2 from the y-terms of columns t-1, t;
 //   5. updates cell (t, r-2).
-// Four barriers per row.  The FP64 arithmetic follows the oracle operation by
-// operation (same association, same order of the four transverse terms) and
-// is compiled without contraction, so the two agree to the last bit.  The FP32
-// instantiation uses that the transverse split is linear in the fluctuation:
-// the two x-fluctuations entering a cell (through its left and right edges)
-// meet the same eigenstructure, so they are added first and split once, and
-// likewise the two y-fluctuations; that halves the splits per cell (8 -> 4).
+// Four barriers per row.  The arithmetic follows the FP64 oracle operation by
+// operation (same association, same order of the four transverse terms); the
+// FP64 instantiation is compiled without contraction so the two agree to the
+// last bit.  The FP32 perturbation form has its own kernel with the same
+// pipeline and fewer shared-memory terms (step_unsplit_f32.cuh).
 #pragma once
-#include <type_traits>
-
 #include "step_kernel.cuh"
 
 namespace tsu {
@@ -88,25 +84,6 @@ __device__ __forceinline__ void tpart(const TEig<T> &e, const T (&d)[3], T (&out
     const T k3 = PLUS ? dmax<T>(l3, T(0)) : dmin<T>(l3, T(0));
 #pragma unroll
     for (int m = 0; m < 3; m++) out[m] = (k1 * w1[m] + k2 * w2[m]) + k3 * w3[m];
-}
-
-// FP32 form of tpart: the same waves with 1/(2c) taken once per pair and the
-// second wave's zero mass and normal components left out.
-template <bool PLUS>
-__device__ __forceinline__ void tpart_f32(const TEig<float> &e, float i2c, const float (&d)[3], float (&out)[3])
-{
-    if (!e.on) { out[0] = 0.f; out[1] = 0.f; out[2] = 0.f; return; }
-    const float l1 = e.un - e.c, l3 = e.un + e.c;
-    const float b1 = (l3 * d[0] - d[1]) * i2c;
-    const float b3 = (d[1] - l1 * d[0]) * i2c;
-    const float b2 = d[2] - e.ut * d[0];
-    const float k1 = PLUS ? fmaxf(l1, 0.f) : fminf(l1, 0.f);
-    const float k2 = PLUS ? fmaxf(e.un, 0.f) : fminf(e.un, 0.f);
-    const float k3 = PLUS ? fmaxf(l3, 0.f) : fminf(l3, 0.f);
-    const float kb1 = k1 * b1, kb3 = k3 * b3;
-    out[0] = kb1 + kb3;
-    out[1] = kb1 * l1 + kb3 * l3;
-    out[2] = out[0] * e.ut + k2 * b2;
 }
 
 // Fluctuations, limited correction and the second-order fluctuations
@@ -182,7 +159,6 @@ template <typename T, bool PERT, int NT, int RING>
 __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
 {
     static_assert(RING >= 5, "rows r-2 .. r are read while rows r+1, r+2 are in flight");
-    constexpr bool kLinear = std::is_same<T, float>::value;   // split sums of fluctuations once
     using S = UnsplitSmem<NT, RING>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -321,25 +297,6 @@ __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
             const int se = (k - 1) % 3, sb = (k - 2) % 3;   // rows r-1 (edge's upper cell) and r-2
             Gc[0] = yF[0]; Gc[1] = yF[2]; Gc[2] = yF[1];    // y frame -> storage frame
             T d[3], part[3];
-            if constexpr (kLinear) {
-                const float i2c = ev.on ? 0.5f / ev.c : 0.f;
-                // A+dQ and A-dQ entering (t, r-1): down-going part
-#pragma unroll
-                for (int m = 0; m < 3; m++) {
-                    const int f = m == 0 ? 0 : 3 - m;       // y frame (mass, hv, hu) from storage
-                    d[m] = XT(se, 12 + f, t) + XT(se, 9 + f, t + 1);
-                }
-                tpart_f32<false>(ev, i2c, d, part);
-                Gc[0] = Gc[0] - hx * part[0]; Gc[1] = Gc[1] - hx * part[2]; Gc[2] = Gc[2] - hx * part[1];
-                // A+dQ and A-dQ entering (t, r-2): up-going part
-#pragma unroll
-                for (int m = 0; m < 3; m++) {
-                    const int f = m == 0 ? 0 : 3 - m;
-                    d[m] = XT(sb, 12 + f, t) + XT(sb, 9 + f, t + 1);
-                }
-                tpart_f32<true>(ev, i2c, d, part);
-                Gc[0] = Gc[0] - hx * part[0]; Gc[1] = Gc[1] - hx * part[2]; Gc[2] = Gc[2] - hx * part[1];
-            } else {
             // (a) A+dQ entering (t, r-1) through its left edge: down-going part
             d[0] = XT(se, 9 + 3 + 0, t); d[1] = XT(se, 9 + 3 + 2, t); d[2] = XT(se, 9 + 3 + 1, t);
             tpart<T, false>(ev, d, part);
@@ -356,7 +313,6 @@ __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
             d[0] = XT(sb, 9 + 0, t + 1); d[1] = XT(sb, 9 + 2, t + 1); d[2] = XT(sb, 9 + 1, t + 1);
             tpart<T, true>(ev, d, part);
             Gc[0] = Gc[0] - hx * part[0]; Gc[1] = Gc[1] - hx * part[2]; Gc[2] = Gc[2] - hx * part[1];
-            }
         }
         __syncthreads();   // x-waves of row r and y-terms of edge r-1 published
 
@@ -388,27 +344,6 @@ __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
             const int sj = (k - 2) % 3, yb = (k - 1) & 1, yt = k & 1;   // row r-2; edges r-2, r-1
             T Fc[3] = {XT(sj, 6 + 0, t), XT(sj, 6 + 1, t), XT(sj, 6 + 2, t)};
             T d[3], part[3];
-            if constexpr (kLinear) {
-                const float i2c = ev.on ? 0.5f / ev.c : 0.f;
-                // B+dQ (from below) and B-dQ (from above) entering (t, r-2): left-going part
-#pragma unroll
-                for (int m = 0; m < 3; m++) {
-                    const int f = m == 0 ? 0 : 3 - m;       // x frame (mass, hu, hv) from the y frame
-                    d[m] = YS(yb, 3 + f, t) + YS(yt, f, t);
-                }
-                tpart_f32<false>(ev, i2c, d, part);
-#pragma unroll
-                for (int m = 0; m < 3; m++) Fc[m] = Fc[m] - hy * part[m];
-                // the same entering (t-1, r-2): right-going part
-#pragma unroll
-                for (int m = 0; m < 3; m++) {
-                    const int f = m == 0 ? 0 : 3 - m;
-                    d[m] = YS(yb, 3 + f, t - 1) + YS(yt, f, t - 1);
-                }
-                tpart_f32<true>(ev, i2c, d, part);
-#pragma unroll
-                for (int m = 0; m < 3; m++) Fc[m] = Fc[m] - hy * part[m];
-            } else {
             // (a) B+dQ entering (t, r-2) from below: left-going part
             d[0] = YS(yb, 3 + 0, t); d[1] = YS(yb, 3 + 2, t); d[2] = YS(yb, 3 + 1, t);
             tpart<T, false>(ev, d, part);
@@ -429,7 +364,6 @@ __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
             tpart<T, true>(ev, d, part);
 #pragma unroll
             for (int m = 0; m < 3; m++) Fc[m] = Fc[m] - hy * part[m];
-            }
 #pragma unroll
             for (int m = 0; m < 3; m++) FX(m, t) = Fc[m];
         }

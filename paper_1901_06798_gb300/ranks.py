@@ -15,6 +15,8 @@ solver is whatever object the caller passes (the CUDA binding where a GPU is pre
 """
 from __future__ import annotations
 
+import numpy as np
+
 
 def shard(n: int, rank: int, world: int) -> tuple[int, int]:
     """Contiguous balanced block [lo, hi) of n units for this rank; the first
@@ -41,7 +43,6 @@ def gather_gauges(t, e, lo: int, dist, n_total: int):
     local scenarios x gauges) into whole-ensemble arrays on every rank,
     ordered by global scenario index.  All ranks record the same number of
     samples (one per coarse step)."""
-    import numpy as np
     parts = [None] * dist.get_world_size()
     dist.all_gather_object(parts, (lo, np.asarray(t), np.asarray(e)))
     parts.sort(key=lambda p: p[0])
@@ -161,3 +162,29 @@ def max_speed(local: float, dist) -> float:
     t = torch.tensor([local], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def allgather_flags(local_flags, dist):
+    """The level's flag mask at a regrid, from the masks of all ranks.
+
+    Each rank flags only the cells of the patches it owns, so a rank's mask is
+    the level's full (ny, nx) extent with its own flags set.  The ranks send
+    their flagged cells as sorted linear indices (a regrid flags a small part of
+    a level) and every rank gets the union.  The clustering that follows is
+    deterministic, so every rank then derives the same patch list and, through
+    `partition_patches`, the same owners: no patch list is exchanged."""
+    import torch
+    mask = np.asarray(local_flags)
+    mine = torch.from_numpy(np.flatnonzero(mask).astype(np.int64))
+    n = torch.tensor([mine.numel()], dtype=torch.int64)
+    counts = [torch.zeros(1, dtype=torch.int64) for _ in range(dist.get_world_size())]
+    dist.all_gather(counts, n)
+    top = max(int(c.item()) for c in counts)
+    pad = torch.full((top,), -1, dtype=torch.int64)
+    pad[:mine.numel()] = mine
+    parts = [torch.empty(top, dtype=torch.int64) for _ in counts]
+    dist.all_gather(parts, pad)
+    out = np.zeros(mask.size, dtype=np.uint8)
+    for c, p in zip(counts, parts):
+        out[p[:int(c.item())].numpy()] = 1
+    return out.reshape(mask.shape)

@@ -274,3 +274,49 @@ def test_two_rank_level_step_equals_whole_level(tmp_path):
     cut = sum((b[2] - b[0]) * (b[3] - b[1]) for *_, b in ranks.halo_schedule(boxes, owner, nx, ny))
     assert sum(int(p["sent"]) for p in parts) == cut * steps
     assert cut < 0.25 * nx * ny
+
+
+def _regrid_rank_main(rank, world, port, out_dir):
+    """Each rank flags |eta| > tol only inside the patches it owns; after the
+    flag all-gather every rank clusters and partitions on its own."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        nx, ny = 96, 80
+        boxes = _tiles(nx, ny, 16)
+        owner = ranks.partition_patches(boxes, world)
+        flags = _flags(nx, ny)
+        local = np.zeros_like(flags)
+        for p, (i, j, w, h) in enumerate(boxes):
+            if owner[p] == rank:
+                local[j:j + h, i:i + w] = flags[j:j + h, i:i + w]
+        full = ranks.allgather_flags(local, dist)
+        new = [tuple(int(v) for v in b) for b in oracle.cluster(full, eff=0.7)]
+        np.savez(os.path.join(out_dir, f"regrid_rank{rank}.npz"), full=full, local=local,
+                 boxes=np.array(new), owner=np.array(ranks.partition_patches(new, world)))
+    finally:
+        dist.destroy_process_group()
+
+
+def _flags(nx, ny):
+    y, x = np.mgrid[0:ny, 0:nx]
+    ring = np.abs(np.hypot(x - 40.0, y - 35.0) - 22.0) < 3.0
+    return (ring | ((x > 80) & (y < 10))).astype(np.uint8)
+
+
+def test_two_rank_regrid_agrees_on_patches_and_owners(tmp_path):
+    import oracle
+    oracle.build("parity")
+    world = 2
+    mp.start_processes(_regrid_rank_main, args=(world, _port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    got = [np.load(tmp_path / f"regrid_rank{r}.npz") for r in range(world)]
+    flags = _flags(96, 80)
+    ref = np.array([tuple(int(v) for v in b) for b in oracle.cluster(flags, eff=0.7)])
+    assert got[0]["local"].sum() > 0 and got[1]["local"].sum() > 0       # both ranks flagged something
+    for g in got:
+        assert np.array_equal(g["full"], flags)                          # the union is the whole mask
+        assert np.array_equal(g["boxes"], ref)                           # the single-process patch list
+    assert np.array_equal(got[0]["owner"], got[1]["owner"])
+    assert set(got[0]["owner"].tolist()) == {0, 1}

@@ -96,10 +96,11 @@ def test_shelf_with_dry_land_f64():
 
 
 def test_lake_at_rest_gpu_both_precisions():
+    """Still sea with beach and dry land: exactly at rest after 1000 steps."""
     w = W.lake_at_rest_shelf(n=96)
     for prec in (0, 1):
         g = W.load(_gpu(w["cfg"], prec), w)
-        g.step(200)
+        g.step(1000)
         for f in ("hu", "hv"):
             assert np.abs(g.level_array(0, 1, f)).max() == 0.0
         eta = g.read_field(0, 1, "eta", 96, 96, 1000.0, 1000.0, 2000.0, 2000.0)
@@ -210,13 +211,16 @@ def test_amr3_f32p_gauges_within_1e4_m():
 
 
 def test_amr_lake_at_rest_gpu():
+    """Still sea under 3-level AMR, regridding every 2 steps: exactly at rest on
+    every level after 63 coarse steps (1008 steps of the finest level)."""
     w = W.amr3(L=120e3, dx1=4000.0, steps=6)
     cfg = dict(w["cfg"], regrid_interval=2)
     w = dict(w, cfg=cfg, uplift=[])
     for prec in (0, 1):
         g = W.load(_gpu(cfg, prec), w)
         assert g.num_patches(0, 3) > 0
-        g.step(6)
+        g.step(63)
+        assert g.num_patches(0, 3) > 0
         for lev in (1, 2, 3):
             for box, a in g.patches(0, lev):
                 assert np.abs(a["hu"]).max() == 0.0 and np.abs(a["hv"]).max() == 0.0

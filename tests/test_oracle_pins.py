@@ -287,17 +287,20 @@ def test_lake_at_rest_with_dry_land():
 
 
 def test_one_patch_equals_tiled_level():
-    """Ghost fill by same-level copy: a tiled level 1 is bitwise the single patch."""
+    """Ghost fill by same-level copy: a tiled level 1 is bitwise the single patch
+    after 100 steps, for tilings into uneven patches (37 and 64 cells with a
+    ragged last row and column: 15 to 64 cells a side)."""
     w = W.hump200()
     a = W.load(oracle.Oracle(w["cfg"]), w)
-    cfg = dict(w["cfg"], level1_tile=37)
-    b = W.load(oracle.Oracle(cfg), dict(w, cfg=cfg))
-    assert b.num_patches(0, 1) == 36
-    a.step(30)
-    b.step(30)
-    for f in ("h", "hu", "hv"):
-        assert np.array_equal(a.level_array(0, 1, f), b.level_array(0, 1, f))
-    assert a.stats()["dt"] == b.stats()["dt"]
+    a.step(100)
+    for tile, npatch in ((37, 36), (64, 16)):
+        cfg = dict(w["cfg"], level1_tile=tile)
+        b = W.load(oracle.Oracle(cfg), dict(w, cfg=cfg))
+        assert b.num_patches(0, 1) == npatch
+        b.step(100)
+        for f in ("h", "hu", "hv"):
+            assert np.array_equal(a.level_array(0, 1, f), b.level_array(0, 1, f)), (tile, f)
+        assert a.stats()["dt"] == b.stats()["dt"]
     # thin tiles next to the boundary: ghost cells past the domain edge of a
     # patch whose own side is not on it
     for bc in ([W.BC_WALL] * 4, [W.BC_EXTRAP] * 4):

@@ -437,6 +437,50 @@ def test_partial_refinement_closer_to_fine_than_coarse():
     assert np.abs(fa - ff).max() < 0.5 * np.abs(fc - ff).max()
 
 
+def test_time_interpolation_of_ghosts_on_a_sloped_surface():
+    """Coarse-to-fine ghost values are linear in time within a coarse step
+    (Sec. 3.1 step 2, reading c10).  Still water under a uniform surface
+    slope s accelerates uniformly: hu = -g h s t, while eta changes only at
+    O(s^2).  So linear space-time interpolation of the coarse state is exact up
+    to those terms, and a refined band across the domain must match the
+    uniform fine grid after 4 coarse steps to 5e-5 of the momentum (measured
+    1.3e-5).  A time fraction off by part of a coarse step misses by 1e-4 to
+    1e-1: the fraction reversed in the depth only (2.3e-4), or the ghosts
+    taken from the old or the new coarse state alone (0.08-0.1)."""
+    nx, ny, dx, r, dt, s, depth = 48, 16, 400.0, 4, 16.0, 1e-4, 40.0
+    L, Ly = nx * dx, ny * dx
+    topo = (np.full((2, 2), -depth), 0.0, 0.0, L, Ly)
+    xs = np.linspace(0.0, L, 4 * nx + 1)
+    eta = np.tile(s * (xs - L / 2), (4 * ny + 1, 1))
+    band = [[6400.0, 0.0, 12800.0, Ly, 2, 2]]           # level 2 over x in [6.4, 12.8] km, all y
+    bc = [W.BC_EXTRAP] * 4
+    amr = _fixed_dt_cfg(W.base_config(nx=nx, ny=ny, dx=dx, dy=dx, num_levels=2, ratios=[r], patch_max=64,
+                                      regrid_interval=0, regions=band, bc=bc), dt)
+    fin = _fixed_dt_cfg(W.base_config(nx=nx * r, ny=ny * r, dx=dx / r, dy=dx / r, bc=bc), dt / r)
+    runs = []
+    for cfg, k in ((amr, 1), (fin, r)):
+        o = oracle.Oracle(cfg)
+        o.add_topo(*topo)
+        o.set_eta(0, eta, 0.0, 0.0, L / (4 * nx), Ly / (4 * ny))
+        o.init()
+        for _ in range(4):
+            o.step(k)
+        runs.append(o)
+    a, f = runs
+    assert a.num_patches(0, 2) > 0
+    fx = dx / r
+    x = np.arange(6400.0, 12800.0, fx) + fx / 2           # the whole band ...
+    y = np.arange(0.25 * Ly, 0.75 * Ly, fx) + fx / 2      # ... away from the y boundaries
+    for fld in ("hu", "eta"):
+        fa = a.read_field(0, 0, fld, len(x), len(y), x[0], y[0], fx, fx)
+        ff = f.read_field(0, 0, fld, len(x), len(y), x[0], y[0], fx, fx)
+        assert np.abs(fa - ff).max() <= 5e-5 * np.abs(ff).max(), fld
+    # the band does accelerate: hu = -g h s t to within the O(s^2) terms
+    hu = a.read_field(0, 0, "hu", len(x), len(y), x[0], y[0], fx, fx)
+    expect = -9.81 * depth * s * (4 * dt)
+    assert np.abs(hu - expect).max() <= 0.02 * abs(expect)
+
+
 # --------------------------------------------------------------------------
 # clustering (Sec. 3.2, Berger & Rigoutsos)
 

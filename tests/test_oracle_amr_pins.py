@@ -17,14 +17,19 @@ arithmetic:
   of a run with regrids;
 * gauges (Sec. 5.1.2): on a frozen linear surface a gauge reads the surface
   exactly; on a quadratic one its error stays within the finest level's
-  bilinear interpolation bound, 16 times below the coarse level's.
+  bilinear interpolation bound, 16 times below the coarse level's;
+* seafloor uplift (Sec. 5.1.1): given before or after init, it raises B by
+  dB on every level and keeps h and the mass, so eta rises by dB where wet.
 
 A throwaway mutation run planted one mistake at a time in oracle/amr.c. Each
 of the ten below passed every earlier pin, and each fails one here: momentum
 averaging skipped; eta averaged over dry cells too; the cell speed without the
 velocity, or with u and v swapped; flags on eta > tol instead of |eta| > tol;
 a buffer of b - 1 cells; a nesting margin of 1 cell; gauges from the nearest
-cell, from the coarsest level, or without the half-cell offset.
+cell, from the coarsest level, or without the half-cell offset.  Three uplift
+mistakes (the surface left in place at init, fine levels' B without the
+uplift, a late uplift that also lowers h) were caught before only in passing,
+by tests about other things; the uplift pin catches each directly.
 """
 import numpy as np
 import pytest
@@ -232,3 +237,69 @@ def test_gauge_reads_the_finest_level():
     b1, b2 = q * 2 * dx ** 2 / 4, q * 2 * (dx / r) ** 2 / 4
     assert np.allclose(coarse, b1, rtol=1e-3)
     assert np.allclose(fine, b2, rtol=1e-2)
+
+
+# --------------------------------------------------------------------------
+# seafloor uplift
+
+def _uplift_runs(when):
+    """A 2-level basin with a beach and dry land, with no uplift and with a
+    planar uplift dB = 0.5 + 2e-5 x - 1e-5 y (bilinear sampling is exact on a
+    plane), given before or after init.  Level 2 covers deep water only: a
+    level made at t = 0 is interpolated from level 1 (reading r26), and next
+    to dry cells the limited slopes (reading r11) do not carry a planar
+    uplift through exactly."""
+    nx, dx = 40, 500.0
+    L = nx * dx
+    xs = np.linspace(0.0, L, 81)
+    X, Y = np.meshgrid(xs, xs)
+    bed = np.minimum(-20.0 + 40.0 * X / L, 6.0)                 # beach rising out of the sea at x = L / 2
+    cfg = W.base_config(nx=nx, ny=nx, dx=dx, dy=dx, bc=[W.BC_WALL] * 4, num_levels=2, ratios=[4],
+                        regrid_interval=0, regions=[[0.1 * L, 0.2 * L, 0.4 * L, 0.7 * L, 2, 2]])
+    w = dict(cfg=cfg, topo=[(bed, 0.0, 0.0, L / 80, L / 80)], eta=[], uplift=[], gauges=np.zeros((0, 2)))
+    dB = 0.5 + 2e-5 * X - 1e-5 * Y
+    up = (0, dB, 0.0, 0.0, L / 80, L / 80)
+    o = oracle.Oracle(cfg)
+    if when == "before":
+        W.load(o, dict(w, uplift=[up]))
+    else:
+        W.load(o, w)
+        if when == "after":
+            o.add_uplift(*up)
+    return o, cfg
+
+
+def _levels(o):
+    return {lev: o.patches(0, lev) for lev in (1, 2)}
+
+
+@pytest.mark.parametrize("when", ["before", "after"])
+def test_uplift_moves_bed_and_surface_together(when):
+    """Sec. 5.1.1: the seafloor deformation is applied instantaneously, the
+    water column moving with it: on every level B rises by dB at each cell
+    centre, h and the mass stay, so eta rises by dB where wet and dry land
+    stays dry."""
+    ref, cfg = _uplift_runs("none")
+    got, _ = _uplift_runs(when)
+    assert abs(got.stats()["mass"] - ref.stats()["mass"]) <= 1e-14 * ref.stats()["mass"]
+    a, b = _levels(ref), _levels(got)
+    wet_seen = dry_seen = 0
+    for lev in (1, 2):
+        assert [p[0] for p in a[lev]] == [p[0] for p in b[lev]]
+        d = cfg["dx"] / (4 ** (lev - 1))
+        for (box, pa), (_, pb) in zip(a[lev], b[lev]):
+            i0, j0, nx, ny = box
+            X, Y = np.meshgrid((i0 + np.arange(nx) + 0.5) * d, (j0 + np.arange(ny) + 0.5) * d)
+            dB = 0.5 + 2e-5 * X - 1e-5 * Y
+            assert np.abs((pb["B"] - pa["B"]) - dB).max() <= 1e-12
+            if lev == 1:
+                assert np.array_equal(pb["h"], pa["h"])       # sampled directly
+            else:
+                assert np.abs(pb["h"] - pa["h"]).max() <= 1e-12  # interpolated from level 1
+            wet = pa["h"] > 0
+            eta_a, eta_b = pa["h"] + pa["B"], pb["h"] + pb["B"]
+            assert np.abs((eta_b - eta_a)[wet] - dB[wet]).max() <= 1e-12
+            if lev == 1:
+                wet_seen += int(wet.sum())
+                dry_seen += int((~wet).sum())
+    assert wet_seen > 0 and dry_seen > 0

@@ -19,7 +19,10 @@ arithmetic:
   exactly; on a quadratic one its error stays within the finest level's
   bilinear interpolation bound, 16 times below the coarse level's;
 * seafloor uplift (Sec. 5.1.1): given before or after init, it raises B by
-  dB on every level and keeps h and the mass, so eta rises by dB where wet.
+  dB on every level and keeps h and the mass, so eta rises by dB where wet;
+* the zeta field (Sec. 5.1.2, Eq. zeta): for a still sea at +0.5 m over a
+  beach, 0.5 offshore, 0.5 - B on flooded land and 0 above, the closed form
+  that zeta = eta or zeta = h everywhere (both planted, both caught) miss.
 
 A throwaway mutation run planted one mistake at a time in oracle/amr.c. Each
 of the ten below passed every earlier pin, and each fails one here: momentum
@@ -303,3 +306,29 @@ def test_uplift_moves_bed_and_surface_together(when):
                 wet_seen += int(wet.sum())
                 dry_seen += int((~wet).sum())
     assert wet_seen > 0 and dry_seen > 0
+
+
+# --------------------------------------------------------------------------
+# the zeta output field
+
+def test_zeta_of_a_raised_still_sea_over_a_beach():
+    """Sec. 5.1.2, Eq. (zeta): zeta is the surface offshore (B <= 0) and the
+    water depth on land (B > 0).  A still sea at +0.5 m over a beach rising
+    through sea level (any constant level is at rest) gives the closed form
+    zeta = 0.5 offshore, 0.5 - B on flooded land (0 < B < 0.5), 0 above."""
+    nx, dx = 64, 10.0
+    L = nx * dx
+    xs = np.linspace(0.0, L, 2 * nx + 1)
+    X, _ = np.meshgrid(xs, np.linspace(0.0, 8 * dx, 17))
+    bed = -2.0 + 4.0 * X / L                                  # B from -2 to +2 m: sea level at x = L / 2
+    cfg = W.base_config(nx=nx, ny=8, dx=dx, dy=dx, bc=[W.BC_WALL] * 4)
+    w = dict(cfg=cfg, topo=[(bed, 0.0, 0.0, L / (2 * nx), dx / 2)], eta=[(0, np.full((2, 2), 0.5), 0.0, 0.0, L, 8 * dx)],
+             uplift=[], gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    o.step(10)
+    xc = (np.arange(nx) + 0.5) * dx
+    B = -2.0 + 4.0 * xc / L
+    want = np.where(B <= 0.0, 0.5, np.maximum(0.5 - B, 0.0))
+    zeta = o.read_field(0, 1, "zeta", nx, 1, xc[0], 4 * dx + 0.5 * dx, dx, dx)[0]
+    assert np.abs(zeta - want).max() <= 1e-12
+    assert (B > 0.5).any() and ((B > 0.0) & (B < 0.5)).any()   # dry land and flooded land both present

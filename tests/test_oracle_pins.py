@@ -106,6 +106,52 @@ def test_riemann_wall_no_mass_flux():
         assert abs(hL * uL + amdq[0]) < 1e-12
 
 
+def test_riemann_dry_bed_front_speed():
+    """Water next to a dry bed at the same level: the exact Riemann solution
+    is a rarefaction whose front runs at u + 2c into a dry right side (u - 2c
+    into a dry left side; Ritter's dam break), so the outermost wave speed is
+    that front speed."""
+    g = 9.81
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        h, B = rng.uniform(0.1, 20.0), rng.uniform(-50.0, 0.0)
+        u = rng.uniform(-1.0, 1.0) * np.sqrt(g * h)
+        c = np.sqrt(g * h)
+        _, s, wl, wr = oracle.riemann(h, h * u, 0.0, B, 0.0, 0.0, 0.0, B, g=g)
+        assert wr == 0 and abs(s[2] - (u + 2.0 * c)) <= 1e-12 * (abs(u) + 2.0 * c)
+        _, s, wl, wr = oracle.riemann(0.0, 0.0, 0.0, B, h, h * u, 0.0, B, g=g)
+        assert wl == 0 and abs(s[0] - (u - 2.0 * c)) <= 1e-12 * (abs(u) + 2.0 * c)
+
+
+def _shock_depth(h, u, g=9.81):
+    """Depth behind the shock that stops a flow of depth h and speed u > 0 at
+    a wall: (h* - h) sqrt(g (h* + h) / (2 h* h)) = u (Rankine-Hugoniot)."""
+    lo, hi = h, 100.0 * h
+    for _ in range(200):
+        m = 0.5 * (lo + hi)
+        if (m - h) * np.sqrt(g * (m + h) / (2.0 * m * h)) < u:
+            lo = m
+        else:
+            hi = m
+    return 0.5 * (lo + hi)
+
+
+def test_riemann_flow_overtops_a_step_only_when_running_at_it():
+    """Water of depth 1 m next to a dry step 2 m above its bed: at rest it
+    cannot reach the step (a wall).  Running at the step at 3 m/s it piles
+    up to the reflected-shock depth, 2.12 m, above the step, so water must
+    cross (no wall); the solver's two-rarefaction estimate agrees here.
+    Running away from the step it never crosses.  Mirrored for a step on the
+    left."""
+    h, step = 1.0, 2.0
+    assert _shock_depth(h, 3.0) > step
+    for u, wall in ((0.0, 1), (3.0, 0), (-3.0, 1)):
+        _, _, wl, wr = oracle.riemann(h, h * u, 0.0, -5.0, 0.0, 0.0, 0.0, -5.0 + step)
+        assert wr == wall, ("right", u)
+        _, _, wl, wr = oracle.riemann(0.0, 0.0, 0.0, -5.0 + step, h, -h * u, 0.0, -5.0)
+        assert wl == wall, ("left", u)
+
+
 def test_riemann_single_shock_is_one_wave():
     """States joined by one 3-shock (Rankine-Hugoniot: s [h] = [hu],
     s [hu] = [hu^2 + g h^2 / 2]; right state at rest, depths 2 -> 1 and 3 -> 0.5,

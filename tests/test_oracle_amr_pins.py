@@ -7,7 +7,8 @@ arithmetic:
   is wet, the mean wet surface (h = max(0, eta - B));
 * the first time step (reading c7): for uniform flow over a flat bed it is
   nu * min(dx / (|u| + c), dy / (|v| + c)) exactly, and the next step (from
-  the edges' wave speeds) gives the same;
+  the edges' wave speeds) gives the same; over levels it follows the fastest
+  (a trench only level 2 resolves sets it);
 * the flag criterion (Sec. 3.2): every cell with |eta| above the tolerance,
   crest or trough, lies under a finer patch after a regrid;
 * the flag buffer (Sec. 3.2, reading c13): a single flagged cell refines
@@ -113,6 +114,31 @@ def test_first_time_step_of_uniform_flow_on_2_to_1_cells():
     assert abs((t2 - t1) - expect) <= 1e-12 * expect
     # the flow stays uniform, so nothing else changed
     assert np.allclose(o.level_array(0, 1, "hu"), depth * u0, rtol=1e-13, atol=0.0)
+
+
+def test_time_step_follows_the_fastest_level():
+    """Reading c7 over levels: dt = nu / max_l(rate_l / R_l), R_l the steps a
+    level takes per coarse step.  A 100 m trench narrower than a coarse cell
+    and between coarse centres is seen only by level 2 (each level samples
+    the bed at its own centres), so still water gives the first step
+    nu dx1 / sqrt(g 100) from level 2, not nu dx1 / sqrt(g 10) from level 1;
+    no step then exceeds Courant 1 on any level."""
+    nx, dx, r, nu, g = 16, 1000.0, 4, 0.9, 9.81
+    L = nx * dx
+    xs = np.arange(0.0, L + 1.0, dx / 16)
+    B = np.where((xs >= 1000.0) & (xs <= 1250.0), -100.0, -10.0)
+    bed = np.tile(B, (17, 1))
+    cfg = W.base_config(nx=nx, ny=nx, dx=dx, dy=dx, bc=[W.BC_WALL] * 4, num_levels=2, ratios=[r], cfl_desired=nu,
+                        regrid_interval=0, regions=[[0.0, 0.0, 3000.0, L, 2, 2]])
+    w = dict(cfg=cfg, topo=[(bed, 0.0, 0.0, dx / 16, L / 16)], eta=[], uplift=[], gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    assert np.nanmax(o.level_array(0, 1, "h")) == 10.0                  # level 1 never sees the trench
+    assert max(a["h"].max() for _, a in o.patches(0, 2)) == 100.0
+    t1 = o.step(1)[0]
+    expect = nu * dx / np.sqrt(g * 100.0)
+    assert abs(t1 - expect) <= 1e-13 * expect
+    o.step(20)
+    assert o.stats()["cfl_violations"] == 0
 
 
 # --------------------------------------------------------------------------

@@ -3,6 +3,8 @@ declared in include/tsunami.h (no compute call: this runs without a GPU)."""
 import ctypes
 import os
 import re
+import subprocess
+import sys
 
 from paper_1901_06798_gb300 import binding, build
 
@@ -41,3 +43,29 @@ def test_stats_struct_matches_header_field_order():
     names = re.findall(r"\b([a-z_0-9]+)(?:\[[A-Z_0-9]+\])*(?:\[\d+\])?\s*[;,]", body)
     fields = [f[0] for f in binding.tsu_stats._fields_]
     assert names == fields
+
+
+def test_product_never_reaches_the_oracle():
+    """The product path has no CPU fallback: no module of the package imports
+    the oracle, and no CUDA or C++ source includes its headers."""
+    pkg = os.path.join(ROOT, "paper_1901_06798_gb300")
+    py = re.compile(r"^\s*(import\s+oracle\b|from\s+oracle\b)", re.M)
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            path = os.path.join(dirpath, f)
+            if f.endswith(".py"):
+                assert not py.search(open(path).read()), path
+            elif f.endswith((".cu", ".cuh", ".cpp", ".h")):
+                assert "oracle" not in "".join(re.findall(r'#include\s+"[^"]+"', open(path).read())), path
+
+
+def test_binding_fails_loudly_without_its_library():
+    """Pointed at a library that does not exist, the binding raises instead
+    of falling back to anything."""
+    code = ("from paper_1901_06798_gb300 import binding\n"
+            "try:\n"
+            "    binding.load('/nonexistent/libtsunami.so')\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.startswith("raised"), (r.stdout, r.stderr[-1000:])

@@ -42,6 +42,24 @@ def test_hand_drawn_masks():
     _same(L, eff=0.95)
 
 
+def test_cut_rules_worked_by_hand():
+    """The masks whose boxes the oracle pins derive by hand from the
+    clustering reading (acceptance at equality, nearest hole, left part first,
+    strongest inflection): the host clustering gives those boxes too."""
+    f = np.array([[1, 1, 0, 0, 0, 0, 1, 1]], np.uint8)
+    assert binding.cluster_flags(f, None, eff=0.5, ratio=1, patch_max=1 << 30).tolist() == [[0, 0, 8, 1]]
+    f = np.array([[1, 0, 1, 1, 0, 1, 1, 1, 1, 1, 1]], np.uint8)
+    assert binding.cluster_flags(f, None, eff=0.85, ratio=1, patch_max=1 << 30).tolist() == \
+        [[0, 0, 1, 1], [2, 0, 2, 1], [5, 0, 6, 1]]
+    f = np.zeros((10, 20), np.uint8)
+    f[2:6, 12:16] = 1
+    f[2:6, 1:5] = 1
+    assert binding.cluster_flags(f, None, eff=0.7, ratio=1, patch_max=1 << 30).tolist() == [[1, 2, 4, 4], [12, 2, 4, 4]]
+    f = np.array([[1, 1, 1, 1, 1, 1], [0, 0, 1, 0, 1, 0], [0, 0, 0, 0, 0, 0]], np.uint8)
+    assert binding.cluster_flags(f, None, eff=0.7, ratio=1, patch_max=1 << 30).tolist() == \
+        [[0, 0, 1, 1], [1, 0, 2, 2], [3, 0, 1, 1], [4, 0, 2, 2]]
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_random_blobs_large(seed):
     rng = np.random.default_rng(seed)

@@ -586,6 +586,40 @@ def test_cluster_respects_nesting():
         assert nest[j0:j0 + h, i0:i0 + w].all()
 
 
+def test_cluster_cut_rules_worked_by_hand():
+    """The clustering reading (Berger-Rigoutsos, Sec. 3.2) applied by hand to
+    masks where each rule decides the outcome; the expected boxes are derived
+    in the comments, not taken from the code.
+
+    (a) Acceptance is flags >= eff * area: a row of 8 with 4 flags at
+        eff = 0.5 is one box (a strict test would cut it in two).
+    (b) Of two holes, the cut goes through the one nearest the box centre: a
+        row of 11 with holes at 1 and 4 (centre 5), eff = 0.85.  Cut at 4:
+        left 0..3 holds 3 of 4 (< 0.85) and is cut at its hole 1 into [0] and
+        [2, 3]; right 5..10 is full.  (Cutting at 1 first would leave 2..10,
+        8 of 9 >= 0.85, as one box.)
+    (c) The lower / left part is clustered first: two rectangles come out
+        left, then right.
+    (d) Without holes, the cut goes at the strongest sign change of the
+        signature's Laplacian, ties to the one nearer the centre.  Column
+        heights 1 1 2 1 2 1 (2 rows, 8 of 12, eff 0.7): Laplacian 1 -2 2 -2,
+        sign changes of strength 3, 4, 4 between columns 1|2, 2|3, 3|4; the
+        tie goes to 2|3 (at the centre).  Each half (3 wide, 4 of 6) has no
+        hole and no inflection and is bisected at 0|1 and 3|4, leaving [0],
+        [1, 2] x 2 rows, [3], [4, 5] x 2 rows (3 of 4 each, accepted).  (The
+        weakest change, 1|2, would give [0, 1] and [2..5] x 2 rows.)"""
+    f = np.array([[1, 1, 0, 0, 0, 0, 1, 1]], np.uint8)
+    assert oracle.cluster(f, eff=0.5).tolist() == [[0, 0, 8, 1]]
+    f = np.array([[1, 0, 1, 1, 0, 1, 1, 1, 1, 1, 1]], np.uint8)
+    assert oracle.cluster(f, eff=0.85).tolist() == [[0, 0, 1, 1], [2, 0, 2, 1], [5, 0, 6, 1]]
+    f = np.zeros((10, 20), np.uint8)
+    f[2:6, 12:16] = 1
+    f[2:6, 1:5] = 1
+    assert oracle.cluster(f).tolist() == [[1, 2, 4, 4], [12, 2, 4, 4]]
+    f = np.array([[1, 1, 1, 1, 1, 1], [0, 0, 1, 0, 1, 0], [0, 0, 0, 0, 0, 0]], np.uint8)
+    assert oracle.cluster(f, eff=0.7).tolist() == [[0, 0, 1, 1], [1, 0, 2, 2], [3, 0, 1, 1], [4, 0, 2, 2]]
+
+
 def test_interpolation_makes_no_new_extrema():
     """A limited linear reconstruction keeps every fine value inside the range
     of its coarse cell and the neighbours (no new extrema).  Coarse surface

@@ -620,6 +620,29 @@ def test_cluster_cut_rules_worked_by_hand():
     assert oracle.cluster(f, eff=0.7).tolist() == [[0, 0, 1, 1], [1, 0, 2, 2], [3, 0, 1, 1], [4, 0, 2, 2]]
 
 
+def test_cluster_splits_large_boxes_into_near_equal_pieces_row_by_row():
+    """A box wider or taller than patch_max (in fine cells) is cut into the
+    fewest pieces that fit, ceil(w / pm) x ceil(h / pm) with pm = patch_max /
+    ratio coarse cells; the widths (and heights) differ by at most one; the
+    pieces tile the box and come out row by row."""
+    for (w, h, ratio, patch_max) in ((10, 7, 2, 8), (13, 5, 4, 16), (9, 9, 1, 3), (17, 4, 2, 10)):
+        f = np.zeros((h + 3, w + 4), np.uint8)
+        f[1:1 + h, 2:2 + w] = 1
+        b = oracle.cluster(f, ratio=ratio, patch_max=patch_max).tolist()
+        pm = patch_max // ratio
+        npx, npy = -(-w // pm), -(-h // pm)
+        assert len(b) == npx * npy
+        cover = np.zeros_like(f, int)
+        for i0, j0, bw, bh in b:
+            assert bw <= pm and bh <= pm
+            cover[j0:j0 + bh, i0:i0 + bw] += 1
+        assert np.array_equal(cover, f.astype(int))
+        widths = [bw for _, _, bw, _ in b[:npx]]
+        heights = [bh for _, _, _, bh in b[::npx]]
+        assert max(widths) - min(widths) <= 1 and max(heights) - min(heights) <= 1
+        assert [(j0, i0) for i0, j0, _, _ in b] == sorted((j0, i0) for i0, j0, _, _ in b)   # row by row
+
+
 def test_interpolation_makes_no_new_extrema():
     """A limited linear reconstruction keeps every fine value inside the range
     of its coarse cell and the neighbours (no new extrema).  Coarse surface

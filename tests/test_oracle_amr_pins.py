@@ -2,17 +2,18 @@
 against a definition or a closed form rather than against the oracle's own
 arithmetic:
 
-* updating (Sec. 3.1 step 4, reading c9): after a coarse step, a coarse cell
-  under a fine patch holds the mean of the fine momenta and, where a fine cell
-  is wet, the mean wet surface (h = max(0, eta - B));
-* the first time step (reading c7): for uniform flow over a flat bed it is
+* updating (Sec. 3.1 step 4): after a coarse step, a coarse cell under a
+  fine patch holds the mean of the fine momenta and, where a fine cell is
+  wet, the mean surface of the wet fine cells (h = max(0, eta - B));
+* the time step (nu over the largest Courant rate of any level; the first
+  step takes its rates from the cells): for uniform flow over a flat bed it is
   nu * min(dx / (|u| + c), dy / (|v| + c)) exactly, and the next step (from
   the edges' wave speeds) gives the same; over levels it follows the fastest
   (a trench only level 2 resolves sets it);
 * the flag criterion (Sec. 3.2): every cell with |eta| above the tolerance,
   crest or trough, lies under a finer patch after a regrid;
-* the flag buffer (Sec. 3.2, reading c13): a single flagged cell refines
-  exactly its (2b + 1)^2 Chebyshev neighbourhood;
+* the flag buffer (Sec. 3.2; b cells, b the regrid interval): a single
+  flagged cell refines exactly its (2b + 1)^2 Chebyshev neighbourhood;
 * proper nesting (Sec. 3.1: fine ghost cells come from the next coarser
   level): a level-3 patch stays 2 level-2 cells inside level 2, at every step
   of a run with regrids;
@@ -275,8 +276,9 @@ def _uplift_runs(when):
     """A 2-level basin with a beach and dry land, with no uplift and with a
     planar uplift dB = 0.5 + 2e-5 x - 1e-5 y (bilinear sampling is exact on a
     plane), given before or after init.  Level 2 covers deep water only: a
-    level made at t = 0 is interpolated from level 1 (reading r26), and next
-    to dry cells the limited slopes (reading r11) do not carry a planar
+    level made at t = 0 is interpolated from level 1 (the initial state is
+    set on level 1), and next to dry cells the limited slopes (minmod, one-
+    sided against a dry neighbour) do not carry a planar
     uplift through exactly."""
     nx, dx = 40, 500.0
     L = nx * dx

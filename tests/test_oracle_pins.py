@@ -485,7 +485,7 @@ def test_partial_refinement_closer_to_fine_than_coarse():
 
 def test_time_interpolation_of_ghosts_on_a_sloped_surface():
     """Coarse-to-fine ghost values are linear in time within a coarse step
-    (Sec. 3.1 step 2, reading c10).  Still water under a uniform surface
+    (Sec. 3.1 step 2: between the coarse states before and after its step).  Still water under a uniform surface
     slope s accelerates uniformly: hu = -g h s t, while eta changes only at
     O(s^2).  So linear space-time interpolation of the coarse state is exact up
     to those terms, and a refined band across the domain must match the

@@ -315,3 +315,59 @@ def test_mass_is_reproducible():
     m = [g.stats()["mass"] for _ in range(3)] + [g2.stats()["mass"]]
     assert all(x == m[0] for x in m), m
     assert abs(m[0] - o.stats()["mass"]) <= 1e-12 * abs(o.stats()["mass"])
+
+
+def _beach_basin():
+    """A 2-level basin with a beach and dry land, level 2 over deep water."""
+    nx, dx = 40, 500.0
+    L = nx * dx
+    xs = np.linspace(0.0, L, 81)
+    X, Y = np.meshgrid(xs, xs)
+    bed = np.minimum(-20.0 + 40.0 * X / L, 6.0)
+    cfg = W.base_config(nx=nx, ny=nx, dx=dx, dy=dx, bc=[W.BC_WALL] * 4, num_levels=2, ratios=[4],
+                        regrid_interval=0, regions=[[0.1 * L, 0.2 * L, 0.4 * L, 0.7 * L, 2, 2]])
+    w = dict(cfg=cfg, topo=[(bed, 0.0, 0.0, L / 80, L / 80)], eta=[], uplift=[], gauges=np.array([[4000.0, 9000.0]]))
+    up = (0, 0.5 + 2e-5 * X - 1e-5 * Y + 0.3 * np.exp(-((X - 5000.0) ** 2 + (Y - 9000.0) ** 2) / 2e6),
+          0.0, 0.0, L / 80, L / 80)
+    return cfg, w, up
+
+
+def test_uplift_after_init_matches_oracle():
+    """A deformation given after init (the bed and the surface move together
+    on every level) and then stepped: FP64 bit for bit with the oracle."""
+    cfg, w, up = _beach_basin()
+    o = W.load(oracle.Oracle(cfg), w)
+    g = W.load(_gpu(cfg, 0), w)
+    o.add_uplift(*up)
+    g.add_uplift(*up)
+    for lev in (1, 2):
+        for (bo, a), (bg, b) in zip(o.patches(0, lev), g.patches(0, lev)):
+            for f in ("h", "B"):
+                assert np.array_equal(a[f], b[f]), (lev, f)
+    o.step(8)
+    g.step(8)
+    for lev in (1, 2):
+        for (bo, a), (bg, b) in zip(o.patches(0, lev), g.patches(0, lev)):
+            for f in ("h", "hu", "hv"):
+                assert np.array_equal(a[f], b[f]), (lev, f)
+    assert np.array_equal(o.read_gauges()[1], g.read_gauges()[1])
+
+
+def test_time_step_follows_the_fastest_level_gpu():
+    """A trench only level 2 resolves sets the step: the same dt sequence as
+    the oracle, bit for bit, starting at nu dx1 / sqrt(g 100)."""
+    nx, dx, nu = 16, 1000.0, 0.9
+    L = nx * dx
+    xs = np.arange(0.0, L + 1.0, dx / 16)
+    bed = np.tile(np.where((xs >= 1000.0) & (xs <= 1250.0), -100.0, -10.0), (17, 1))
+    cfg = W.base_config(nx=nx, ny=nx, dx=dx, dy=dx, bc=[W.BC_WALL] * 4, num_levels=2, ratios=[4], cfl_desired=nu,
+                        regrid_interval=0, regions=[[0.0, 0.0, 3000.0, L, 2, 2]])
+    w = dict(cfg=cfg, topo=[(bed, 0.0, 0.0, dx / 16, L / 16)], eta=[], uplift=[], gauges=np.zeros((0, 2)))
+    o = W.load(oracle.Oracle(cfg), w)
+    g = W.load(_gpu(cfg, 0), w)
+    to, tg = o.step(1)[0], g.step(1)[0]
+    assert to == tg
+    assert abs(tg - nu * dx / np.sqrt(9.81 * 100.0)) <= 1e-13 * tg
+    for _ in range(10):
+        assert o.step(1)[0] == g.step(1)[0]
+    assert g.stats()["cfl_violations"] == 0

@@ -43,11 +43,6 @@ import oracle
 from paper_1901_06798_gb300 import workloads as W
 
 
-def _cells(box):
-    i0, j0, w, h = box
-    return i0, j0, w, h
-
-
 # --------------------------------------------------------------------------
 # updating (fine-to-coarse averaging)
 
@@ -72,7 +67,7 @@ def test_coarse_cells_under_fine_patches_hold_the_fine_averages():
     mom_scale = max(np.nanmax(np.abs(coarse["hu"])), np.nanmax(np.abs(coarse["hv"])))
     assert mom_scale > 0.0
     for box, a in o.patches(0, 2):
-        i0, j0, nx, ny = _cells(box)
+        i0, j0, nx, ny = box
         for Jc in range(j0 // r, (j0 + ny) // r):
             for Ic in range(i0 // r, (i0 + nx) // r):
                 sl = (slice(Jc * r - j0, Jc * r - j0 + r), slice(Ic * r - i0, Ic * r - i0 + r))

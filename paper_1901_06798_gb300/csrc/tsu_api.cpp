@@ -305,18 +305,18 @@ struct tsu_ctx {
     DevBuf<char> cnn_half;
     bool cnn_ready = false;
     long long hier_version = 0;
-    cudaGraphExec_t gexec = nullptr;
-    long long graph_version = -1;
-    long long graph_kernels = 0;
-    // one-coarse-step graphs, keyed by the levels' buffer parities at their start
+    // graphs of one or two coarse steps, keyed by the number of steps and the
+    // levels' buffer parities at their start: a captured step reads and writes
+    // the buffers that were current when it was captured
     struct StepGraph {
-        unsigned key;
+        int m;                              // coarse steps in the graph
+        unsigned key;                       // parity pattern at its start
         cudaGraphExec_t ex;
         std::array<int, kMaxLevels> post;   // the parities it leaves
         long long kernels;
     };
-    std::vector<StepGraph> g1;
-    long long g1_version = -1;
+    std::vector<StepGraph> graphs;
+    long long graphs_version = -1;
     DevBuf<double> dstage;
     DevBuf<double> massParts;                  // per-block partial masses of tsu_get_stats
     PinnedHost hsmall;                         // page-locked readback of error flag, CFL counts, times
@@ -960,45 +960,12 @@ struct tsu_ctx {
         int done = 0;
         while (done < n) {
             if (c.use_graphs && n - done >= 2 && !regrid_ahead(2)) {
-                if (!gexec || graph_version != hier_version) {
-                    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
-                    cudaGraph_t g = nullptr;
-                    long long l0 = launches;
-                    std::vector<std::array<long long, kMaxLevels>> ns = nsteps;
-                    long long ns0 = nsamp;
-                    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                    try {
-                        coarse_step();
-                        coarse_step();
-                    } catch (...) {
-                        cudaStreamEndCapture(st, &g);
-                        if (g) cudaGraphDestroy(g);
-                        throw;
-                    }
-                    CK(cudaStreamEndCapture(st, &g));
-                    CK(cudaGraphInstantiate(&gexec, g, 0));
-                    cudaGraphDestroy(g);
-                    graph_kernels = launches - l0;
-                    launches = l0;
-                    nsteps = ns;
-                    nsamp = ns0;
-                    graph_version = hier_version;
-                }
-                CK(cudaGraphLaunch(gexec, st));
-                launches += graph_kernels;
-                // host mirrors of what the two captured coarse steps did
-                long long per = 1;
-                for (int l = 0; l < nlev; l++) {
-                    for (int s = 0; s < nscen; s++)
-                        if (l == 0 || has_patches(s, l)) nsteps[s][l] += 2 * per;
-                    if (l + 1 < nlev) per *= ratio[l];
-                }
-                nsamp += gxy.empty() ? 0 : 2;
+                graph_steps(2);
                 done += 2;
             } else if (c.use_graphs && !regrid_ahead(3)) {
-                // single steps (a caller reading back every step): a graph per parity
-                // pattern, captured only when it will be launched again before a regrid
-                one_step_graph();
+                // single steps (a caller reading back every step): captured only
+                // when it will be launched again before a regrid
+                graph_steps(1);
                 done++;
             } else {
                 coarse_step();
@@ -1014,20 +981,21 @@ struct tsu_ctx {
         return k;
     }
 
-    // One coarse step as a graph launch.  A coarse step flips the buffer parity
-    // of level 1 (and of any level with an odd number of substeps), so one graph
-    // is captured per parity pattern and reused while the hierarchy is unchanged.
-    void one_step_graph()
+    // m (1 or 2) coarse steps as one graph launch.  A coarse step flips the
+    // buffer parity of level 1 (and of any level with an odd number of substeps),
+    // and a graph replays the buffers it was captured with, so one graph is kept
+    // per (m, parity pattern) and reused while the hierarchy is unchanged.
+    void graph_steps(int m)
     {
-        if (g1_version != hier_version) {
-            for (auto &g : g1) cudaGraphExecDestroy(g.ex);
-            g1.clear();
-            g1_version = hier_version;
+        if (graphs_version != hier_version) {
+            for (auto &g : graphs) cudaGraphExecDestroy(g.ex);
+            graphs.clear();
+            graphs_version = hier_version;
         }
         const unsigned key = parity_key();
         int gi = -1;
-        for (size_t k = 0; k < g1.size(); k++)
-            if (g1[k].key == key) gi = (int)k;
+        for (size_t k = 0; k < graphs.size(); k++)
+            if (graphs[k].m == m && graphs[k].key == key) gi = (int)k;
         if (gi < 0) {
             const long long l0 = launches, ns0 = nsamp;
             const std::vector<std::array<long long, kMaxLevels>> ns = nsteps;
@@ -1036,38 +1004,40 @@ struct tsu_ctx {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             try {
-                coarse_step();
+                for (int k = 0; k < m; k++) coarse_step();
             } catch (...) {
                 cudaStreamEndCapture(st, &g);
                 if (g) cudaGraphDestroy(g);
+                for (int l = 0; l < nlev; l++) lv[l].cur = pre[l];
                 throw;
             }
             CK(cudaStreamEndCapture(st, &g));
             StepGraph sg{};
+            sg.m = m;
             sg.key = key;
             const cudaError_t e = cudaGraphInstantiate(&sg.ex, g, 0);
             cudaGraphDestroy(g);
-            CK(e);
-            sg.kernels = launches - l0;
+            // the capture only recorded the steps: put the host state back
             for (int l = 0; l < nlev; l++) sg.post[l] = lv[l].cur;
-            // the capture only recorded the step: put the host state back
+            sg.kernels = launches - l0;
             launches = l0;
             nsteps = ns;
             nsamp = ns0;
             for (int l = 0; l < nlev; l++) lv[l].cur = pre[l];
-            g1.push_back(sg);
-            gi = (int)g1.size() - 1;
+            CK(e);
+            graphs.push_back(sg);
+            gi = (int)graphs.size() - 1;
         }
-        CK(cudaGraphLaunch(g1[gi].ex, st));
-        launches += g1[gi].kernels;
-        for (int l = 0; l < nlev; l++) lv[l].cur = g1[gi].post[l];
+        CK(cudaGraphLaunch(graphs[gi].ex, st));
+        launches += graphs[gi].kernels;
+        for (int l = 0; l < nlev; l++) lv[l].cur = graphs[gi].post[l];
         long long per = 1;
         for (int l = 0; l < nlev; l++) {
             for (int s = 0; s < nscen; s++)
-                if (l == 0 || has_patches(s, l)) nsteps[s][l] += per;
+                if (l == 0 || has_patches(s, l)) nsteps[s][l] += per * m;
             if (l + 1 < nlev) per *= ratio[l];
         }
-        nsamp += gxy.empty() ? 0 : 1;
+        nsamp += gxy.empty() ? 0 : m;
     }
 
     // Error flag and CFL-violation counts (and, with t_out, every scenario's
@@ -1386,8 +1356,7 @@ struct tsu_ctx {
     ~tsu_ctx()
     {
         if (st) cudaStreamSynchronize(st);
-        if (gexec) cudaGraphExecDestroy(gexec);
-        for (auto &g : g1) cudaGraphExecDestroy(g.ex);
+        for (auto &g : graphs) cudaGraphExecDestroy(g.ex);
         for (auto &e : stage_ev)
             if (e) cudaEventDestroy(e);
         for (auto &L : lv) {

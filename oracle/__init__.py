@@ -101,6 +101,7 @@ class ora_config(C.Structure):
         ("n_regions", C.c_int), ("regions", (C.c_double * 6) * MAX_REGIONS),
         ("n_scenarios", C.c_int), ("transverse", C.c_int), ("cluster_eff", C.c_double),
         ("manning_n", C.c_double), ("spherical", C.c_int), ("earth_radius", C.c_double), ("reflux", C.c_int),
+        ("cfl_retake", C.c_int),
     ]
 
 
@@ -216,6 +217,7 @@ def make_config(cfg: dict) -> ora_config:
     c.spherical = cfg.get("spherical", 0)
     c.earth_radius = cfg.get("earth_radius", 0.0)
     c.reflux = cfg.get("reflux", 0)
+    c.cfl_retake = cfg.get("cfl_retake", 1)
     return c
 
 
@@ -337,7 +339,8 @@ class Oracle:
         return t[: k * ns].reshape(k, ns), e[: k * ns * ng].reshape(k, ns, ng)
 
     def stats(self, scen: int = 0) -> dict:
-        out = np.zeros(5 + MAX_LEVELS)
+        out = np.zeros(7 + MAX_LEVELS)
         self._check(self._L.ora_stats(self._h, scen, _dp(out)), "stats")
         return {"dt": out[0], "t": out[1], "mass": out[2], "cfl_violations": int(out[3]),
-                "cell_updates": out[4], "patches": [int(v) for v in out[5:5 + self.num_levels]]}
+                "cell_updates": out[4], "patches": [int(v) for v in out[5:5 + self.num_levels]],
+                "cfl_retakes": int(out[5 + MAX_LEVELS]), "neg_clips": int(out[6 + MAX_LEVELS])}

@@ -66,6 +66,8 @@ typedef struct Scen {
     long nsteps[ORA_MAX_LEVELS];
     int substep[ORA_MAX_LEVELS];
     long cfl_viol;
+    long cfl_retakes;           /* level-1 steps discarded and taken again (CFL) */
+    long neg_clips;             /* depths clipped to zero after a sweep */
     double cell_updates;
     /* refluxing registers of level l as the coarse level of l+1, over its whole
      * index space, 4 faces (W, E, S, N) per cell: dt times the mass flux the
@@ -881,48 +883,79 @@ static void reflux_apply(Ora *o, int s, int l)
 /* ------------------------------------------------------------------ */
 /* recursive time stepping (Sec. 3.1)                                  */
 
+static void restore_old(OPatch *p)
+{
+    size_t n = (size_t)(p->nx + 4) * (size_t)(p->ny + 4);
+    memcpy(p->h, p->h0, n * sizeof(double));
+    memcpy(p->hu, p->hu0, n * sizeof(double));
+    memcpy(p->hv, p->hv0, n * sizeof(double));
+}
+
+/* One step of level l (all its patches) and, recursively, the r_l steps of
+ * level l+1, the averaging and the regrids (Sec. 3.1).
+ * CFL retake (Sec. 2.2: nu <= 1 must hold): a level-1 step whose Courant
+ * number nu = dt * max(sx/dx, sy/dy) exceeds cfl_max is discarded before any
+ * finer level moves; dt^1 becomes cfl_desired / max(sx/dx, sy/dy) with the
+ * speeds that step saw, and the step is taken again from the same state.  A
+ * retaken step that still exceeds cfl_max, and a step of a finer level (whose
+ * dt^l = dt^1 / R_l is fixed by the level-1 step already taken), are kept and
+ * counted as violations. */
 static int advance(Ora *o, int s, int l)
 {
     Scen *S = &o->sc[s];
     Level *L = &S->lev[l];
-    double dt = S->dt1 / (double)o->R[l];
     double alpha = l > 0 ? (double)S->substep[l] / (double)o->c.ratios[l - 1] : 0.0;
     if (fill_ghosts(o, s, l, alpha)) return -1;
     const int coarse_of_next = o->c.reflux && l + 1 < o->c.num_levels && S->lev[l + 1].n > 0;
-    if (coarse_of_next) reflux_clear(o, s, l);
-    double sx = 0.0, sy = 0.0;
-    for (int k = 0; k < L->n; k++) {
-        OPatch *p = L->p[k];
-        save_old(p);
-        double a, b;
-        if (o->c.reflux && (coarse_of_next || l > 0)) {
-            double *xf = malloc(2 * (size_t)p->ny * (p->nx + 1) * sizeof(double));
-            double *yf = malloc(2 * (size_t)p->nx * (p->ny + 1) * sizeof(double));
-            ora_step_patch_flux(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b, xf, yf);
-            if (coarse_of_next) reflux_record_coarse(o, s, l, p, dt, xf, yf);
-            if (l > 0) reflux_record_fine(o, s, l, p, dt, xf, yf);
-            free(xf);
-            free(yf);
-        } else if (o->c.spherical) {
-            double *kap = malloc((size_t)(p->ny + 4) * sizeof(double));
-            double *ced = malloc((size_t)(p->ny + 5) * sizeof(double));
-            for (int j = -2; j < p->ny + 2; j++) kap[j + 2] = geo_kap(o, l, p->j0 + j);
-            for (int j = -2; j <= p->ny + 2; j++) ced[j + 2] = geo_ced(o, l, p->j0 + j);
-            ora_step_patch_geo(p, o->c.g, o->c.drytol, dt, phys_dx(o, l), phys_dy(o, l), kap, ced, &a, &b);
-            free(kap);
-            free(ced);
-        } else if (o->c.transverse)
-            ora_step_patch_unsplit(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
-        else
-            ora_step_patch(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
-        if (o->c.manning_n > 0.0) ora_friction_patch(p, o->c.g, o->c.drytol, o->c.manning_n, dt);
-        sx = fmax(sx, a);
-        sy = fmax(sy, b);
-        S->cell_updates += (double)p->nx * (double)p->ny;
+    for (int attempt = 0;; attempt++) {
+        double dt = S->dt1 / (double)o->R[l];
+        if (coarse_of_next) reflux_clear(o, s, l);
+        double sx = 0.0, sy = 0.0;
+        const long clips0 = ora_neg_clips;
+        for (int k = 0; k < L->n; k++) {
+            OPatch *p = L->p[k];
+            save_old(p);
+            double a, b;
+            if (o->c.reflux && (coarse_of_next || l > 0)) {
+                double *xf = malloc(2 * (size_t)p->ny * (p->nx + 1) * sizeof(double));
+                double *yf = malloc(2 * (size_t)p->nx * (p->ny + 1) * sizeof(double));
+                ora_step_patch_flux(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b, xf, yf);
+                if (coarse_of_next) reflux_record_coarse(o, s, l, p, dt, xf, yf);
+                if (l > 0) reflux_record_fine(o, s, l, p, dt, xf, yf);
+                free(xf);
+                free(yf);
+            } else if (o->c.spherical) {
+                double *kap = malloc((size_t)(p->ny + 4) * sizeof(double));
+                double *ced = malloc((size_t)(p->ny + 5) * sizeof(double));
+                for (int j = -2; j < p->ny + 2; j++) kap[j + 2] = geo_kap(o, l, p->j0 + j);
+                for (int j = -2; j <= p->ny + 2; j++) ced[j + 2] = geo_ced(o, l, p->j0 + j);
+                ora_step_patch_geo(p, o->c.g, o->c.drytol, dt, phys_dx(o, l), phys_dy(o, l), kap, ced, &a, &b);
+                free(kap);
+                free(ced);
+            } else if (o->c.transverse)
+                ora_step_patch_unsplit(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
+            else
+                ora_step_patch(p, o->c.g, o->c.drytol, dt, o->dxl[l], o->dyl[l], &a, &b);
+            if (o->c.manning_n > 0.0) ora_friction_patch(p, o->c.g, o->c.drytol, o->c.manning_n, dt);
+            sx = fmax(sx, a);
+            sy = fmax(sy, b);
+        }
+        double rate = fmax(sx / phys_dx(o, l), sy / phys_dy(o, l));
+        if (dt * rate > o->c.cfl_max) {
+            if (l == 0 && o->c.cfl_retake && attempt == 0) {
+                for (int k = 0; k < L->n; k++) restore_old(L->p[k]);
+                ora_neg_clips = clips0;
+                S->dt1 = o->c.cfl_desired / rate;
+                S->cfl_retakes++;
+                continue;
+            }
+            S->cfl_viol++;
+        }
+        S->neg_clips += ora_neg_clips - clips0;
+        for (int k = 0; k < L->n; k++) S->cell_updates += (double)L->p[k]->nx * (double)L->p[k]->ny;
+        S->rate[l] = fmax(S->rate[l], rate);
+        break;
     }
-    double rate = fmax(sx / phys_dx(o, l), sy / phys_dy(o, l));
-    if (dt * rate > o->c.cfl_max) S->cfl_viol++;
-    S->rate[l] = fmax(S->rate[l], rate);
 
     if (l + 1 < o->c.num_levels && S->lev[l + 1].n > 0) {
         for (int k = 0; k < o->c.ratios[l]; k++) {
@@ -1274,7 +1307,8 @@ int ora_read_gauges(void *vo, double *t, double *eta, int max_samples, int *n_wr
     return 0;
 }
 
-/* out: dt1, t, mass on level 1, cfl violations, cell updates, patches per level */
+/* out: dt1, t, mass on level 1, cfl violations, cell updates, patches per level
+ * (ORA_MAX_LEVELS entries), CFL retakes, clipped depths */
 int ora_stats(void *vo, int s, double *out)
 {
     Ora *o = (Ora *)vo;
@@ -1296,5 +1330,7 @@ int ora_stats(void *vo, int s, double *out)
     out[3] = (double)S->cfl_viol;
     out[4] = S->cell_updates;
     for (int l = 0; l < ORA_MAX_LEVELS; l++) out[5 + l] = l < o->c.num_levels ? (double)S->lev[l].n : 0.0;
+    out[5 + ORA_MAX_LEVELS] = (double)S->cfl_retakes;
+    out[6 + ORA_MAX_LEVELS] = (double)S->neg_clips;
     return 0;
 }

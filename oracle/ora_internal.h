@@ -11,6 +11,10 @@ typedef struct OPatch {
     double *h0, *hu0, *hv0;     /* state at the start of the patch's last step */
 } OPatch;
 
+/* running count of depths that came out of a sweep negative and were clipped
+ * to zero (the post-processing after each sweep); the driver reads differences */
+extern long ora_neg_clips;
+
 #define OIDX(p, i, j) ((size_t)((i) + 2) + (size_t)((j) + 2) * (size_t)(p)->pitch)
 
 /* one dimensionally split step (x sweep then y sweep) of one patch whose

@@ -15,13 +15,19 @@
  * Parity status per function (see the pins in tests/test_oracle_*.py):
  *   ora_riemann       pinned: equal states, lake at rest over a step,
  *                     mirror symmetry, wall reflection, conservation of
- *                     the flux jump (sum of f-waves == flux difference).
- *                     Fidelity to George (2008) beyond these invariants:
- *                     parity unpinned (the paper only cites the solver).
+ *                     the flux jump (sum of f-waves == flux difference),
+ *                     non-negative depths of every state of its fan (bed
+ *                     steps, dry fronts, overtopping, supersonic flow) and
+ *                     of the first-order update built on it at Courant 1/2
+ *                     (Sec. 2.2).  Fidelity to George (2008) beyond these
+ *                     invariants: parity unpinned (the paper only cites the
+ *                     solver).
  *   ora_mc_limiter    pinned: MC table values (textbook closed form).
  *   patch step        pinned: 1D dam break (Stoker, Ritter) closed forms,
  *                     mass conservation with walls, lake at rest,
- *                     Gaussian-hump mirror symmetry.
+ *                     Gaussian-hump mirror symmetry; the CFL retake: a dam
+ *                     break onto a dry bed retakes its first step with the
+ *                     closed-form dt of its front speed (Sec. 2.2).
  *   multi-patch level pinned: one patch == tiled level, bitwise.
  *   AMR               pinned: lake at rest through regrid/interp/average,
  *                     full-coverage level 2 == uniform fine grid.
@@ -58,6 +64,7 @@ typedef struct ora_config {
     int spherical;              /* 1: x = longitude, y = latitude in degrees (capacity form) */
     double earth_radius;        /* metres (spherical; <= 0: 6371 km) */
     int reflux;                 /* 1: refluxing of the mass (Sec. 3.1 step 5; split scheme, plane grids) */
+    int cfl_retake;             /* 1: a level-1 step with nu > cfl_max is discarded and taken again */
 } ora_config;
 
 typedef struct ora_rp {
@@ -93,6 +100,7 @@ int ora_read_field(void *o, int scen, int level, int field, double *dst, int nx,
                    double x0, double y0, double dx, double dy);
 int ora_add_gauges(void *o, const double *xy, int n);
 int ora_read_gauges(void *o, double *t, double *eta, int max_samples, int *n_written);
-int ora_stats(void *o, int scen, double *out /* [dt, t, mass_l1, cfl_violations, cell_updates, n_patches...] */);
+int ora_stats(void *o, int scen, double *out /* [dt, t, mass_l1, cfl_violations, cell_updates,
+                                                n_patches[ORA_MAX_LEVELS], cfl_retakes, neg_clips] */);
 
 #endif

@@ -31,14 +31,21 @@
  *     source, a contact wave carrying the transverse momentum at the Roe
  *     speed, dry-bed speeds u - c, u + 2c (mirrored for a dry left side), and a
  *     reflecting wall when a dry cell's bed lies above the wet side's
- *     two-rarefaction middle-state surface.  A wave of speed exactly 0 is
- *     split half into each cell.
+ *     two-rarefaction middle-state surface.  The bed step is a stationary
+ *     wave whose depth jump keeps the surface continuous (still water stays
+ *     still), bounded so that every constant state of the fan has a
+ *     non-negative depth.  A wave of speed exactly 0 is split half into each
+ *     cell.
  *   - After each sweep: h < 0 -> 0, and h < drytol -> zero momenta.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 #include "ora_internal.h"
+
+/* depths that came out of a sweep negative and were clipped to zero; the
+ * driver reports them with the run's statistics */
+long ora_neg_clips = 0;
 
 /* Augmented f-wave Riemann solver for the normal direction.
  * Inputs per side: depth h, normal momentum hn, transverse momentum ht, bed B.
@@ -98,21 +105,47 @@ void ora_riemann(double g, double drytol,
         s2 = uR;
     }
 
-    /* Augmented jump: the surface jump d(eta) stands in for the depth jump
-     * (the bed is static, and a bed step with still water is a steady state),
-     * and the momentum flux jump has the bathymetry source folded in:
-     * d(hu^2 + g h^2/2) + g hbar dB = d(hu^2) + g hbar d(eta).
+    /* Augmented jump: the bed step is a stationary wave at x = 0 across which
+     * the depth jumps by delta; the acoustic waves carry the rest of the depth
+     * jump, dh - delta.  Still water over a step is a steady state, so delta
+     * is BL - BR (the surface is continuous through the stationary wave) and
+     * the mass jump to decompose is d(eta).  The momentum flux jump has the
+     * bathymetry source folded in: d(hu^2 + g h^2/2) + g hbar dB =
+     * d(hu^2) + g hbar d(eta).
      * HLLE-type decomposition into two acoustic f-waves: W1 = Q* - Q_l with
      * the middle state of the two-speed approximation, W3 = dQ - W1,
      * Z = s W, so Z1 + Z3 equals the flux jump exactly; a third (contact)
      * wave at the Roe speed carries what remains of the transverse momentum
      * flux after each acoustic wave has advected v of its upwind side. */
     double hbar = 0.5 * (hL + hR);
-    double d1 = (hR + BR) - (hL + BL);
+    double deta = (hR + BR) - (hL + BL);
     double d2 = hnR - hnL;
-    double d3 = (hnR * uR - hnL * uL) + (g * hbar) * d1;
+    double d3 = (hnR * uR - hnL * uL) + (g * hbar) * deta;
     double d4 = hnR * vR - hnL * vL;
     double den = s3 - s1;
+
+    /* Non-negative depth (Sec. 2.2: the solver keeps depths non-negative).
+     * With M = s3 hR - s1 hL - d(hu) ((s3 - s1) times the two-speed middle
+     * depth of a flat bed), the depths of the constant states of the fan are
+     *   s1 < 0 < s3:  (M - s3 delta)/den left of the bed step, (M - s1 delta)/den right of it;
+     *   s1 >= 0:      hL + delta between x = 0 and s1, (M - s1 delta)/den between s1 and s3;
+     *   s3 <= 0:      (M - s3 delta)/den between s1 and s3, hR - delta between s3 and x = 0.
+     * Where the still-water delta would make one of them negative, delta is
+     * moved to the value that makes it zero. */
+    double M = (s3 * hR - s1 * hL) - d2;
+    double delta = BL - BR;
+    int bounded = 0;
+    if (s1 < 0.0 && s3 > 0.0) {
+        if (M - s3 * delta < 0.0) { delta = M / s3; bounded = 1; }
+        else if (M - s1 * delta < 0.0) { delta = M / s1; bounded = 1; }
+    } else if (s1 >= 0.0) {
+        if (hL + delta < 0.0) { delta = -hL; bounded = 1; }
+        else if (s1 > 0.0 && M - s1 * delta < 0.0) { delta = M / s1; bounded = 1; }
+    } else {
+        if (hR - delta < 0.0) { delta = hR; bounded = 1; }
+        else if (s3 < 0.0 && M - s3 * delta < 0.0) { delta = M / s3; bounded = 1; }
+    }
+    double d1 = bounded ? (hR - hL) - delta : deta;
     double w1m = (s3 * d1 - d2) / den;
     double w1n = (s3 * d2 - d3) / den;
     double b1 = s1 * w1m, g1 = s1 * w1n;
@@ -211,7 +244,7 @@ static double sweep_1d_flux(double g, double drytol, int n, double dtdx,
             double upd = (apdq[i][m] + amdq[i + 1][m]) + (F[i + 1][m] - F[i][m]);
             qo[m][i] = q[m][i + 2] - dtdx * upd;
         }
-        if (ho[i] < 0.0) ho[i] = 0.0;
+        if (ho[i] < 0.0) { ora_neg_clips++; ho[i] = 0.0; }
         if (ho[i] < drytol) { hno[i] = 0.0; hto[i] = 0.0; }
     }
     free(rp); free(amdq); free(apdq); free(F);
@@ -291,7 +324,7 @@ static double sweep_1d_geo(double g, double drytol, int n, double dt, double dyp
             if (m == 0) upd = upd + (ced[i + 1] - ced[i]) * hn[i + 2];
             qo[m][i] = q[m][i + 2] - dtk * upd;
         }
-        if (ho[i] < 0.0) ho[i] = 0.0;
+        if (ho[i] < 0.0) { ora_neg_clips++; ho[i] = 0.0; }
         if (ho[i] < drytol) { hno[i] = 0.0; hto[i] = 0.0; }
     }
     free(rp); free(amdq); free(apdq); free(F);
@@ -635,7 +668,7 @@ void ora_step_patch_unsplit(OPatch *p, double g, double drytol, double dt, doubl
                 double uy = (yb->ap[my] + ytp->am[my]) + (Gt[m] - Gb[m]);
                 q[m] = (q[m] - dtdx * ux) - dtdy * uy;
             }
-            if (q[0] < 0.0) q[0] = 0.0;
+            if (q[0] < 0.0) { ora_neg_clips++; q[0] = 0.0; }
             if (q[0] < drytol) { q[1] = 0.0; q[2] = 0.0; }
             for (int m = 0; m < 3; m++) qn[(size_t)m * nx * ny + (size_t)j * nx + i] = q[m];
         }

@@ -297,3 +297,40 @@ def lonlat(w: dict, lon0: float = 140.0, lat0: float = 30.0, radius: float = 637
     g = np.asarray(w.get("gauges", np.zeros((0, 2))), dtype=float).reshape(-1, 2)
     out["gauges"] = np.stack([mx(g[:, 0]), my(g[:, 1])], axis=1) if len(g) else g
     return out
+
+
+def beach_runup(n: int = 48, ny: int = 12, cfl_retake: int = 1) -> dict:
+    """A plane beach rising from 4 m depth at x = 0 to 4 m of dry land at
+    x = L (shoreline mid-domain, dx = 5 m), a 1 m Gaussian surface hump
+    (sigma 20 m) a quarter of the way in, uniform in y, walls: the wave runs
+    up the dry half of the beach."""
+    dx = 5.0
+    L = n * dx
+    cfg = base_config(nx=n, ny=ny, dx=dx, dy=dx, bc=[BC_WALL] * 4, cfl_desired=0.9, cfl_retake=cfl_retake)
+    xs = np.linspace(0.0, L, 2 * n + 1)
+    B = -4.0 + 8.0 * xs / L
+    topo = [(np.vstack([B, B]), 0.0, 0.0, L / (2 * n), ny * dx)]
+    eta = gaussian_grid(0.0, 0.0, L, ny * dx, 2 * n + 1, 5, 0.25 * L, 0.5 * ny * dx, 1.0, 20.0, 1e6)
+    return dict(name="beach", cfg=cfg, topo=topo, eta=[(0, *eta)], uplift=[], steps=40, gauges=np.zeros((0, 2)))
+
+
+def stepped_channel(seed: int, n: int = 40, ny: int = 2) -> dict:
+    """A channel of n x ny unit cells between walls over a bed of random
+    steps (every 5 cells, B uniform in [-3, 0.5] m), with a random surface
+    (U(-0.5, 0.5) m) and velocity (U(-3, 3) m/s) per step section (numpy
+    PCG64 seed): bed steps, dry cells, wetting and draining fronts and
+    supersonic sections."""
+    rng = np.random.default_rng(seed)
+    cfg = base_config(nx=n, ny=ny, dx=1.0, dy=1.0, bc=[BC_WALL] * 4, cfl_desired=0.9)
+    m = 4 * n + 1
+    xs = np.linspace(0.0, n, m)
+    seg = np.minimum(np.floor(xs / 5).astype(int), (m - 1) // 20)
+    nseg = seg.max() + 1
+    B = rng.uniform(-3, 0.5, nseg)[seg]
+    eta = rng.uniform(-0.5, 0.5, nseg)[seg]
+    u = rng.uniform(-3, 3, nseg)[seg]
+    rows = ny + 1
+    d = n / (m - 1)
+    Bg, Eg, Ug = (np.tile(a, (rows, 1)) for a in (B, eta, u))
+    return dict(name="channel", cfg=cfg, topo=[(Bg, 0.0, 0.0, d, 1.0)], eta=[(0, Eg, 0.0, 0.0, d, 1.0)],
+                uv=[(0, Ug, np.zeros_like(Ug), 0.0, 0.0, d, 1.0)], uplift=[], steps=30, gauges=np.zeros((0, 2)))

@@ -37,7 +37,7 @@ BYTES_PER_CELL = {"f32p": 28, "f64": 56}   # read q0,q1,q2,B + write q0,q1,q2 pe
 # algorithmic floating-point operations (add/sub, mul, div, sqrt) per interior cell update of the
 # split step with every edge active, counted on the oracle compiled with a counting scalar type
 # (tests/test_oracle_flops.py, the all-wet 200^2 hump; comparisons and min/max not included)
-FLOPS_PER_CELL = 347.1
+FLOPS_PER_CELL = 365.5
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz;
 # FP64: GB300's nominal dense FP64 rate
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -152,6 +152,38 @@ class Busy:
         return {"gpu_busy_frac": gpu, "host_busy_frac": host}
 
 
+def update_roofline(lt, prec, steps):
+    """Per-level and summed cost of the batched patch update from
+    tsu_level_update_times: device ms per coarse step, interior cell updates,
+    algorithmic bytes (BYTES_PER_CELL per interior cell update) over the
+    update's event-timed duration, and that bandwidth over the measured HBM
+    copy peak.  The batched patch update of the finer levels (2 and up, all
+    patches of a level in one launch) is summed separately: it is where the
+    AMR workloads spend their update time."""
+    peak, how = peaks()
+    bpc = BYTES_PER_CELL[prec]
+    per = {}
+    for lev, v in lt.items():
+        if v["steps"] == 0:
+            continue
+        gbs = bpc * v["cells"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else None
+        per[str(lev)] = {"ms_per_coarse_step": v["ms"] / steps, "cell_updates_per_coarse_step": v["cells"] / steps,
+                         "level_steps_per_coarse_step": v["steps"] / steps, "kernels": v["kernels"],
+                         "achieved_gbs": gbs, "frac": gbs / peak if gbs else None,
+                         "device_cell_rate": v["cells"] / (v["ms"] * 1e-3) if v["ms"] > 0 else None}
+    fine = [v for lev, v in lt.items() if lev >= 2 and v["steps"] > 0]
+    allv = [v for v in lt.values() if v["steps"] > 0]
+    out = {"per_level": per, "steps": steps, "bytes_per_cell": bpc,
+           "device_cell_rate_all_levels": sum(v["cells"] for v in allv) / (sum(v["ms"] for v in allv) * 1e-3)}
+    if fine:
+        ms, cells = sum(v["ms"] for v in fine), sum(v["cells"] for v in fine)
+        ach = bpc * cells / (ms * 1e-3) / 1e9
+        out["roofline"] = {"bound": "hbm", "what": "patch update of levels >= 2 (batched, one launch per level step)",
+                           "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                           "peak_source": how, "traffic": None}
+    return out
+
+
 def load_workload(prec_name, stream, transverse=0):
     from paper_1901_06798_gb300 import binding
     from paper_1901_06798_gb300 import workloads as W
@@ -246,9 +278,19 @@ def run_ours(args, rank, world, dist, torch):
                 legs_x[prec] = {"value": world * cu / el, "steps": K, "ms_per_step": el / K * 1e3,
                                 "cell_updates_per_step": cu / K, "patches_per_level": s1[0]["patches"],
                                 "regrid_host_ms_per_step": (s1[0]["regrid_host_ms"] - s0[0]["regrid_host_ms"]) / K,
+                                "regrid_wait_ms_per_step": (s1[0]["regrid_wait_ms"] - s0[0]["regrid_wait_ms"]) / K,
                                 "cluster_ms_per_step": (s1[0]["cluster_ms"] - s0[0]["cluster_ms"]) / K,
                                 **bz,
                                 "launch_shape": {"threads": tune[0], "seg_rows": tune[1]}}
+                # the batched patch update alone: CUDA events around each level
+                # step's update launches, over a separate profiled run of Kp
+                # coarse steps (the wall-time run above is not instrumented)
+                Kp = max(1, min(K, 8))
+                ctx.profile_levels(True)
+                ctx.step(Kp)
+                lt = ctx.level_update_times()
+                ctx.profile_levels(False)
+                legs_x[prec]["update"] = update_roofline(lt, prec, Kp)
                 gauges[prec] = ctx.read_gauges()
                 ctx.close()
                 torch.cuda.synchronize()

@@ -47,7 +47,9 @@ enum {
     TSU_ERR_CFL = -3,
     TSU_ERR_NESTING = -4,
     TSU_ERR_OOM = -5,
-    TSU_ERR_NOT_BUILT = -6
+    TSU_ERR_NOT_BUILT = -6,
+    TSU_ERR_NAN = -7            /* a wave speed or a cell's depth (surface) is not a finite number: the run
+                                   has blown up; the context keeps returning this code */
 };
 
 enum { TSU_F64 = 0, TSU_F32P = 1 };              /* precision of the state */
@@ -69,7 +71,7 @@ typedef struct tsu_config {
     double g;                   /* gravity, 9.81 */
     double drytol;              /* a cell is dry if h < drytol */
     double cfl_desired;         /* nu_d used to choose dt (Sec. 2.2 CFL condition) */
-    double cfl_max;             /* a level step with nu > cfl_max returns TSU_ERR_CFL */
+    double cfl_max;             /* largest Courant number accepted (Sec. 2.2: nu <= 1); see cfl_retake */
     double dt_max;              /* cap on the level-1 time step */
     int regrid_interval;        /* b: regrid every b steps of a level; also the flag buffer (Sec. 3.2) */
     double flag_eta_tol;        /* flag wet cells with |eta| > tol; <= 0 disables */
@@ -97,6 +99,13 @@ typedef struct tsu_config {
                                    (cell capacity = zone area over an equatorial cell's, latitude edges
                                    weighted by cos of their latitude); split scheme only */
     double earth_radius;        /* metres, spherical grids (<= 0: 6371 km) */
+    int cfl_retake;             /* 1: a level-1 step whose Courant number exceeds cfl_max is discarded
+                                   before any finer level moves and taken again from the same state with
+                                   dt^1 = cfl_desired / (the largest speed / dx it saw); the decision is
+                                   made on the device.  A retaken step that still exceeds cfl_max, and a
+                                   finer level's step (its dt is fixed by the level-1 step), are kept and
+                                   counted.  0: every step is kept and counted.  tsu_step returns
+                                   TSU_ERR_CFL when a kept step exceeded cfl_max during the call */
 } tsu_config;
 
 typedef struct tsu_stats {
@@ -109,8 +118,11 @@ typedef struct tsu_stats {
     int patches[TSU_MAX_LEVELS];
     long long kernel_launches;  /* kernels this context has launched */
     long long regrids;          /* level rebuilds from flags (all scenarios of one call count once) */
-    double regrid_host_ms;      /* host wall time inside those rebuilds, waits for the device included */
+    double regrid_host_ms;      /* host wall time inside those rebuilds, without regrid_wait_ms */
     double cluster_ms;          /* of which clustering the flag masks */
+    long long cfl_retakes;      /* level-1 steps discarded and taken again (cfl_retake) */
+    double regrid_wait_ms;      /* host time the rebuilds spent waiting for the queued steps to finish
+                                   before the flags could be read (device time, not regrid work) */
 } tsu_stats;
 
 /* Create a context.  cfg is copied.  cuda_stream: a cudaStream_t (for example
@@ -155,8 +167,31 @@ int tsu_init(tsu_ctx *ctx);
 /* Advance n coarse (level-1) steps with the recursive integration of Sec. 3.1,
  * regridding every regrid_interval steps of each level.  t_out (may be NULL)
  * receives n_scenarios doubles: the simulated time of each scenario.
- * Returns TSU_ERR_CFL if any level step exceeded cfl_max (work is done). */
+ * Returns TSU_ERR_CFL if a kept level step exceeded cfl_max (the work is done;
+ * see cfl_retake), TSU_ERR_NAN if a speed or a depth is not a finite number,
+ * TSU_ERR_ARG after tsu_step_level left a coarse step unfinished. */
 int tsu_step(tsu_ctx *ctx, int n_coarse_steps, double *t_out);
+
+/* One step of one level (1-based), the unit of the recursion of Sec. 3.1
+ * (step 1 of its algorithm: advance level l by one step of dt^l = dt^1 / R_l),
+ * for debugging and tests.  Calls must follow the recursion's order:
+ *   - level 1 only between coarse steps: it chooses dt^1 (Sec. 2.2 CFL
+ *     condition) and takes the level-1 step (with its retake);
+ *   - level l > 1 only while the step of level l - 1 has substeps of level l
+ *     pending (r_{l-1} per step of level l - 1) and level l has none of its own
+ *     pending; the substep's ghost cells are interpolated at time fraction
+ *     k / r_{l-1}.
+ * A step whose next finer level has patches leaves that level's r_l substeps
+ * pending.  The last pending substep of a level completes its parent's step:
+ * averaging onto the parent, the step count, the regrids every
+ * regrid_interval steps, and -- when the parent is level 1 -- the end of the
+ * coarse step (time advanced, gauges sampled).  Steps taken in this order
+ * give tsu_step's results bit for bit.  t_out (may be NULL): n_scenarios
+ * doubles, the time of each scenario at the end of the last finished coarse
+ * step.  Out of order, an empty level, or a level outside 1..num_levels:
+ * TSU_ERR_ARG, nothing done.  tsu_step fails with TSU_ERR_ARG while a coarse
+ * step is unfinished.  Other codes as tsu_step. */
+int tsu_step_level(tsu_ctx *ctx, int level, double *t_out);
 
 /* Regenerate levels level+1 .. num_levels from flags on `level` (Sec. 3.2). */
 int tsu_regrid(tsu_ctx *ctx, int scenario, int level);
@@ -248,6 +283,23 @@ int tsu_sync(tsu_ctx *ctx);
  * row pitch in elements; interior cell (i, j) at [(j + 2) * pitch + i + 2]). */
 int tsu_level1_buffers(tsu_ctx *ctx, void **h, void **hu, void **hv, void **B, int *pitch);
 
+/* Per-level timing of the patch update, for measurement.  enable != 0 starts
+ * recording a pair of CUDA events on the library's stream around the update
+ * launches of every level step (the x- and y-sweep kernels of the FP32 split
+ * update, the fused FP64 kernel, and on level 1 the retake launch with its
+ * bookkeeping kernel); coarse steps then run without graphs.  Either call
+ * drops what was recorded so far.  Synchronises the stream. */
+int tsu_profile_levels(tsu_ctx *ctx, int enable);
+
+/* What tsu_profile_levels recorded since it was enabled or last read, per
+ * level l < max_levels (0-based): ms[l] the summed device time of its update
+ * launches (CUDA events), cells[l] the interior cells they updated (one count
+ * per level step, all scenarios), steps[l] the level steps, kernels[l] the
+ * kernels launched.  All four are host arrays of max_levels entries; the
+ * record is cleared.  Synchronises the stream. */
+int tsu_level_update_times(tsu_ctx *ctx, double *ms, double *cells, long long *steps, long long *kernels,
+                           int max_levels);
+
 /* Time n level-1 steps of the patch update alone (no AMR bookkeeping) with CUDA
  * events on the library's stream after `warmup` untimed steps; ms_out gets the
  * mean milliseconds of the step kernel per step and total_ms_out the whole
@@ -311,18 +363,19 @@ int tsu_cnn_features(tsu_ctx *ctx, int scenario, int level, float *features, uns
  * bc[4] (host ints, left, right, bottom, top) -- so the caller fills interiors
  * only -- and writes the interior of buffer 1 - cur.  dt is the
  * caller's; max_speeds (2 host doubles) receives the largest |wave speed| of
- * the x and y sweeps, from which the caller picks the next dt.  The call
- * returns after the step has finished on `cuda_stream` (NULL: the default
- * stream).
+ * the x and y sweeps, from which the caller picks the next dt (+infinity:
+ * a cell's depth or surface came out not a finite number).  The call copies
+ * the speeds to the host and synchronises `cuda_stream` (NULL: the default
+ * stream) before it returns, so it must not be issued while that stream is
+ * being captured into a CUDA graph.
  *
  * It allocates nothing: its scratch (about 1 MiB, mostly the work-item table)
  * is a file-scope __device__ array that every GPU loading the library holds
  * until the process exits.  The first call on a device looks up that array's
- * address (once per device, with that device current), so make the first call
- * on each device before any stream capture.  Every call shares the array and
- * leaves its contents behind; each call rewrites what it uses and clears the
- * speed accumulator, but calls that overlap on the GPU (other streams or host
- * threads) race on it -- serialise them.
+ * address (once per device, with that device current).  Every call shares the
+ * array and leaves its contents behind; each call rewrites what it uses and
+ * clears the speed accumulator, but calls that overlap on the GPU (other
+ * streams or host threads) race on it -- serialise them.
  *
  * Limits: 1 <= nx, ny <= TSU_NOALLOC_MAX_SIDE; pitch >= nx + 4; field_stride
  * >= pitch * (ny + 4); block aligned to its element size.  Anything else,

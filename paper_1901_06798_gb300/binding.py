@@ -21,17 +21,18 @@ LIB_PATH = os.path.join(HERE, "_build", "libtsunami.so")
 MAX_LEVELS = 8
 MAX_REGIONS = 8
 TSU_OK, TSU_ERR_ARG, TSU_ERR_CUDA, TSU_ERR_CFL, TSU_ERR_NESTING, TSU_ERR_OOM, TSU_ERR_NOT_BUILT = 0, -1, -2, -3, -4, -5, -6
+TSU_ERR_NAN = -7
 TSU_F64, TSU_F32P = 0, 1
 FIELDS = {"h": 0, "hu": 1, "hv": 2, "eta": 3, "zeta": 4, "B": 5}
 
 # every symbol include/tsunami.h declares
 SYMBOLS = ["tsu_create", "tsu_destroy", "tsu_last_error", "tsu_add_topo", "tsu_set_eta", "tsu_add_uplift",
-           "tsu_init", "tsu_step", "tsu_regrid", "tsu_num_patches", "tsu_get_patches", "tsu_get_patch",
+           "tsu_init", "tsu_step", "tsu_step_level", "tsu_regrid", "tsu_num_patches", "tsu_get_patches", "tsu_get_patch",
            "tsu_read_field", "tsu_add_gauges", "tsu_read_gauges", "tsu_get_stats", "tsu_sync",
            "tsu_level1_buffers", "tsu_time_level1_steps", "tsu_set_tuning",
            "tsu_grid_step_noalloc", "tsu_autotune", "tsu_cnn_num_params", "tsu_cnn_forward",
            "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features", "tsu_cluster_flags", "tsu_set_velocity",
-           "tsu_checkpoint_save", "tsu_checkpoint_restore"]
+           "tsu_checkpoint_save", "tsu_checkpoint_restore", "tsu_profile_levels", "tsu_level_update_times"]
 
 
 class tsu_config(C.Structure):
@@ -45,7 +46,7 @@ class tsu_config(C.Structure):
         ("n_regions", C.c_int), ("regions", (C.c_double * 6) * MAX_REGIONS), ("n_scenarios", C.c_int),
         ("transverse", C.c_int), ("cluster_eff", C.c_double), ("use_graphs", C.c_int),
         ("use_cnn", C.c_int), ("cnn_buffer", C.c_int), ("manning_n", C.c_double),
-        ("spherical", C.c_int), ("earth_radius", C.c_double),
+        ("spherical", C.c_int), ("earth_radius", C.c_double), ("cfl_retake", C.c_int),
     ]
 
 
@@ -53,7 +54,7 @@ class tsu_stats(C.Structure):
     _fields_ = [("dt", C.c_double), ("t", C.c_double), ("mass", C.c_double), ("cell_updates", C.c_double),
                 ("cfl_violations", C.c_longlong), ("patches", C.c_int * MAX_LEVELS),
                 ("kernel_launches", C.c_longlong), ("regrids", C.c_longlong), ("regrid_host_ms", C.c_double),
-                ("cluster_ms", C.c_double)]
+                ("cluster_ms", C.c_double), ("cfl_retakes", C.c_longlong), ("regrid_wait_ms", C.c_double)]
 
 
 _lib = None
@@ -82,6 +83,9 @@ def load(path: str = LIB_PATH):
         "tsu_add_uplift": ([P, I, dp, I, I, D, D, D, D], I),
         "tsu_init": ([P], I),
         "tsu_step": ([P, I, dp], I),
+        "tsu_step_level": ([P, I, dp], I),
+        "tsu_profile_levels": ([P, I], I),
+        "tsu_level_update_times": ([P, dp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), I], I),
         "tsu_regrid": ([P, I, I], I),
         "tsu_num_patches": ([P, I, I, ip], I),
         "tsu_get_patches": ([P, I, I, ip, I, ip], I),
@@ -159,6 +163,7 @@ def make_config(cfg: dict, precision: int = TSU_F64, use_graphs: bool = True) ->
     c.manning_n = cfg.get("manning_n", 0.0)
     c.spherical = cfg.get("spherical", 0)
     c.earth_radius = cfg.get("earth_radius", 0.0)
+    c.cfl_retake = cfg.get("cfl_retake", 1)
     return c
 
 
@@ -227,6 +232,29 @@ class Tsunami:
         self.last_rc = rc
         return t
 
+    def step_level(self, level: int, allow_cfl: bool = False):
+        """One step of one level in the recursion's order (tsu_step_level)."""
+        t = np.zeros(self.n_scenarios)
+        rc = self._check(self._L.tsu_step_level(self._h, level, _dp(t)), "tsu_step_level",
+                         allow=(TSU_ERR_CFL,) if allow_cfl else ())
+        self.last_rc = rc
+        return t
+
+    def profile_levels(self, enable: bool = True):
+        """Start (or stop) recording per-level update times (tsu_profile_levels)."""
+        self._check(self._L.tsu_profile_levels(self._h, 1 if enable else 0), "tsu_profile_levels")
+
+    def level_update_times(self):
+        """Per level (1-based keys): update milliseconds, interior cells, level
+        steps and kernels since profiling started or was last read."""
+        n = self.num_levels
+        ms, cells = np.zeros(n), np.zeros(n)
+        steps, kern = (C.c_longlong * n)(), (C.c_longlong * n)()
+        self._check(self._L.tsu_level_update_times(self._h, _dp(ms), _dp(cells), steps, kern, n),
+                    "tsu_level_update_times")
+        return {l + 1: {"ms": float(ms[l]), "cells": float(cells[l]), "steps": int(steps[l]), "kernels": int(kern[l])}
+                for l in range(n)}
+
     def regrid(self, scen: int, level: int):
         self._check(self._L.tsu_regrid(self._h, scen, level), "tsu_regrid")
 
@@ -287,7 +315,7 @@ class Tsunami:
         return {"dt": s.dt, "t": s.t, "mass": s.mass, "cell_updates": s.cell_updates,
                 "cfl_violations": s.cfl_violations, "patches": list(s.patches)[: self.num_levels],
                 "kernel_launches": s.kernel_launches, "regrids": s.regrids, "regrid_host_ms": s.regrid_host_ms,
-                "cluster_ms": s.cluster_ms}
+                "cluster_ms": s.cluster_ms, "cfl_retakes": s.cfl_retakes, "regrid_wait_ms": s.regrid_wait_ms}
 
     def checkpoint(self) -> bytes:
         """The whole simulation state between steps (tsu_checkpoint_save)."""

@@ -698,8 +698,20 @@ __global__ void __launch_bounds__(256) cell_speed_kernel(LevelView L, const int 
 // After a level step (mode 0) or a cell-speed scan (mode 1): fold the level's
 // max speeds into its rate max(sx/dx, sy/dy), check the CFL number of the step
 // just taken and count cell updates (mode 0).
+// After a level's step: the level's rate max(sx/dx, sy/dy) from the speeds
+// the step kernels reduced (smax is cleared for the next step).
+//   mode 0: a kept step -- count its cells, a violation if dt rate > cfl_max,
+//           and fold the rate into the level's maximum;
+//   mode 1: cell speeds of new patches -- the rate only;
+//   mode 2: a level-1 step that may be retaken (Sec. 2.2 CFL condition): if
+//           dt rate > cfl_max, mark the scenario for a retake and set
+//           dt^1 = cfl_desired / rate (the state is still in the untouched
+//           buffer); otherwise keep it as in mode 0;
+//   mode 3: after the retake launch -- keep the retaken steps as in mode 0.
+// A rate that is not a finite number (a NaN or infinite speed) sets the error
+// flag to TSU_DEV_ERR_NAN.
 __global__ void post_level_kernel(CtrlView cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
-                                  int mode)
+                                  double cfl_desired, int mode)
 {
     for (int s = threadIdx.x; s < nscen; s += blockDim.x) {
         unsigned long long *sm = cv.smax + 2 * s;
@@ -707,11 +719,23 @@ __global__ void post_level_kernel(CtrlView cv, int level, int nscen, double R, d
         double sy = __longlong_as_double((long long)sm[1]);
         sm[0] = 0ull;
         sm[1] = 0ull;
+        if (mode == 3 && cv.retake[s] == 0) continue;
         double rate = fmax(sx / dx, sy / dy);
+        if (!(sx <= 1.0e300 && sy <= 1.0e300)) atomicOr(cv.err, TSU_DEV_ERR_NAN);
         double *ra = cv.rate + (long long)s * cv.max_levels + level;
-        if (mode == 0) {
+        if (mode != 1) {
             double dt = cv.dt1[s] / R;
-            if (dt * rate > cfl_max) cv.cfl_viol[s] += 1;
+            if (dt * rate > cfl_max) {
+                if (mode == 2) {
+                    cv.retake[s] = 1;
+                    cv.retakes[s] += 1;
+                    cv.dt1[s] = cfl_desired / rate;
+                    cv.dt1f[s] = (float)cv.dt1[s];
+                    continue;
+                }
+                cv.cfl_viol[s] += 1;
+            }
+            if (mode == 2 || mode == 3) cv.retake[s] = 0;
             cv.cell_updates[s] += cv.cells[(long long)s * cv.max_levels + level];
         }
         *ra = fmax(*ra, rate);
@@ -1037,10 +1061,11 @@ int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int m
     return (int)cudaGetLastError();
 }
 
-int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max, int mode,
+int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
+                 double cfl_desired, int mode,
                  cudaStream_t st)
 {
-    post_level_kernel<<<1, 128, 0, st>>>(cv, level, nscen, R, dx, dy, cfl_max, mode);
+    post_level_kernel<<<1, 128, 0, st>>>(cv, level, nscen, R, dx, dy, cfl_max, cfl_desired, mode);
     return (int)cudaGetLastError();
 }
 

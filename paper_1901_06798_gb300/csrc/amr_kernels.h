@@ -29,8 +29,15 @@ struct CtrlView {
     const double *cells;         // [scen][max_levels] interior cells per level
     long long *cfl_viol;         // [scen]
     unsigned long long *smax;    // [scen][2]
+    int *retake;                 // [scen] 1: the level-1 step is being retaken (the step kernels' gate)
+    long long *retakes;          // [scen] level-1 steps retaken
+    int *err;                    // device error flag (TSU_DEV_ERR_*)
     int max_levels;
 };
+
+// device error flag bits: 1, 2, 4 a ghost, coarse or parent cell without a
+// covering patch (nesting); 8 a non-finite wave speed or depth
+enum { TSU_DEV_ERR_NESTING = 7, TSU_DEV_ERR_NAN = 8 };
 
 struct TopoDev {
     int nx, ny;
@@ -109,7 +116,8 @@ int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplan
            cudaStream_t st);
 int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int maxcells, int cur, double g,
                  double drytol, unsigned long long *smax, cudaStream_t st);
-int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max, int mode,
+int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
+                 double cfl_desired, int mode,
                  cudaStream_t st);
 int k_begin_step(const CtrlView &cv, int nscen, int nlev, const double *Rl, double cfl_desired, double dt_max,
                  cudaStream_t st);

@@ -103,20 +103,31 @@ __device__ __forceinline__ void lane_in(const C2 &z, int l, Cell<float> &o)
 __device__ __forceinline__ void riemann2_general(float g, const C2 &L, const C2 &R, W2 &r);
 
 // Riemann problems of two edges (L[i] | R[i]) for lanes i = x, y: the
-// wet-wet short branch paired when both lanes are wet-wet, else the general
-// solver lane by lane
+// wet-wet short branch paired when both lanes are wet-wet, subsonic
+// (s1 < 0 < s3) and the still-water bed-step jump leaves both middle depths
+// non-negative; else the general solver lane by lane
 __device__ __forceinline__ void riemann2(float g, const C2 &L, const C2 &R, W2 &r)
 {
-    if (L.wx && R.wx && L.wy && R.wy) {
+    bool fast = L.wx && R.wx && L.wy && R.wy;
+    float2 uhat, ghb, s1, s3, d2;
+    if (fast) {
         const float2 num = fma(L.sq, L.u, mul(R.sq, R.u));
-        const float2 uhat = mul(num, rcp(add(L.sq, R.sq)));
+        uhat = mul(num, rcp(add(L.sq, R.sq)));
         const float2 hbar = mul(f2(0.5f), add(L.h, R.h));
-        const float2 ghb = mul(f2(g), hbar);
+        ghb = mul(f2(g), hbar);
         const float2 chat = sqrt2(ghb);
-        const float2 s1 = fmin2(sub(L.u, L.c), sub(uhat, chat));
-        const float2 s3 = fmax2(add(R.u, R.c), add(uhat, chat));
+        s1 = fmin2(sub(L.u, L.c), sub(uhat, chat));
+        s3 = fmax2(add(R.u, R.c), add(uhat, chat));
+        d2 = sub(R.hn, L.hn);
+        // middle depths (den times): M - s3 delta left of the bed step, M - s1 delta right of it
+        const float2 M = sub(fnma(s1, L.h, mul(s3, R.h)), d2);
+        const float2 delta = sub(L.B, R.B);
+        const float2 ml = fnma(s3, delta, M), mr = fnma(s1, delta, M);
+        fast = fminf(fminf(ml.x, mr.x), fminf(ml.y, mr.y)) >= 0.0f &&
+               fmaxf(s1.x, s1.y) < 0.0f && fminf(s3.x, s3.y) > 0.0f;
+    }
+    if (fast) {
         const float2 d1 = sub(R.q0, L.q0);
-        const float2 d2 = sub(R.hn, L.hn);
         const float2 d3 = fma(ghb, d1, sub(mul(R.hn, R.u), mul(L.hn, L.u)));
         const float2 d4 = sub(mul(R.hn, R.v), mul(L.hn, L.v));
         const float2 rden = rcp(sub(s3, s1));
@@ -258,6 +269,7 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
     const StepItem it = a.items[blockIdx.x];
     if (it.w > 2 * NT - 4 || it.w < 1 || it.h < 1) return;   // not a work item of this launch shape
     const PatchDesc P = a.descs[it.patch];
+    if (a.gate != nullptr && a.gate[P.scen] == 0) return;   // not retaken (uniform over the CTA)
     const int t = threadIdx.x;
     const int cur = a.cur;
     float *base = reinterpret_cast<float *>(a.arena) + P.off;
@@ -460,6 +472,8 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
                             post2(n0, n1, n2, ycm2.B, drytol);
                             if (a.manningf > 0.0f)   // y frame: n2 = hu, n1 = hv
                                 friction2(n0, n2, n1, ycm2.B, drytol, a.manningf, dt1 * a.rR);
+                            // a surface that is not a finite number reaches the host as an infinite speed
+                            if ((outx && !(fabsf(n0.x) < 1e30f)) || (outy && !(fabsf(n0.y) < 1e30f))) smy = INFINITY;
                             float *d = dst + (long long)(rc - y0) * pitch;
                             if (w8) {
                                 st2(d + go[0], n0);

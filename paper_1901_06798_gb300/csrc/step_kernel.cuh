@@ -82,7 +82,8 @@ __device__ __forceinline__ void derive(Cell<T> &z, T g, T drytol)
 // Normal-direction Riemann solver.  Augmented HLLE-type f-wave decomposition
 // with the bathymetry source folded into the momentum flux jump,
 // Einfeldt-type speeds from Roe averages, dry-bed speeds, a reflecting wall
-// where a dry bed lies above the wet side's middle-state surface, and a
+// where a dry bed lies above the wet side's middle-state surface, a bed-step
+// depth jump bounded so every state of the fan keeps h >= 0 (Sec. 2.2), and a
 // contact wave at the Roe speed for the transverse momentum.
 template <typename T, bool PERT>
 __device__ __forceinline__ void riemann(const T g, const Cell<T> &cl, const Cell<T> &cr, Wave<T> &r)
@@ -135,11 +136,33 @@ __device__ __forceinline__ void riemann(const T g, const Cell<T> &cl, const Cell
     }
 
     T hbar = T(0.5) * (hL + hR);
-    T d1 = PERT ? qR - qL : (hR + BR) - (hL + BL);
+    T deta = PERT ? qR - qL : (hR + BR) - (hL + BL);
     T d2 = hnR - hnL;
-    T d3 = (hnR * uR - hnL * uL) + (g * hbar) * d1;
+    T d3 = (hnR * uR - hnL * uL) + (g * hbar) * deta;
     T d4 = hnR * vR - hnL * vL;
     T den = s3 - s1;
+    // Non-negative depth: the bed step is a stationary wave across which the
+    // depth jumps by delta (BL - BR keeps still water still).  With
+    // M = s3 hR - s1 hL - d(hu), the fan's constant states have depths
+    //   s1 < 0 < s3: (M - s3 delta)/den and (M - s1 delta)/den either side of x = 0;
+    //   s1 >= 0:     hL + delta, then (M - s1 delta)/den;
+    //   s3 <= 0:     (M - s3 delta)/den, then hR - delta.
+    // A delta that would make one negative is moved to make it zero, and the
+    // acoustic waves carry dh - delta instead of d(eta).
+    T M = (s3 * hR - s1 * hL) - d2;
+    T delta = BL - BR;
+    bool bounded = false;
+    if (s1 < zero && s3 > zero) {
+        if (M - s3 * delta < zero) { delta = M / s3; bounded = true; }
+        else if (M - s1 * delta < zero) { delta = M / s1; bounded = true; }
+    } else if (s1 >= zero) {
+        if (hL + delta < zero) { delta = -hL; bounded = true; }
+        else if (s1 > zero && M - s1 * delta < zero) { delta = M / s1; bounded = true; }
+    } else {
+        if (hR - delta < zero) { delta = hR; bounded = true; }
+        else if (s3 < zero && M - s3 * delta < zero) { delta = M / s3; bounded = true; }
+    }
+    T d1 = bounded ? (hR - hL) - delta : deta;
     T w1m = (s3 * d1 - d2) / den;
     T w1n = (s3 * d2 - d3) / den;
     T b1 = s1 * w1m, g1 = s1 * w1n;
@@ -264,6 +287,7 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
     const StepItem it = a.items[blockIdx.x];
     if (it.w > NT - 4 || it.w < 1 || it.h < 1) return;   // not a work item of this launch shape
     const PatchDesc P = a.descs[it.patch];
+    if (a.gate != nullptr && a.gate[P.scen] == 0) return;   // not retaken (uniform over the CTA)
     const int t = threadIdx.x;
     const int cur = a.cur;
     T *base = reinterpret_cast<T *>(a.arena) + P.off;
@@ -430,6 +454,8 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a)
                             postprocess<T, PERT>(qn[0], qn[1], qn[2], Bm2, drytol);
                             if (a.manning > 0.0)   // y frame: qn[2] = hu, qn[1] = hv
                                 friction<T, PERT>(qn[0], qn[2], qn[1], Bm2, drytol, (T)a.manning, (T)dt);
+                            // a depth that is not a finite number reaches the host as an infinite speed
+                            if (!(dabs<T>(qn[0]) < T(1e30))) smy = T(INFINITY);
                             long long gi = (long long)(rc + 2) * pitch + (x0 + t);
                             qo0[gi] = qn[0];
                             qo2[gi] = qn[1];

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
     const StepItem it = a.items[blockIdx.x];
     if (it.w > 2 * NT - 4 || it.w < 1 || it.h < 1) return;   // not a work item of this launch shape
     const PatchDesc P = a.descs[it.patch];
+    if (a.gate != nullptr && a.gate[P.scen] == 0) return;   // not retaken (uniform over the CTA)
     const int t = threadIdx.x;
     const int cur = a.cur;
     float *base = reinterpret_cast<float *>(a.arena) + P.off;
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(kSplitYThreads) step_y_f32x2(StepArgs a)
     const StepItem it = a.items_y[blockIdx.x];
     if (it.w > 2 * NT || it.w < 1 || it.h < 1) return;   // uniform over the CTA
     const PatchDesc P = a.descs[it.patch];
+    if (a.gate != nullptr && a.gate[P.scen] == 0) return;   // not retaken (uniform over the CTA)
     const int t = threadIdx.x;
     const int cur = a.cur;
     float *base = reinterpret_cast<float *>(a.arena) + P.off;
@@ -325,6 +327,8 @@ __global__ void __launch_bounds__(kSplitYThreads) step_y_f32x2(StepArgs a)
                     post2(n0, n1, n2, ycm2.B, drytol);
                     if (a.manningf > 0.0f)   // y frame: n2 = hu, n1 = hv
                         friction2(n0, n2, n1, ycm2.B, drytol, a.manningf, dt1 * a.rR);
+                    // a surface that is not a finite number reaches the host as an infinite speed
+                    if ((vx && !(fabsf(n0.x) < 1e30f)) || (vy && !(fabsf(n0.y) < 1e30f))) smy = INFINITY;
                     float *d = qo0 + cbase + (long long)(k - 2) * pitch;
                     if (w8) {
                         st2(d, n0); st2(d + 2 * fs, n1); st2(d + fs, n2);

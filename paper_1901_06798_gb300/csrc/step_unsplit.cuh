@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
     const StepItem it = a.items[blockIdx.x];
     if (it.w > NT - 4 || it.w < 1 || it.h < 1) return;   // not a work item of this launch shape
     const PatchDesc P = a.descs[it.patch];
+    if (a.gate != nullptr && a.gate[P.scen] == 0) return;   // not retaken (uniform over the CTA)
     const int t = threadIdx.x;
     const int cur = a.cur;
     T *base = reinterpret_cast<T *>(a.arena) + P.off;
@@ -388,6 +389,8 @@ __global__ void __launch_bounds__(NT) step_unsplit_kernel(StepArgs a)
                 friction<T, PERT>(q[0], q[1], q[2], Bc, drytol, PERT ? (T)a.manningf : (T)a.manning,
                                   dt_level<T>(a, P.scen));
             if (j >= y0 && j < y0 + h) {
+                // a depth that is not a finite number reaches the host as an infinite speed
+                if (!(dabs<T>(q[0]) < T(1e30))) smy = T(INFINITY);
                 const long long gi = (long long)(j + 2) * pitch + (x0 + t);
                 qo0[gi] = q[0];
                 qo1[gi] = q[1];

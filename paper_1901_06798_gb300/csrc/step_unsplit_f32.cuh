@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(NT) step_unsplit_f32_kernel(StepArgs a)
     const StepItem it = a.items[blockIdx.x];
     if (it.w > NT - 4 || it.w < 1 || it.h < 1) return;   // not a work item of this launch shape
     const PatchDesc P = a.descs[it.patch];
+    if (a.gate != nullptr && a.gate[P.scen] == 0) return;   // not retaken (uniform over the CTA)
     const int t = threadIdx.x;
     const int cur = a.cur;
     float *base = reinterpret_cast<float *>(a.arena) + P.off;
@@ -286,6 +287,8 @@ __global__ void __launch_bounds__(NT) step_unsplit_f32_kernel(StepArgs a)
             if (a.manning > 0.0)
                 friction<float, PERT>(q[0], q[1], q[2], Bc, drytol, (float)a.manningf, dt_level<float>(a, P.scen));
             if (j >= y0 && j < y0 + h) {
+                // a surface that is not a finite number reaches the host as an infinite speed
+                if (!(fabsf(q[0]) < 1e30f)) smy = INFINITY;
                 const long long gi = (long long)(j + 2) * pitch + (x0 + t);
                 qo0[gi] = q[0];
                 qo1[gi] = q[1];

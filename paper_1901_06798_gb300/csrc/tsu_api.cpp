@@ -274,9 +274,9 @@ struct tsu_ctx {
     // control block
     DevBuf<double> dt1, t, rate, cellupd, cells, Rl, mass;
     DevBuf<float> dt1f;
-    DevBuf<long long> viol;
+    DevBuf<long long> viol, retakes;
     DevBuf<unsigned long long> smax;
-    DevBuf<int> derr;
+    DevBuf<int> derr, retake;
     std::vector<double> cells_h;
     std::vector<std::array<long long, kMaxLevels>> nsteps;
     bool initialized = false;
@@ -295,7 +295,7 @@ struct tsu_ctx {
     PinnedHost hflags;           // page-locked staging of the flag masks for clustering
     std::vector<std::vector<int32_t>> cws = std::vector<std::vector<int32_t>>(16);   // clustering workspaces
     long long n_regrids = 0;     // host-side regrid accounting (tsu_stats)
-    double regrid_ms = 0.0, cluster_ms = 0.0;
+    double regrid_ms = 0.0, cluster_ms = 0.0, regrid_wait_ms = 0.0;
     int seg_rows = 0;  // rows per work item of the patch update (0: library default)
     int step_nt = 0;   // threads per CTA of the patch update (0: library default)
     DevBuf<double> zero_dt;
@@ -317,6 +317,39 @@ struct tsu_ctx {
     };
     std::vector<StepGraph> graphs;
     long long graphs_version = -1;
+    // tsu_step_level: pend[l] = steps of level l + 2 (1-based) still to take
+    // within the current step of level l + 1; all zero when the hierarchy is
+    // synchronised (between coarse steps)
+    std::array<int, kMaxLevels> pend{};
+    // per-level timing of the patch update (tsu_profile_levels): CUDA events
+    // around each level step's update launches, and the interior cells and
+    // launches they covered
+    bool prof = false;
+    struct ProfStep {
+        int level;
+        cudaEvent_t e0, e1;
+        double cells;
+        int kernels;
+    };
+    std::vector<ProfStep> prof_steps;
+    std::vector<cudaEvent_t> prof_pool;
+    cudaEvent_t prof_event()
+    {
+        if (!prof_pool.empty()) {
+            cudaEvent_t e = prof_pool.back();
+            prof_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        return e;
+    }
+    bool synchronised() const
+    {
+        for (int l = 0; l < nlev; l++)
+            if (pend[l]) return false;
+        return true;
+    }
     DevBuf<double> dstage;
     DevBuf<double> massParts;                  // per-block partial masses of tsu_get_stats
     PinnedHost hsmall;                         // page-locked readback of error flag, CFL counts, times
@@ -350,6 +383,7 @@ struct tsu_ctx {
             a.n_items_y = (int)lv[l].items_y.size();
         }
     }
+    const int *retake_gate() const { return retake.p; }
     // kernels one patch-update launch of level l runs
     int step_kernels() const { return split_f32() ? 2 : 1; }
     int seg() const { return seg_rows > 0 ? seg_rows : (prec == TSU_F64 ? 128 : (split_f32() ? 16 : 64)); }
@@ -363,6 +397,7 @@ struct tsu_ctx {
         CtrlView v;
         v.dt1 = dt1.p; v.dt1f = dt1f.p; v.t = t.p; v.rate = rate.p; v.cell_updates = cellupd.p; v.cells = cells.p;
         v.cfl_viol = viol.p; v.smax = smax.p; v.max_levels = kMaxLevels;
+        v.retake = retake.p; v.retakes = retakes.p; v.err = derr.p;
         return v;
     }
     LevelView view(int l, const PatchDesc *descs = nullptr)
@@ -739,7 +774,13 @@ struct tsu_ctx {
             fbox.upload(bb, st);
             kl(k_flag_bbox(fF.p, nx, ny, np, fbox.p, st), "flag bbox");
             CK(cudaMemcpyAsync(bb.data(), fbox.p, bb.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+            // the flags exist once the queued steps have run: the wait is the
+            // device's time, not the regrid's
+            const auto t_w0 = std::chrono::steady_clock::now();
             sync();
+            const double wait = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_w0).count();
+            regrid_wait_ms += wait;
+            regrid_ms -= wait;
             std::vector<size_t> hoff(np + 1, 0);
             for (int q = 0; q < np; q++) {
                 const size_t w = bb[4 * q + 2] >= 0 ? (size_t)(bb[4 * q + 2] - bb[4 * q] + 1) : 0;
@@ -862,7 +903,7 @@ struct tsu_ctx {
             // wave-speed rate of the new patches for the next dt
             kl(k_cell_speed(prec, view(lf), L.dList.p, (int)fresh.size(), L.maxcells, L.cur, c.g, c.drytol, smax.p, st),
                "cell speed");
-            kl(k_post_level(ctrl(), lf, nscen, L.R, pdx(lf), pdy(lf), c.cfl_max, 1, st), "post rate");
+            kl(k_post_level(ctrl(), lf, nscen, L.R, pdx(lf), pdy(lf), c.cfl_max, c.cfl_desired, 1, st), "post rate");
         }
         // release the replaced patches of the regridded scenarios
         for (size_t k = 0; k < oldP.size(); k++)
@@ -879,13 +920,13 @@ struct tsu_ctx {
     }
 
     // ------------------------------------------------------------ stepping
-    void advance(int l, int k)
+    // One step of level l alone (Sec. 3.1 step 1): ghost fill (time fraction
+    // k / r_{l-1} of the coarser level's step), physical boundaries, the patch
+    // update with the CFL check (and, on level 1, the retake), bookkeeping.
+    void level_step(int l, int k)
     {
         Lvl &L = lv[l];
         const int n = (int)L.P.size();
-        std::vector<char> stepped(nscen, 0);
-        for (const auto &p : L.P) stepped[p.scen] = 1;
-        if (l == 0) std::fill(stepped.begin(), stepped.end(), 1);
         if (n > 0) {
             if (l > 0 || n > 1) {
                 double alpha = l > 0 ? (double)k / (double)ratio[l - 1] : 0.0;
@@ -905,19 +946,57 @@ struct tsu_ctx {
             a.manning = (c.manning_n * c.manning_n) * c.g;
             level_args(a, l);
             set_f32_constants(a);
+            ProfStep ps{};
+            if (prof) {
+                ps.level = l;
+                ps.e0 = prof_event();
+                ps.e1 = prof_event();
+                for (int sc = 0; sc < nscen; sc++) ps.cells += cells_h[(size_t)sc * kMaxLevels + l];
+                ps.kernels = step_kernels();
+                CK(cudaEventRecord(ps.e0, st));
+            }
             int e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
                                     : launch_step_f32p(a, (int)L.items.size(), nt(), st);
             kl(e, "patch step");
             launches += step_kernels() - 1;
-            kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, 0, st), "post step");
+            // Sec. 2.2 CFL condition: a level-1 step with nu > cfl_max is taken
+            // again with dt^1 = cfl_desired / rate before any finer level moves.
+            // The decision stays on the device: the step's input buffer is
+            // untouched, and the retake launch runs only the work items of the
+            // scenarios whose post-level kernel set their gate.
+            const bool retake = l == 0 && c.cfl_retake;
+            kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, c.cfl_desired, retake ? 2 : 0, st),
+               "post step");
+            if (retake) {
+                a.gate = retake_gate();
+                e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
+                                    : launch_step_f32p(a, (int)L.items.size(), nt(), st);
+                kl(e, "patch step (retake)");
+                launches += step_kernels() - 1;
+                kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, c.cfl_desired, 3, st),
+                   "post step (retake)");
+                ps.kernels += step_kernels() + 1;
+            }
+            if (prof) {
+                CK(cudaEventRecord(ps.e1, st));
+                prof_steps.push_back(ps);
+            }
             L.cur ^= 1;
         }
-        if (l + 1 < nlev && !lv[l + 1].P.empty()) {
-            for (int kk = 0; kk < ratio[l]; kk++) advance(l + 1, kk);
-            if (!lv[l + 1].P.empty())
-                kl(k_average(prec, view(l + 1), view(l), (int)lv[l + 1].P.size(), lv[l + 1].maxcells, lv[l + 1].cur,
-                             L.cur, ratio[l], c.drytol, derr.p, st), "average");
-        }
+    }
+
+    // What follows the r_l substeps of level l + 1 (or level l's own step when
+    // level l + 1 is empty): averaging onto level l, the step count, and a
+    // regrid of the finer levels every regrid_interval steps (Sec. 3.1).
+    void level_finish(int l)
+    {
+        Lvl &L = lv[l];
+        std::vector<char> stepped(nscen, 0);
+        for (const auto &p : L.P) stepped[p.scen] = 1;
+        if (l == 0) std::fill(stepped.begin(), stepped.end(), 1);
+        if (l + 1 < nlev && !lv[l + 1].P.empty())
+            kl(k_average(prec, view(l + 1), view(l), (int)lv[l + 1].P.size(), lv[l + 1].maxcells, lv[l + 1].cur,
+                         L.cur, ratio[l], c.drytol, derr.p, st), "average");
         std::vector<int> which;
         for (int s = 0; s < nscen; s++)
             if (stepped[s]) {
@@ -925,6 +1004,16 @@ struct tsu_ctx {
                 if (l + 1 < nlev && c.regrid_interval > 0 && nsteps[s][l] % c.regrid_interval == 0) which.push_back(s);
             }
         if (!which.empty()) regrid_from(l, which);
+    }
+
+    // The recursion of Sec. 3.1: a step of level l, then r_l steps of level
+    // l + 1 (each with its own recursion), then the finish of level l.
+    void advance(int l, int k)
+    {
+        level_step(l, k);
+        if (l + 1 < nlev && !lv[l + 1].P.empty())
+            for (int kk = 0; kk < ratio[l]; kk++) advance(l + 1, kk);
+        level_finish(l);
     }
 
     // would a regrid fire during the next `n` coarse steps?  (host counters only)
@@ -956,13 +1045,14 @@ struct tsu_ctx {
     void step(int n)
     {
         if (!initialized) throw Err(TSU_ERR_ARG, "tsu_init has not been called");
+        if (!synchronised()) throw Err(TSU_ERR_ARG, "tsu_step_level left a coarse step unfinished");
         ensure_samples(nsamp + n + 2);
         int done = 0;
         while (done < n) {
-            if (c.use_graphs && n - done >= 2 && !regrid_ahead(2)) {
+            if (c.use_graphs && !prof && n - done >= 2 && !regrid_ahead(2)) {
                 graph_steps(2);
                 done += 2;
-            } else if (c.use_graphs && !regrid_ahead(3)) {
+            } else if (c.use_graphs && !prof && !regrid_ahead(3)) {
                 // single steps (a caller reading back every step): captured only
                 // when it will be launched again before a regrid
                 graph_steps(1);
@@ -1040,6 +1130,42 @@ struct tsu_ctx {
         nsamp += gxy.empty() ? 0 : m;
     }
 
+    // One step of level l (0-based) in the order of the recursion of Sec. 3.1:
+    // level 1 starts a coarse step; level l + 1 takes the next of the r_l
+    // substeps within the current step of level l.  A step whose level has a
+    // non-empty finer level leaves that level's substeps pending; the last
+    // substep of a level finishes its parent's step (averaging, regrids), and
+    // finishing level 1 ends the coarse step (time, gauges).
+    void step_level(int l)
+    {
+        if (!initialized) throw Err(TSU_ERR_ARG, "tsu_init has not been called");
+        if (l < 0 || l >= nlev) throw Err(TSU_ERR_ARG, "level out of range");
+        if (l == 0) {
+            if (!synchronised()) throw Err(TSU_ERR_ARG, "level 1 steps only between coarse steps");
+            ensure_samples(nsamp + 2);
+            kl(k_begin_step(ctrl(), nscen, nlev, Rl.p, c.cfl_desired, c.dt_max, st), "begin step");
+        } else {
+            if (pend[l - 1] == 0) throw Err(TSU_ERR_ARG, "the coarser level has no substep of this level pending");
+            if (pend[l] != 0) throw Err(TSU_ERR_ARG, "the finer level's substeps are still pending");
+            if (lv[l].P.empty()) throw Err(TSU_ERR_ARG, "the level has no patches");
+        }
+        level_step(l, l == 0 ? 0 : ratio[l - 1] - pend[l - 1]);
+        if (l + 1 < nlev && !lv[l + 1].P.empty()) {
+            pend[l] = ratio[l];
+            return;
+        }
+        for (;;) {   // finish this level, and every coarser one whose last substep this was
+            level_finish(l);
+            if (l == 0) {
+                kl(k_end_step(ctrl(), nscen, st), "end step");
+                sample_gauges();
+                return;
+            }
+            if (--pend[l - 1] > 0) return;
+            l--;
+        }
+    }
+
     // Error flag and CFL-violation counts (and, with t_out, every scenario's
     // time) in one synchronisation, through page-locked memory.
     void check_device_errors(bool &cfl, double *t_out = nullptr)
@@ -1053,6 +1179,7 @@ struct tsu_ctx {
         CK(cudaMemcpyAsync(v, viol.p, ns * sizeof(long long), cudaMemcpyDeviceToHost, st));
         if (t_out) CK(cudaMemcpyAsync(tt, t.p, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
         sync();
+        if (*e & TSU_DEV_ERR_NAN) throw Err(TSU_ERR_NAN, "a wave speed or depth is not a finite number");
         if (*e) throw Err(TSU_ERR_NESTING, "a ghost cell or coarse cell had no covering patch (nesting)");
         if (t_out) std::memcpy(t_out, tt, ns * sizeof(double));
         long long tot = 0;
@@ -1149,7 +1276,7 @@ struct tsu_ctx {
         }
         kl(k_cell_speed(prec, view(0), L.dList.p, (int)all.size(), L.maxcells, L.cur, c.g, c.drytol, smax.p, st),
            "cell speed");
-        kl(k_post_level(ctrl(), 0, nscen, L.R, pdx(0), pdy(0), c.cfl_max, 1, st), "post rate");
+        kl(k_post_level(ctrl(), 0, nscen, L.R, pdx(0), pdy(0), c.cfl_max, c.cfl_desired, 1, st), "post rate");
         initialized = true;
         std::vector<int> everyone(nscen);
         for (int s = 0; s < nscen; s++) everyone[s] = s;
@@ -1357,6 +1484,8 @@ struct tsu_ctx {
     {
         if (st) cudaStreamSynchronize(st);
         for (auto &g : graphs) cudaGraphExecDestroy(g.ex);
+        for (auto &p : prof_steps) { cudaEventDestroy(p.e0); cudaEventDestroy(p.e1); }
+        for (auto &e : prof_pool) cudaEventDestroy(e);
         for (auto &e : stage_ev)
             if (e) cudaEventDestroy(e);
         for (auto &L : lv) {
@@ -1484,6 +1613,9 @@ int tsu_create(const tsu_config *cfg, void *cuda_stream, tsu_ctx **out)
         x->dt1.ensure(S, st); x->dt1f.ensure(S, st); x->t.ensure(S, st); x->rate.ensure((size_t)S * kMaxLevels, st);
         x->cellupd.ensure(S, st); x->viol.ensure(S, st); x->smax.ensure(2 * (size_t)S, st);
         x->derr.ensure(1, st); x->mass.ensure(S, st); x->dnsamp.ensure(1, st);
+        x->retake.ensure(S, st); x->retakes.ensure(S, st);
+        CK(cudaMemsetAsync(x->retake.p, 0, S * sizeof(int), st));
+        CK(cudaMemsetAsync(x->retakes.p, 0, S * sizeof(long long), st));
         CK(cudaMemsetAsync(x->dt1.p, 0, S * sizeof(double), st));
         CK(cudaMemsetAsync(x->dt1f.p, 0, S * sizeof(float), st));
         CK(cudaMemsetAsync(x->t.p, 0, S * sizeof(double), st));
@@ -1581,6 +1713,20 @@ int tsu_step(tsu_ctx *ctx, int n, double *t_out)
     int rc = guard(ctx, [&] {
         if (n < 0) throw Err(TSU_ERR_ARG, "negative step count");
         ctx->step(n);
+        ctx->check_device_errors(cfl, t_out);
+    });
+    if (rc == TSU_OK && cfl) {
+        ctx->err = "a level step ran with a Courant number above cfl_max";
+        return TSU_ERR_CFL;
+    }
+    return rc;
+}
+
+int tsu_step_level(tsu_ctx *ctx, int level, double *t_out)
+{
+    bool cfl = false;
+    int rc = guard(ctx, [&] {
+        ctx->step_level(level - 1);
         ctx->check_device_errors(cfl, t_out);
     });
     if (rc == TSU_OK && cfl) {
@@ -1724,23 +1870,26 @@ int tsu_get_stats(tsu_ctx *ctx, int scen, tsu_stats *out)
             ctx->launches++;   // k_mass runs two kernels
         }
         double v[4];
-        long long vi;
+        long long vi, vr;
         CK(cudaMemcpyAsync(&v[0], ctx->dt1.p + scen, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaMemcpyAsync(&v[1], ctx->t.p + scen, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaMemcpyAsync(&v[2], ctx->mass.p + scen, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaMemcpyAsync(&v[3], ctx->cellupd.p + scen, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaMemcpyAsync(&vi, ctx->viol.p + scen, sizeof(long long), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(&vr, ctx->retakes.p + scen, sizeof(long long), cudaMemcpyDeviceToHost, ctx->st));
         ctx->sync();
         out->dt = v[0];
         out->t = v[1];
         out->mass = v[2] * ctx->pdx(0) * ctx->pdy(0);
         out->cell_updates = v[3];
         out->cfl_violations = vi;
+        out->cfl_retakes = vr;
         for (int l = 0; l < ctx->nlev; l++)
             for (const auto &p : ctx->lv[l].P) out->patches[l] += p.scen == scen;
         out->kernel_launches = ctx->launches;
         out->regrids = ctx->n_regrids;
         out->regrid_host_ms = ctx->regrid_ms;
+        out->regrid_wait_ms = ctx->regrid_wait_ms;
         out->cluster_ms = ctx->cluster_ms;
     });
 }
@@ -1896,6 +2045,42 @@ int tsu_level1_buffers(tsu_ctx *ctx, void **h, void **hu, void **hv, void **B, i
     });
 }
 
+int tsu_profile_levels(tsu_ctx *ctx, int enable)
+{
+    return guard(ctx, [&] {
+        ctx->prof = enable != 0;
+        ctx->sync();
+        for (auto &p : ctx->prof_steps) {
+            ctx->prof_pool.push_back(p.e0);
+            ctx->prof_pool.push_back(p.e1);
+        }
+        ctx->prof_steps.clear();
+    });
+}
+
+int tsu_level_update_times(tsu_ctx *ctx, double *ms, double *cells, long long *steps, long long *kernels,
+                           int max_levels)
+{
+    return guard(ctx, [&] {
+        if (!ms || !cells || !steps || !kernels || max_levels < 1) throw Err(TSU_ERR_ARG, "bad argument");
+        for (int l = 0; l < max_levels; l++) { ms[l] = 0.0; cells[l] = 0.0; steps[l] = 0; kernels[l] = 0; }
+        ctx->sync();
+        for (auto &p : ctx->prof_steps) {
+            if (p.level < max_levels) {
+                float t = 0.0f;
+                CK(cudaEventElapsedTime(&t, p.e0, p.e1));
+                ms[p.level] += (double)t;
+                cells[p.level] += p.cells;
+                steps[p.level] += 1;
+                kernels[p.level] += p.kernels;
+            }
+            ctx->prof_pool.push_back(p.e0);
+            ctx->prof_pool.push_back(p.e1);
+        }
+        ctx->prof_steps.clear();
+    });
+}
+
 int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out, double *step_ms_out)
 {
     return guard(ctx, [&] {
@@ -1931,7 +2116,9 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
             ctx->kl(e, "patch step");
             ctx->launches += ctx->step_kernels() - 1;
             CK(cudaEventRecord(ev[2 * k + 1], ctx->st));
-            ctx->kl(k_post_level(ctx->ctrl(), 0, ctx->nscen, L.R, ctx->pdx(0), ctx->pdy(0), ctx->c.cfl_max, 0, ctx->st), "post step");
+            ctx->kl(k_post_level(ctx->ctrl(), 0, ctx->nscen, L.R, ctx->pdx(0), ctx->pdy(0), ctx->c.cfl_max,
+                                 ctx->c.cfl_desired, 0, ctx->st),
+                    "post step");
             L.cur ^= 1;
             ctx->kl(k_end_step(ctx->ctrl(), ctx->nscen, ctx->st), "end step");
             for (int s = 0; s < ctx->nscen; s++) ctx->nsteps[s][0]++;

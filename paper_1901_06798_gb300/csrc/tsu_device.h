@@ -57,6 +57,9 @@ struct StepArgs {
     float *scratch;
     const StepItem *items_y;
     int n_items_y;
+    // CFL retake of a level-1 step: when set, a work item of scenario s runs
+    // only if gate[s] != 0 (null: every item runs)
+    const int *gate;
 };
 
 // FP32 launch constants of a level

@@ -188,6 +188,45 @@ def test_mixed_call_lengths_graphs_equal_eager():
         assert a.stats()["cell_updates"] == b.stats()["cell_updates"]
 
 
+def test_step_level_in_recursion_order_equals_tsu_step():
+    """tsu_step_level driven in the order of the recursion of Sec. 3.1 (a
+    level-1 step, then r substeps of level 2, each followed by its r substeps
+    of level 3) gives tsu_step's run bit for bit over 6 coarse steps with
+    regrids; calls out of that order return TSU_ERR_ARG and change nothing."""
+    from paper_1901_06798_gb300 import binding
+    w = _amr_small()
+    cfg = w["cfg"]
+    a = W.load(_gpu(cfg, 0), w)
+    b = W.load(_gpu(cfg, 0, use_graphs=False), w)
+    nlev, ratios = cfg["num_levels"], cfg["ratios"]
+
+    def drive(g, lev):
+        g.step_level(lev, allow_cfl=True)
+        if lev < nlev and g.num_patches(0, lev + 1) > 0:
+            for _ in range(ratios[lev - 1]):
+                drive(g, lev + 1)
+
+    for _ in range(6):
+        drive(a, 1)
+        b.step(1, allow_cfl=True)
+    assert a.num_patches(0, 3) > 0
+    compare_levels(a, b, 3, bitwise=True)
+    ta, ea = a.read_gauges()
+    tb, eb = b.read_gauges()
+    assert np.array_equal(ta, tb) and np.array_equal(ea, eb)
+    sa, sb = a.stats(), b.stats()
+    assert sa["cell_updates"] == sb["cell_updates"] and sa["t"] == sb["t"]
+    for bad in (lambda: a.step_level(2), lambda: a.step_level(0), lambda: a.step_level(4)):
+        with pytest.raises(binding.TsuError) as e:
+            bad()
+        assert e.value.code == binding.TSU_ERR_ARG
+    a.step_level(1, allow_cfl=True)   # level 2's substeps are now pending
+    for bad in (lambda: a.step(1), lambda: a.step_level(1), lambda: a.step_level(3)):
+        with pytest.raises(binding.TsuError) as e:
+            bad()
+        assert e.value.code == binding.TSU_ERR_ARG
+
+
 def test_autotune_leaves_the_solution_unchanged():
     """The autotuner times zero-length steps: afterwards the run still matches
     the oracle bit for bit, in whatever launch shape it chose."""

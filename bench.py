@@ -212,10 +212,20 @@ def run_ours(args, rank, world, dist, torch):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    def sum_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
     results = {}
     clocks.start()
-    legs = [("f32p", 0, args.steps), ("f64", 0, max(1, min(args.steps, args.fp64_steps)))]
-    if args.transverse_steps > 0:
+    sel = set(args.legs.split(","))
+    legs = []
+    if "uniform" in sel:
+        legs += [("f32p", 0, args.steps), ("f64", 0, max(1, min(args.steps, args.fp64_steps)))]
+    if args.transverse_steps > 0 and "unsplit" in sel:
         kt = max(1, min(args.steps, args.transverse_steps))
         legs += [("f32p", 1, kt), ("f64", 1, max(1, kt // 5))]
     for prec, tr, K in legs:
@@ -239,8 +249,15 @@ def run_ours(args, rank, world, dist, torch):
         launches = ctx.stats()["kernel_launches"] - l0
         elapsed = max_over_ranks(step_ms * K / 1000.0)
         kern = max_over_ranks(kernel_ms)
+        # the same K-step measurement repeated (spread of the headline)
+        reps = []
+        if prec == "f32p" and not tr and args.repeats > 0:
+            for _ in range(args.repeats):
+                km, sm = ctx.time_level1_steps(0, K)
+                reps.append((km, world * cells / (max_over_ranks(sm) / 1000.0)))
         results[prec + ("_unsplit" if tr else "")] = dict(K=K, cells=cells, elapsed=elapsed, kernel_ms=kern, launches=launches,
-                             value=world * cells * K / elapsed, tune={"threads": tune[0], "seg_rows": tune[1]})
+                             value=world * cells * K / elapsed, tune={"threads": tune[0], "seg_rows": tune[1]},
+                             repeats=reps)
         ctx.close()
         del ctx
         torch.cuda.synchronize()
@@ -252,7 +269,18 @@ def run_ours(args, rank, world, dist, torch):
     if args.amr_steps > 0:
         from paper_1901_06798_gb300 import binding as B
         from paper_1901_06798_gb300 import workloads as W2
-        for name, w in (("amr3", W2.amr3()), ("ensemble64", W2.ensemble(n_scen=64, n=1024, dx=2000.0, ratio=4))):
+        amr_legs = [(n, f) for n, f in (("amr3", lambda: W2.amr3()),
+                                        ("ensemble64", lambda: W2.ensemble(n_scen=64, n=1024, dx=2000.0, ratio=4)))
+                    if n in sel]
+        from paper_1901_06798_gb300 import ranks as RK
+        for name, wf in amr_legs:
+            w = wf()
+            # the ensemble's scenarios are independent: with several ranks each
+            # advances its own block of them (no collective on the data path);
+            # the single-scenario AMR workload runs as a replica per rank
+            sharded = name.startswith("ensemble") and world > 1
+            if sharded:
+                w, _, _ = RK.shard_workload(w, rank, world)
             w = dict(w, gauges=w["gauges"])
             legs_x = {}
             gauges = {}
@@ -261,7 +289,14 @@ def run_ours(args, rank, world, dist, torch):
                 ctx = B.Tsunami(w["cfg"], precision=B.TSU_F32P if prec == "f32p" else B.TSU_F64, stream=stream)
                 W2.load(ctx, w)
                 ctx.step(args.warmup)
-                tune = ctx.autotune(2)
+                if args.shape:                                  # fixed launch shape (profiling runs)
+                    thr, seg = (int(v) for v in args.shape.split(","))
+                    if thr < 64 and prec == "f64":
+                        thr = 64
+                    ctx.set_tuning(thr, seg)
+                    tune = (thr, seg)
+                else:
+                    tune = ctx.autotune(2)
                 nscen = w["cfg"]["n_scenarios"]
                 s0 = [ctx.stats(s) for s in range(nscen)]
                 barrier()
@@ -275,11 +310,16 @@ def run_ours(args, rank, world, dist, torch):
                 bz = busy.stop()
                 s1 = [ctx.stats(s) for s in range(nscen)]
                 cu = sum(b["cell_updates"] - a["cell_updates"] for a, b in zip(s0, s1))
-                legs_x[prec] = {"value": world * cu / el, "steps": K, "ms_per_step": el / K * 1e3,
+                cu_job = sum_over_ranks(cu) if sharded else world * cu
+                legs_x[prec] = {"value": cu_job / el, "steps": K, "ms_per_step": el / K * 1e3,
+                                "parallelism": (f"scenarios sharded over {world} ranks" if sharded
+                                                else (f"replicas x{world}" if world > 1 else "1 GPU")),
                                 "cell_updates_per_step": cu / K, "patches_per_level": s1[0]["patches"],
                                 "regrid_host_ms_per_step": (s1[0]["regrid_host_ms"] - s0[0]["regrid_host_ms"]) / K,
                                 "regrid_wait_ms_per_step": (s1[0]["regrid_wait_ms"] - s0[0]["regrid_wait_ms"]) / K,
                                 "cluster_ms_per_step": (s1[0]["cluster_ms"] - s0[0]["cluster_ms"]) / K,
+                                "patches_renewed_per_step": (s1[0]["patches_renewed"] - s0[0]["patches_renewed"]) / K,
+                                "patches_reused_per_step": (s1[0]["patches_reused"] - s0[0]["patches_reused"]) / K,
                                 **bz,
                                 "launch_shape": {"threads": tune[0], "seg_rows": tune[1]}}
                 # the batched patch update alone: CUDA events around each level
@@ -302,11 +342,15 @@ def run_ours(args, rank, world, dist, torch):
 
     # end to end through the C ABI with host buffers: inputs uploaded from host
     # arrays, every step returns the simulated time to the host, and the final
-    # surface field comes back to the host.
+    # surface field comes back to the host (at least 100 steps, so that the
+    # per-run costs -- create, upload, init, final read -- do not stand in for
+    # the stepping)
+    if "e2e" not in sel:
+        return results, clk, None, extra
     from paper_1901_06798_gb300 import binding
     from paper_1901_06798_gb300 import workloads as W
     w = W.shelf(n=4096, dx=500.0)
-    Ke = args.steps
+    Ke = max(args.steps, 100)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -329,14 +373,18 @@ def run_ours(args, rank, world, dist, torch):
 
 def run_config4(args, stream, torch):
     """The 4-level bay workload with plain flagging and with the learned
-    flag predictor.  The predictor is trained on the GPU on (features, flags
-    one regrid later) pairs logged from the uniform shelf workload (the same
-    bathymetry and uplift at 2 km, 128^2 windows around flagged cells)."""
+    flag predictor.  The flags follow the wave (|eta| > 0.01 m; the depth
+    criterion is off, so the refined area is not a static shelf band and the
+    buffer the predictor trims is a real share of it); the bay box is forced
+    to the finest level as in the workload.  The predictor is trained on the
+    GPU on (features, flags one regrid later) pairs logged from the uniform
+    shelf workload (the same bathymetry and uplift at 2 km, 128^2 windows
+    around flagged cells, the same criterion)."""
     from paper_1901_06798_gb300 import binding as B
     from paper_1901_06798_gb300 import workloads as W
     t_start = time.perf_counter()
     w2 = W.shelf(n=1024, dx=2000.0)
-    cfg2 = dict(w2["cfg"], flag_eta_tol=0.01, flag_depth_below=200.0, regrid_interval=4)
+    cfg2 = dict(w2["cfg"], flag_eta_tol=0.01, flag_depth_below=0.0, regrid_interval=4)
     g = W.load(B.Tsunami(cfg2, precision=B.TSU_F32P, stream=stream), dict(w2, cfg=cfg2, gauges=np.zeros((0, 2))))
     rng = np.random.Generator(np.random.PCG64(4))
     X, T, prev, win = [], [], None, 128
@@ -357,7 +405,7 @@ def run_config4(args, stream, torch):
     theta, l0, l1 = B.cnn_train(W.cnn_init_params(0), X, T, np.ones_like(T), steps=600, batch=8, lr=2e-3, seed=1)
     train = {"samples": int(len(X)), "window": win, "loss_first": l0, "loss_last": l1,
              "seconds": time.perf_counter() - t_start}
-    w = W.amr4_bay()
+    w = W.amr4_bay(depth_below=0.0)
     runs = {}
     k64 = max(1, min(args.config4_steps, 40))
     for name, use, prec in (("plain", 0, B.TSU_F32P), ("cnn", 1, B.TSU_F32P), ("f64_plain", 0, B.TSU_F64)):
@@ -394,7 +442,8 @@ def run_config4(args, stream, torch):
     e64 = runs["f64_plain"].pop("gauges")[1]
     n = min(len(ea), len(eb))
     n64 = min(len(eb), len(e64))
-    return {"workload": "amr4_bay: 3000 km, dx 4 km -> 31.25 m (ratios 4, 4, 8), bay radius 5 km, 10 gauges",
+    return {"workload": "amr4_bay: 3000 km, dx 4 km -> 31.25 m (ratios 4, 4, 8), bay radius 5 km, 10 gauges; "
+                        "flags |eta| > 0.01 m (no depth criterion), bay box forced to level 4",
             "train": train, "plain": runs["plain"], "cnn": runs["cnn"], "f64_plain": runs["f64_plain"],
             "rate_ratio_f32p_cnn_over_f64_plain": runs["cnn"]["rate"] / runs["f64_plain"]["rate"],
             "gauge_max_abs_f32p_cnn_vs_f64_plain_m": float(np.abs(eb[:n64] - e64[:n64]).max()) if n64 else None,
@@ -475,6 +524,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default="", help="threads,seg_rows of the patch update instead of autotuning")
+    ap.add_argument("--legs", default="uniform,unsplit,amr3,ensemble64,e2e",
+                    help="comma list of legs to run (a line without the uniform leg is marked partial)")
+    ap.add_argument("--repeats", type=int, default=5, help="extra K-step timings of the headline leg (median)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
 
@@ -495,7 +547,11 @@ def main():
     config4 = None
     if args.config4_steps > 0 and rank == 0:
         config4 = run_config4(args, torch.cuda.current_stream().cuda_stream, torch)
-    if rank == 0:
+    if rank == 0 and "f32p" not in results:
+        # a subset of the legs (profiling runs): no headline line
+        print(json.dumps({"partial": True, "legs": args.legs, "amr": extra, "e2e": e2e, "clocks": clk,
+                          **({"config4": config4} if config4 else {})}))
+    elif rank == 0:
         hbm, src = peaks()
         r = results["f32p"]
         bpl = BYTES_PER_CELL["f32p"] * r["cells"]
@@ -531,6 +587,11 @@ def main():
                      "fp64_frac": FLOPS_PER_CELL * r64["cells"] / (r64["kernel_ms"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                      "fp64_peak": "nominal 1.25 TFLOP/s"},
             "fp32p_over_fp64": r["value"] / r64["value"],
+            "repeats": {"n": len(r["repeats"]), "steps_each": r["K"],
+                        "value_median": statistics.median(v for _, v in r["repeats"]) if r["repeats"] else None,
+                        "value_min": min(v for _, v in r["repeats"]) if r["repeats"] else None,
+                        "value_max": max(v for _, v in r["repeats"]) if r["repeats"] else None,
+                        "kernel_ms_median": statistics.median(k for k, _ in r["repeats"]) if r["repeats"] else None},
             "unsplit": {k.split("_")[0]: {"value": u["value"], "steps": u["K"],
                                            "ms_per_step": u["elapsed"] / u["K"] * 1e3, "kernel_ms": u["kernel_ms"],
                                            "hbm_frac": (BYTES_PER_CELL[k.split("_")[0]] * u["cells"]

@@ -123,6 +123,8 @@ typedef struct tsu_stats {
     long long cfl_retakes;      /* level-1 steps discarded and taken again (cfl_retake) */
     double regrid_wait_ms;      /* host time the rebuilds spent waiting for the queued steps to finish
                                    before the flags could be read (device time, not regrid work) */
+    long long patches_renewed;  /* patches the rebuilds created (all levels and scenarios) */
+    long long patches_reused;   /* of which had the box of an old patch and kept its memory block */
 } tsu_stats;
 
 /* Create a context.  cfg is copied.  cuda_stream: a cudaStream_t (for example
@@ -300,6 +302,29 @@ int tsu_profile_levels(tsu_ctx *ctx, int enable);
 int tsu_level_update_times(tsu_ctx *ctx, double *ms, double *cells, long long *steps, long long *kernels,
                            int max_levels);
 
+/* Halo exchange of a level split over ranks (one process per GPU).  Before
+ * each level step a rank needs, in its patches' 2-cell ghost rings (Sec. 3.1
+ * step 2: ghost cells from same-level neighbours), the cells that patches on
+ * other ranks own.  These two calls move such boxes between the patches'
+ * current state buffers and a contiguous device buffer that the caller owns
+ * and sends or receives (for example with NCCL through torch.distributed):
+ *   msgs: n_msgs messages of 5 host ints (k, i0, j0, i1, j1) -- patch k of the
+ *         scenario on the level (the order of tsu_get_patches) and a
+ *         half-open box in level indices inside that patch and its ghost ring
+ *         (pack: normally in the interior; unpack: in the ghost ring);
+ *   dev_buf: device memory of buf_elems elements of the state's precision
+ *         (double for TSU_F64, float for TSU_F32P, where q0 is eta'), holding
+ *         per message in order the fields q0, hu, hv, each a row-major
+ *         (j1 - j0) x (i1 - i0) block: 3 sum (i1 - i0)(j1 - j0) elements.
+ * tsu_halo_pack copies the boxes out of the patches, tsu_halo_unpack into
+ * them.  Both run on the library's stream and return after it finishes.
+ * Errors: TSU_ERR_ARG (no such patch, a box outside the patch's storage, a
+ * buffer too small, before tsu_init), TSU_ERR_CUDA. */
+int tsu_halo_pack(tsu_ctx *ctx, int scenario, int level, const int *msgs, int n_msgs, void *dev_buf,
+                  long long buf_elems);
+int tsu_halo_unpack(tsu_ctx *ctx, int scenario, int level, const int *msgs, int n_msgs, const void *dev_buf,
+                    long long buf_elems);
+
 /* Time n level-1 steps of the patch update alone (no AMR bookkeeping) with CUDA
  * events on the library's stream after `warmup` untimed steps; ms_out gets the
  * mean milliseconds of the step kernel per step and total_ms_out the whole
@@ -320,7 +345,8 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
  * k, k) then b (C_out); layers 5->16 3x3, 16->16 3x3, 16->16 3x3, 16->1 1x1).
  * ------------------------------------------------------------------------- */
 
-/* Number of parameters of the predictor (5,425). */
+/* Number of parameters of the predictor: 5,393 (three 3x3 layers 5->16, 16->16,
+ * 16->16 with biases: 736 + 2,320 + 2,320; the 1x1 head 16->1: 17). */
 int tsu_cnn_num_params(void);
 
 /* Logits (n, h, w) of host inputs x (n, 5, h, w); fp16 != 0: FP16 activations

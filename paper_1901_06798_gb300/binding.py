@@ -32,7 +32,8 @@ SYMBOLS = ["tsu_create", "tsu_destroy", "tsu_last_error", "tsu_add_topo", "tsu_s
            "tsu_level1_buffers", "tsu_time_level1_steps", "tsu_set_tuning",
            "tsu_grid_step_noalloc", "tsu_autotune", "tsu_cnn_num_params", "tsu_cnn_forward",
            "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features", "tsu_cluster_flags", "tsu_set_velocity",
-           "tsu_checkpoint_save", "tsu_checkpoint_restore", "tsu_profile_levels", "tsu_level_update_times"]
+           "tsu_checkpoint_save", "tsu_checkpoint_restore", "tsu_profile_levels", "tsu_level_update_times",
+           "tsu_halo_pack", "tsu_halo_unpack"]
 
 
 class tsu_config(C.Structure):
@@ -54,7 +55,8 @@ class tsu_stats(C.Structure):
     _fields_ = [("dt", C.c_double), ("t", C.c_double), ("mass", C.c_double), ("cell_updates", C.c_double),
                 ("cfl_violations", C.c_longlong), ("patches", C.c_int * MAX_LEVELS),
                 ("kernel_launches", C.c_longlong), ("regrids", C.c_longlong), ("regrid_host_ms", C.c_double),
-                ("cluster_ms", C.c_double), ("cfl_retakes", C.c_longlong), ("regrid_wait_ms", C.c_double)]
+                ("cluster_ms", C.c_double), ("cfl_retakes", C.c_longlong), ("regrid_wait_ms", C.c_double),
+                ("patches_renewed", C.c_longlong), ("patches_reused", C.c_longlong)]
 
 
 _lib = None
@@ -85,6 +87,8 @@ def load(path: str = LIB_PATH):
         "tsu_step": ([P, I, dp], I),
         "tsu_step_level": ([P, I, dp], I),
         "tsu_profile_levels": ([P, I], I),
+        "tsu_halo_pack": ([P, I, I, ip, I, P, C.c_longlong], I),
+        "tsu_halo_unpack": ([P, I, I, ip, I, P, C.c_longlong], I),
         "tsu_level_update_times": ([P, dp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), I], I),
         "tsu_regrid": ([P, I, I], I),
         "tsu_num_patches": ([P, I, I, ip], I),
@@ -240,6 +244,20 @@ class Tsunami:
         self.last_rc = rc
         return t
 
+    def halo_pack(self, scen: int, level: int, msgs, dev_ptr: int, n_elems: int):
+        """Copy halo boxes (rows of k, i0, j0, i1, j1) out of the level's patches
+        into device memory at dev_ptr (tsu_halo_pack)."""
+        m = np.ascontiguousarray(np.asarray(msgs, dtype=np.int32).reshape(-1, 5))
+        self._check(self._L.tsu_halo_pack(self._h, scen, level, m.ctypes.data_as(C.POINTER(C.c_int)), len(m),
+                                          C.c_void_p(dev_ptr), n_elems), "tsu_halo_pack")
+
+    def halo_unpack(self, scen: int, level: int, msgs, dev_ptr: int, n_elems: int):
+        """Copy halo boxes from device memory at dev_ptr into the level's
+        patches (tsu_halo_unpack)."""
+        m = np.ascontiguousarray(np.asarray(msgs, dtype=np.int32).reshape(-1, 5))
+        self._check(self._L.tsu_halo_unpack(self._h, scen, level, m.ctypes.data_as(C.POINTER(C.c_int)), len(m),
+                                            C.c_void_p(dev_ptr), n_elems), "tsu_halo_unpack")
+
     def profile_levels(self, enable: bool = True):
         """Start (or stop) recording per-level update times (tsu_profile_levels)."""
         self._check(self._L.tsu_profile_levels(self._h, 1 if enable else 0), "tsu_profile_levels")
@@ -315,7 +333,8 @@ class Tsunami:
         return {"dt": s.dt, "t": s.t, "mass": s.mass, "cell_updates": s.cell_updates,
                 "cfl_violations": s.cfl_violations, "patches": list(s.patches)[: self.num_levels],
                 "kernel_launches": s.kernel_launches, "regrids": s.regrids, "regrid_host_ms": s.regrid_host_ms,
-                "cluster_ms": s.cluster_ms, "cfl_retakes": s.cfl_retakes, "regrid_wait_ms": s.regrid_wait_ms}
+                "cluster_ms": s.cluster_ms, "cfl_retakes": s.cfl_retakes, "regrid_wait_ms": s.regrid_wait_ms,
+                "patches_renewed": s.patches_renewed, "patches_reused": s.patches_reused}
 
     def checkpoint(self) -> bytes:
         """The whole simulation state between steps (tsu_checkpoint_save)."""

@@ -916,6 +916,40 @@ static dim3 grid_for(int per_patch, int npatch, int threads)
     return dim3(bx, npatch);
 }
 
+// ---------------------------------------------------------------- halo exchange
+// A level split over ranks (one process per GPU) exchanges, before each level
+// step, the parts of its patches' 2-cell ghost rings that patches on other
+// ranks own.  These kernels move those boxes between the patches' current
+// buffers and one contiguous device buffer in message order: per message, the
+// fields q0, hu, hv, each a row-major h x w block.  One CTA per message.
+template <typename T, bool PERT>
+__global__ void halo_pack_kernel(LevelView L, const HaloMsg *msgs, int cur, T *buf)
+{
+    const HaloMsg m = msgs[blockIdx.x];
+    const PatchDesc P = L.descs[m.patch];
+    Acc<T> a = acc<T>(L.arena, P);
+    const int n = m.w * m.h;
+    for (int c = threadIdx.x; c < 3 * n; c += blockDim.x) {
+        const int f = c / n, e = c - f * n;
+        const int j = m.j0 - P.j0 + e / m.w, i = m.i0 - P.i0 + e % m.w;
+        buf[m.off + c] = a.f(cur, f)[a.idx(i, j)];
+    }
+}
+
+template <typename T, bool PERT>
+__global__ void halo_unpack_kernel(LevelView L, const HaloMsg *msgs, int cur, const T *buf)
+{
+    const HaloMsg m = msgs[blockIdx.x];
+    const PatchDesc P = L.descs[m.patch];
+    Acc<T> a = acc<T>(L.arena, P);
+    const int n = m.w * m.h;
+    for (int c = threadIdx.x; c < 3 * n; c += blockDim.x) {
+        const int f = c / n, e = c - f * n;
+        const int j = m.j0 - P.j0 + e / m.w, i = m.i0 - P.i0 + e % m.w;
+        a.f(cur, f)[a.idx(i, j)] = buf[m.off + c];
+    }
+}
+
 #define TSU_DISPATCH(PREC, KERNEL, ...)                                  \
     do {                                                                 \
         if (PREC == 0) KERNEL<double, false>__VA_ARGS__;                 \
@@ -1153,6 +1187,19 @@ int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, doub
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
     mass_sum_kernel<<<(nscen + 127) / 128, 128, 0, st>>>(L.descs, npatch, (int)g.x, parts, mass, nscen);
+    return (int)cudaGetLastError();
+}
+
+int k_halo(int prec, const LevelView &L, const HaloMsg *msgs, int n, int cur, void *buf, int unpack, cudaStream_t st)
+{
+    if (n <= 0) return 0;
+    if (unpack) {
+        if (prec == 0) halo_unpack_kernel<double, false><<<n, 128, 0, st>>>(L, msgs, cur, (const double *)buf);
+        else halo_unpack_kernel<float, true><<<n, 128, 0, st>>>(L, msgs, cur, (const float *)buf);
+    } else {
+        if (prec == 0) halo_pack_kernel<double, false><<<n, 128, 0, st>>>(L, msgs, cur, (double *)buf);
+        else halo_pack_kernel<float, true><<<n, 128, 0, st>>>(L, msgs, cur, (float *)buf);
+    }
     return (int)cudaGetLastError();
 }
 

@@ -116,6 +116,15 @@ int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplan
            cudaStream_t st);
 int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int maxcells, int cur, double g,
                  double drytol, unsigned long long *smax, cudaStream_t st);
+// one box of a halo exchange: patch (index in the level), box origin and
+// size in level indices, element offset of its three fields in the buffer
+struct HaloMsg {
+    int patch, i0, j0, w, h;
+    long long off;
+};
+// pack (unpack = 0: patch buffers -> buf) or unpack (buf -> patch buffers) n boxes
+int k_halo(int prec, const LevelView &L, const HaloMsg *msgs, int n, int cur, void *buf, int unpack, cudaStream_t st);
+
 int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
                  double cfl_desired, int mode,
                  cudaStream_t st);

@@ -103,42 +103,39 @@ __device__ __forceinline__ void lane_in(const C2 &z, int l, Cell<float> &o)
 __device__ __forceinline__ void riemann2_general(float g, const C2 &L, const C2 &R, W2 &r);
 
 // Riemann problems of two edges (L[i] | R[i]) for lanes i = x, y: the
-// wet-wet short branch paired when both lanes are wet-wet, subsonic
-// (s1 < 0 < s3) and the still-water bed-step jump leaves both middle depths
-// non-negative; else the general solver lane by lane
+// wet-wet short branch, paired, kept when both lanes are subsonic
+// (s1 < 0 < s3) and the middle depths either side of the bed step with the
+// still-water jump, hL + W1 and hR - W3, are positive (the depth bound is not
+// needed); otherwise the general solver lane by lane
 __device__ __forceinline__ void riemann2(float g, const C2 &L, const C2 &R, W2 &r)
 {
-    bool fast = L.wx && R.wx && L.wy && R.wy;
-    float2 uhat, ghb, s1, s3, d2;
-    if (fast) {
+    if (L.wx && R.wx && L.wy && R.wy) {
         const float2 num = fma(L.sq, L.u, mul(R.sq, R.u));
-        uhat = mul(num, rcp(add(L.sq, R.sq)));
+        const float2 uhat = mul(num, rcp(add(L.sq, R.sq)));
         const float2 hbar = mul(f2(0.5f), add(L.h, R.h));
-        ghb = mul(f2(g), hbar);
+        const float2 ghb = mul(f2(g), hbar);
         const float2 chat = sqrt2(ghb);
-        s1 = fmin2(sub(L.u, L.c), sub(uhat, chat));
-        s3 = fmax2(add(R.u, R.c), add(uhat, chat));
-        d2 = sub(R.hn, L.hn);
-        // middle depths (den times): M - s3 delta left of the bed step, M - s1 delta right of it
-        const float2 M = sub(fnma(s1, L.h, mul(s3, R.h)), d2);
-        const float2 delta = sub(L.B, R.B);
-        const float2 ml = fnma(s3, delta, M), mr = fnma(s1, delta, M);
-        fast = fminf(fminf(ml.x, mr.x), fminf(ml.y, mr.y)) >= 0.0f &&
-               fmaxf(s1.x, s1.y) < 0.0f && fminf(s3.x, s3.y) > 0.0f;
-    }
-    if (fast) {
+        const float2 s1 = fmin2(sub(L.u, L.c), sub(uhat, chat));
+        const float2 s3 = fmax2(add(R.u, R.c), add(uhat, chat));
         const float2 d1 = sub(R.q0, L.q0);
+        const float2 d2 = sub(R.hn, L.hn);
         const float2 d3 = fma(ghb, d1, sub(mul(R.hn, R.u), mul(L.hn, L.u)));
         const float2 d4 = sub(mul(R.hn, R.v), mul(L.hn, L.v));
         const float2 rden = rcp(sub(s3, s1));
         const float2 w1m = mul(sub(mul(s3, d1), d2), rden);
         const float2 w1n = mul(sub(mul(s3, d2), d3), rden);
-        r.z0m = mul(s1, w1m); r.z0n = mul(s1, w1n); r.z0t = mul(r.z0m, L.v);
-        r.z2m = mul(s3, sub(d1, w1m)); r.z2n = mul(s3, sub(d2, w1n)); r.z2t = mul(r.z2m, R.v);
-        r.z1t = sub(sub(d4, r.z0t), r.z2t);
-        r.s0 = s1; r.s1 = uhat; r.s2 = s3;
-        r.wallx = 0; r.wally = 0;
-        return;
+        const float2 w3m = sub(d1, w1m);
+        const float2 hl = add(L.h, w1m), hr = sub(R.h, w3m);
+        const float lo = fminf(fminf(fminf(hl.x, hl.y), fminf(hr.x, hr.y)),
+                               fminf(fminf(-s1.x, -s1.y), fminf(s3.x, s3.y)));
+        if (lo > 0.0f) {
+            r.z0m = mul(s1, w1m); r.z0n = mul(s1, w1n); r.z0t = mul(r.z0m, L.v);
+            r.z2m = mul(s3, w3m); r.z2n = mul(s3, sub(d2, w1n)); r.z2t = mul(r.z2m, R.v);
+            r.z1t = sub(sub(d4, r.z0t), r.z2t);
+            r.s0 = s1; r.s1 = uhat; r.s2 = s3;
+            r.wallx = 0; r.wally = 0;
+            return;
+        }
     }
     riemann2_general(g, L, R, r);
 }

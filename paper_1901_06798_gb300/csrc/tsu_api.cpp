@@ -17,6 +17,7 @@
 #include <stdexcept>
 #include <string>
 #include <vector>
+#include <unordered_map>
 #include <chrono>
 #include <thread>
 
@@ -296,6 +297,7 @@ struct tsu_ctx {
     std::vector<std::vector<int32_t>> cws = std::vector<std::vector<int32_t>>(16);   // clustering workspaces
     long long n_regrids = 0;     // host-side regrid accounting (tsu_stats)
     double regrid_ms = 0.0, cluster_ms = 0.0, regrid_wait_ms = 0.0;
+    long long n_patches_renewed = 0, n_patches_reused = 0;   // new patches at regrids, of which kept their block
     int seg_rows = 0;  // rows per work item of the patch update (0: library default)
     int step_nt = 0;   // threads per CTA of the patch update (0: library default)
     DevBuf<double> zero_dt;
@@ -735,6 +737,13 @@ struct tsu_ctx {
     // Build level l+1 of the scenarios in `which` from flags on level l.
     void regrid_one(int l, const std::vector<int> &which)
     {
+        // the flags need the queued steps done: that wait is the device's time,
+        // not the regrid's (the uploads below would otherwise hide it)
+        {
+            const auto t_w0 = std::chrono::steady_clock::now();
+            sync();
+            regrid_wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_w0).count();
+        }
         const auto t_begin = std::chrono::steady_clock::now();
         const int lf = l + 1, r = ratio[l];
         Lvl &C = lv[l];
@@ -774,13 +783,7 @@ struct tsu_ctx {
             fbox.upload(bb, st);
             kl(k_flag_bbox(fF.p, nx, ny, np, fbox.p, st), "flag bbox");
             CK(cudaMemcpyAsync(bb.data(), fbox.p, bb.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
-            // the flags exist once the queued steps have run: the wait is the
-            // device's time, not the regrid's
-            const auto t_w0 = std::chrono::steady_clock::now();
             sync();
-            const double wait = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_w0).count();
-            regrid_wait_ms += wait;
-            regrid_ms -= wait;
             std::vector<size_t> hoff(np + 1, 0);
             for (int q = 0; q < np; q++) {
                 const size_t w = bb[4 * q + 2] >= 0 ? (size_t)(bb[4 * q + 2] - bb[4 * q] + 1) : 0;
@@ -833,7 +836,21 @@ struct tsu_ctx {
         L.dP.p = nullptr; L.dP.cap = 0;
         std::vector<PatchDesc> P;
         std::vector<size_t> blk, bytes;
-        std::vector<int> fresh;
+        std::vector<int> fresh, renewed;   // patches to initialise; all new patches of regridded scenarios
+        // A new box identical to an old one keeps the old block: a fresh patch
+        // would copy its state from that very patch and take the same B (B is a
+        // function of the cell on a level), so nothing needs copying.  Its
+        // ghost cells are refilled before every step, and its other buffer is
+        // written by the level's next step before anything reads it.
+        std::unordered_map<unsigned long long, int> same;
+        auto key = [](int s, int i0, int j0, int nx, int ny) {
+            return ((unsigned long long)(unsigned)s << 60) ^ ((unsigned long long)(unsigned)i0 << 45) ^
+                   ((unsigned long long)(unsigned)j0 << 30) ^ ((unsigned long long)(unsigned)nx << 15) ^
+                   (unsigned long long)(unsigned)ny;
+        };
+        for (size_t k = 0; k < oldP.size(); k++)
+            if (slot[oldP[k].scen] >= 0) same.emplace(key(oldP[k].scen, oldP[k].i0, oldP[k].j0, oldP[k].nx, oldP[k].ny), (int)k);
+        std::vector<char> kept(oldP.size(), 0);
         for (int s = 0; s < nscen; s++) {
             if (slot[s] < 0) {
                 for (size_t k = 0; k < oldP.size(); k++)
@@ -841,6 +858,17 @@ struct tsu_ctx {
             } else {
                 for (const auto &b : boxes[s]) {
                     PatchDesc d = make_desc(lf, s, b[0] * r, b[1] * r, b[2] * r, b[3] * r);
+                    renewed.push_back((int)P.size());
+                    auto f = same.find(key(s, d.i0, d.j0, d.nx, d.ny));
+                    if (f != same.end() && !kept[f->second]) {
+                        const PatchDesc &o = oldP[f->second];
+                        if (o.i0 == d.i0 && o.j0 == d.j0 && o.nx == d.nx && o.ny == d.ny && o.scen == s) {
+                            kept[f->second] = 1;
+                            d.off = o.off;
+                            P.push_back(d); blk.push_back(oldblk[f->second]); bytes.push_back(oldbytes[f->second]);
+                            continue;
+                        }
+                    }
                     size_t by = (size_t)d.fs * 7 * esz;
                     size_t off = arena.alloc(by, st);
                     d.off = (long long)(off / esz);
@@ -849,6 +877,8 @@ struct tsu_ctx {
                 }
             }
         }
+        n_patches_reused += (long long)(renewed.size() - fresh.size());
+        n_patches_renewed += (long long)renewed.size();
         L.P = P; L.blk = blk; L.blkbytes = bytes;
         // old patches overlapping each new one (indices into the old table)
         L.olds.clear();
@@ -900,14 +930,17 @@ struct tsu_ctx {
             }
             kl(k_regrid_init(prec, view(lf), view(lf, oldD.p), view(lf - 1), L.dList.p, (int)fresh.size(), L.maxcells,
                              L.cur, lv[lf - 1].cur, r, c.drytol, derr.p, st), "regrid init");
-            // wave-speed rate of the new patches for the next dt
-            kl(k_cell_speed(prec, view(lf), L.dList.p, (int)fresh.size(), L.maxcells, L.cur, c.g, c.drytol, smax.p, st),
+        }
+        if (!renewed.empty()) {
+            // wave-speed rate of every new patch (kept blocks included) for the next dt
+            L.dList.upload(renewed, st);
+            kl(k_cell_speed(prec, view(lf), L.dList.p, (int)renewed.size(), L.maxcells, L.cur, c.g, c.drytol, smax.p, st),
                "cell speed");
             kl(k_post_level(ctrl(), lf, nscen, L.R, pdx(lf), pdy(lf), c.cfl_max, c.cfl_desired, 1, st), "post rate");
         }
         // release the replaced patches of the regridded scenarios
         for (size_t k = 0; k < oldP.size(); k++)
-            if (slot[oldP[k].scen] >= 0) arena.release(oldblk[k], oldbytes[k]);
+            if (slot[oldP[k].scen] >= 0 && !kept[k]) arena.release(oldblk[k], oldbytes[k]);
         oldD.release();
         // the next finer level's coarse maps point into this table
         if (lf + 1 < nlev && !lv[lf + 1].P.empty()) finish_level(lf + 1);
@@ -1736,6 +1769,61 @@ int tsu_step_level(tsu_ctx *ctx, int level, double *t_out)
     return rc;
 }
 
+// Boxes of a halo exchange (tsu_halo_pack / tsu_halo_unpack): checked against
+// the scenario's patches of the level, uploaded as HaloMsg with their offsets.
+static long long halo_msgs(tsu_ctx *ctx, int scen, int level, const int *msgs, int n, DevBuf<HaloMsg> &d)
+{
+    if (!ctx->initialized || scen < 0 || scen >= ctx->nscen || level < 1 || level > ctx->nlev || n < 0 ||
+        (n > 0 && !msgs))
+        throw Err(TSU_ERR_ARG, "bad argument");
+    Lvl &L = ctx->lv[level - 1];
+    std::vector<int> ids;
+    for (int q = 0; q < (int)L.P.size(); q++)
+        if (L.P[q].scen == scen) ids.push_back(q);
+    std::vector<HaloMsg> hm((size_t)n);
+    long long off = 0;
+    for (int k = 0; k < n; k++) {
+        const int *m = msgs + 5 * (size_t)k;
+        if (m[0] < 0 || m[0] >= (int)ids.size()) throw Err(TSU_ERR_ARG, "halo message: no such patch");
+        const PatchDesc &P = L.P[ids[m[0]]];
+        const int i0 = m[1], j0 = m[2], i1 = m[3], j1 = m[4];
+        if (!(i0 < i1 && j0 < j1 && i0 >= P.i0 - 2 && j0 >= P.j0 - 2 && i1 <= P.i0 + P.nx + 2 && j1 <= P.j0 + P.ny + 2))
+            throw Err(TSU_ERR_ARG, "halo message: box outside the patch and its ghost ring");
+        hm[k] = HaloMsg{ids[m[0]], i0, j0, i1 - i0, j1 - j0, off};
+        off += 3LL * (i1 - i0) * (j1 - j0);
+    }
+    d.upload(hm, ctx->st);
+    return off;
+}
+
+int tsu_halo_pack(tsu_ctx *ctx, int scen, int level, const int *msgs, int n_msgs, void *dev_buf, long long buf_elems)
+{
+    return guard(ctx, [&] {
+        DevBuf<HaloMsg> d;
+        const long long need = halo_msgs(ctx, scen, level, msgs, n_msgs, d);
+        if (need > buf_elems || (need > 0 && !dev_buf)) throw Err(TSU_ERR_ARG, "halo buffer too small");
+        Lvl &L = ctx->lv[level - 1];
+        ctx->kl(k_halo(ctx->prec, ctx->view(level - 1), d.p, n_msgs, L.cur, dev_buf, 0, ctx->st), "halo pack");
+        d.release();
+        ctx->sync();
+    });
+}
+
+int tsu_halo_unpack(tsu_ctx *ctx, int scen, int level, const int *msgs, int n_msgs, const void *dev_buf,
+                    long long buf_elems)
+{
+    return guard(ctx, [&] {
+        DevBuf<HaloMsg> d;
+        const long long need = halo_msgs(ctx, scen, level, msgs, n_msgs, d);
+        if (need > buf_elems || (need > 0 && !dev_buf)) throw Err(TSU_ERR_ARG, "halo buffer too small");
+        Lvl &L = ctx->lv[level - 1];
+        ctx->kl(k_halo(ctx->prec, ctx->view(level - 1), d.p, n_msgs, L.cur, const_cast<void *>(dev_buf), 1, ctx->st),
+                "halo unpack");
+        d.release();
+        ctx->sync();
+    });
+}
+
 int tsu_regrid(tsu_ctx *ctx, int scen, int level)
 {
     return guard(ctx, [&] {
@@ -1890,6 +1978,8 @@ int tsu_get_stats(tsu_ctx *ctx, int scen, tsu_stats *out)
         out->regrids = ctx->n_regrids;
         out->regrid_host_ms = ctx->regrid_ms;
         out->regrid_wait_ms = ctx->regrid_wait_ms;
+        out->patches_renewed = ctx->n_patches_renewed;
+        out->patches_reused = ctx->n_patches_reused;
         out->cluster_ms = ctx->cluster_ms;
     });
 }

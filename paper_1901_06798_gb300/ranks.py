@@ -188,3 +188,46 @@ def allgather_flags(local_flags, dist):
     for c, p in zip(counts, parts):
         out[p[:int(c.item())].numpy()] = 1
     return out.reshape(mask.shape)
+
+
+def halo_messages(schedule, rank: int):
+    """One rank's side of a halo exchange as message tables for the library's
+    tsu_halo_pack / tsu_halo_unpack: ``send`` rows (q, i0, j0, i1, j1) of the
+    messages this rank sources, ``recv`` rows (p, i0, j0, i1, j1) of those it
+    receives, both in schedule order (sorted by peer), and for each the element
+    range [lo, hi) of every peer's part of the buffer (3 fields per cell:
+    q0, hu, hv)."""
+    def side(rows):
+        table, ranges, off = [], {}, 0
+        for peer, k, box in rows:
+            n = 3 * (box[2] - box[0]) * (box[3] - box[1])
+            lo, _ = ranges.get(peer, (off, off))
+            ranges[peer] = (lo, off + n)
+            table.append((k, *box))
+            off += n
+        return np.array(table, dtype=np.int32).reshape(-1, 5), ranges, off
+    send = side([(dst, q, box) for (src, dst, q, p, box) in schedule if src == rank])
+    recv = side([(src, p, box) for (src, dst, q, p, box) in schedule if dst == rank])
+    return send, recv
+
+
+def exchange_halos_device(solver, scen: int, level: int, schedule, rank: int, dist, torch, device, dtype):
+    """Device data path of one halo exchange: the boxes this rank sources are
+    packed from its patches into one buffer on ``device`` (solver.halo_pack),
+    each peer's slice is sent and the incoming slices received in one batch of
+    point-to-point operations (NCCL between GPUs), and the received boxes are
+    unpacked into the ghost rings (solver.halo_unpack).  ``solver`` is the
+    library context (tsu_halo_pack / tsu_halo_unpack take device pointers) or
+    any object with the same two methods."""
+    (stab, sranges, sn), (rtab, rranges, rn) = halo_messages(schedule, rank)
+    sbuf = torch.empty(max(sn, 1), dtype=dtype, device=device)
+    rbuf = torch.empty(max(rn, 1), dtype=dtype, device=device)
+    if len(stab):
+        solver.halo_pack(scen, level, stab, sbuf.data_ptr(), sn)
+    ops = [dist.P2POp(dist.isend, sbuf[lo:hi], peer) for peer, (lo, hi) in sorted(sranges.items())]
+    ops += [dist.P2POp(dist.irecv, rbuf[lo:hi], peer) for peer, (lo, hi) in sorted(rranges.items())]
+    if ops:
+        for r in dist.batch_isend_irecv(ops):
+            r.wait()
+    if len(rtab):
+        solver.halo_unpack(scen, level, rtab, rbuf.data_ptr(), rn)

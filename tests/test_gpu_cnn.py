@@ -96,6 +96,13 @@ def _log_pairs(n_scen=6, regrids=16, b=4):
 
 
 def test_trained_predictor_gains_over_plain_buffering():
+    """The gain at an equal gauge error: with the trained predictor (flags =
+    criterion now, union prediction, buffer 1) against plain b = 4 buffering,
+    on an uplift the network has not seen, over 40 coarse steps: no cell the
+    criterion flags is left unrefined, fewer cell updates, and every gauge
+    within 1e-4 m of the plain run's.  The flags follow the wave (|eta| >
+    0.02 m, no depth criterion).  Wall times are printed (-s)."""
+    import time
     from paper_1901_06798_gb300 import binding
     X, T = _log_pairs()
     theta, l0, l1 = binding.cnn_train(ocnn.init_params(0), X, T, np.ones_like(T), steps=600, batch=8, lr=2e-3, seed=1)
@@ -112,6 +119,8 @@ def test_trained_predictor_gains_over_plain_buffering():
             c.cnn_set_weights(theta)
         W.load(c, dict(w, gauges=gauges))
         misses = 0
+        c.sync()
+        t0 = time.perf_counter()
         for _ in range(40):
             c.step(1)
             _, fl = c.cnn_features(0, 1)
@@ -119,22 +128,18 @@ def test_trained_predictor_gains_over_plain_buffering():
             for (i0, j0, nx, ny) in c.boxes(0, 2):
                 cov[j0 // 4:(j0 + ny) // 4, i0 // 4:(i0 + nx) // 4] = True
             misses += int(((fl > 0) & ~cov).sum())
+        c.sync()
+        wall = time.perf_counter() - t0
         t, e = c.read_gauges()
-        runs[name] = (c.stats()["cell_updates"], misses, t[:, 0], e[:, 0, :])
-    # uniform grid at the fine resolution as the reference for gauge errors
-    ref_cfg = W.base_config(nx=1024, ny=1024, dx=1000.0, dy=1000.0, bc=[W.BC_EXTRAP] * 4)
-    r = binding.Tsunami(ref_cfg, precision=1)
-    W.load(r, dict(_ensemble_cfg(1), cfg=ref_cfg, uplift=up, gauges=gauges))
-    t_end = runs["plain"][2][-1]
-    while r.stats()["t"] < t_end:
-        r.step(8)
-    tr, er = r.read_gauges()
-    err = {}
-    for name, (_, _, t, e) in runs.items():
-        ref = np.stack([np.interp(t, tr[:, 0], er[:, 0, k]) for k in range(gauges.shape[0])], axis=1)
-        err[name] = np.abs(e - ref).max()
-    cu_p, mi_p = runs["plain"][0], runs["plain"][1]
-    cu_c, mi_c = runs["cnn"][0], runs["cnn"][1]
+        runs[name] = (c.stats()["cell_updates"], misses, t[:, 0], e[:, 0, :], wall)
+    cu_p, mi_p, t_p, e_p, w_p = runs["plain"]
+    cu_c, mi_c, t_c, e_c, w_c = runs["cnn"]
+    # both runs choose their own dt (the refined areas differ): compare at the plain run's times
+    n = min(len(t_p), len(t_c))
+    e_ci = np.stack([np.interp(t_p[:n], t_c, e_c[:, k]) for k in range(gauges.shape[0])], axis=1)
+    diff = np.abs(e_ci - e_p[:n]).max()
+    print(f"\npredictor: cell updates {cu_c / cu_p:.3f} of plain buffering, wall {w_c:.3f} s vs {w_p:.3f} s "
+          f"(with the per-step flag checks), gauges within {diff:.2e} m, misses {mi_c}")
     assert mi_p == 0 and mi_c == 0
     assert cu_c < cu_p
-    assert err["cnn"] <= 1.1 * err["plain"] + 2e-3, err
+    assert diff <= 1e-4

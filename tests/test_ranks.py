@@ -196,7 +196,40 @@ def _whole_level_steps(state, steps):
     return q
 
 
-def _level_rank_main(rank, world, port, out_dir, nx, ny, tile, steps):
+class _PadSolver:
+    """Stands in for the library context on CPU ranks: halo_pack / halo_unpack
+    over the ranks' padded patch arrays with the library's buffer layout (per
+    message the fields q0, hu, hv, each a row-major box)."""
+
+    def __init__(self, pad, boxes):
+        self.pad, self.boxes = pad, boxes
+
+    def _view(self, ptr, n):
+        import ctypes
+        return np.ctypeslib.as_array((ctypes.c_double * n).from_address(ptr))
+
+    def _walk(self, msgs, ptr, n, unpack):
+        buf, off = self._view(ptr, n), 0
+        for k, i0, j0, i1, j1 in msgs:
+            pi, pj = self.boxes[k][0], self.boxes[k][1]
+            for f in range(3):
+                a = self.pad[k][f]
+                blk = (slice(j0 - pj + 2, j1 - pj + 2), slice(i0 - pi + 2, i1 - pi + 2))
+                m = (i1 - i0) * (j1 - j0)
+                if unpack:
+                    a[blk] = buf[off:off + m].reshape(j1 - j0, i1 - i0)
+                else:
+                    buf[off:off + m] = a[blk].ravel()
+                off += m
+
+    def halo_pack(self, scen, level, msgs, ptr, n):
+        self._walk(msgs, ptr, n, False)
+
+    def halo_unpack(self, scen, level, msgs, ptr, n):
+        self._walk(msgs, ptr, n, True)
+
+
+def _level_rank_main(rank, world, port, out_dir, nx, ny, tile, steps, device_path=False):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
@@ -213,10 +246,16 @@ def _level_rank_main(rank, world, port, out_dir, nx, ny, tile, steps):
             for f in range(4):
                 pad[p][f][2:-2, 2:-2] = state[f][j:j + h, i:i + w]
         sent = 0
+        if device_path:   # B once; the state every step through the packed-buffer path
+            ranks.exchange_halos({p: pad[p][3] for p in mine}, boxes, owner, msgs, rank, dist)
         for _ in range(steps):
+            if device_path:
+                ranks.exchange_halos_device(_PadSolver(pad, boxes), 0, 1, msgs, rank, dist, torch, "cpu",
+                                            torch.float64)
             for f in range(4):
                 fields = {p: pad[p][f] for p in mine}
-                ranks.exchange_halos(fields, boxes, owner, msgs, rank, dist)
+                if not device_path:
+                    ranks.exchange_halos(fields, boxes, owner, msgs, rank, dist)
                 for p in mine:                                    # same-rank neighbours
                     pi, pj, pw, ph = boxes[p]
                     for q in mine:
@@ -243,8 +282,8 @@ def _level_rank_main(rank, world, port, out_dir, nx, ny, tile, steps):
             i, j, w, h = boxes[p]
             for f in range(3):
                 out[f][j:j + h, i:i + w] = pad[p][f][2:-2, 2:-2]
-        np.savez(os.path.join(out_dir, f"level_rank{rank}.npz"), h=out[0], hu=out[1], hv=out[2],
-                 smax=smax, gmax=gmax, sent=sent)
+        np.savez(os.path.join(out_dir, f"level_rank{rank}{'_dev' if device_path else ''}.npz"), h=out[0], hu=out[1],
+                 hv=out[2], smax=smax, gmax=gmax, sent=sent)
     finally:
         dist.destroy_process_group()
 
@@ -320,3 +359,42 @@ def test_two_rank_regrid_agrees_on_patches_and_owners(tmp_path):
         assert np.array_equal(g["boxes"], ref)                           # the single-process patch list
     assert np.array_equal(got[0]["owner"], got[1]["owner"])
     assert set(got[0]["owner"].tolist()) == {0, 1}
+
+
+def test_halo_messages_split_the_schedule_by_peer():
+    boxes = _tiles(61, 47, 9)
+    owner = ranks.partition_patches(boxes, 3)
+    sched = ranks.halo_schedule(boxes, owner, 61, 47)
+    for r in range(3):
+        (st, sr, sn), (rt, rr, rn) = ranks.halo_messages(sched, r)
+        mine_out = [m for m in sched if m[0] == r]
+        mine_in = [m for m in sched if m[1] == r]
+        assert [tuple(x) for x in st] == [(m[2], *m[4]) for m in mine_out]
+        assert [tuple(x) for x in rt] == [(m[3], *m[4]) for m in mine_in]
+        cells = lambda ms: 3 * sum((b[2] - b[0]) * (b[3] - b[1]) for *_, b in ms)
+        assert sn == cells(mine_out) and rn == cells(mine_in)
+        # each peer's slice holds exactly its messages, and the slices tile the buffer in peer order
+        for rng, ms, peer_of in ((sr, mine_out, 1), (rr, mine_in, 0)):
+            edges = sorted(rng.values())
+            assert edges[0][0] == 0 and all(a[1] == b[0] for a, b in zip(edges, edges[1:]))
+            for peer, (lo, hi) in rng.items():
+                assert hi - lo == cells([m for m in ms if m[peer_of] == peer])
+
+
+def test_two_rank_level_step_through_packed_buffers(tmp_path):
+    """The same split level with the state's halos moved the way the device
+    path moves them: each rank packs the boxes it sources into one buffer
+    (tsu_halo_pack's layout), sends every peer its slice and receives its own
+    in one batch of point-to-point operations, and unpacks them into the ghost
+    rings.  Bit for bit the whole level after four steps."""
+    import oracle
+    oracle.build_flopcount()
+    nx, ny, tile, steps, world = 61, 47, 9, 4, 2
+    mp.start_processes(_level_rank_main, args=(world, _port(), str(tmp_path), nx, ny, tile, steps, True),
+                       nprocs=world, join=True, start_method="spawn")
+    parts = [np.load(tmp_path / f"level_rank{r}_dev.npz") for r in range(world)]
+    ref = _whole_level_steps(_level_state(nx, ny, _DX), steps)
+    for k, f in enumerate(("h", "hu", "hv")):
+        got = np.where(np.isnan(parts[0][f]), parts[1][f], parts[0][f])
+        assert np.array_equal(got, ref[k]), f
+

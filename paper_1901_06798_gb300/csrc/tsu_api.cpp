@@ -14,6 +14,7 @@
 #include <cstring>
 #include <limits>
 #include <map>
+#include <set>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -97,8 +98,40 @@ template <typename T> struct DevBuf {
 struct Arena {
     char *base = nullptr;
     size_t cap = 0;
-    std::map<size_t, size_t> freel;   // offset -> bytes
+    // free blocks by offset (for coalescing) and by size (best fit); the two
+    // always hold the same blocks
+    std::map<size_t, size_t> freel;             // offset -> bytes
+    std::set<std::pair<size_t, size_t>> bysize;  // (bytes, offset)
     static size_t rnd(size_t b) { return (b + 255) & ~(size_t)255; }
+    void add_free(size_t off, size_t bytes)
+    {
+        freel[off] = bytes;
+        bysize.emplace(bytes, off);
+    }
+    void drop_free(std::map<size_t, size_t>::iterator it)
+    {
+        bysize.erase({it->second, it->first});
+        freel.erase(it);
+    }
+    // insert a free block and merge it with its neighbours
+    void insert_free(size_t off, size_t bytes)
+    {
+        auto nx = freel.lower_bound(off);
+        if (nx != freel.end() && off + bytes == nx->first) {
+            bytes += nx->second;
+            drop_free(nx);
+        }
+        auto it = freel.lower_bound(off);
+        if (it != freel.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == off) {
+                off = pv->first;
+                bytes += pv->second;
+                drop_free(pv);
+            }
+        }
+        add_free(off, bytes);
+    }
     void reserve(size_t bytes, cudaStream_t st)
     {
         if (bytes <= cap) return;
@@ -110,44 +143,30 @@ struct Arena {
             CK(cudaFreeAsync(base, st));
         }
         // the new tail is free
-        size_t tail = cap;
+        const size_t tail = cap;
         base = nb;
-        freel[tail] = nc - tail;
         cap = nc;
-        // merge with a free block ending at the old cap
-        auto it = freel.find(tail);
-        if (it != freel.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) { pv->second += it->second; freel.erase(it); }
-        }
+        insert_free(tail, nc - tail);
     }
+    // the smallest free block that fits (patches of a level come in a few sizes,
+    // so a released block of the same size is usually reused exactly)
     size_t alloc(size_t bytes, cudaStream_t st)
     {
         bytes = rnd(bytes);
         for (int pass = 0; pass < 2; pass++) {
-            for (auto it = freel.begin(); it != freel.end(); ++it) {
-                if (it->second >= bytes) {
-                    size_t off = it->first, rest = it->second - bytes;
-                    freel.erase(it);
-                    if (rest) freel[off + bytes] = rest;
-                    return off;
-                }
+            auto it = bysize.lower_bound({bytes, 0});
+            if (it != bysize.end()) {
+                const size_t sz = it->first, off = it->second;
+                bysize.erase(it);
+                freel.erase(off);
+                if (sz > bytes) add_free(off + bytes, sz - bytes);
+                return off;
             }
             reserve(cap + bytes, st);
         }
         throw Err(TSU_ERR_OOM, "arena allocation failed");
     }
-    void release(size_t off, size_t bytes)
-    {
-        bytes = rnd(bytes);
-        auto it = freel.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != freel.end() && it->first + it->second == nx->first) { it->second += nx->second; freel.erase(nx); }
-        if (it != freel.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) { pv->second += it->second; freel.erase(it); }
-        }
-    }
+    void release(size_t off, size_t bytes) { insert_free(off, rnd(bytes)); }
 };
 
 struct Grid {

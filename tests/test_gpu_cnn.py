@@ -95,51 +95,65 @@ def _log_pairs(n_scen=6, regrids=16, b=4):
     return np.stack(X), np.stack(T)
 
 
-def test_trained_predictor_gains_over_plain_buffering():
-    """The gain at an equal gauge error: with the trained predictor (flags =
-    criterion now, union prediction, buffer 1) against plain b = 4 buffering,
-    on an uplift the network has not seen, over 40 coarse steps: no cell the
-    criterion flags is left unrefined, fewer cell updates, and every gauge
-    within 1e-4 m of the plain run's.  The flags follow the wave (|eta| >
-    0.02 m, no depth criterion).  Wall times are printed (-s)."""
+def _cnn_vs_plain(theta, buffer):
+    """One unseen uplift scenario over 40 coarse steps with plain b = 4 buffering
+    and with the predictor (flags = criterion now, union prediction, dilated by
+    `buffer`): cell updates, criterion-flagged cells left unrefined, wall time,
+    and the largest gauge difference between the two runs at the plain run's
+    times (each run chooses its own dt)."""
     import time
     from paper_1901_06798_gb300 import binding
-    X, T = _log_pairs()
-    theta, l0, l1 = binding.cnn_train(ocnn.init_params(0), X, T, np.ones_like(T), steps=600, batch=8, lr=2e-3, seed=1)
-    assert l1 < 0.1 * l0
-
-    # a scenario the network has not seen
     up = [(0, *W.shelf_uplift(1024e3, 1024e3, scale=0.5, amp=3.0, s_km=640.0, yc=540e3))]
     gauges = np.array([[674e3, 540e3], [744e3, 560e3], [774e3, 500e3]])
     runs = {}
     for name, use in (("plain", 0), ("cnn", 1)):
         w = dict(_ensemble_cfg(1, use_cnn=use), uplift=up)
+        w = dict(w, cfg=dict(w["cfg"], cnn_buffer=buffer))
         c = binding.Tsunami(w["cfg"], precision=1)
         if use:
             c.cnn_set_weights(theta)
         W.load(c, dict(w, gauges=gauges))
-        misses = 0
-        c.sync()
-        t0 = time.perf_counter()
+        misses, wall = 0, 0.0
         for _ in range(40):
+            c.sync()
+            t0 = time.perf_counter()
             c.step(1)
+            c.sync()
+            wall += time.perf_counter() - t0
             _, fl = c.cnn_features(0, 1)
             cov = np.zeros_like(fl, dtype=bool)
             for (i0, j0, nx, ny) in c.boxes(0, 2):
                 cov[j0 // 4:(j0 + ny) // 4, i0 // 4:(i0 + nx) // 4] = True
             misses += int(((fl > 0) & ~cov).sum())
-        c.sync()
-        wall = time.perf_counter() - t0
         t, e = c.read_gauges()
         runs[name] = (c.stats()["cell_updates"], misses, t[:, 0], e[:, 0, :], wall)
     cu_p, mi_p, t_p, e_p, w_p = runs["plain"]
     cu_c, mi_c, t_c, e_c, w_c = runs["cnn"]
-    # both runs choose their own dt (the refined areas differ): compare at the plain run's times
     n = min(len(t_p), len(t_c))
     e_ci = np.stack([np.interp(t_p[:n], t_c, e_c[:, k]) for k in range(gauges.shape[0])], axis=1)
-    diff = np.abs(e_ci - e_p[:n]).max()
-    print(f"\npredictor: cell updates {cu_c / cu_p:.3f} of plain buffering, wall {w_c:.3f} s vs {w_p:.3f} s "
-          f"(with the per-step flag checks), gauges within {diff:.2e} m, misses {mi_c}")
-    assert mi_p == 0 and mi_c == 0
-    assert cu_c < cu_p
-    assert diff <= 1e-4
+    diff = float(np.abs(e_ci - e_p[:n]).max())
+    print(f"\npredictor, buffer {buffer}: cell updates {cu_c / cu_p:.3f} of plain b = 4, step wall time "
+          f"{w_c:.3f} s vs {w_p:.3f} s, gauges within {diff:.2e} m of plain (amplitude "
+          f"{np.abs(e_p).max():.2f} m), misses {mi_c}")
+    return cu_c / cu_p, mi_p, mi_c, diff
+
+
+def test_trained_predictor_against_plain_buffering():
+    """What the trained predictor buys over plain b = 4 buffering, judged by
+    the criterion (no flagged cell left unrefined) and by the gauges.  With the
+    predictor's cells dilated by 1 it refines fewer cells than plain
+    buffering; dilated by 2 its gauges agree with plain buffering's within
+    1e-4 m.  On this workload the two do not meet: at an equal gauge error the
+    learned flags refine about 2% more cells, and the 2% fewer cells of buffer
+    1 cost gauge differences of a few mm, because the plain buffer also keeps
+    the wave's tail below the criterion refined (the numbers are printed)."""
+    from paper_1901_06798_gb300 import binding
+    X, T = _log_pairs()
+    theta, l0, l1 = binding.cnn_train(ocnn.init_params(0), X, T, np.ones_like(T), steps=600, batch=8, lr=2e-3, seed=1)
+    assert l1 < 0.1 * l0
+    r1, mp1, mc1, d1 = _cnn_vs_plain(theta, 1)
+    assert mp1 == 0 and mc1 == 0
+    assert r1 < 1.0
+    r2, mp2, mc2, d2 = _cnn_vs_plain(theta, 2)
+    assert mp2 == 0 and mc2 == 0
+    assert d2 <= 1e-4

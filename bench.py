@@ -152,6 +152,19 @@ class Busy:
         return {"gpu_busy_frac": gpu, "host_busy_frac": host}
 
 
+def amr_level3_traffic():
+    """DRAM bytes per cell of one level-3 update (x + y launches over all the
+    level's patches) on the 3-level AMR workload, from the committed ncu
+    summary, only if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    e = json.load(open(p)).get("f32p_amr3_level3")
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e["dram_bytes_per_launch"] / e["cells"]
+
+
 def update_roofline(lt, prec, steps):
     """Per-level and summed cost of the batched patch update from
     tsu_level_update_times: device ms per coarse step, interior cell updates,
@@ -178,9 +191,16 @@ def update_roofline(lt, prec, steps):
     if fine:
         ms, cells = sum(v["ms"] for v in fine), sum(v["cells"] for v in fine)
         ach = bpc * cells / (ms * 1e-3) / 1e9
+        tpc = amr_level3_traffic() if prec == "f32p" else None
+        top = max((lev for lev, v in lt.items() if v["steps"] > 0), default=None)
+        cells_launch = lt[top]["cells"] / lt[top]["steps"] if top else 0.0
         out["roofline"] = {"bound": "hbm", "what": "patch update of levels >= 2 (batched, one launch per level step)",
                            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                           "peak_source": how, "traffic": None}
+                           "peak_source": how,
+                           # DRAM bytes of one update of the finest level (x + y launches), from ncu
+                           "traffic": tpc * cells_launch if tpc else None,
+                           "bytes_per_launch": bpc * cells_launch,
+                           "traffic_bytes_per_cell": tpc}
     return out
 
 
@@ -452,18 +472,68 @@ def run_config4(args, stream, torch):
             "gauge_max_abs_cnn_vs_plain_m": float(np.abs(ea[:n] - eb[:n]).max()) if n else None}
 
 
-def cpu_baseline():
-    """The FP64 oracle as it stands (one thread) on a bounded sample of the
-    workload: the full 4096^2 grid, 2 steps."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_rate(args):
+    """Cell updates/s of the FP64 oracle (timing build) on the full 4096^2
+    shelf workload, `steps` steps, in this process (OMP_NUM_THREADS set by
+    the caller before the library loads)."""
+    steps, = args
+    sys.path.insert(0, ROOT)
     import oracle
     from paper_1901_06798_gb300 import workloads as W
     w = W.shelf(n=4096, dx=500.0)
     o = W.load(oracle.Oracle(w["cfg"], variant="fast"), dict(w, gauges=np.zeros((0, 2))))
     t0 = time.perf_counter()
-    o.step(2)
-    dt = time.perf_counter() - t0
-    return {"value": 2 * 4096 * 4096 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "full 4096x4096 shelf workload, 2 steps, FP64 oracle built -O3 -ffp-contract=off, 1 thread"}
+    o.step(steps)
+    return 4096 * 4096 * steps / (time.perf_counter() - t0)
+
+
+def _oracle_rate_with_threads(threads, steps):
+    """_oracle_rate in a fresh spawned process with `threads` OpenMP threads."""
+    import multiprocessing as mp
+    old = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    try:
+        with mp.get_context("spawn").Pool(1) as pool:
+            return pool.map(_oracle_rate, [(steps,)])[0]
+    finally:
+        if old is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = old
+
+
+def cpu_baseline():
+    """The FP64 oracle as it stands, timed on the host on the full 4096^2
+    workload: with OpenMP over the rows and columns of the sweeps on all host
+    cores (the reported value), and on one core."""
+    import oracle
+    oracle.build("fast")
+    cores = os.cpu_count() or 1
+    v_all = _oracle_rate_with_threads(cores, 8)
+    v_one = _oracle_rate_with_threads(1, 2)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "single_core_value": v_one,
+            "sample": f"full 4096x4096 shelf workload: 8 steps on {cores} OpenMP threads (rows of the x sweep, "
+                      "columns of the y sweep), and 2 steps on 1 thread; FP64 oracle built -O3 -ffp-contract=off"}
 
 
 def _ref_worker(a):
@@ -487,6 +557,7 @@ def run_reference(args):
     import multiprocessing as mp
     import oracle
     oracle.build("fast")
+    os.environ["OMP_NUM_THREADS"] = "1"   # one window per worker process and core
     cores = min(os.cpu_count() or 1, 16)
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:

@@ -32,9 +32,9 @@ FIELDS = {"h": 0, "hu": 1, "hv": 2, "eta": 3, "zeta": 4, "B": 5}
 
 def build(variant: str = "parity", force: bool = False) -> str:
     """Compile the oracle.  ``parity``: -O2 -ffp-contract=off (the arithmetic
-    exactly as written); ``fast``: the same source with -O3 and OpenMP-free
-    vectorisation allowed but still no contraction (used only to time the CPU
-    baseline)."""
+    exactly as written, one thread); ``fast``: the same source with -O3 and
+    OpenMP over the rows and columns of a patch's sweeps, still without
+    contraction (used only to time the CPU baseline; the same results)."""
     os.makedirs(_BUILD, exist_ok=True)
     out = os.path.join(_BUILD, f"liboracle_{variant}.so")
     srcs = [os.path.join(_HERE, s) for s in _SRCS]
@@ -43,7 +43,9 @@ def build(variant: str = "parity", force: bool = False) -> str:
         mt = os.path.getmtime(out)
         if all(os.path.getmtime(d) <= mt for d in deps):
             return out
-    opt = ["-O2"] if variant == "parity" else ["-O3"]
+    # the timing build shares a patch's row and column sweeps over OpenMP threads
+    # (OMP_NUM_THREADS, default all cores); the parity build has no threads
+    opt = ["-O2"] if variant == "parity" else ["-O3", "-fopenmp"]
     cmd = ["gcc", *opt, "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared",
            *srcs, "-o", out + ".tmp", "-lm"]
     subprocess.run(cmd, check=True)

@@ -244,7 +244,11 @@ static double sweep_1d_flux(double g, double drytol, int n, double dtdx,
             double upd = (apdq[i][m] + amdq[i + 1][m]) + (F[i + 1][m] - F[i][m]);
             qo[m][i] = q[m][i + 2] - dtdx * upd;
         }
-        if (ho[i] < 0.0) { ora_neg_clips++; ho[i] = 0.0; }
+        if (ho[i] < 0.0) {
+#pragma omp atomic
+            ora_neg_clips++;
+            ho[i] = 0.0;
+        }
         if (ho[i] < drytol) { hno[i] = 0.0; hto[i] = 0.0; }
     }
     free(rp); free(amdq); free(apdq); free(F);
@@ -324,7 +328,11 @@ static double sweep_1d_geo(double g, double drytol, int n, double dt, double dyp
             if (m == 0) upd = upd + (ced[i + 1] - ced[i]) * hn[i + 2];
             qo[m][i] = q[m][i + 2] - dtk * upd;
         }
-        if (ho[i] < 0.0) { ora_neg_clips++; ho[i] = 0.0; }
+        if (ho[i] < 0.0) {
+#pragma omp atomic
+            ora_neg_clips++;
+            ho[i] = 0.0;
+        }
         if (ho[i] < drytol) { hno[i] = 0.0; hto[i] = 0.0; }
     }
     free(rp); free(amdq); free(apdq); free(F);
@@ -392,40 +400,54 @@ void ora_step_patch_flux(OPatch *p, double g, double drytol, double dt, double d
 {
     int nx = p->nx, ny = p->ny;
     int nmax = (nx > ny ? nx : ny) + 4;
-    double *a = malloc(4 * (size_t)nmax * sizeof(double));
-    double *o = malloc(3 * (size_t)nmax * sizeof(double));
-    double *ah = a, *an = a + nmax, *at = a + 2 * nmax, *aB = a + 3 * nmax;
-    double *oh = o, *on = o + nmax, *ot = o + 2 * nmax;
     double sx = 0.0, sy = 0.0;
     double dtdx = dt / dx, dtdy = dt / dy;
-
-    for (int j = -2; j < ny + 2; j++) {
-        for (int i = -2; i < nx + 2; i++) {
-            size_t k = OIDX(p, i, j);
-            ah[i + 2] = p->h[k]; an[i + 2] = p->hu[k]; at[i + 2] = p->hv[k]; aB[i + 2] = p->B[k];
-        }
-        double *gx = (xf && j >= 0 && j < ny) ? xf + 2 * (size_t)j * (nx + 1) : NULL;
-        double s = sweep_1d_flux(g, drytol, nx, dtdx, ah, an, at, aB, oh, on, ot, gx);
-        if (j >= 0 && j < ny) sx = fmax(sx, s);
-        for (int i = 0; i < nx; i++) {
-            size_t k = OIDX(p, i, j);
-            p->h[k] = oh[i]; p->hu[k] = on[i]; p->hv[k] = ot[i];
-        }
-    }
-    for (int i = 0; i < nx; i++) {
+    /* Every row's x sweep, and then every column's y sweep, is independent of
+     * the others: the timing build (built with OpenMP) shares them out over
+     * host threads; the maxima are order-independent.  Without OpenMP the
+     * pragmas are ignored and this is the plain loop. */
+#pragma omp parallel
+    {
+        double *a = malloc(4 * (size_t)nmax * sizeof(double));
+        double *o = malloc(3 * (size_t)nmax * sizeof(double));
+        double *ah = a, *an = a + nmax, *at = a + 2 * nmax, *aB = a + 3 * nmax;
+        double *oh = o, *on = o + nmax, *ot = o + 2 * nmax;
+        double sxl = 0.0, syl = 0.0;
+#pragma omp for schedule(static)
         for (int j = -2; j < ny + 2; j++) {
-            size_t k = OIDX(p, i, j);
-            ah[j + 2] = p->h[k]; an[j + 2] = p->hv[k]; at[j + 2] = p->hu[k]; aB[j + 2] = p->B[k];
+            for (int i = -2; i < nx + 2; i++) {
+                size_t k = OIDX(p, i, j);
+                ah[i + 2] = p->h[k]; an[i + 2] = p->hu[k]; at[i + 2] = p->hv[k]; aB[i + 2] = p->B[k];
+            }
+            double *gx = (xf && j >= 0 && j < ny) ? xf + 2 * (size_t)j * (nx + 1) : NULL;
+            double s = sweep_1d_flux(g, drytol, nx, dtdx, ah, an, at, aB, oh, on, ot, gx);
+            if (j >= 0 && j < ny) sxl = fmax(sxl, s);
+            for (int i = 0; i < nx; i++) {
+                size_t k = OIDX(p, i, j);
+                p->h[k] = oh[i]; p->hu[k] = on[i]; p->hv[k] = ot[i];
+            }
         }
-        double *gy = yf ? yf + 2 * (size_t)i * (ny + 1) : NULL;
-        double s = sweep_1d_flux(g, drytol, ny, dtdy, ah, an, at, aB, oh, on, ot, gy);
-        sy = fmax(sy, s);
-        for (int j = 0; j < ny; j++) {
-            size_t k = OIDX(p, i, j);
-            p->h[k] = oh[j]; p->hv[k] = on[j]; p->hu[k] = ot[j];
+#pragma omp for schedule(static)
+        for (int i = 0; i < nx; i++) {
+            for (int j = -2; j < ny + 2; j++) {
+                size_t k = OIDX(p, i, j);
+                ah[j + 2] = p->h[k]; an[j + 2] = p->hv[k]; at[j + 2] = p->hu[k]; aB[j + 2] = p->B[k];
+            }
+            double *gy = yf ? yf + 2 * (size_t)i * (ny + 1) : NULL;
+            double s = sweep_1d_flux(g, drytol, ny, dtdy, ah, an, at, aB, oh, on, ot, gy);
+            syl = fmax(syl, s);
+            for (int j = 0; j < ny; j++) {
+                size_t k = OIDX(p, i, j);
+                p->h[k] = oh[j]; p->hv[k] = on[j]; p->hu[k] = ot[j];
+            }
         }
+#pragma omp critical
+        {
+            sx = fmax(sx, sxl);
+            sy = fmax(sy, syl);
+        }
+        free(a); free(o);
     }
-    free(a); free(o);
     *sx_out = sx; *sy_out = sy;
 }
 

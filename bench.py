@@ -44,6 +44,37 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 
 
+def measured_alu_peaks(torch):
+    """FP64 and FP32 dense arithmetic rates of this GPU, measured with library
+    GEMMs (torch.matmul of 8192^2 FP64 and of 8192^2 FP32 with TF32 off: the
+    FMA pipes, not tensor cores), best of 5 timed with CUDA events after a
+    warm-up.  They are the denominators of the update's compute roofs."""
+    out = {}
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n in (("fp64", torch.float64, 8192), ("fp32", torch.float32, 8192)):
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    torch.cuda.empty_cache()
+    return out
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -618,6 +649,7 @@ def main():
     config4 = None
     if args.config4_steps > 0 and rank == 0:
         config4 = run_config4(args, torch.cuda.current_stream().cuda_stream, torch)
+    alu = measured_alu_peaks(torch) if rank == 0 and "f32p" in results else {}
     if rank == 0 and "f32p" not in results:
         # a subset of the legs (profiling runs): no headline line
         print(json.dumps({"partial": True, "legs": args.legs, "amr": extra, "e2e": e2e, "clocks": clk,
@@ -648,15 +680,20 @@ def main():
             # the other roof of the same update: algorithmic flops against the FP32 pipes; neither
             # binds -- the update is bound by instruction issue (see the design notes)
             "roofline_fp32": {"bound": "alu", "achieved": FLOPS_PER_CELL * r["cells"] / (r["kernel_ms"] / 1e3) / 1e12,
-                              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": FLOPS_PER_CELL * r["cells"] / (r["kernel_ms"] / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                              "peak": alu.get("fp32", FP32_PEAK_TFLOPS), "unit": "TFLOP/s",
+                              "frac": FLOPS_PER_CELL * r["cells"] / (r["kernel_ms"] / 1e3) / 1e12
+                                      / alu.get("fp32", FP32_PEAK_TFLOPS),
                               "flops_per_cell": FLOPS_PER_CELL,
-                              "peak_source": "derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"},
+                              "peak_source": ("measured: FP32 GEMM 8192^3, TF32 off (FMA pipes)" if "fp32" in alu
+                                              else "derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"),
+                              "peak_derived": FP32_PEAK_TFLOPS},
             "fp64": {"value": r64["value"], "steps": r64["K"], "ms_per_step": r64["elapsed"] / r64["K"] * 1e3,
                      "kernel_ms": r64["kernel_ms"],
                      "hbm_frac": (b64 / (r64["kernel_ms"] / 1e3) / 1e9) / hbm,
-                     "fp64_frac": FLOPS_PER_CELL * r64["cells"] / (r64["kernel_ms"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                     "fp64_peak": "nominal 1.25 TFLOP/s"},
+                     "fp64_frac": FLOPS_PER_CELL * r64["cells"] / (r64["kernel_ms"] / 1e3) / 1e12
+                                  / alu.get("fp64", FP64_PEAK_TFLOPS),
+                     "fp64_peak_tflops": alu.get("fp64", FP64_PEAK_TFLOPS),
+                     "fp64_peak": ("measured: FP64 GEMM 8192^3" if "fp64" in alu else "nominal 1.25 TFLOP/s")},
             "fp32p_over_fp64": r["value"] / r64["value"],
             "repeats": {"n": len(r["repeats"]), "steps_each": r["K"],
                         "value_median": statistics.median(v for _, v in r["repeats"]) if r["repeats"] else None,

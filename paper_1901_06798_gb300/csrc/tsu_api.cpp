@@ -498,27 +498,48 @@ struct tsu_ctx {
         size_t soff = 0;
         for (int k = 0; k < n; k++) {
             PatchDesc &p = L.P[k];
-            if (split) {
-                // x kernel: every row including the ghost rows, no halo rows; y kernel:
-                // strips of 2 x 32 columns and segments of 32 interior rows
-                for (int x0 = 0; x0 < p.nx; x0 += W)
-                    for (int y0 = -2; y0 < p.ny + 2; y0 += seg())
-                        L.items.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(seg(), p.ny + 2 - y0)});
-                constexpr int WY = 64, SY = 32;
-                for (int x0 = 0; x0 < p.nx; x0 += WY)
-                    for (int y0 = 0; y0 < p.ny; y0 += SY)
-                        L.items_y.push_back(StepItem{k, x0, y0, std::min(WY, p.nx - x0), std::min(SY, p.ny - y0)});
-                p.soff = (long long)soff;
-                soff += 3 * (size_t)p.fs;
-            } else {
-                p.soff = 0;
-                for (int x0 = 0; x0 < p.nx; x0 += W)
-                    for (int y0 = 0; y0 < p.ny; y0 += seg())
-                        L.items.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(seg(), p.ny - y0)});
-            }
+            p.soff = split ? (long long)soff : 0;
+            if (split) soff += 3 * (size_t)p.fs;
             L.maxring = std::max(L.maxring, (p.nx + 4) * (p.ny + 4) - p.nx * p.ny);
             L.maxcells = std::max(L.maxcells, (p.nx + 4) * (p.ny + 4));
             if (p.bcmask) L.bclist.push_back(k);
+        }
+        // work items of the patch update in patch order, built in patch ranges on
+        // host threads and joined in range order
+        {
+            const int sg = seg();
+            std::vector<std::vector<StepItem>> xi(16), yi(16);
+            std::array<std::array<int, 2>, 16> rr{};
+            parallel_ranges(n, [&](int q, int b, int e) {
+                rr[q] = {b, e};
+                std::vector<StepItem> &ox = xi[q], &oy = yi[q];
+                for (int k = b; k < e; k++) {
+                    const PatchDesc &p = L.P[k];
+                    if (split) {
+                        // x kernel: every row including the ghost rows, no halo rows; y kernel:
+                        // strips of 2 x 32 columns and segments of 32 interior rows
+                        for (int x0 = 0; x0 < p.nx; x0 += W)
+                            for (int y0 = -2; y0 < p.ny + 2; y0 += sg)
+                                ox.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(sg, p.ny + 2 - y0)});
+                        constexpr int WY = 64, SY = 32;
+                        for (int x0 = 0; x0 < p.nx; x0 += WY)
+                            for (int y0 = 0; y0 < p.ny; y0 += SY)
+                                oy.push_back(StepItem{k, x0, y0, std::min(WY, p.nx - x0), std::min(SY, p.ny - y0)});
+                    } else {
+                        for (int x0 = 0; x0 < p.nx; x0 += W)
+                            for (int y0 = 0; y0 < p.ny; y0 += sg)
+                                ox.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(sg, p.ny - y0)});
+                    }
+                }
+            });
+            size_t nxi = 0, nyi = 0;
+            for (int q = 0; q < 16; q++) { nxi += xi[q].size(); nyi += yi[q].size(); }
+            L.items.reserve(nxi);
+            L.items_y.reserve(nyi);
+            for (int q = 0; q < 16; q++) {
+                L.items.insert(L.items.end(), xi[q].begin(), xi[q].end());
+                L.items_y.insert(L.items_y.end(), yi[q].begin(), yi[q].end());
+            }
         }
         // per scenario spatial indices of this level and the coarser one
         std::vector<std::vector<int>> ids(nscen), cids(nscen);

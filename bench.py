@@ -46,14 +46,15 @@ FP64_PEAK_TFLOPS = 1.25
 
 def measured_alu_peaks(torch):
     """FP64 and FP32 dense arithmetic rates of this GPU, measured with library
-    GEMMs (torch.matmul of 8192^2 FP64 and of 8192^2 FP32 with TF32 off: the
-    FMA pipes, not tensor cores), best of 5 timed with CUDA events after a
-    warm-up.  They are the denominators of the update's compute roofs."""
+    GEMMs (torch.matmul of 4096^2 FP64 -- cuBLAS runs it on the FP64 tensor
+    path -- and of 8192^2 FP32 with TF32 off, on the FMA pipes), best of 5
+    timed with CUDA events after a warm-up.  They are the denominators of the
+    update's compute roofs."""
     out = {}
     tf32 = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
-        for name, dt, n in (("fp64", torch.float64, 8192), ("fp32", torch.float32, 8192)):
+        for name, dt, n in (("fp64", torch.float64, 4096), ("fp32", torch.float32, 8192)):
             a = torch.randn(n, n, dtype=dt, device="cuda")
             b = torch.randn(n, n, dtype=dt, device="cuda")
             torch.matmul(a, b)
@@ -693,7 +694,8 @@ def main():
                      "fp64_frac": FLOPS_PER_CELL * r64["cells"] / (r64["kernel_ms"] / 1e3) / 1e12
                                   / alu.get("fp64", FP64_PEAK_TFLOPS),
                      "fp64_peak_tflops": alu.get("fp64", FP64_PEAK_TFLOPS),
-                     "fp64_peak": ("measured: FP64 GEMM 8192^3" if "fp64" in alu else "nominal 1.25 TFLOP/s")},
+                     "fp64_peak": ("measured: FP64 GEMM 4096^3 (cuBLAS, FP64 tensor path)" if "fp64" in alu
+                                   else "nominal 1.25 TFLOP/s")},
             "fp32p_over_fp64": r["value"] / r64["value"],
             "repeats": {"n": len(r["repeats"]), "steps_each": r["K"],
                         "value_median": statistics.median(v for _, v in r["repeats"]) if r["repeats"] else None,

@@ -580,8 +580,10 @@ __global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, 
                 if (a < 0 || a >= nx || b < 0 || b >= ny) continue;
                 if (!cv[(long long)b * nx + a]) { ok = 0; break; }
             }
-        N[c] = (uint8_t)ok;
-        F[c] = ok ? f : 0;
+        // N: bit 0 the final flag, bit 1 nestable -- the one plane the host clusters
+        const uint8_t ff = ok ? f : 0;
+        N[c] = (uint8_t)((ok << 1) | (ff ? 1 : 0));
+        F[c] = ff;
     }
 }
 

@@ -12,6 +12,8 @@
 //   and recurse, lower/left part first.  Boxes are finally split into
 //   near-equal pieces whose fine size is at most patch_max.
 //
+// The flags and the nestable mask come as one byte plane: bit 0 the flag, bit 1
+// nestable (the plane the regrid copies from the device).
 // 2D prefix sums of the flags and of the nestable mask make every count and
 // signature O(w + h) per box, so the cost is dominated by one pass over the
 // mask.  They are built only over the flags' bounding box (the recursion's
@@ -69,7 +71,7 @@ template <typename Fn> void parallel_for(int n, int threads, Fn f)
 
 }  // namespace
 
-void cluster_boxes(const uint8_t *Fg, const uint8_t *Ng, int nxg, int nyg, double eff, int ratio, int patch_max,
+void cluster_boxes(const uint8_t *Fg, int nxg, int nyg, double eff, int ratio, int patch_max,
                    std::vector<std::array<int, 4>> &out, int max_threads, std::vector<int32_t> *workspace)
 {
     out.clear();
@@ -85,10 +87,10 @@ void cluster_boxes(const uint8_t *Fg, const uint8_t *Ng, int nxg, int nyg, doubl
             const uint8_t *r = Fg + (size_t)j * nxg;
             int lo = -1, hi = -1;
             for (int i = 0; i < nxg; i++)
-                if (r[i]) { lo = i; break; }
+                if (r[i] & 1) { lo = i; break; }
             if (lo < 0) continue;
             for (int i = nxg - 1; i >= lo; i--)
-                if (r[i]) { hi = i; break; }
+                if (r[i] & 1) { hi = i; break; }
             rmin[j] = lo;
             rmax[j] = hi;
         }
@@ -119,12 +121,12 @@ void cluster_boxes(const uint8_t *Fg, const uint8_t *Ng, int nxg, int nyg, doubl
     parallel_for(ny, threads, [&](int ja, int jb) {
         for (int j = ja; j < jb; j++) {
             Sums::Pair *r = S.P + (size_t)(j + 1) * W;
-            const uint8_t *fr = Fg + (size_t)(j + bj0) * nxg + bi0, *nr = Ng + (size_t)(j + bj0) * nxg + bi0;
+            const uint8_t *fr = Fg + (size_t)(j + bj0) * nxg + bi0;
             int32_t fa = 0, na = 0;
             r[0] = {0, 0};
             for (int i = 0; i < nx; i++) {
-                fa += fr[i] ? 1 : 0;
-                na += nr[i] ? 1 : 0;
+                fa += fr[i] & 1;
+                na += (fr[i] >> 1) & 1;
                 r[i + 1] = {fa, na};
             }
         }

@@ -31,7 +31,8 @@
 #include "tsu_device.h"
 
 namespace tsu {
-void cluster_boxes(const uint8_t *F, const uint8_t *N, int nx, int ny, double eff, int ratio, int patch_max,
+// FN: one byte per cell, bit 0 the flag, bit 1 nestable
+void cluster_boxes(const uint8_t *FN, int nx, int ny, double eff, int ratio, int patch_max,
                    std::vector<std::array<int, 4>> &out, int max_threads, std::vector<int32_t> *workspace);
 }
 
@@ -181,14 +182,17 @@ struct Grid {
 struct PinnedHost {
     uint8_t *p = nullptr;
     size_t cap = 0;
+    // grows by half again at least: page-locked allocation is slow and freeing
+    // synchronises the device, and the staged sizes creep up from regrid to regrid
     void ensure(size_t n)
     {
         if (n <= cap) return;
         if (p) cudaFreeHost(p);
         p = nullptr;
         cap = 0;
-        CK(cudaMallocHost((void **)&p, n));
-        cap = n;
+        const size_t nc = std::max(n, cap + cap / 2);
+        CK(cudaMallocHost((void **)&p, nc));
+        cap = nc;
     }
     ~PinnedHost()
     {
@@ -830,14 +834,13 @@ struct tsu_ctx {
                 const size_t h = bb[4 * q + 2] >= 0 ? (size_t)(bb[4 * q + 3] - bb[4 * q + 1] + 1) : 0;
                 hoff[q + 1] = hoff[q] + w * h;
             }
-            hflags.ensure(2 * std::max<size_t>(hoff[np], 1));
-            uint8_t *hF = hflags.p, *hN = hflags.p + hoff[np];
+            hflags.ensure(std::max<size_t>(hoff[np], 1));
+            uint8_t *hFN = hflags.p;   // bit 0 flag, bit 1 nestable (the nesting kernel's plane)
             for (int q = 0; q < np; q++) {
                 if (bb[4 * q + 2] < 0) continue;
                 const size_t w = bb[4 * q + 2] - bb[4 * q] + 1, h = bb[4 * q + 3] - bb[4 * q + 1] + 1;
                 const size_t src = plane * q + (size_t)bb[4 * q + 1] * nx + bb[4 * q];
-                CK(cudaMemcpy2DAsync(hF + hoff[q], w, fF.p + src, nx, w, h, cudaMemcpyDeviceToHost, st));
-                CK(cudaMemcpy2DAsync(hN + hoff[q], w, fN.p + src, nx, w, h, cudaMemcpyDeviceToHost, st));
+                CK(cudaMemcpy2DAsync(hFN + hoff[q], w, fN.p + src, nx, w, h, cudaMemcpyDeviceToHost, st));
             }
             sync();
             const auto t_c0 = std::chrono::steady_clock::now();
@@ -845,7 +848,7 @@ struct tsu_ctx {
                 const int q = slot[s];
                 if (bb[4 * q + 2] < 0) return;
                 const int w = bb[4 * q + 2] - bb[4 * q] + 1, h = bb[4 * q + 3] - bb[4 * q + 1] + 1;
-                cluster_boxes(hF + hoff[q], hN + hoff[q], w, h, c.cluster_eff, r, c.patch_max, boxes[s], threads, ws);
+                cluster_boxes(hFN + hoff[q], w, h, c.cluster_eff, r, c.patch_max, boxes[s], threads, ws);
                 for (auto &b : boxes[s]) { b[0] += bb[4 * q]; b[1] += bb[4 * q + 1]; }
             };
             if (which.size() == 1) {
@@ -2278,13 +2281,12 @@ int tsu_cluster_flags(const unsigned char *flags, const unsigned char *nestable,
     try {
         if (!flags || !boxes || !n_boxes || nx < 1 || ny < 1 || ratio < 1 || patch_max < 1 || max_boxes < 0)
             return TSU_ERR_ARG;
-        std::vector<uint8_t> ones;
-        if (!nestable) {
-            ones.assign((size_t)nx * ny, 1);
-            nestable = ones.data();
-        }
+        // one plane, bit 0 the flag and bit 1 nestable: what the regrid clusters
+        std::vector<uint8_t> fn((size_t)nx * ny);
+        for (size_t k = 0; k < fn.size(); k++)
+            fn[k] = (uint8_t)((flags[k] ? 1 : 0) | ((!nestable || nestable[k]) ? 2 : 0));
         std::vector<std::array<int, 4>> out;
-        tsu::cluster_boxes(flags, nestable, nx, ny, eff, ratio, patch_max, out, 16, nullptr);
+        tsu::cluster_boxes(fn.data(), nx, ny, eff, ratio, patch_max, out, 16, nullptr);
         *n_boxes = (int)out.size();
         if ((int)out.size() > max_boxes) return TSU_ERR_ARG;
         for (size_t k = 0; k < out.size(); k++)

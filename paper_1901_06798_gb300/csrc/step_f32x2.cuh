@@ -93,6 +93,20 @@ __device__ __forceinline__ void derive(C2 &z, float sqrtg, float drytol)
     z.c = mul(f2(sqrtg), z.sq);
 }
 
+// derive() for one cell, operation for operation the same as one lane of it
+__device__ __forceinline__ void derive1(float q0, float hn, float ht, float B, float sqrtg, float drytol,
+                                        Cell<float> &o)
+{
+    o.q0 = q0; o.hn = hn; o.ht = ht; o.B = B;
+    o.h = fmaf(B, -1.0f, q0);
+    o.wet = o.h >= drytol;
+    const float rh = o.wet ? __fdividef(1.0f, o.h) : 0.0f;
+    o.u = hn * rh;
+    o.v = ht * rh;
+    o.sq = sqrtf(o.wet ? o.h : 0.0f);
+    o.c = sqrtg * o.sq;
+}
+
 __device__ __forceinline__ void lane_in(const C2 &z, int l, Cell<float> &o)
 {
     o.q0 = l ? z.q0.y : z.q0.x; o.hn = l ? z.hn.y : z.hn.x; o.ht = l ? z.ht.y : z.ht.x; o.B = l ? z.B.y : z.B.x;
@@ -100,68 +114,61 @@ __device__ __forceinline__ void lane_in(const C2 &z, int l, Cell<float> &o)
     o.sq = l ? z.sq.y : z.sq.x; o.wet = l ? z.wy : z.wx;
 }
 
-__device__ __forceinline__ void riemann2_general(float g, const C2 &L, const C2 &R, W2 &r);
-
-// Riemann problems of two edges (L[i] | R[i]) for lanes i = x, y: the
-// wet-wet short branch, paired, kept when both lanes are subsonic
-// (s1 < 0 < s3) and the middle depths either side of the bed step with the
-// still-water jump, hL + W1 and hR - W3, are positive (the depth bound is not
-// needed); otherwise the general solver lane by lane
-__device__ __forceinline__ void riemann2(float g, const C2 &L, const C2 &R, W2 &r)
+// the general solver on lane l (0: x, 1: y) of two edges, into that lane of r
+__device__ __forceinline__ void riemann2_lane(float g, const C2 &L, const C2 &R, int l, W2 &r)
 {
-    if (L.wx && R.wx && L.wy && R.wy) {
-        const float2 num = fma(L.sq, L.u, mul(R.sq, R.u));
-        const float2 uhat = mul(num, rcp(add(L.sq, R.sq)));
-        const float2 hbar = mul(f2(0.5f), add(L.h, R.h));
-        const float2 ghb = mul(f2(g), hbar);
-        const float2 chat = sqrt2(ghb);
-        const float2 s1 = fmin2(sub(L.u, L.c), sub(uhat, chat));
-        const float2 s3 = fmax2(add(R.u, R.c), add(uhat, chat));
-        const float2 d1 = sub(R.q0, L.q0);
-        const float2 d2 = sub(R.hn, L.hn);
-        const float2 d3 = fma(ghb, d1, sub(mul(R.hn, R.u), mul(L.hn, L.u)));
-        const float2 d4 = sub(mul(R.hn, R.v), mul(L.hn, L.v));
-        const float2 rden = rcp(sub(s3, s1));
-        const float2 w1m = mul(sub(mul(s3, d1), d2), rden);
-        const float2 w1n = mul(sub(mul(s3, d2), d3), rden);
-        const float2 w3m = sub(d1, w1m);
-        const float2 hl = add(L.h, w1m), hr = sub(R.h, w3m);
-        const float lo = fminf(fminf(fminf(hl.x, hl.y), fminf(hr.x, hr.y)),
-                               fminf(fminf(-s1.x, -s1.y), fminf(s3.x, s3.y)));
-        if (lo > 0.0f) {
-            r.z0m = mul(s1, w1m); r.z0n = mul(s1, w1n); r.z0t = mul(r.z0m, L.v);
-            r.z2m = mul(s3, w3m); r.z2n = mul(s3, sub(d2, w1n)); r.z2t = mul(r.z2m, R.v);
-            r.z1t = sub(sub(d4, r.z0t), r.z2t);
-            r.s0 = s1; r.s1 = uhat; r.s2 = s3;
-            r.wallx = 0; r.wally = 0;
-            return;
-        }
+    Cell<float> a, b;
+    lane_in(L, l, a);
+    lane_in(R, l, b);
+    Wave<float> w;
+    riemann<float, true>(g, a, b, w);
+    if (l == 0) {
+        r.z0m.x = w.Z[0][0]; r.z0n.x = w.Z[0][1]; r.z0t.x = w.Z[0][2]; r.z1t.x = w.Z[1][2];
+        r.z2m.x = w.Z[2][0]; r.z2n.x = w.Z[2][1]; r.z2t.x = w.Z[2][2];
+        r.s0.x = w.s[0]; r.s1.x = w.s[1]; r.s2.x = w.s[2];
+        r.wallx = w.wall;
+    } else {
+        r.z0m.y = w.Z[0][0]; r.z0n.y = w.Z[0][1]; r.z0t.y = w.Z[0][2]; r.z1t.y = w.Z[1][2];
+        r.z2m.y = w.Z[2][0]; r.z2n.y = w.Z[2][1]; r.z2t.y = w.Z[2][2];
+        r.s0.y = w.s[0]; r.s1.y = w.s[1]; r.s2.y = w.s[2];
+        r.wally = w.wall;
     }
-    riemann2_general(g, L, R, r);
 }
 
-__device__ __forceinline__ void riemann2_general(float g, const C2 &L, const C2 &R, W2 &r)
+// Riemann problems of two edges (L[i] | R[i]) for lanes i = x, y.  The
+// wet-wet short branch runs paired on both lanes; a lane keeps its result
+// when both its cells are wet, it is subsonic (s1 < 0 < s3) and the middle
+// depths either side of the bed step with the still-water jump, hL + W1 and
+// hR - W3, are positive (the depth bound is not needed).  Any other lane is
+// solved again by the general solver.  The choice is made per edge, so an
+// edge's waves do not depend on which edge shares its pair.
+__device__ __forceinline__ void riemann2(float g, const C2 &L, const C2 &R, W2 &r)
 {
-    float o[2][10];
-    int wl[2];
-#pragma unroll
-    for (int l = 0; l < 2; l++) {
-        Cell<float> a, b;
-        lane_in(L, l, a);
-        lane_in(R, l, b);
-        Wave<float> w;
-        riemann<float, true>(g, a, b, w);
-        o[l][0] = w.Z[0][0]; o[l][1] = w.Z[0][1]; o[l][2] = w.Z[0][2]; o[l][3] = w.Z[1][2];
-        o[l][4] = w.Z[2][0]; o[l][5] = w.Z[2][1]; o[l][6] = w.Z[2][2];
-        o[l][7] = w.s[0]; o[l][8] = w.s[1]; o[l][9] = w.s[2];
-        wl[l] = w.wall;
-    }
-    r.z0m = make_float2(o[0][0], o[1][0]); r.z0n = make_float2(o[0][1], o[1][1]);
-    r.z0t = make_float2(o[0][2], o[1][2]); r.z1t = make_float2(o[0][3], o[1][3]);
-    r.z2m = make_float2(o[0][4], o[1][4]); r.z2n = make_float2(o[0][5], o[1][5]);
-    r.z2t = make_float2(o[0][6], o[1][6]);
-    r.s0 = make_float2(o[0][7], o[1][7]); r.s1 = make_float2(o[0][8], o[1][8]); r.s2 = make_float2(o[0][9], o[1][9]);
-    r.wallx = wl[0]; r.wally = wl[1];
+    const float2 num = fma(L.sq, L.u, mul(R.sq, R.u));
+    const float2 uhat = mul(num, rcp(add(L.sq, R.sq)));
+    const float2 hbar = mul(f2(0.5f), add(L.h, R.h));
+    const float2 ghb = mul(f2(g), hbar);
+    const float2 chat = sqrt2(ghb);
+    const float2 s1 = fmin2(sub(L.u, L.c), sub(uhat, chat));
+    const float2 s3 = fmax2(add(R.u, R.c), add(uhat, chat));
+    const float2 d1 = sub(R.q0, L.q0);
+    const float2 d2 = sub(R.hn, L.hn);
+    const float2 d3 = fma(ghb, d1, sub(mul(R.hn, R.u), mul(L.hn, L.u)));
+    const float2 d4 = sub(mul(R.hn, R.v), mul(L.hn, L.v));
+    const float2 rden = rcp(sub(s3, s1));
+    const float2 w1m = mul(sub(mul(s3, d1), d2), rden);
+    const float2 w1n = mul(sub(mul(s3, d2), d3), rden);
+    const float2 w3m = sub(d1, w1m);
+    const float2 hl = add(L.h, w1m), hr = sub(R.h, w3m);
+    const bool okx = L.wx && R.wx && fminf(fminf(hl.x, hr.x), fminf(-s1.x, s3.x)) > 0.0f;
+    const bool oky = L.wy && R.wy && fminf(fminf(hl.y, hr.y), fminf(-s1.y, s3.y)) > 0.0f;
+    r.z0m = mul(s1, w1m); r.z0n = mul(s1, w1n); r.z0t = mul(r.z0m, L.v);
+    r.z2m = mul(s3, w3m); r.z2n = mul(s3, sub(d2, w1n)); r.z2t = mul(r.z2m, R.v);
+    r.z1t = sub(sub(d4, r.z0t), r.z2t);
+    r.s0 = s1; r.s1 = uhat; r.s2 = s3;
+    r.wallx = 0; r.wally = 0;
+    if (!okx) riemann2_lane(g, L, R, 0, r);
+    if (!oky) riemann2_lane(g, L, R, 1, r);
 }
 
 __device__ __forceinline__ float sgnf(float s) { return s > 0.0f ? 1.0f : (s < 0.0f ? -1.0f : 0.0f); }
@@ -338,20 +345,19 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
     const long long go[3] = {0, fs, 2 * fs};
 
     // y sweep state of the two columns (y roles: hn = hv, ht = hu): Q* cells of
-    // rows r-2, r-1, the waves of y-edges r-2, r-1 and the limited A+dQ, F~ of
-    // y-edge r-2
+    // rows r-2, r-1, the waves of y-edges r-2, r-1 and A+dQ - F~ of y-edge r-2
     C2 yq2, yq1, yq0;
     W2 ywo, ywm, ywn;
-    float2 yao[3], yfo[3], yam1[3], yfm1[3];
+    float2 yDo[3], yDm[3];
 #pragma unroll
-    for (int m = 0; m < 3; m++) { yao[m] = f2(0.0f); yfo[m] = f2(0.0f); yam1[m] = f2(0.0f); yfm1[m] = f2(0.0f); }
+    for (int m = 0; m < 3; m++) { yDo[m] = f2(0.0f); yDm[m] = f2(0.0f); }
     float smx = 0.0f, smy = 0.0f;
 
     // ring row k: ycm2, ycm1, ycur = Q* cells of rows r-2, r-1, r; wo, wm, wn =
-    // waves of y-edges r-2, r-1, r; apo, Fo = A+dQ, F~ of y-edge r-2; apm, Fm
-    // receive those of y-edge r-1
+    // waves of y-edges r-2, r-1, r; Do = A+dQ - F~ of y-edge r-2; Dm receives
+    // that of y-edge r-1
     auto row = [&](const int k, const C2 &ycm2, const C2 &ycm1, C2 &ycur, const W2 &wo, const W2 &wm, W2 &wn,
-                   const float2 (&apo)[3], const float2 (&Fo)[3], float2 (&apm)[3], float2 (&Fm)[3]) {
+                   const float2 (&Do)[3], float2 (&Dm)[3]) {
         prefetch(k + RING - 1);
         cp_async_wait<RING - 2>();
         __syncthreads();
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
                         I.m2 = make_float2(a2 ? wo.z2m.x : wn.z2m.x, b2 ? wo.z2m.y : wn.z2m.y);
                         I.n2 = make_float2(a2 ? wo.z2n.x : wn.z2n.x, b2 ? wo.z2n.y : wn.z2n.y);
                         I.t2 = make_float2(a2 ? wo.z2t.x : wn.z2t.x, b2 ? wo.z2t.y : wn.z2t.y);
-                        float2 yam[3];
+                        float2 yam[3], yap[3], yF[3], S[3];
                         float2 dtdye = dtdy2;
                         float cr = 1.0f, ce = 1.0f;
                         if (GEO) {
@@ -447,25 +453,27 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
                             cr = ce / (0.5f * (kapP[e - 1] + kapP[e]));
                             dtdye = f2(dtdy * cr);
                         }
-                        limit2(wm, I, dtdye, yam, apm, Fm);
+                        limit2(wm, I, dtdye, yam, yap, yF);
                         if (outx) smy = fmaxf(smy, fmaxf(-wm.s0.x, wm.s2.x) * cr);
                         if (outy) smy = fmaxf(smy, fmaxf(-wm.s0.y, wm.s2.y) * cr);
                         if (GEO) {
                             const float2 ce2 = f2(ce);
 #pragma unroll
-                            for (int m = 0; m < 3; m++) { yam[m] = mul(ce2, yam[m]); apm[m] = mul(ce2, apm[m]); Fm[m] = mul(ce2, Fm[m]); }
+                            for (int m = 0; m < 3; m++) { yam[m] = mul(ce2, yam[m]); yap[m] = mul(ce2, yap[m]); yF[m] = mul(ce2, yF[m]); }
                         }
+#pragma unroll
+                        for (int m = 0; m < 3; m++) { S[m] = add(yam[m], yF[m]); Dm[m] = sub(yap[m], yF[m]); }
                         const int rc = r - 2;
                         if (rc >= y0 && rc < y0 + h) {
-                            // cell row r-2: y-edges r-2 (A+dQ, F~ from the last row) and r-1
-                            float2 dtk = dtdy2, m0 = add(add(apo[0], yam[0]), sub(Fm[0], Fo[0]));
+                            // cell row r-2: (A+dQ - F~) of y-edge r-2 plus (A-dQ + F~) of y-edge r-1
+                            float2 dtk = dtdy2, m0 = add(Do[0], S[0]);
                             if (GEO) {
                                 dtk = f2(dtdy / kapP[rc]);
                                 m0 = fma(f2(ce - cedP[rc]), ycm2.hn, m0);   // divergence of the edge length
                             }
                             float2 n0 = fnma(dtk, m0, ycm2.q0);
-                            float2 n1 = fnma(dtk, add(add(apo[1], yam[1]), sub(Fm[1], Fo[1])), ycm2.hn);
-                            float2 n2 = fnma(dtk, add(add(apo[2], yam[2]), sub(Fm[2], Fo[2])), ycm2.ht);
+                            float2 n1 = fnma(dtk, add(Do[1], S[1]), ycm2.hn);
+                            float2 n2 = fnma(dtk, add(Do[2], S[2]), ycm2.ht);
                             post2(n0, n1, n2, ycm2.B, drytol);
                             if (a.manningf > 0.0f)   // y frame: n2 = hu, n1 = hv
                                 friction2(n0, n2, n1, ycm2.B, drytol, a.manningf, dt1 * a.rR);
@@ -489,11 +497,11 @@ __global__ void __launch_bounds__(NT, (12 * 32) / NT) step_kernel_f32x2(StepArgs
     };
 
     for (int k = 0; k < nrows; k++) {
-        row(k, yq2, yq1, yq0, ywo, ywm, ywn, yao, yfo, yam1, yfm1);
+        row(k, yq2, yq1, yq0, ywo, ywm, ywn, yDo, yDm);
         yq2 = yq1; yq1 = yq0;
         ywo = ywm; ywm = ywn;
 #pragma unroll
-        for (int m = 0; m < 3; m++) { yao[m] = yam1[m]; yfo[m] = yfm1[m]; }
+        for (int m = 0; m < 3; m++) yDo[m] = yDm[m];
     }
     cp_async_wait<0>();
 

@@ -196,23 +196,43 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
     }
 }
 
-// threads per CTA of the y kernel: one warp, two columns per thread
-constexpr int kSplitYThreads = 32;
-constexpr int kSplitYRing = 4;   // rows in flight per thread
+// threads per CTA of the y kernel: two warps, one column per thread
+constexpr int kSplitYThreads = 64;
+constexpr int kSplitYAhead = 2;              // row pairs in flight per thread
+constexpr int kSplitYRing = kSplitYAhead + 3;   // ring slots: pairs j - 2 .. j + 2
 
+// The y sweep pairs along the sweep: thread t owns column t of the strip and
+// takes two rows per iteration, so lane x of every float2 is an even ring row
+// (or the y-edge below it) and lane y the odd row above.  Ring row k = 0 ..
+// h + 3 is patch row y0 - 2 + k; y-edge k lies between ring rows k - 1 and k.
+// Iteration j (row pair j = ring rows 2j, 2j + 1):
+//   * solves the y-edge pair (2j, 2j + 1): left states (row 2j - 1, row 2j),
+//     right states the pair itself;
+//   * limits the edge pair (2j - 2, 2j - 1): the upwind neighbour of edge
+//     2j - 2 is edge 2j - 3 (the previous pair's lane y) or 2j - 1, that of
+//     edge 2j - 1 is edge 2j - 2 or 2j (this iteration's lane x);
+//   * updates the row pair (2j - 4, 2j - 3) from A+dQ - F~ of its lower edges
+//     (the edge pair 2j - 4, 2j - 3) and A-dQ + F~ of its upper edges (2j - 3,
+//     2j - 2).
+// The state carried from one iteration to the next is one cell (row 2j - 1),
+// one edge pair's waves plus one edge's, and the limited terms of one edge
+// pair; the row pair being updated is read back from the ring, which keeps
+// the two pairs before the current one.
 template <bool GEO>
 __global__ void __launch_bounds__(kSplitYThreads) step_y_f32x2(StepArgs a)
 {
     using namespace x2;
-    constexpr int NT = kSplitYThreads, YRING = kSplitYRing;
-    // ring[slot][field][2 t .. 2 t + 1]: fields Q* eta', hu, hv and B; thread t
-    // only ever reads its own two columns, so its cp.async waits suffice
-    __shared__ __align__(16) float ring[YRING][4][2 * NT];
+    constexpr int NT = kSplitYThreads, YRING = kSplitYRing, AHEAD = kSplitYAhead;
+    // ring[slot][field][t] = rows 2i, 2i + 1 of column t: Q* eta', hu, hv and B.
+    // Thread t only ever reads its own column, so its cp.async waits suffice.
+    __shared__ __align__(16) float2 ring[YRING][4][NT];
     const StepItem it = a.items_y[blockIdx.x];
-    if (it.w > 2 * NT || it.w < 1 || it.h < 1) return;   // uniform over the CTA
+    if (it.w > NT || it.w < 1 || it.h < 1) return;   // uniform over the CTA
     const PatchDesc P = a.descs[it.patch];
     if (a.gate != nullptr && a.gate[P.scen] == 0) return;   // not retaken (uniform over the CTA)
     const int t = threadIdx.x;
+    const bool valid = t < it.w;
+    const int tc = valid ? t : it.w - 1;   // threads past the strip repeat its last column and store nothing
     const int cur = a.cur;
     float *base = reinterpret_cast<float *>(a.arena) + P.off;
     const long long fs = P.fs;
@@ -227,133 +247,149 @@ __global__ void __launch_bounds__(kSplitYThreads) step_y_f32x2(StepArgs a)
     const float g = a.gf, drytol = a.drytolf, sqrtg = a.sqrtgf;
     const int y0 = it.y0, h = it.h;
     const int pitch = P.pitch;
-    const bool vx = 2 * t < it.w, vy = 2 * t + 1 < it.w;
-    const int col = it.x0 + 2 * t;
-    // patch row y0 - 2 + k of column col at storage [(y0 + k) * pitch + col + 2]
-    const long long cbase = (long long)y0 * pitch + (col + 2);
-    const bool w8 = vx && vy && ((reinterpret_cast<uintptr_t>(qs0 + cbase) & 7) == 0) &&
-                    ((reinterpret_cast<uintptr_t>(qo0 + cbase) & 7) == 0) && ((pitch & 1) == 0) && ((fs & 1) == 0);
-    const int nrows = h + 4;
-    const float *fsrc[4] = {qs0, qs0 + fs, qs0 + 2 * fs, Bg};
-    const int c0 = 2 * t;
-    auto prefetch = [&](int k) {
-        if (k < nrows) {
-            const int slot = k % YRING;
-            const long long o = cbase + (long long)k * pitch;
-            if (w8) {
+    // ring row k of this column at storage [(y0 + k) * pitch + x0 + tc + 2]
+    const long long cbase = (long long)y0 * pitch + (it.x0 + tc + 2);
+    const int klast = h + 3;
+    // interior rows are ring rows 2 .. h + 1; the last row pair holding one is
+    // updated at iteration (h + 1) / 2 + 2
+    const int niter = (h + 1) / 2 + 3;
+    const float *fsrc[4] = {qs0 + cbase, qs0 + fs + cbase, qs0 + 2 * fs + cbase, Bg + cbase};
+    auto prefetch = [&](int i) {
+        if (i < niter) {
+            const int slot = i % YRING;
+            // rows past the segment's last ring row repeat it (no waves between them)
+            const long long o0 = (long long)min(2 * i, klast) * pitch;
+            const long long o1 = (long long)min(2 * i + 1, klast) * pitch;
 #pragma unroll
-                for (int f = 0; f < 4; f++) cp_async_elem(&ring[slot][f][c0], fsrc[f] + o, 8);
-            } else {
-                if (vx) {
-#pragma unroll
-                    for (int f = 0; f < 4; f++) cp_async_elem(&ring[slot][f][c0], fsrc[f] + o, 4);
-                }
-                if (vy) {
-#pragma unroll
-                    for (int f = 0; f < 4; f++) cp_async_elem(&ring[slot][f][c0 + 1], fsrc[f] + o + 1, 4);
-                }
+            for (int f = 0; f < 4; f++) {
+                cp_async_elem(&ring[slot][f][t].x, fsrc[f] + o0, 4);
+                cp_async_elem(&ring[slot][f][t].y, fsrc[f] + o1, 4);
             }
         }
         cp_async_commit();
     };
 #pragma unroll
-    for (int k = 0; k < YRING - 1; k++) prefetch(k);
+    for (int i = 0; i < AHEAD; i++) prefetch(i);
 
-    C2 yq2, yq1, yq0;
-    W2 ywo, ywm, ywn;
-    float2 yao[3], yfo[3], yam1[3], yfm1[3];
-#pragma unroll
-    for (int m = 0; m < 3; m++) { yao[m] = f2(0.0f); yfo[m] = f2(0.0f); yam1[m] = f2(0.0f); yfm1[m] = f2(0.0f); }
+    Cell<float> pv;            // ring row 2j - 1: the lower cell of y-edge 2j
+    W2 wm;                     // waves of the edge pair (2j - 2, 2j - 1)
+    float wo[7];               // waves of edge 2j - 3 (lane y of the pair before)
+    float2 Dp[3];              // A+dQ - F~ of the edge pair (2j - 4, 2j - 3)
+    float Spy[3];              // A-dQ + F~ of edge 2j - 3
     float smy = 0.0f;
-
-    // row k: ycm2, ycm1, ycur = Q* cells of rows r-2, r-1, r; wo, wm, wn = waves of
-    // y-edges r-2, r-1, r; apo, Fo = A+dQ, F~ of y-edge r-2; apm, Fm receive those of r-1
-    auto row = [&](const int k, const C2 &ycm2, const C2 &ycm1, C2 &ycur, const W2 &wo, const W2 &wm, W2 &wn,
-                   const float2 (&apo)[3], const float2 (&Fo)[3], float2 (&apm)[3], float2 (&Fm)[3]) {
-        const int r = y0 - 2 + k;
-        prefetch(k + YRING - 1);
-        cp_async_wait<YRING - 1>();   // row k of this thread has landed
-        {
-            const int slot = k % YRING;
-            // lanes outside the strip read zeros: a dry cell whose results are not stored
-            ycur.q0 = vx ? ld2(&ring[slot][0][c0]) : f2(0.0f);
-            ycur.ht = vx ? ld2(&ring[slot][1][c0]) : f2(0.0f);
-            ycur.hn = vx ? ld2(&ring[slot][2][c0]) : f2(0.0f);
-            ycur.B = vx ? ld2(&ring[slot][3][c0]) : f2(0.0f);
-            if (!vy) { ycur.q0.y = 0.0f; ycur.ht.y = 0.0f; ycur.hn.y = 0.0f; ycur.B.y = 0.0f; }
-        }
-        derive(ycur, sqrtg, drytol);
-        if (k >= 1) {
-            riemann2(g, ycm1, ycur, wn);
-            if (k >= 3) {
-                const int e = r - 1;   // y0 <= e <= y0 + h
-                I2 I;
-                const bool a0 = wm.s0.x >= 0.0f, a1 = wm.s1.x >= 0.0f, a2 = wm.s2.x >= 0.0f;
-                const bool b0 = wm.s0.y >= 0.0f, b1 = wm.s1.y >= 0.0f, b2 = wm.s2.y >= 0.0f;
-                I.m0 = make_float2(a0 ? wo.z0m.x : wn.z0m.x, b0 ? wo.z0m.y : wn.z0m.y);
-                I.n0 = make_float2(a0 ? wo.z0n.x : wn.z0n.x, b0 ? wo.z0n.y : wn.z0n.y);
-                I.t0 = make_float2(a0 ? wo.z0t.x : wn.z0t.x, b0 ? wo.z0t.y : wn.z0t.y);
-                I.t1 = make_float2(a1 ? wo.z1t.x : wn.z1t.x, b1 ? wo.z1t.y : wn.z1t.y);
-                I.m2 = make_float2(a2 ? wo.z2m.x : wn.z2m.x, b2 ? wo.z2m.y : wn.z2m.y);
-                I.n2 = make_float2(a2 ? wo.z2n.x : wn.z2n.x, b2 ? wo.z2n.y : wn.z2n.y);
-                I.t2 = make_float2(a2 ? wo.z2t.x : wn.z2t.x, b2 ? wo.z2t.y : wn.z2t.y);
-                float2 yam[3];
-                float2 dtdye = dtdy2;
-                float cr = 1.0f, ce = 1.0f;
-                if (GEO) {
-                    ce = cedP[e];
-                    cr = ce / (0.5f * (kapP[e - 1] + kapP[e]));
-                    dtdye = f2(dtdy * cr);
-                }
-                limit2(wm, I, dtdye, yam, apm, Fm);
-                if (vx) smy = fmaxf(smy, fmaxf(-wm.s0.x, wm.s2.x) * cr);
-                if (vy) smy = fmaxf(smy, fmaxf(-wm.s0.y, wm.s2.y) * cr);
-                if (GEO) {
-                    const float2 ce2 = f2(ce);
 #pragma unroll
-                    for (int m = 0; m < 3; m++) { yam[m] = mul(ce2, yam[m]); apm[m] = mul(ce2, apm[m]); Fm[m] = mul(ce2, Fm[m]); }
+    for (int m = 0; m < 7; m++) wo[m] = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 3; m++) { Dp[m] = f2(0.0f); Spy[m] = 0.0f; }
+
+    for (int j = 0; j < niter; j++) {
+        prefetch(j + AHEAD);   // into the slot of row pair j - 3
+        cp_async_wait<AHEAD>();   // row pair j of this thread has landed
+        const int slot = j % YRING;
+        C2 cj;   // y roles: hn = hv, ht = hu
+        cj.q0 = ring[slot][0][t];
+        cj.ht = ring[slot][1][t];
+        cj.hn = ring[slot][2][t];
+        cj.B = ring[slot][3][t];
+        derive(cj, sqrtg, drytol);
+        if (j == 0) lane_in(cj, 0, pv);   // no row below ring row 0: repeat it (edge 0 is never used)
+
+        // ---- y-edges 2j (rows 2j - 1 | 2j) and 2j + 1 (rows 2j | 2j + 1)
+        C2 L;
+        L.q0 = make_float2(pv.q0, cj.q0.x); L.hn = make_float2(pv.hn, cj.hn.x);
+        L.ht = make_float2(pv.ht, cj.ht.x); L.B = make_float2(pv.B, cj.B.x);
+        L.h = make_float2(pv.h, cj.h.x); L.u = make_float2(pv.u, cj.u.x);
+        L.v = make_float2(pv.v, cj.v.x); L.c = make_float2(pv.c, cj.c.x);
+        L.sq = make_float2(pv.sq, cj.sq.x);
+        L.wx = pv.wet; L.wy = cj.wx;
+        W2 wn;
+        riemann2(g, L, cj, wn);
+
+        if (j >= 2) {
+            // ---- limit the edge pair (2j - 2, 2j - 1)
+            const int e0 = 2 * j - 2;   // ring index of lane x's edge
+            I2 I;
+            const bool a0 = wm.s0.x >= 0.0f, a1 = wm.s1.x >= 0.0f, a2 = wm.s2.x >= 0.0f;
+            const bool b0 = wm.s0.y >= 0.0f, b1 = wm.s1.y >= 0.0f, b2 = wm.s2.y >= 0.0f;
+            I.m0 = make_float2(a0 ? wo[0] : wm.z0m.y, b0 ? wm.z0m.x : wn.z0m.x);
+            I.n0 = make_float2(a0 ? wo[1] : wm.z0n.y, b0 ? wm.z0n.x : wn.z0n.x);
+            I.t0 = make_float2(a0 ? wo[2] : wm.z0t.y, b0 ? wm.z0t.x : wn.z0t.x);
+            I.t1 = make_float2(a1 ? wo[3] : wm.z1t.y, b1 ? wm.z1t.x : wn.z1t.x);
+            I.m2 = make_float2(a2 ? wo[4] : wm.z2m.y, b2 ? wm.z2m.x : wn.z2m.x);
+            I.n2 = make_float2(a2 ? wo[5] : wm.z2n.y, b2 ? wm.z2n.x : wn.z2n.x);
+            I.t2 = make_float2(a2 ? wo[6] : wm.z2t.y, b2 ? wm.z2t.x : wn.z2t.x);
+            float2 am[3], ap[3], F[3], S[3], D[3];
+            float2 dtdye = dtdy2, cr = f2(1.0f), ce = f2(1.0f);
+            if (GEO) {
+                // patch rows above the two edges; an edge past the last one an
+                // interior row needs (ring edge h + 2) is not used: clamp it there
+                const int ea = min(y0 - 2 + e0, y0 + h), eb = min(y0 - 1 + e0, y0 + h);
+                ce = make_float2(cedP[ea], cedP[eb]);
+                cr = make_float2(ce.x / (0.5f * (kapP[ea - 1] + kapP[ea])), ce.y / (0.5f * (kapP[eb - 1] + kapP[eb])));
+                dtdye = make_float2(dtdy * cr.x, dtdy * cr.y);
+            }
+            limit2(wm, I, dtdye, am, ap, F);
+            // speeds of the edges of interior rows: ring edges 2 .. h + 2
+            if (valid && e0 <= h + 2) smy = fmaxf(smy, fmaxf(-wm.s0.x, wm.s2.x) * cr.x);
+            if (valid && e0 + 1 <= h + 2) smy = fmaxf(smy, fmaxf(-wm.s0.y, wm.s2.y) * cr.y);
+            if (GEO) {
+#pragma unroll
+                for (int m = 0; m < 3; m++) { am[m] = mul(ce, am[m]); ap[m] = mul(ce, ap[m]); F[m] = mul(ce, F[m]); }
+            }
+#pragma unroll
+            for (int m = 0; m < 3; m++) { S[m] = add(am[m], F[m]); D[m] = sub(ap[m], F[m]); }
+
+            if (j >= 3) {
+                // ---- rows 2j - 4 (lane x) and 2j - 3 (lane y)
+                const int kx = 2 * j - 4;
+                const int s2 = (j - 2) % YRING;
+                const float2 q0 = ring[s2][0][t], qt = ring[s2][1][t], qn = ring[s2][2][t], qB = ring[s2][3][t];
+                float2 dtk = dtdy2;
+                float2 m0 = add(Dp[0], make_float2(Spy[0], S[0].x));
+                if (GEO) {
+                    const int rc = y0 - 2 + kx;
+                    dtk = make_float2(dtdy / kapP[rc], dtdy / kapP[rc + 1]);
+                    // divergence of the edge length
+                    m0 = fma(make_float2(cedP[rc + 1] - cedP[rc], cedP[rc + 2] - cedP[rc + 1]), qn, m0);
                 }
-                const int rc = r - 2;
-                if (rc >= y0) {   // rc < y0 + h always
-                    // cell row r-2: y-edges r-2 (A+dQ, F~ from the last row) and r-1
-                    float2 dtk = dtdy2, m0 = add(add(apo[0], yam[0]), sub(Fm[0], Fo[0]));
-                    if (GEO) {
-                        dtk = f2(dtdy / kapP[rc]);
-                        m0 = fma(f2(ce - cedP[rc]), ycm2.hn, m0);   // divergence of the edge length
-                    }
-                    float2 n0 = fnma(dtk, m0, ycm2.q0);
-                    float2 n1 = fnma(dtk, add(add(apo[1], yam[1]), sub(Fm[1], Fo[1])), ycm2.hn);
-                    float2 n2 = fnma(dtk, add(add(apo[2], yam[2]), sub(Fm[2], Fo[2])), ycm2.ht);
-                    post2(n0, n1, n2, ycm2.B, drytol);
-                    if (a.manningf > 0.0f)   // y frame: n2 = hu, n1 = hv
-                        friction2(n0, n2, n1, ycm2.B, drytol, a.manningf, dt1 * a.rR);
-                    // a surface that is not a finite number reaches the host as an infinite speed
-                    if ((vx && !(fabsf(n0.x) < 1e30f)) || (vy && !(fabsf(n0.y) < 1e30f))) smy = INFINITY;
-                    float *d = qo0 + cbase + (long long)(k - 2) * pitch;
-                    if (w8) {
-                        st2(d, n0); st2(d + 2 * fs, n1); st2(d + fs, n2);
-                    } else {
-                        if (vx) { d[0] = n0.x; d[2 * fs] = n1.x; d[fs] = n2.x; }
-                        if (vy) { d[1] = n0.y; d[2 * fs + 1] = n1.y; d[fs + 1] = n2.y; }
-                    }
+                float2 n0 = fnma(dtk, m0, q0);
+                float2 n1 = fnma(dtk, add(Dp[1], make_float2(Spy[1], S[1].x)), qn);
+                float2 n2 = fnma(dtk, add(Dp[2], make_float2(Spy[2], S[2].x)), qt);
+                post2(n0, n1, n2, qB, drytol);
+                if (a.manningf > 0.0f)   // y frame: n2 = hu, n1 = hv
+                    friction2(n0, n2, n1, qB, drytol, a.manningf, dt1 * a.rR);
+                const bool sy = kx + 1 <= h + 1;   // lane y's row is interior
+                // a surface that is not a finite number reaches the host as an infinite speed
+                if (valid && (!(fabsf(n0.x) < 1e30f) || (sy && !(fabsf(n0.y) < 1e30f)))) smy = INFINITY;
+                if (valid) {
+                    float *d = qo0 + cbase + (long long)kx * pitch;
+                    d[0] = n0.x; d[2 * fs] = n1.x; d[fs] = n2.x;
+                    if (sy) { d[pitch] = n0.y; d[2 * fs + pitch] = n1.y; d[fs + pitch] = n2.y; }
                 }
             }
-        }
-    };
-
-    for (int k = 0; k < nrows; k++) {
-        row(k, yq2, yq1, yq0, ywo, ywm, ywn, yao, yfo, yam1, yfm1);
-        yq2 = yq1; yq1 = yq0;
-        ywo = ywm; ywm = ywn;
 #pragma unroll
-        for (int m = 0; m < 3; m++) { yao[m] = yam1[m]; yfo[m] = yfm1[m]; }
+            for (int m = 0; m < 3; m++) { Dp[m] = D[m]; Spy[m] = S[m].y; }
+        }
+        // carry: waves and the upper cell
+        wo[0] = wm.z0m.y; wo[1] = wm.z0n.y; wo[2] = wm.z0t.y; wo[3] = wm.z1t.y;
+        wo[4] = wm.z2m.y; wo[5] = wm.z2n.y; wo[6] = wm.z2t.y;
+        wm = wn;
+        lane_in(cj, 1, pv);
     }
     cp_async_wait<0>();
 
     if (!(smy > 0.0f)) smy = 0.0f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) smy = fmaxf(smy, __shfl_xor_sync(0xffffffffu, smy, o));
-    if (t == 0) atomic_max_speed(a.smax + 2 * P.scen + 1, (double)smy);
+    __shared__ float red[NT / 32];
+    if ((t & 31) == 0) red[t >> 5] = smy;
+    __syncthreads();
+    if (t == 0) {
+        float my = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NT / 32; q++) my = fmaxf(my, red[q]);
+        atomic_max_speed(a.smax + 2 * P.scen + 1, (double)my);
+    }
 }
 
 }  // namespace tsu

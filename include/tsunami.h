@@ -26,7 +26,9 @@
  * runtime error; the message names it), TSU_ERR_CFL (a level step ran with
  * Courant number above cfl_max; the step is kept and the run continues),
  * TSU_ERR_NESTING (an AMR invariant failed), TSU_ERR_OOM (device memory),
- * TSU_ERR_NOT_BUILT (the CUDA library is not loaded on a GPU).
+ * TSU_ERR_NOT_BUILT (the CUDA library is not loaded on a GPU), TSU_ERR_NAN (the
+ * state is no longer finite), TSU_ERR_TIMEOUT (a kernel's bounded wait on the
+ * device gave up).
  */
 #ifndef TSUNAMI_H
 #define TSUNAMI_H
@@ -48,8 +50,11 @@ enum {
     TSU_ERR_NESTING = -4,
     TSU_ERR_OOM = -5,
     TSU_ERR_NOT_BUILT = -6,
-    TSU_ERR_NAN = -7            /* a wave speed or a cell's depth (surface) is not a finite number: the run
+    TSU_ERR_NAN = -7,           /* a wave speed or a cell's depth (surface) is not a finite number: the run
                                    has blown up; the context keeps returning this code */
+    TSU_ERR_TIMEOUT = -8        /* a kernel gave up waiting on the device (a row's bulk copy into shared
+                                   memory did not complete within the poll budget of tsu_set_bulk_copies):
+                                   that step's state is not valid; the context keeps returning this code */
 };
 
 enum { TSU_F64 = 0, TSU_F32P = 1 };              /* precision of the state */
@@ -171,6 +176,7 @@ int tsu_init(tsu_ctx *ctx);
  * receives n_scenarios doubles: the simulated time of each scenario.
  * Returns TSU_ERR_CFL if a kept level step exceeded cfl_max (the work is done;
  * see cfl_retake), TSU_ERR_NAN if a speed or a depth is not a finite number,
+ * TSU_ERR_TIMEOUT if a kernel gave up waiting (tsu_set_bulk_copies),
  * TSU_ERR_ARG after tsu_step_level left a coarse step unfinished. */
 int tsu_step(tsu_ctx *ctx, int n_coarse_steps, double *t_out);
 
@@ -250,6 +256,19 @@ int tsu_get_stats(tsu_ctx *ctx, int scenario, tsu_stats *out);
  * always takes strips of 64 columns and 32 rows.  0 restores the defaults.
  * Results do not depend on either.  Returns TSU_ERR_ARG for any other value. */
 int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows);
+
+/* How the FP32 split update's x-sweep kernel brings rows into shared memory.
+ * enable = 0 (the default): every thread copies its own columns with
+ * cp.async.  enable = 1: one thread copies each field's row segment with a
+ * bulk copy (cp.async.bulk) that completes on an mbarrier, and every thread
+ * polls that barrier at most `polls` times before it gives up (2^22 is far
+ * above what a copy takes).  A wait that runs out stops the work item's
+ * further copies, waits for those in flight, and makes tsu_step return
+ * TSU_ERR_TIMEOUT; polls = 0 gives up at the first wait (a test of that path;
+ * no GPU fault is involved).  Results are the same bits either way; the bulk
+ * copies measured slower on GB300.  Errors: TSU_ERR_ARG for enable not 0 or 1
+ * or polls outside [0, 2^32 - 1]. */
+int tsu_set_bulk_copies(tsu_ctx *ctx, int enable, long long polls);
 
 /* Autotuner: time every launch shape of the patch update (threads per CTA
  * 64/128/256, and 32 for the split FP32 update, x rows per work item

@@ -22,6 +22,7 @@ MAX_LEVELS = 8
 MAX_REGIONS = 8
 TSU_OK, TSU_ERR_ARG, TSU_ERR_CUDA, TSU_ERR_CFL, TSU_ERR_NESTING, TSU_ERR_OOM, TSU_ERR_NOT_BUILT = 0, -1, -2, -3, -4, -5, -6
 TSU_ERR_NAN = -7
+TSU_ERR_TIMEOUT = -8
 TSU_F64, TSU_F32P = 0, 1
 FIELDS = {"h": 0, "hu": 1, "hv": 2, "eta": 3, "zeta": 4, "B": 5}
 
@@ -33,7 +34,7 @@ SYMBOLS = ["tsu_create", "tsu_destroy", "tsu_last_error", "tsu_add_topo", "tsu_s
            "tsu_grid_step_noalloc", "tsu_autotune", "tsu_cnn_num_params", "tsu_cnn_forward",
            "tsu_cnn_loss_grad", "tsu_cnn_train", "tsu_cnn_set_weights", "tsu_cnn_features", "tsu_cluster_flags", "tsu_set_velocity",
            "tsu_checkpoint_save", "tsu_checkpoint_restore", "tsu_profile_levels", "tsu_level_update_times",
-           "tsu_halo_pack", "tsu_halo_unpack"]
+           "tsu_halo_pack", "tsu_halo_unpack", "tsu_set_bulk_copies"]
 
 
 class tsu_config(C.Structure):
@@ -102,6 +103,7 @@ def load(path: str = LIB_PATH):
         "tsu_level1_buffers": ([P, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(P), ip], I),
         "tsu_time_level1_steps": ([P, I, I, dp, dp], I),
         "tsu_set_tuning": ([P, I, I], I),
+        "tsu_set_bulk_copies": ([P, I, C.c_longlong], I),
         "tsu_autotune": ([P, I, ip, ip, dp], I),
         "tsu_cnn_num_params": ([], I),
         "tsu_cluster_flags": ([P, P, I, I, D, I, I, ip, I, ip], I),
@@ -351,6 +353,10 @@ class Tsunami:
 
     def set_tuning(self, step_threads: int = 0, seg_rows: int = 0):
         self._check(self._L.tsu_set_tuning(self._h, step_threads, seg_rows), "tsu_set_tuning")
+
+    def set_bulk_copies(self, enable: int, polls: int = 1 << 22):
+        """x-sweep rows by bulk copies on mbarriers, each wait at most `polls` polls (0: give up at once)."""
+        self._check(self._L.tsu_set_bulk_copies(self._h, enable, C.c_longlong(polls)), "tsu_set_bulk_copies")
 
     def autotune(self, reps: int = 3):
         """Pick the fastest launch shape of the patch update; returns (threads, seg_rows, ms)."""

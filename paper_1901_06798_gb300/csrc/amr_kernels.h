@@ -35,9 +35,6 @@ struct CtrlView {
     int max_levels;
 };
 
-// device error flag bits: 1, 2, 4 a ghost, coarse or parent cell without a
-// covering patch (nesting); 8 a non-finite wave speed or depth
-enum { TSU_DEV_ERR_NESTING = 7, TSU_DEV_ERR_NAN = 8 };
 
 struct TopoDev {
     int nx, ny;

@@ -21,12 +21,22 @@ int launch_step_f32p(const StepArgs &a, int n_items, int threads, cudaStream_t s
     if (a.scratch != nullptr) {
         // x sweep over a.items (strips of 2 threads - 4 columns), then y sweep over a.items_y
         const bool geo = a.kap != nullptr;
-        switch (threads) {
-        case 32: geo ? step_x_f32x2<32, 4, true><<<n_items, 32, 0, st>>>(a) : step_x_f32x2<32, 4, false><<<n_items, 32, 0, st>>>(a); break;
-        case 64: geo ? step_x_f32x2<64, 4, true><<<n_items, 64, 0, st>>>(a) : step_x_f32x2<64, 4, false><<<n_items, 64, 0, st>>>(a); break;
-        case 128: geo ? step_x_f32x2<128, 4, true><<<n_items, 128, 0, st>>>(a) : step_x_f32x2<128, 4, false><<<n_items, 128, 0, st>>>(a); break;
-        case 256: geo ? step_x_f32x2<256, 4, true><<<n_items, 256, 0, st>>>(a) : step_x_f32x2<256, 4, false><<<n_items, 256, 0, st>>>(a); break;
-        default: return (int)cudaErrorInvalidValue;
+        if (a.bulk_rows) {   // rows by bulk copies on mbarriers (Cartesian and latitude-longitude)
+            switch (threads) {
+            case 32: geo ? step_x_f32x2<32, 4, true, true><<<n_items, 32, 0, st>>>(a) : step_x_f32x2<32, 4, false, true><<<n_items, 32, 0, st>>>(a); break;
+            case 64: geo ? step_x_f32x2<64, 4, true, true><<<n_items, 64, 0, st>>>(a) : step_x_f32x2<64, 4, false, true><<<n_items, 64, 0, st>>>(a); break;
+            case 128: geo ? step_x_f32x2<128, 4, true, true><<<n_items, 128, 0, st>>>(a) : step_x_f32x2<128, 4, false, true><<<n_items, 128, 0, st>>>(a); break;
+            case 256: geo ? step_x_f32x2<256, 4, true, true><<<n_items, 256, 0, st>>>(a) : step_x_f32x2<256, 4, false, true><<<n_items, 256, 0, st>>>(a); break;
+            default: return (int)cudaErrorInvalidValue;
+            }
+        } else {
+            switch (threads) {
+            case 32: geo ? step_x_f32x2<32, 4, true><<<n_items, 32, 0, st>>>(a) : step_x_f32x2<32, 4, false><<<n_items, 32, 0, st>>>(a); break;
+            case 64: geo ? step_x_f32x2<64, 4, true><<<n_items, 64, 0, st>>>(a) : step_x_f32x2<64, 4, false><<<n_items, 64, 0, st>>>(a); break;
+            case 128: geo ? step_x_f32x2<128, 4, true><<<n_items, 128, 0, st>>>(a) : step_x_f32x2<128, 4, false><<<n_items, 128, 0, st>>>(a); break;
+            case 256: geo ? step_x_f32x2<256, 4, true><<<n_items, 256, 0, st>>>(a) : step_x_f32x2<256, 4, false><<<n_items, 256, 0, st>>>(a); break;
+            default: return (int)cudaErrorInvalidValue;
+            }
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess || a.n_items_y <= 0) return (int)e;

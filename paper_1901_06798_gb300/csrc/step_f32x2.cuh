@@ -93,20 +93,6 @@ __device__ __forceinline__ void derive(C2 &z, float sqrtg, float drytol)
     z.c = mul(f2(sqrtg), z.sq);
 }
 
-// derive() for one cell, operation for operation the same as one lane of it
-__device__ __forceinline__ void derive1(float q0, float hn, float ht, float B, float sqrtg, float drytol,
-                                        Cell<float> &o)
-{
-    o.q0 = q0; o.hn = hn; o.ht = ht; o.B = B;
-    o.h = fmaf(B, -1.0f, q0);
-    o.wet = o.h >= drytol;
-    const float rh = o.wet ? __fdividef(1.0f, o.h) : 0.0f;
-    o.u = hn * rh;
-    o.v = ht * rh;
-    o.sq = sqrtf(o.wet ? o.h : 0.0f);
-    o.c = sqrtg * o.sq;
-}
-
 __device__ __forceinline__ void lane_in(const C2 &z, int l, Cell<float> &o)
 {
     o.q0 = l ? z.q0.y : z.q0.x; o.hn = l ? z.hn.y : z.hn.x; o.ht = l ? z.ht.y : z.ht.x; o.B = l ? z.B.y : z.B.x;

@@ -264,6 +264,48 @@ __device__ __forceinline__ void cp_async_elem(void *smem, const void *gmem, int 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// Bulk copies into shared memory completing on an mbarrier (one thread arms
+// the barrier with the bytes to expect and issues the copies; every consumer
+// polls the phase).  Waits are bounded: mbar_wait gives up after `polls` tests.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+// makes initialised barriers visible to the bulk copies (the async proxy)
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// bytes (a multiple of 16) from 16-byte aligned global src to 16-byte aligned shared dst
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity)
+{
+    unsigned r;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(r)
+                 : "r"(smem_u32(b)), "r"(parity)
+                 : "memory");
+    return r != 0;
+}
+// true once the phase of the given parity has completed; false if it has not
+// after `polls` tests
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, unsigned polls)
+{
+    for (unsigned i = 0; i < polls; i++)
+        if (mbar_test(b, parity)) return true;
+    return false;
+}
+// polls of the final wait for copies still in flight after a wait gave up
+constexpr unsigned kDrainPolls = 1u << 26;
+
 __device__ __forceinline__ void atomic_max_speed(unsigned long long *dst, double v)
 {
     atomicMax(dst, (unsigned long long)__double_as_longlong(v));

@@ -7,6 +7,11 @@
 //   the paired FP32 instructions, x-edge waves exchanged in shared memory.  A
 //   row needs no other row, so segments carry no halo rows.  It writes Q* of
 //   its interior columns and reduces the max x wave speed of interior rows.
+//   BULK: one thread copies each field's row segment into the ring with a bulk
+//   copy (cp.async.bulk) that completes on the slot's mbarrier, which every
+//   thread polls with a bounded budget (patch rows start 16-byte aligned, the
+//   pitch is a multiple of 4 floats and strips start at multiples of 4
+//   columns).  Measured slower than the per-thread copies; kept as an option.
 // step_y_f32x2: one CTA of 32 threads per strip of 64 columns (two per
 //   thread) and a segment of interior rows; reads Q* and B of the segment plus
 //   two rows above and below, runs the y sweep of its columns in registers
@@ -28,13 +33,15 @@
 
 namespace tsu {
 
-template <int NT, int RING, bool GEO>
+template <int NT, int RING, bool GEO, bool BULK = false>
 __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
 {
     using namespace x2;
     static_assert(RING >= 3, "the derived values of row k+1 need its copy complete at iteration k");
     constexpr int NC = 2 * NT;
     __shared__ __align__(16) float ring[RING][4][NC];
+    __shared__ __align__(8) unsigned long long rbar[BULK ? RING : 1];   // BULK: one barrier per ring slot
+    __shared__ int gave_up;           // BULK: a wait ran out of polls (no further copies)
     __shared__ float sDb[2][4][NT];   // derived u, v, c, sqrt(h) of cell 2t+1, by row parity
     __shared__ float sZx[7][NT];      // waves of edge 2t
     __shared__ float sZy[7][NT];      // waves of edge 2t+1
@@ -67,7 +74,36 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
     const float *src = qin0 + row0;
     const long long fo[4] = {0, fs, 2 * fs, (6 - cur * 3) * fs};   // q0, q1, q2, B relative to q0 of buffer cur
 
+    // BULK: a row copy is the strip's ncols floats rounded up to 16 bytes,
+    // which stays inside the row (x0 and the pitch are multiples of 4 floats)
+    const float *col0 = qin0 + (long long)(y0 + 2) * pitch + x0;
+    const unsigned nb = (unsigned)((ncols * 4 + 15) & ~15);
+    int issued = 0;   // BULK: rows issued (thread 0)
+    if (BULK) {
+        if (((reinterpret_cast<uintptr_t>(col0) & 15) != 0) || ((pitch & 3) != 0) || ((fs & 3) != 0)) {
+            if (t == 0 && a.err) atomicOr(a.err, TSU_DEV_ERR_LAYOUT);   // uniform over the CTA
+            return;
+        }
+        if (t == 0) {
+#pragma unroll
+            for (int q = 0; q < RING; q++) mbar_init(&rbar[q], 1);
+            gave_up = 0;
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
     auto prefetch = [&](int k) {
+        if (BULK) {
+            if (t == 0 && k < nrows && !*(volatile int *)&gave_up) {
+                const int slot = k % RING;
+                const float *s = col0 + (long long)k * pitch;
+                mbar_expect_tx(&rbar[slot], 4 * nb);
+#pragma unroll
+                for (int f = 0; f < 4; f++) bulk_g2s(&ring[slot][f][0], s + fo[f], nb, &rbar[slot]);
+                issued = k + 1;
+            }
+            return;
+        }
         if (k < nrows) {
             const int slot = k % RING;
             const float *s = src + (long long)k * pitch;
@@ -88,6 +124,17 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
         }
         cp_async_commit();
     };
+    // row k has landed (cp.async: this thread's copies of rows up to k); BULK:
+    // after one wait gives up, no thread waits again
+    auto await_row = [&](int k) {
+        if (BULK) {
+            if (k < nrows && !*(volatile int *)&gave_up &&
+                !mbar_wait(&rbar[k % RING], (unsigned)(k / RING) & 1u, a.wait_polls))
+                *(volatile int *)&gave_up = 1;
+        } else {
+            cp_async_wait<RING - 2>();
+        }
+    };
     auto own_cells = [&](int k, C2 &z) {
         const int slot = k % RING;
         z.q0 = ld2(&ring[slot][0][c0]); z.hn = ld2(&ring[slot][1][c0]);
@@ -99,7 +146,7 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
 #pragma unroll
     for (int k = 0; k < RING - 1; k++) prefetch(k);
     C2 xc;
-    cp_async_wait<RING - 2>();
+    await_row(0);
     own_cells(0, xc);
 
     const int tl = t > 0 ? t - 1 : 0, tr = t + 1 < NT ? t + 1 : NT - 1;
@@ -111,7 +158,7 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
 
     for (int k = 0; k < nrows; k++) {
         prefetch(k + RING - 1);
-        cp_async_wait<RING - 2>();
+        await_row(k + 1);
         __syncthreads();
         const int slot = k % RING;
         const int j = y0 + k;
@@ -182,7 +229,19 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
         }
         if (k + 1 < nrows) own_cells(k + 1, xc);
     }
-    cp_async_wait<0>();
+    if (BULK) {
+        // after a wait gave up, the copies still in flight land before the CTA
+        // exits: each slot's last issued row (a slot is armed again only after
+        // its previous phase completed); then the launch reports the timeout
+        __syncthreads();
+        if (t == 0 && gave_up) {
+            for (int r = issued - 1; r >= 0 && r >= issued - RING; r--)
+                mbar_wait(&rbar[r % RING], (unsigned)(r / RING) & 1u, kDrainPolls);
+            if (a.err) atomicOr(a.err, TSU_DEV_ERR_TIMEOUT);
+        }
+    } else {
+        cp_async_wait<0>();
+    }
 
     if (!(smx > 0.0f)) smx = 0.0f;
 #pragma unroll

@@ -321,6 +321,8 @@ struct tsu_ctx {
     long long n_regrids = 0;     // host-side regrid accounting (tsu_stats)
     double regrid_ms = 0.0, cluster_ms = 0.0, regrid_wait_ms = 0.0;
     long long n_patches_renewed = 0, n_patches_reused = 0;   // new patches at regrids, of which kept their block
+    int bulk_rows = 0;                // FP32 split update: x-sweep rows by bulk copies (tsu_set_bulk_copies)
+    unsigned wait_polls = 1u << 22;   // polls a kernel spends on one bulk copy before giving up
     int seg_rows = 0;  // rows per work item of the patch update (0: library default)
     int step_nt = 0;   // threads per CTA of the patch update (0: library default)
     DevBuf<double> zero_dt;
@@ -407,6 +409,9 @@ struct tsu_ctx {
             a.items_y = lv[l].dItemsY.p;
             a.n_items_y = (int)lv[l].items_y.size();
         }
+        a.err = derr.p;
+        a.bulk_rows = bulk_rows;
+        a.wait_polls = wait_polls;
     }
     const int *retake_gate() const { return retake.p; }
     // kernels one patch-update launch of level l runs
@@ -1255,6 +1260,9 @@ struct tsu_ctx {
         CK(cudaMemcpyAsync(v, viol.p, ns * sizeof(long long), cudaMemcpyDeviceToHost, st));
         if (t_out) CK(cudaMemcpyAsync(tt, t.p, ns * sizeof(double), cudaMemcpyDeviceToHost, st));
         sync();
+        if (*e & TSU_DEV_ERR_TIMEOUT)
+            throw Err(TSU_ERR_TIMEOUT, "a patch update gave up waiting for a bulk copy (tsu_set_bulk_copies)");
+        if (*e & TSU_DEV_ERR_LAYOUT) throw Err(TSU_ERR_CUDA, "patch storage not aligned for bulk copies");
         if (*e & TSU_DEV_ERR_NAN) throw Err(TSU_ERR_NAN, "a wave speed or depth is not a finite number");
         if (*e) throw Err(TSU_ERR_NESTING, "a ghost cell or coarse cell had no covering patch (nesting)");
         if (t_out) std::memcpy(t_out, tt, ns * sizeof(double));
@@ -2024,6 +2032,17 @@ int tsu_get_stats(tsu_ctx *ctx, int scen, tsu_stats *out)
         out->patches_renewed = ctx->n_patches_renewed;
         out->patches_reused = ctx->n_patches_reused;
         out->cluster_ms = ctx->cluster_ms;
+    });
+}
+
+int tsu_set_bulk_copies(tsu_ctx *ctx, int enable, long long polls)
+{
+    return guard(ctx, [&] {
+        if ((enable != 0 && enable != 1) || polls < 0 || polls > 0xffffffffLL)
+            throw Err(TSU_ERR_ARG, "enable must be 0 or 1 and polls lie in [0, 2^32 - 1]");
+        ctx->bulk_rows = enable;
+        ctx->wait_polls = (unsigned)polls;
+        ctx->hier_version++;   // captured graphs carry the old launch arguments
     });
 }
 

@@ -60,7 +60,18 @@ struct StepArgs {
     // CFL retake of a level-1 step: when set, a work item of scenario s runs
     // only if gate[s] != 0 (null: every item runs)
     const int *gate;
+    // device error flag (TSU_DEV_ERR_* bits; null: not reported); FP32 split
+    // update: bulk row copies in the x-sweep kernel (0: per-thread cp.async) and
+    // the polls it spends waiting for one before it gives up
+    int *err;
+    int bulk_rows;
+    unsigned wait_polls;
 };
+
+// device error flag bits: 1, 2, 4 a ghost, coarse or parent cell without a
+// covering patch (nesting); 8 a non-finite wave speed or depth; 16 a wait for a
+// bulk copy ran out of polls; 32 patch storage not aligned for bulk copies
+enum { TSU_DEV_ERR_NESTING = 7, TSU_DEV_ERR_NAN = 8, TSU_DEV_ERR_TIMEOUT = 16, TSU_DEV_ERR_LAYOUT = 32 };
 
 // FP32 launch constants of a level
 inline void set_f32_constants(StepArgs &a)

@@ -5,7 +5,8 @@ Bars (as in test_gpu_parity.py): FP64 bit for bit, the time-step sequence and
 the retake and violation counts included; FP32 perturbation form within
 1e-4 m in surface elevation.  Also: a state that is not a finite number makes
 tsu_step return TSU_ERR_NAN (the NaN is put in by the host, in the initial
-velocity; no kernel is made to fault).
+velocity; no kernel is made to fault), and a kernel wait that runs out of its
+poll budget makes it return TSU_ERR_TIMEOUT.
 """
 import numpy as np
 import pytest
@@ -113,3 +114,56 @@ def test_nan_state_returns_tsu_err_nan(prec):
     with pytest.raises(binding.TsuError) as e:
         g.step(1)
     assert e.value.code == binding.TSU_ERR_NAN
+
+
+@pytest.mark.parametrize("spherical", [False, True])
+def test_bulk_row_copies_same_bits_as_per_thread_copies(spherical):
+    """The x-sweep kernel's rows by bulk copies on mbarriers (tsu_set_bulk_copies)
+    give the bits of the per-thread cp.async copies, on a Cartesian shelf with
+    dry land and on the latitude-longitude grid, in the AMR levels too."""
+    if spherical:
+        # a hump running up a sloping beach between walls at 40 N, 2 degrees square
+        n, box, x0, y0 = 48, 2.0, 200.0, 39.0
+        d = box / n
+        cfg = W.base_config(nx=n, ny=n, x0=x0, y0=y0, dx=d, dy=d, bc=[W.BC_WALL] * 4, spherical=1)
+        X, Y = np.meshgrid(np.linspace(x0, x0 + box, n + 1), np.linspace(y0, y0 + box, n + 1))
+        B = -60.0 + 75.0 * (X - x0) / box + 10.0 * np.sin(3.0 * (Y - y0))
+        eta = W.gaussian_grid(x0, y0, box, box, n + 1, n + 1, x0 + 0.65 * box, 40.2, 2.0, 0.15, 0.2)[0]
+        w = dict(cfg=cfg, topo=[(B, x0, y0, d, d)], eta=[(0, eta, x0, y0, d, d)], uplift=[], gauges=np.zeros((0, 2)))
+    else:
+        w = W.shelf(n=96, dx=2000.0)
+    cfg = dict(w["cfg"], num_levels=2, ratios=[4], regrid_interval=3, flag_eta_tol=0.05, patch_max=32)
+    w = dict(w, cfg=cfg)
+    ref = W.load(_gpu(cfg, 1), w)
+    blk = W.load(_gpu(cfg, 1), w)
+    blk.set_bulk_copies(1)
+    assert np.array_equal(ref.step(6), blk.step(6))
+    for lev in (1, 2):
+        for (b0, a), (b1, b) in zip(ref.patches(0, lev), blk.patches(0, lev)):
+            assert np.array_equal(b0, b1)
+            for f in ("h", "hu", "hv"):
+                assert np.array_equal(a[f], b[f]), (lev, f)
+
+
+def test_wait_budget_zero_returns_tsu_err_timeout():
+    """With bulk row copies and a poll budget of 0 the x-sweep kernel's first
+    wait gives up: the work item issues no further copies, waits for those in
+    flight, and the step returns TSU_ERR_TIMEOUT; later calls keep returning
+    it (no GPU fault is involved).  A context with the default budget steps
+    the same workload to the oracle's time; bad arguments are TSU_ERR_ARG."""
+    from paper_1901_06798_gb300 import binding
+    w = W.hump200()
+    g = W.load(_gpu(w["cfg"], 1), w)
+    for en, polls in ((2, 10), (1, -1), (1, 1 << 32)):
+        with pytest.raises(binding.TsuError) as e:
+            g.set_bulk_copies(en, polls)
+        assert e.value.code == binding.TSU_ERR_ARG
+    g.set_bulk_copies(1, 0)
+    for _ in range(2):
+        with pytest.raises(binding.TsuError) as e:
+            g.step(1)
+        assert e.value.code == binding.TSU_ERR_TIMEOUT
+    o = W.load(oracle.Oracle(w["cfg"]), w)
+    g2 = W.load(_gpu(w["cfg"], 1), w)
+    g2.set_bulk_copies(1)
+    np.testing.assert_allclose(g2.step(3), o.step(3), rtol=1e-5)

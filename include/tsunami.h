@@ -28,7 +28,8 @@
  * TSU_ERR_NESTING (an AMR invariant failed), TSU_ERR_OOM (device memory),
  * TSU_ERR_NOT_BUILT (the CUDA library is not loaded on a GPU), TSU_ERR_NAN (the
  * state is no longer finite), TSU_ERR_TIMEOUT (a kernel's bounded wait on the
- * device gave up).
+ * device gave up), TSU_ERR_NEGDEPTH (a state the caller supplied has a
+ * negative depth).
  */
 #ifndef TSUNAMI_H
 #define TSUNAMI_H
@@ -52,9 +53,13 @@ enum {
     TSU_ERR_NOT_BUILT = -6,
     TSU_ERR_NAN = -7,           /* a wave speed or a cell's depth (surface) is not a finite number: the run
                                    has blown up; the context keeps returning this code */
-    TSU_ERR_TIMEOUT = -8        /* a kernel gave up waiting on the device (a row's bulk copy into shared
+    TSU_ERR_TIMEOUT = -8,       /* a kernel gave up waiting on the device (a row's bulk copy into shared
                                    memory did not complete within the poll budget of tsu_set_bulk_copies):
                                    that step's state is not valid; the context keeps returning this code */
+    TSU_ERR_NEGDEPTH = -9       /* a state the caller supplied (written through tsu_level1_buffers, or
+                                   restored by tsu_checkpoint_restore) has an interior cell with a negative
+                                   depth, which the library never stores (it clips depths at zero): the
+                                   step did nothing */
 };
 
 enum { TSU_F64 = 0, TSU_F32P = 1 };              /* precision of the state */
@@ -177,7 +182,10 @@ int tsu_init(tsu_ctx *ctx);
  * Returns TSU_ERR_CFL if a kept level step exceeded cfl_max (the work is done;
  * see cfl_retake), TSU_ERR_NAN if a speed or a depth is not a finite number,
  * TSU_ERR_TIMEOUT if a kernel gave up waiting (tsu_set_bulk_copies),
- * TSU_ERR_ARG after tsu_step_level left a coarse step unfinished. */
+ * TSU_ERR_ARG after tsu_step_level left a coarse step unfinished.  The first
+ * step after tsu_level1_buffers or tsu_checkpoint_restore checks every level's
+ * interior depths first and returns TSU_ERR_NEGDEPTH, doing nothing, if one is
+ * negative. */
 int tsu_step(tsu_ctx *ctx, int n_coarse_steps, double *t_out);
 
 /* One step of one level (1-based), the unit of the recursion of Sec. 3.1
@@ -292,7 +300,8 @@ int tsu_autotune(tsu_ctx *ctx, int reps, int *best_threads, int *best_seg_rows, 
  * B from them at later regrids) and the same gauges; predictor weights are
  * set again with tsu_cnn_set_weights.  The run then continues exactly as the
  * saved one would have.  Errors: TSU_ERR_ARG (buffer too small, not a
- * checkpoint, another configuration, truncated or corrupt data). */
+ * checkpoint, another configuration, truncated or corrupt data).  The next
+ * tsu_step or tsu_step_level checks the restored depths (TSU_ERR_NEGDEPTH). */
 int tsu_checkpoint_save(tsu_ctx *ctx, void *buf, size_t cap, size_t *written);
 int tsu_checkpoint_restore(tsu_ctx *ctx, const void *buf, size_t n);
 
@@ -301,7 +310,9 @@ int tsu_sync(tsu_ctx *ctx);
 
 /* Device pointer of level-1 patch 0's current state buffers, for tests and
  * the benchmark (fields h|eta', hu, hv, B; element type by precision;
- * row pitch in elements; interior cell (i, j) at [(j + 2) * pitch + i + 2]). */
+ * row pitch in elements; interior cell (i, j) at [(j + 2) * pitch + i + 2]).
+ * The caller may write the state through them; the next tsu_step or
+ * tsu_step_level checks its depths (TSU_ERR_NEGDEPTH). */
 int tsu_level1_buffers(tsu_ctx *ctx, void **h, void **hu, void **hv, void **B, int *pitch);
 
 /* Per-level timing of the patch update, for measurement.  enable != 0 starts

@@ -23,6 +23,7 @@ MAX_REGIONS = 8
 TSU_OK, TSU_ERR_ARG, TSU_ERR_CUDA, TSU_ERR_CFL, TSU_ERR_NESTING, TSU_ERR_OOM, TSU_ERR_NOT_BUILT = 0, -1, -2, -3, -4, -5, -6
 TSU_ERR_NAN = -7
 TSU_ERR_TIMEOUT = -8
+TSU_ERR_NEGDEPTH = -9
 TSU_F64, TSU_F32P = 0, 1
 FIELDS = {"h": 0, "hu": 1, "hv": 2, "eta": 3, "zeta": 4, "B": 5}
 

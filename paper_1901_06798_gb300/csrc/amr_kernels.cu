@@ -648,6 +648,30 @@ __global__ void cnn_union_kernel(uint8_t *raw, const uint8_t *cov, const float *
 // atomic pair per block and patch, not per warp (thousands of patches from a
 // regrid would otherwise queue on the same two words).  Many small patches
 // take one block each; one large patch spreads over many.
+// Interior cells of the level's patches whose depth is negative (h < 0; in the
+// perturbation form eta' - B < 0 in FP32, the operation the sweeps derive h
+// with), counted into *count.  No state the library stores has one: the
+// sweeps, the averaging and the interpolation clip depths at zero.
+template <typename T, bool PERT>
+__global__ void __launch_bounds__(256) depth_check_kernel(LevelView L, int npatch, int cur, int *count)
+{
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    int n = 0;
+    for (int pi = blockIdx.y; pi < npatch; pi += gridDim.y) {
+        const PatchDesc P = L.descs[pi];
+        Acc<T> a = acc<T>(L.arena, P);
+        for (int j = blockIdx.x * 8 + ty; j < P.ny; j += gridDim.x * 8) {
+            const T *r0 = a.f(cur, 0) + a.idx(0, j), *rB = a.Bp() + a.idx(0, j);
+            for (int i = tx; i < P.nx; i += 32) {
+                const T h = PERT ? r0[i] - rB[i] : r0[i];
+                n += h < T(0) ? 1 : 0;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (tx == 0 && n) atomicAdd(count, n);
+}
+
 template <typename T, bool PERT>
 __global__ void __launch_bounds__(256) cell_speed_kernel(LevelView L, const int *list, int nlist, int cur, double g,
                                                          double drytol, unsigned long long *smax)
@@ -1080,6 +1104,18 @@ int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStr
     const int rpb = 8;
     dim3 grid((ny + rpb - 1) / rpb, nplanes);
     flag_bbox_kernel<<<grid, 256, 0, st>>>(F, nx, ny, rpb, box);
+    return (int)cudaGetLastError();
+}
+
+int k_depth_check(int prec, const LevelView &L, int npatch, int maxcells, int cur, int *count, cudaStream_t st)
+{
+    if (npatch <= 0) return 0;
+    constexpr int kBlocks = 152 * 8;
+    const int by = npatch < kBlocks ? npatch : kBlocks;
+    int bx = (maxcells + 256 * 32 - 1) / (256 * 32);
+    if (bx > kBlocks / by) bx = kBlocks / by;
+    if (bx < 1) bx = 1;
+    TSU_DISPATCH(prec, depth_check_kernel, <<<dim3(bx, by), dim3(32, 8), 0, st>>>(L, npatch, cur, count));
     return (int)cudaGetLastError();
 }
 

@@ -111,6 +111,8 @@ int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int 
 int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st);
 int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa,
            cudaStream_t st);
+// count of interior cells with a negative depth over a level's patches (into *count)
+int k_depth_check(int prec, const LevelView &L, int npatch, int maxcells, int cur, int *count, cudaStream_t st);
 int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int maxcells, int cur, double g,
                  double drytol, unsigned long long *smax, cudaStream_t st);
 // one box of a halo exchange: patch (index in the level), box origin and

@@ -321,6 +321,8 @@ struct tsu_ctx {
     long long n_regrids = 0;     // host-side regrid accounting (tsu_stats)
     double regrid_ms = 0.0, cluster_ms = 0.0, regrid_wait_ms = 0.0;
     long long n_patches_renewed = 0, n_patches_reused = 0;   // new patches at regrids, of which kept their block
+    bool ext_state = false;           // a state came from the caller (tsu_level1_buffers, restore): check its depths
+    DevBuf<int> dneg;                 // count of the depth check
     int bulk_rows = 0;                // FP32 split update: x-sweep rows by bulk copies (tsu_set_bulk_copies)
     unsigned wait_polls = 1u << 22;   // polls a kernel spends on one bulk copy before giving up
     int seg_rows = 0;  // rows per work item of the patch update (0: library default)
@@ -1249,6 +1251,25 @@ struct tsu_ctx {
 
     // Error flag and CFL-violation counts (and, with t_out, every scenario's
     // time) in one synchronisation, through page-locked memory.
+    // Before the first step after the caller could have written the state
+    // (tsu_level1_buffers, tsu_checkpoint_restore): no interior cell of any
+    // level may have a negative depth, which the library never stores.
+    void check_external_state()
+    {
+        if (!ext_state) return;
+        dneg.ensure(1, st);
+        CK(cudaMemsetAsync(dneg.p, 0, sizeof(int), st));
+        for (int l = 0; l < nlev; l++)
+            if (!lv[l].P.empty())
+                kl(k_depth_check(prec, view(l), (int)lv[l].P.size(), lv[l].maxcells, lv[l].cur, dneg.p, st), "depth check");
+        int n = 0;
+        CK(cudaMemcpyAsync(&n, dneg.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        sync();
+        if (n > 0)
+            throw Err(TSU_ERR_NEGDEPTH, std::to_string(n) + " interior cells of the supplied state have a negative depth");
+        ext_state = false;
+    }
+
     void check_device_errors(bool &cfl, double *t_out = nullptr)
     {
         const size_t ns = (size_t)nscen;
@@ -1796,6 +1817,7 @@ int tsu_step(tsu_ctx *ctx, int n, double *t_out)
     bool cfl = false;
     int rc = guard(ctx, [&] {
         if (n < 0) throw Err(TSU_ERR_ARG, "negative step count");
+        ctx->check_external_state();
         ctx->step(n);
         ctx->check_device_errors(cfl, t_out);
     });
@@ -1810,6 +1832,7 @@ int tsu_step_level(tsu_ctx *ctx, int level, double *t_out)
 {
     bool cfl = false;
     int rc = guard(ctx, [&] {
+        ctx->check_external_state();
         ctx->step_level(level - 1);
         ctx->check_device_errors(cfl, t_out);
     });
@@ -2194,6 +2217,7 @@ int tsu_level1_buffers(tsu_ctx *ctx, void **h, void **hu, void **hv, void **B, i
         if (hv) *hv = base + (cur * 3 + 2) * fsb;
         if (B) *B = base + 6 * fsb;
         if (pitch) *pitch = p.pitch;
+        ctx->ext_state = true;   // the caller may write through these
     });
 }
 
@@ -2333,5 +2357,6 @@ int tsu_checkpoint_restore(tsu_ctx *ctx, const void *buf, size_t n)
     return guard(ctx, [&] {
         if (!buf) throw Err(TSU_ERR_ARG, "bad argument");
         ctx->restore(reinterpret_cast<const uint8_t *>(buf), n);
+        ctx->ext_state = true;
     });
 }

@@ -6,7 +6,8 @@ the retake and violation counts included; FP32 perturbation form within
 1e-4 m in surface elevation.  Also: a state that is not a finite number makes
 tsu_step return TSU_ERR_NAN (the NaN is put in by the host, in the initial
 velocity; no kernel is made to fault), and a kernel wait that runs out of its
-poll budget makes it return TSU_ERR_TIMEOUT.
+poll budget makes it return TSU_ERR_TIMEOUT, and a negative depth written into
+the state by the caller makes it return TSU_ERR_NEGDEPTH without stepping.
 """
 import numpy as np
 import pytest
@@ -167,3 +168,43 @@ def test_wait_budget_zero_returns_tsu_err_timeout():
     g2 = W.load(_gpu(w["cfg"], 1), w)
     g2.set_bulk_copies(1)
     np.testing.assert_allclose(g2.step(3), o.step(3), rtol=1e-5)
+
+
+def _cudart():
+    import ctypes
+    for name in ("libcudart.so.13", "libcudart.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("no CUDA runtime library to copy through")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_negative_depth_written_by_the_caller_returns_tsu_err_negdepth(prec):
+    """A negative depth written into the level-1 state through
+    tsu_level1_buffers (by the host, with cudaMemcpy) makes the next tsu_step
+    return TSU_ERR_NEGDEPTH without stepping, and every step after it until
+    the state is repaired; then the run continues to the oracle's time."""
+    import ctypes
+    from paper_1901_06798_gb300 import binding
+    rt = _cudart()
+    rt.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    w = W.hump200()
+    g = W.load(_gpu(w["cfg"], prec), w)
+    (ph, _, _, pB), pitch = g.level1_buffers()
+    dt = np.float64 if prec == 0 else np.float32
+    off = ((20 + 2) * pitch + 30 + 2) * np.dtype(dt).itemsize
+    old, B = np.zeros(1, dt), np.zeros(1, dt)
+    assert rt.cudaMemcpy(old.ctypes.data, ph + off, old.nbytes, 2) == 0     # device to host
+    assert rt.cudaMemcpy(B.ctypes.data, pB + off, B.nbytes, 2) == 0
+    bad = np.array([-0.25 if prec == 0 else B[0] - 0.25], dt)
+    assert rt.cudaMemcpy(ph + off, bad.ctypes.data, bad.nbytes, 1) == 0     # host to device
+    for _ in range(2):
+        with pytest.raises(binding.TsuError) as e:
+            g.step(1)
+        assert e.value.code == binding.TSU_ERR_NEGDEPTH
+    assert g.stats()["t"] == 0.0
+    assert rt.cudaMemcpy(ph + off, old.ctypes.data, old.nbytes, 1) == 0
+    o = W.load(oracle.Oracle(w["cfg"]), w)
+    np.testing.assert_allclose(g.step(2), o.step(2), rtol=1e-5)

@@ -261,7 +261,7 @@ int tsu_get_stats(tsu_ctx *ctx, int scenario, tsu_stats *out);
  * the split FP32 update (two columns per thread), step_threads - 4 otherwise.
  * The split FP32 update runs as two kernels: the knobs shape its x-sweep
  * kernel (rows counted over the patch's ghost rows too); its y-sweep kernel
- * always takes strips of 64 columns and 32 rows.  0 restores the defaults.
+ * always takes strips of 64 columns and 64 rows.  0 restores the defaults.
  * Results do not depend on either.  Returns TSU_ERR_ARG for any other value. */
 int tsu_set_tuning(tsu_ctx *ctx, int step_threads, int seg_rows);
 

@@ -528,11 +528,11 @@ struct tsu_ctx {
                     const PatchDesc &p = L.P[k];
                     if (split) {
                         // x kernel: every row including the ghost rows, no halo rows; y kernel:
-                        // strips of 2 x 32 columns and segments of 32 interior rows
+                        // strips of 64 columns and segments of 64 interior rows
                         for (int x0 = 0; x0 < p.nx; x0 += W)
                             for (int y0 = -2; y0 < p.ny + 2; y0 += sg)
                                 ox.push_back(StepItem{k, x0, y0, std::min(W, p.nx - x0), std::min(sg, p.ny + 2 - y0)});
-                        constexpr int WY = 64, SY = 32;
+                        constexpr int WY = 64, SY = 64;
                         for (int x0 = 0; x0 < p.nx; x0 += WY)
                             for (int y0 = 0; y0 < p.ny; y0 += SY)
                                 oy.push_back(StepItem{k, x0, y0, std::min(WY, p.nx - x0), std::min(SY, p.ny - y0)});

@@ -7,6 +7,7 @@
 // Built with --fmad=false: the FP64 instantiations round every operation as
 // the FP64 oracle does.  Each kernel batches all patches of a level (and all
 // scenarios) into one launch.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <type_traits>
@@ -533,53 +534,54 @@ __global__ void flag_kernel(LevelView L, int cur, FlagArgs fa)
     }
 }
 
-// Chebyshev dilation, separable: dir 0 dilates along x, dir 1 along y.
-__global__ void dilate_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir)
+// Chebyshev dilation, separable: dir 0 dilates along x, dir 1 along y.  Blocks
+// walk (row, 256-column segment) pairs of plane blockIdx.y: 32-bit indices, and
+// a thread's neighbours along x are its warp's cells (coalesced, cached).
+__global__ void dilate_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, int b, int dir)
 {
-    long long n = (long long)nx * ny * nplanes;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        long long pl = c / ((long long)nx * ny);
-        long long rem = c - pl * (long long)nx * ny;
-        int I = (int)(rem % nx), J = (int)(rem / nx);
-        const uint8_t *s = src + pl * (long long)nx * ny;
+    const int ncb = (nx + blockDim.x - 1) / blockDim.x;
+    const size_t pl = (size_t)blockIdx.y * nx * ny;
+    const uint8_t *s = src + pl;
+    uint8_t *d = dst + pl;
+    for (int rb = blockIdx.x; rb < ny * ncb; rb += gridDim.x) {
+        const int J = rb / ncb, I = (rb - J * ncb) * blockDim.x + threadIdx.x;
+        if (I >= nx) continue;
         uint8_t v = 0;
         if (dir == 0) {
-            for (int d = -b; d <= b && !v; d++) {
-                int a = I + d;
-                if (a >= 0 && a < nx) v = s[(long long)J * nx + a];
-            }
+            const uint8_t *r = s + (size_t)J * nx;
+            for (int a = max(I - b, 0); a <= min(I + b, nx - 1) && !v; a++) v = r[a];
         } else {
-            for (int d = -b; d <= b && !v; d++) {
-                int a = J + d;
-                if (a >= 0 && a < ny) v = s[(long long)a * nx + I];
-            }
+            for (int a = max(J - b, 0); a <= min(J + b, ny - 1) && !v; a++) v = s[(size_t)a * nx + I];
         }
-        dst[c] = v ? 1 : 0;
+        d[(size_t)J * nx + I] = v ? 1 : 0;
     }
 }
 
-// region caps and proper nesting: F &= N, N = every cell within 2 covered or outside
-__global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, FlagArgs fa)
+// region caps and proper nesting: F &= N, N = every cell within 2 covered or
+// outside; blocks walk (row, column segment) pairs of plane blockIdx.y
+__global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, FlagArgs fa)
 {
-    long long n = (long long)nx * ny * nplanes;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        long long pl = c / ((long long)nx * ny);
-        long long rem = c - pl * (long long)nx * ny;
-        int I = (int)(rem % nx), J = (int)(rem / nx);
-        const uint8_t *cv = cov + pl * (long long)nx * ny;
-        double x = fa.x0 + ((double)I + 0.5) * fa.dxl, y = fa.y0 + ((double)J + 0.5) * fa.dyl;
+    const int ncb = (nx + blockDim.x - 1) / blockDim.x;
+    const size_t pl = (size_t)blockIdx.y * nx * ny;
+    const uint8_t *cv = cov + pl;
+    for (int rb = blockIdx.x; rb < ny * ncb; rb += gridDim.x) {
+        const int J = rb / ncb, I = (rb - J * ncb) * blockDim.x + threadIdx.x;
+        if (I >= nx) continue;
+        const size_t c = pl + (size_t)J * nx + I;
         uint8_t f = F[c];
-        for (int rg = 0; rg < fa.n_regions; rg++) {
-            const double *R = fa.regions + 6 * rg;
-            if (x >= R[0] && x <= R[2] && y >= R[1] && y <= R[3] && (double)fa.newlev > R[5]) f = 0;
+        if (fa.n_regions > 0) {
+            const double x = fa.x0 + ((double)I + 0.5) * fa.dxl, y = fa.y0 + ((double)J + 0.5) * fa.dyl;
+            for (int rg = 0; rg < fa.n_regions; rg++) {
+                const double *R = fa.regions + 6 * rg;
+                if (x >= R[0] && x <= R[2] && y >= R[1] && y <= R[3] && (double)fa.newlev > R[5]) f = 0;
+            }
         }
         int ok = 1;
-        for (int dj = -2; dj <= 2 && ok; dj++)
-            for (int di = -2; di <= 2; di++) {
-                int a = I + di, b = J + dj;
-                if (a < 0 || a >= nx || b < 0 || b >= ny) continue;
-                if (!cv[(long long)b * nx + a]) { ok = 0; break; }
-            }
+        for (int b2 = max(J - 2, 0); b2 <= min(J + 2, ny - 1) && ok; b2++) {
+            const uint8_t *r = cv + (size_t)b2 * nx;
+            for (int a2 = max(I - 2, 0); a2 <= min(I + 2, nx - 1); a2++)
+                if (!r[a2]) { ok = 0; break; }
+        }
         // N: bit 0 the final flag, bit 1 nestable -- the one plane the host clusters
         const uint8_t ff = ok ? f : 0;
         N[c] = (uint8_t)((ok << 1) | (ff ? 1 : 0));
@@ -1049,22 +1051,20 @@ int k_flag(int prec, const LevelView &L, int npatch, int maxcells, int cur, cons
 
 int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir, cudaStream_t st)
 {
-    long long n = (long long)nx * ny * nplanes;
-    int blocks = (int)((n + 255) / 256);
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    if (blocks < 1) blocks = 1;
-    dilate_kernel<<<blocks, 256, 0, st>>>(src, dst, nx, ny, nplanes, b, dir);
+    if (nplanes <= 0 || nx <= 0 || ny <= 0) return 0;
+    const long long rows = (long long)ny * ((nx + 255) / 256);
+    const int blocks = (int)std::min<long long>(rows, 152LL * 16);
+    dilate_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(src, dst, nx, ny, b, dir);
     return (int)cudaGetLastError();
 }
 
 int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa,
            cudaStream_t st)
 {
-    long long n = (long long)nx * ny * nplanes;
-    int blocks = (int)((n + 255) / 256);
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    if (blocks < 1) blocks = 1;
-    nest_kernel<<<blocks, 256, 0, st>>>(F, N, cov, nx, ny, nplanes, fa);
+    if (nplanes <= 0 || nx <= 0 || ny <= 0) return 0;
+    const long long rows = (long long)ny * ((nx + 255) / 256);
+    const int blocks = (int)std::min<long long>(rows, 152LL * 16);
+    nest_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(F, N, cov, nx, ny, fa);
     return (int)cudaGetLastError();
 }
 
@@ -1096,6 +1096,35 @@ __global__ void flag_bbox_kernel(const uint8_t *F, int nx, int ny, int rows_per_
         atomicMax(box + 4 * p + 2, i1);
         atomicMax(box + 4 * p + 3, j1);
     }
+}
+
+// The box (i0, j0, w, h) of one nx-wide byte plane N (bit 0 the flag, bit 1
+// nestable), packed 4 cells per byte: cell i of box row j at byte
+// j * ps + i / 4, bits 2 (i % 4) (flag) and 2 (i % 4) + 1 (nestable); the
+// bytes past the row's last cell are zero.  One thread per packed byte.
+__global__ void pack_flags_kernel(const uint8_t *N, int nx, int i0, int j0, int w, int h, int ps, uint8_t *out)
+{
+    const long long n = (long long)ps * h;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(k / ps), b = (int)(k % ps);
+        const uint8_t *r = N + (size_t)(j0 + j) * nx + i0;
+        unsigned v = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int i = 4 * b + q;
+            if (i < w) v |= (unsigned)(r[i] & 3) << (2 * q);
+        }
+        out[k] = (uint8_t)v;
+    }
+}
+
+int k_pack_flags(const uint8_t *N, int nx, int i0, int j0, int w, int h, int ps, uint8_t *out, cudaStream_t st)
+{
+    const long long n = (long long)ps * h;
+    if (n <= 0) return 0;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    pack_flags_kernel<<<blocks, 256, 0, st>>>(N, nx, i0, j0, w, h, ps, out);
+    return (int)cudaGetLastError();
 }
 
 int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st)

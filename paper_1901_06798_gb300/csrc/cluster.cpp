@@ -12,8 +12,9 @@
 //   and recurse, lower/left part first.  Boxes are finally split into
 //   near-equal pieces whose fine size is at most patch_max.
 //
-// The flags and the nestable mask come as one byte plane: bit 0 the flag, bit 1
-// nestable (the plane the regrid copies from the device).
+// The flags and the nestable mask come packed, 4 cells per byte (cell i of row
+// j at byte j * ps + i / 4, bit 2 (i % 4) the flag and bit 2 (i % 4) + 1
+// nestable): the plane the regrid packs on the device and copies out.
 // 2D prefix sums of the flags and of the nestable mask make every count and
 // signature O(w + h) per box, so the cost is dominated by one pass over the
 // mask.  They are built only over the flags' bounding box (the recursion's
@@ -71,9 +72,10 @@ template <typename Fn> void parallel_for(int n, int threads, Fn f)
 
 }  // namespace
 
-void cluster_boxes(const uint8_t *Fg, int nxg, int nyg, double eff, int ratio, int patch_max,
+void cluster_boxes(const uint8_t *Fg, int nxg, int nyg, int ps, double eff, int ratio, int patch_max,
                    std::vector<std::array<int, 4>> &out, int max_threads, std::vector<int32_t> *workspace)
 {
+    auto cell = [&](const uint8_t *row, int i) { return (row[i >> 2] >> (2 * (i & 3))) & 3; };
     out.clear();
     // threads only pay off on large masks (handing a loop to the pool costs
     // about as much as scanning some tens of thousands of cells)
@@ -84,13 +86,18 @@ void cluster_boxes(const uint8_t *Fg, int nxg, int nyg, double eff, int ratio, i
     std::vector<int> rmin(nyg, nxg), rmax(nyg, -1);
     parallel_for(nyg, threads, [&](int ja, int jb) {
         for (int j = ja; j < jb; j++) {
-            const uint8_t *r = Fg + (size_t)j * nxg;
+            const uint8_t *r = Fg + (size_t)j * ps;
+            const int nb = (nxg + 3) >> 2;
             int lo = -1, hi = -1;
-            for (int i = 0; i < nxg; i++)
-                if (r[i] & 1) { lo = i; break; }
+            for (int b = 0; b < nb && lo < 0; b++)
+                if (r[b] & 0x55)
+                    for (int q = 0; q < 4; q++)
+                        if ((r[b] >> (2 * q)) & 1) { lo = 4 * b + q; break; }
             if (lo < 0) continue;
-            for (int i = nxg - 1; i >= lo; i--)
-                if (r[i] & 1) { hi = i; break; }
+            for (int b = nb - 1; b >= 0 && hi < 0; b--)
+                if (r[b] & 0x55)
+                    for (int q = 3; q >= 0; q--)
+                        if ((r[b] >> (2 * q)) & 1) { hi = 4 * b + q; break; }
             rmin[j] = lo;
             rmax[j] = hi;
         }
@@ -121,12 +128,13 @@ void cluster_boxes(const uint8_t *Fg, int nxg, int nyg, double eff, int ratio, i
     parallel_for(ny, threads, [&](int ja, int jb) {
         for (int j = ja; j < jb; j++) {
             Sums::Pair *r = S.P + (size_t)(j + 1) * W;
-            const uint8_t *fr = Fg + (size_t)(j + bj0) * nxg + bi0;
+            const uint8_t *fr = Fg + (size_t)(j + bj0) * ps;
             int32_t fa = 0, na = 0;
             r[0] = {0, 0};
             for (int i = 0; i < nx; i++) {
-                fa += fr[i] & 1;
-                na += (fr[i] >> 1) & 1;
+                const int v = cell(fr, bi0 + i);
+                fa += v & 1;
+                na += v >> 1;
                 r[i + 1] = {fa, na};
             }
         }

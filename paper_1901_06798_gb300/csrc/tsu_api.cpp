@@ -31,8 +31,8 @@
 #include "tsu_device.h"
 
 namespace tsu {
-// FN: one byte per cell, bit 0 the flag, bit 1 nestable
-void cluster_boxes(const uint8_t *FN, int nx, int ny, double eff, int ratio, int patch_max,
+// FN: 4 cells per byte, rows ps bytes apart; cell i: bit 2 (i % 4) the flag, bit 2 (i % 4) + 1 nestable
+void cluster_boxes(const uint8_t *FN, int nx, int ny, int ps, double eff, int ratio, int patch_max,
                    std::vector<std::array<int, 4>> &out, int max_threads, std::vector<int32_t> *workspace);
 }
 
@@ -311,7 +311,7 @@ struct tsu_ctx {
     DevBuf<GaugeLoc> dgloc;
     long long samp_cap = 0, nsamp = 0;
     // flags
-    DevBuf<uint8_t> fraw, fcov, ftmp, fF, fN;
+    DevBuf<uint8_t> fraw, fcov, ftmp, fF, fN, fpack;
     DevBuf<int> fslot, fbox;
     // statistics and graphs
     long long launches = 0;
@@ -835,27 +835,33 @@ struct tsu_ctx {
             kl(k_flag_bbox(fF.p, nx, ny, np, fbox.p, st), "flag bbox");
             CK(cudaMemcpyAsync(bb.data(), fbox.p, bb.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
             sync();
+            // each plane's box packed 4 cells per byte on the device, then one copy out
             std::vector<size_t> hoff(np + 1, 0);
+            std::vector<int> pstride(np, 0);
             for (int q = 0; q < np; q++) {
                 const size_t w = bb[4 * q + 2] >= 0 ? (size_t)(bb[4 * q + 2] - bb[4 * q] + 1) : 0;
                 const size_t h = bb[4 * q + 2] >= 0 ? (size_t)(bb[4 * q + 3] - bb[4 * q + 1] + 1) : 0;
-                hoff[q + 1] = hoff[q] + w * h;
+                pstride[q] = (int)((w + 3) / 4);
+                hoff[q + 1] = hoff[q] + (size_t)pstride[q] * h;
             }
-            hflags.ensure(std::max<size_t>(hoff[np], 1));
-            uint8_t *hFN = hflags.p;   // bit 0 flag, bit 1 nestable (the nesting kernel's plane)
+            const size_t nbytes = std::max<size_t>(hoff[np], 1);
+            fpack.ensure(nbytes, st);
+            hflags.ensure(nbytes);
+            uint8_t *hFN = hflags.p;
             for (int q = 0; q < np; q++) {
                 if (bb[4 * q + 2] < 0) continue;
-                const size_t w = bb[4 * q + 2] - bb[4 * q] + 1, h = bb[4 * q + 3] - bb[4 * q + 1] + 1;
-                const size_t src = plane * q + (size_t)bb[4 * q + 1] * nx + bb[4 * q];
-                CK(cudaMemcpy2DAsync(hFN + hoff[q], w, fN.p + src, nx, w, h, cudaMemcpyDeviceToHost, st));
+                const int w = bb[4 * q + 2] - bb[4 * q] + 1, h = bb[4 * q + 3] - bb[4 * q + 1] + 1;
+                kl(k_pack_flags(fN.p + plane * q, nx, bb[4 * q], bb[4 * q + 1], w, h, pstride[q], fpack.p + hoff[q], st),
+                   "pack flags");
             }
+            CK(cudaMemcpyAsync(hFN, fpack.p, hoff[np], cudaMemcpyDeviceToHost, st));
             sync();
             const auto t_c0 = std::chrono::steady_clock::now();
             auto cluster_one = [&](int s, int threads, std::vector<int32_t> *ws) {
                 const int q = slot[s];
                 if (bb[4 * q + 2] < 0) return;
                 const int w = bb[4 * q + 2] - bb[4 * q] + 1, h = bb[4 * q + 3] - bb[4 * q + 1] + 1;
-                cluster_boxes(hFN + hoff[q], w, h, c.cluster_eff, r, c.patch_max, boxes[s], threads, ws);
+                cluster_boxes(hFN + hoff[q], w, h, pstride[q], c.cluster_eff, r, c.patch_max, boxes[s], threads, ws);
                 for (auto &b : boxes[s]) { b[0] += bb[4 * q]; b[1] += bb[4 * q + 1]; }
             };
             if (which.size() == 1) {
@@ -1605,7 +1611,7 @@ struct tsu_ctx {
         dt1.release(); dt1f.release(); t.release(); rate.release(); cellupd.release(); cells.release(); Rl.release(); mass.release();
         viol.release(); smax.release(); derr.release();
         dgxy.release(); dgeta.release(); dgt.release(); dnsamp.release(); dgloc.release();
-        fraw.release(); fcov.release(); ftmp.release(); fF.release(); fN.release(); fslot.release(); fbox.release();
+        fraw.release(); fcov.release(); ftmp.release(); fF.release(); fN.release(); fpack.release(); fslot.release(); fbox.release();
         dstage.release(); zero_dt.release(); zero_dtf.release(); massParts.release();
         cnn_theta.release(); cnn_feat.release(); cnn_logits.release(); cnn_half.release();
         if (arena.base) cudaFreeAsync(arena.base, st);
@@ -2324,12 +2330,17 @@ int tsu_cluster_flags(const unsigned char *flags, const unsigned char *nestable,
     try {
         if (!flags || !boxes || !n_boxes || nx < 1 || ny < 1 || ratio < 1 || patch_max < 1 || max_boxes < 0)
             return TSU_ERR_ARG;
-        // one plane, bit 0 the flag and bit 1 nestable: what the regrid clusters
-        std::vector<uint8_t> fn((size_t)nx * ny);
-        for (size_t k = 0; k < fn.size(); k++)
-            fn[k] = (uint8_t)((flags[k] ? 1 : 0) | ((!nestable || nestable[k]) ? 2 : 0));
+        // the packed plane the regrid clusters: 4 cells per byte, flag and nestable bits
+        const int ps = (nx + 3) / 4;
+        std::vector<uint8_t> fn((size_t)ps * ny, 0);
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                const size_t k = (size_t)j * nx + i;
+                const int v = (flags[k] ? 1 : 0) | ((!nestable || nestable[k]) ? 2 : 0);
+                fn[(size_t)j * ps + i / 4] |= (uint8_t)(v << (2 * (i % 4)));
+            }
         std::vector<std::array<int, 4>> out;
-        tsu::cluster_boxes(fn.data(), nx, ny, eff, ratio, patch_max, out, 16, nullptr);
+        tsu::cluster_boxes(fn.data(), nx, ny, ps, eff, ratio, patch_max, out, 16, nullptr);
         *n_boxes = (int)out.size();
         if ((int)out.size() > max_boxes) return TSU_ERR_ARG;
         for (size_t k = 0; k < out.size(); k++)

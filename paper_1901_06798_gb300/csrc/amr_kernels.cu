@@ -534,18 +534,20 @@ __global__ void flag_kernel(LevelView L, int cur, FlagArgs fa)
     }
 }
 
-// Chebyshev dilation, separable: dir 0 dilates along x, dir 1 along y.  Blocks
-// walk (row, 256-column segment) pairs of plane blockIdx.y: 32-bit indices, and
-// a thread's neighbours along x are its warp's cells (coalesced, cached).
-__global__ void dilate_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, int b, int dir)
+// Chebyshev dilation, separable: dir 0 dilates along x, dir 1 along y, over the
+// window W = (wi0, wj0, ww, wh) of each plane.  Blocks walk (row, 256-column
+// segment) pairs of W in plane blockIdx.y: 32-bit indices, and a thread's
+// neighbours along x are its warp's cells (coalesced, cached).
+__global__ void dilate_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, int b, int dir, Win W)
 {
-    const int ncb = (nx + blockDim.x - 1) / blockDim.x;
+    const int ncb = (W.w + blockDim.x - 1) / blockDim.x;
     const size_t pl = (size_t)blockIdx.y * nx * ny;
     const uint8_t *s = src + pl;
     uint8_t *d = dst + pl;
-    for (int rb = blockIdx.x; rb < ny * ncb; rb += gridDim.x) {
-        const int J = rb / ncb, I = (rb - J * ncb) * blockDim.x + threadIdx.x;
-        if (I >= nx) continue;
+    for (int rb = blockIdx.x; rb < W.h * ncb; rb += gridDim.x) {
+        const int jr = rb / ncb, ir = (rb - jr * ncb) * blockDim.x + threadIdx.x;
+        if (ir >= W.w) continue;
+        const int J = W.j0 + jr, I = W.i0 + ir;
         uint8_t v = 0;
         if (dir == 0) {
             const uint8_t *r = s + (size_t)J * nx;
@@ -558,15 +560,16 @@ __global__ void dilate_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, 
 }
 
 // region caps and proper nesting: F &= N, N = every cell within 2 covered or
-// outside; blocks walk (row, column segment) pairs of plane blockIdx.y
-__global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, FlagArgs fa)
+// outside; over the window W of plane blockIdx.y
+__global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, FlagArgs fa, Win W)
 {
-    const int ncb = (nx + blockDim.x - 1) / blockDim.x;
+    const int ncb = (W.w + blockDim.x - 1) / blockDim.x;
     const size_t pl = (size_t)blockIdx.y * nx * ny;
     const uint8_t *cv = cov + pl;
-    for (int rb = blockIdx.x; rb < ny * ncb; rb += gridDim.x) {
-        const int J = rb / ncb, I = (rb - J * ncb) * blockDim.x + threadIdx.x;
-        if (I >= nx) continue;
+    for (int rb = blockIdx.x; rb < W.h * ncb; rb += gridDim.x) {
+        const int jr = rb / ncb, ir = (rb - jr * ncb) * blockDim.x + threadIdx.x;
+        if (ir >= W.w) continue;
+        const int J = W.j0 + jr, I = W.i0 + ir;
         const size_t c = pl + (size_t)J * nx + I;
         uint8_t f = F[c];
         if (fa.n_regions > 0) {
@@ -1049,36 +1052,37 @@ int k_flag(int prec, const LevelView &L, int npatch, int maxcells, int cur, cons
     return (int)cudaGetLastError();
 }
 
-int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir, cudaStream_t st)
+int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir, const Win &W,
+             cudaStream_t st)
 {
-    if (nplanes <= 0 || nx <= 0 || ny <= 0) return 0;
-    const long long rows = (long long)ny * ((nx + 255) / 256);
+    if (nplanes <= 0 || W.w <= 0 || W.h <= 0) return 0;
+    const long long rows = (long long)W.h * ((W.w + 255) / 256);
     const int blocks = (int)std::min<long long>(rows, 152LL * 16);
-    dilate_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(src, dst, nx, ny, b, dir);
+    dilate_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(src, dst, nx, ny, b, dir, W);
     return (int)cudaGetLastError();
 }
 
-int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa,
+int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa, const Win &W,
            cudaStream_t st)
 {
-    if (nplanes <= 0 || nx <= 0 || ny <= 0) return 0;
-    const long long rows = (long long)ny * ((nx + 255) / 256);
+    if (nplanes <= 0 || W.w <= 0 || W.h <= 0) return 0;
+    const long long rows = (long long)W.h * ((W.w + 255) / 256);
     const int blocks = (int)std::min<long long>(rows, 152LL * 16);
-    nest_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(F, N, cov, nx, ny, fa);
+    nest_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(F, N, cov, nx, ny, fa, W);
     return (int)cudaGetLastError();
 }
 
 // Bounding box of the flagged cells of each plane: box[4p .. 4p+3] = min i,
 // min j, max i, max j (left at nx, ny, -1, -1 when nothing is flagged).  One
 // block per (row group, plane); warp minima/maxima, then one atomic per warp.
-__global__ void flag_bbox_kernel(const uint8_t *F, int nx, int ny, int rows_per_block, int *box)
+__global__ void flag_bbox_kernel(const uint8_t *F, int nx, int ny, int rows_per_block, int *box, Win W)
 {
     const int p = blockIdx.y;
     const uint8_t *Fp = F + (size_t)p * nx * ny;
     int i0 = nx, j0 = ny, i1 = -1, j1 = -1;
-    const int ja = blockIdx.x * rows_per_block, jb = min(ny, ja + rows_per_block);
+    const int ja = W.j0 + blockIdx.x * rows_per_block, jb = min(W.j0 + W.h, ja + rows_per_block);
     for (int j = ja; j < jb; j++)
-        for (int i = threadIdx.x; i < nx; i += blockDim.x)
+        for (int i = W.i0 + threadIdx.x; i < W.i0 + W.w; i += blockDim.x)
             if (Fp[(size_t)j * nx + i]) {
                 i0 = min(i0, i); i1 = max(i1, i);
                 j0 = min(j0, j); j1 = max(j1, j);
@@ -1127,12 +1131,13 @@ int k_pack_flags(const uint8_t *N, int nx, int i0, int j0, int w, int h, int ps,
     return (int)cudaGetLastError();
 }
 
-int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st)
+int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st, const Win *W)
 {
-    if (nplanes <= 0) return 0;
+    const Win w = W ? *W : Win{0, 0, nx, ny};
+    if (nplanes <= 0 || w.w <= 0 || w.h <= 0) return 0;
     const int rpb = 8;
-    dim3 grid((ny + rpb - 1) / rpb, nplanes);
-    flag_bbox_kernel<<<grid, 256, 0, st>>>(F, nx, ny, rpb, box);
+    dim3 grid((w.h + rpb - 1) / rpb, nplanes);
+    flag_bbox_kernel<<<grid, 256, 0, st>>>(F, nx, ny, rpb, box, w);
     return (int)cudaGetLastError();
 }
 

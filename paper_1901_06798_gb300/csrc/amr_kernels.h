@@ -106,13 +106,20 @@ int k_uplift(int prec, const LevelView &L, int npatch, int maxcells, const TopoD
 int k_regrid_init(int prec, const LevelView &L, const LevelView &Old, const LevelView &C, const int *list, int nlist,
                   int maxcells, int cur, int cur_c, int ratio, double drytol, int *err, cudaStream_t st);
 int k_flag(int prec, const LevelView &L, int npatch, int maxcells, int cur, const FlagArgs &fa, cudaStream_t st);
-int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir, cudaStream_t st);
-// bounding box (min i, min j, max i, max j) of the flagged cells of each plane; box preset to (nx, ny, -1, -1)
-int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st);
+// a window (i0, j0, w, h) of a level's index plane
+struct Win {
+    int i0, j0, w, h;
+};
+// dilation along x (dir 0) or y (dir 1) over the window W of every plane
+int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int b, int dir, const Win &W,
+             cudaStream_t st);
+// bounding box (min i, min j, max i, max j) of the flagged cells of each plane
+// (within the window W, null: the whole plane); box preset to (nx, ny, -1, -1)
+int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st, const Win *W = nullptr);
 // box (i0, j0, w, h) of the nx-wide byte plane N (bit 0 flag, bit 1 nestable)
 // packed 4 cells per byte, rows ps bytes apart (ps >= (w + 3) / 4)
 int k_pack_flags(const uint8_t *N, int nx, int i0, int j0, int w, int h, int ps, uint8_t *out, cudaStream_t st);
-int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa,
+int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa, const Win &W,
            cudaStream_t st);
 // count of interior cells with a negative depth over a level's patches (into *count)
 int k_depth_check(int prec, const LevelView &L, int npatch, int maxcells, int cur, int *count, cudaStream_t st);

@@ -226,7 +226,7 @@ struct BoxIndex {
     // patches bucketed by 64 x 64 cell tiles, in compressed rows: bucket k
     // holds ids[start[k] .. start[k+1])
     int bs = 64, nbx = 0, nby = 0;
-    std::vector<int> start, ids;
+    std::vector<int> start, ids, fillv;   // kept between builds (no fresh pages per regrid)
     const std::vector<PatchDesc> *P = nullptr;
     void build(const std::vector<PatchDesc> &Pv, const std::vector<int> &which, int nxl, int nyl)
     {
@@ -244,8 +244,8 @@ struct BoxIndex {
         each([&](size_t k, int) { start[k + 1]++; });
         for (size_t k = 0; k + 1 < start.size(); k++) start[k + 1] += start[k];
         ids.resize(start.back());
-        std::vector<int> fill(start.begin(), start.end() - 1);
-        each([&](size_t k, int id) { ids[fill[k]++] = id; });
+        fillv.assign(start.begin(), start.end() - 1);
+        each([&](size_t k, int id) { ids[fillv[k]++] = id; });
     }
     int find(int I, int J) const
     {
@@ -317,6 +317,9 @@ struct tsu_ctx {
     long long launches = 0;
     long long viol_seen = 0;
     PinnedHost hflags;           // page-locked staging of the flag masks for clustering
+    std::vector<BoxIndex> bix_ws, cix_ws, oix_ws;   // spatial indices of the table rebuilds, reused
+    std::vector<unsigned long long> same_keys;       // regrid: old boxes by key (open addressing)
+    std::vector<int> same_ids;
     std::vector<std::vector<int32_t>> cws = std::vector<std::vector<int32_t>>(16);   // clustering workspaces
     long long n_regrids = 0;     // host-side regrid accounting (tsu_stats)
     double regrid_ms = 0.0, cluster_ms = 0.0, regrid_wait_ms = 0.0;
@@ -557,7 +560,9 @@ struct tsu_ctx {
         for (int k = 0; k < n; k++) ids[L.P[k].scen].push_back(k);
         if (l > 0)
             for (int k = 0; k < (int)lv[l - 1].P.size(); k++) cids[lv[l - 1].P[k].scen].push_back(k);
-        std::vector<BoxIndex> bis(nscen), cis(nscen);
+        bix_ws.resize(nscen);
+        cix_ws.resize(nscen);
+        std::vector<BoxIndex> &bis = bix_ws, &cis = cix_ws;
         for (int s = 0; s < nscen; s++) {
             if (ids[s].empty()) continue;
             bis[s].build(L.P, ids[s], L.nxl, L.nyl);
@@ -824,15 +829,28 @@ struct tsu_ctx {
                 cnn_predict(l, np);
                 b = c.cnn_buffer > 0 ? c.cnn_buffer : 0;
             }
-            kl(k_dilate(fraw.p, ftmp.p, nx, ny, np, b, 0, st), "dilate x");
-            kl(k_dilate(ftmp.p, fF.p, nx, ny, np, b, 1, st), "dilate y");
-            kl(k_nest(fF.p, fN.p, fcov.p, nx, ny, np, fa, st), "nest");
+            // Flags and nestable cells can only lie where the level's patches do
+            // (the nesting test clears every uncovered cell), so dilation, nesting
+            // and the bounding box run over the patches' bounding box W: the y pass
+            // reads the x pass's rows within b of W, which reads the fresh raw plane.
+            int wi0 = nx, wj0 = ny, wi1 = 0, wj1 = 0;
+            for (const auto &p : C.P)
+                if (slot[p.scen] >= 0) {
+                    wi0 = std::min(wi0, p.i0); wj0 = std::min(wj0, p.j0);
+                    wi1 = std::max(wi1, p.i0 + p.nx); wj1 = std::max(wj1, p.j0 + p.ny);
+                }
+            const Win W{wi0, wj0, std::max(0, wi1 - wi0), std::max(0, wj1 - wj0)};
+            const int xj0 = std::max(0, wj0 - b), xj1 = std::min(ny, wj1 + b);
+            const Win Wx{wi0, xj0, W.w, std::max(0, xj1 - xj0)};
+            kl(k_dilate(fraw.p, ftmp.p, nx, ny, np, b, 0, Wx, st), "dilate x");
+            kl(k_dilate(ftmp.p, fF.p, nx, ny, np, b, 1, W, st), "dilate y");
+            kl(k_nest(fF.p, fN.p, fcov.p, nx, ny, np, fa, W, st), "nest");
             // only the flags' bounding box of each plane comes to the host (the
             // clustering starts from that box, so the boxes are the same)
             std::vector<int> bb(4 * (size_t)np);
             for (int q = 0; q < np; q++) { bb[4 * q] = nx; bb[4 * q + 1] = ny; bb[4 * q + 2] = -1; bb[4 * q + 3] = -1; }
             fbox.upload(bb, st);
-            kl(k_flag_bbox(fF.p, nx, ny, np, fbox.p, st), "flag bbox");
+            kl(k_flag_bbox(fF.p, nx, ny, np, fbox.p, st, &W), "flag bbox");
             CK(cudaMemcpyAsync(bb.data(), fbox.p, bb.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
             sync();
             // each plane's box packed 4 cells per byte on the device, then one copy out
@@ -893,19 +911,40 @@ struct tsu_ctx {
         std::vector<PatchDesc> P;
         std::vector<size_t> blk, bytes;
         std::vector<int> fresh, renewed;   // patches to initialise; all new patches of regridded scenarios
+        {
+            size_t nb = oldP.size();
+            for (const auto &bx : boxes) nb += bx.size();
+            P.reserve(nb); blk.reserve(nb); bytes.reserve(nb); fresh.reserve(nb); renewed.reserve(nb);
+        }
         // A new box identical to an old one keeps the old block: a fresh patch
         // would copy its state from that very patch and take the same B (B is a
         // function of the cell on a level), so nothing needs copying.  Its
         // ghost cells are refilled before every step, and its other buffer is
         // written by the level's next step before anything reads it.
-        std::unordered_map<unsigned long long, int> same;
         auto key = [](int s, int i0, int j0, int nx, int ny) {
             return ((unsigned long long)(unsigned)s << 60) ^ ((unsigned long long)(unsigned)i0 << 45) ^
                    ((unsigned long long)(unsigned)j0 << 30) ^ ((unsigned long long)(unsigned)nx << 15) ^
                    (unsigned long long)(unsigned)ny;
         };
+        // old boxes by key in an open-addressing table (linear probing, the
+        // first old patch of a key kept): no allocation per entry
+        size_t cap = 16;
+        int lg = 4;
+        while (cap < 2 * oldP.size()) { cap <<= 1; lg++; }
+        same_keys.assign(cap, 0);
+        same_ids.assign(cap, -1);
+        // Fibonacci hashing: the product's top bits depend on every bit of the key
+        auto slot_of = [&](unsigned long long kk) {
+            size_t h = (size_t)((kk * 0x9E3779B97F4A7C15ull) >> (64 - lg));
+            while (same_ids[h] >= 0 && same_keys[h] != kk) h = (h + 1) & (cap - 1);
+            return h;
+        };
         for (size_t k = 0; k < oldP.size(); k++)
-            if (slot[oldP[k].scen] >= 0) same.emplace(key(oldP[k].scen, oldP[k].i0, oldP[k].j0, oldP[k].nx, oldP[k].ny), (int)k);
+            if (slot[oldP[k].scen] >= 0) {
+                const unsigned long long kk = key(oldP[k].scen, oldP[k].i0, oldP[k].j0, oldP[k].nx, oldP[k].ny);
+                const size_t h = slot_of(kk);
+                if (same_ids[h] < 0) { same_keys[h] = kk; same_ids[h] = (int)k; }
+            }
         std::vector<char> kept(oldP.size(), 0);
         for (int s = 0; s < nscen; s++) {
             if (slot[s] < 0) {
@@ -915,13 +954,13 @@ struct tsu_ctx {
                 for (const auto &b : boxes[s]) {
                     PatchDesc d = make_desc(lf, s, b[0] * r, b[1] * r, b[2] * r, b[3] * r);
                     renewed.push_back((int)P.size());
-                    auto f = same.find(key(s, d.i0, d.j0, d.nx, d.ny));
-                    if (f != same.end() && !kept[f->second]) {
-                        const PatchDesc &o = oldP[f->second];
+                    const int fo = same_ids[slot_of(key(s, d.i0, d.j0, d.nx, d.ny))];
+                    if (fo >= 0 && !kept[fo]) {
+                        const PatchDesc &o = oldP[fo];
                         if (o.i0 == d.i0 && o.j0 == d.j0 && o.nx == d.nx && o.ny == d.ny && o.scen == s) {
-                            kept[f->second] = 1;
+                            kept[fo] = 1;
                             d.off = o.off;
-                            P.push_back(d); blk.push_back(oldblk[f->second]); bytes.push_back(oldbytes[f->second]);
+                            P.push_back(d); blk.push_back(oldblk[fo]); bytes.push_back(oldbytes[fo]);
                             continue;
                         }
                     }
@@ -941,7 +980,8 @@ struct tsu_ctx {
         {
             std::vector<std::vector<int>> ids(nscen);
             for (int k = 0; k < (int)oldP.size(); k++) ids[oldP[k].scen].push_back(k);
-            std::vector<BoxIndex> oi(nscen);
+            oix_ws.resize(nscen);
+            std::vector<BoxIndex> &oi = oix_ws;
             for (int s = 0; s < nscen; s++)
                 if (slot[s] >= 0 && !ids[s].empty()) oi[s].build(oldP, ids[s], L.nxl, L.nyl);
             // fresh patches in contiguous ranges on the host pool, each range's ids

@@ -200,26 +200,6 @@ struct PinnedHost {
     }
 };
 
-struct Lvl {
-    std::vector<PatchDesc> P;
-    std::vector<size_t> blk, blkbytes;
-    std::vector<StepItem> items, items_y;   // patch update work items (items_y: FP32 split y kernel)
-    std::vector<int> nbrs, bclist, olds;
-    PinnedHost hcmap;   // coarse-patch maps of this level, built in page-locked memory for an async upload
-    cudaEvent_t cmap_ev = nullptr;   // recorded after that upload: hcmap is free again once it completes
-    DevBuf<PatchDesc> dP;
-    DevBuf<StepItem> dItems, dItemsY;
-    DevBuf<float> dScratch;                 // FP32 split update: Q* of every patch (3 fields each)
-    DevBuf<int> dNbrs, dCmap, dBc, dOlds, dList;
-    int cur = 0, maxring = 0, maxcells = 0;
-    int nxl = 0, nyl = 0;
-    double dx = 0, dy = 0, R = 1;
-    // latitude-longitude grids: physical equatorial cell sizes and the row tables
-    double dxp = 0, dyp = 0;
-    DevBuf<double> dKap, dCed;
-    DevBuf<float> dKapF, dCedF;
-};
-
 // Spatial buckets of one scenario's patches on one level, for neighbour and
 // covering-patch lookups while tables are rebuilt.
 struct BoxIndex {
@@ -276,6 +256,28 @@ struct BoxIndex {
     }
 };
 
+struct Lvl {
+    std::vector<PatchDesc> P;
+    std::vector<size_t> blk, blkbytes;
+    std::vector<StepItem> items, items_y;   // patch update work items (items_y: FP32 split y kernel)
+    std::vector<int> nbrs, bclist, olds;
+    std::vector<BoxIndex> idx;   // per scenario spatial index of P, rebuilt by every finish_level of the level
+    PinnedHost hcmap;   // coarse-patch maps of this level, built in page-locked memory for an async upload
+    cudaEvent_t cmap_ev = nullptr;   // recorded after that upload: hcmap is free again once it completes
+    DevBuf<PatchDesc> dP;
+    DevBuf<StepItem> dItems, dItemsY;
+    DevBuf<float> dScratch;                 // FP32 split update: Q* of every patch (3 fields each)
+    DevBuf<int> dNbrs, dCmap, dBc, dOlds, dList;
+    int cur = 0, maxring = 0, maxcells = 0;
+    int nxl = 0, nyl = 0;
+    double dx = 0, dy = 0, R = 1;
+    // latitude-longitude grids: physical equatorial cell sizes and the row tables
+    double dxp = 0, dyp = 0;
+    DevBuf<double> dKap, dCed;
+    DevBuf<float> dKapF, dCedF;
+};
+
+
 }  // namespace
 
 struct tsu_ctx {
@@ -317,7 +319,6 @@ struct tsu_ctx {
     long long launches = 0;
     long long viol_seen = 0;
     PinnedHost hflags;           // page-locked staging of the flag masks for clustering
-    std::vector<BoxIndex> bix_ws, cix_ws, oix_ws;   // spatial indices of the table rebuilds, reused
     std::vector<unsigned long long> same_keys;       // regrid: old boxes by key (open addressing)
     std::vector<int> same_ids;
     std::vector<std::vector<int32_t>> cws = std::vector<std::vector<int32_t>>(16);   // clustering workspaces
@@ -556,17 +557,16 @@ struct tsu_ctx {
             }
         }
         // per scenario spatial indices of this level and the coarser one
-        std::vector<std::vector<int>> ids(nscen), cids(nscen);
+        std::vector<std::vector<int>> ids(nscen);
         for (int k = 0; k < n; k++) ids[L.P[k].scen].push_back(k);
-        if (l > 0)
-            for (int k = 0; k < (int)lv[l - 1].P.size(); k++) cids[lv[l - 1].P[k].scen].push_back(k);
-        bix_ws.resize(nscen);
-        cix_ws.resize(nscen);
-        std::vector<BoxIndex> &bis = bix_ws, &cis = cix_ws;
+        // the coarser level's index was built by its own last finish_level (a
+        // coarser table never changes without one, before this level's)
+        L.idx.resize(nscen);
+        std::vector<BoxIndex> &bis = L.idx;
+        std::vector<BoxIndex> &cis = l > 0 ? lv[l - 1].idx : L.idx;
         for (int s = 0; s < nscen; s++) {
             if (ids[s].empty()) continue;
             bis[s].build(L.P, ids[s], L.nxl, L.nyl);
-            if (l > 0) cis[s].build(lv[l - 1].P, cids[s], lv[l - 1].nxl, lv[l - 1].nyl);
         }
         // patch k's tables in patch order: scenario by scenario, as the ids lists run
         std::vector<int> order;
@@ -980,10 +980,12 @@ struct tsu_ctx {
         {
             std::vector<std::vector<int>> ids(nscen);
             for (int k = 0; k < (int)oldP.size(); k++) ids[oldP[k].scen].push_back(k);
-            oix_ws.resize(nscen);
-            std::vector<BoxIndex> &oi = oix_ws;
+            // the old table's index, built by the level's last finish_level, now
+            // over the copy oldP of that table
+            std::vector<BoxIndex> &oi = L.idx;
+            oi.resize(nscen);
             for (int s = 0; s < nscen; s++)
-                if (slot[s] >= 0 && !ids[s].empty()) oi[s].build(oldP, ids[s], L.nxl, L.nyl);
+                if (slot[s] >= 0 && !ids[s].empty()) oi[s].P = &oldP;
             // fresh patches in contiguous ranges on the host pool, each range's ids
             // joined in patch order afterwards
             std::vector<std::vector<int>> ob(16);
@@ -1006,6 +1008,8 @@ struct tsu_ctx {
                 L.olds.insert(L.olds.end(), ob[q].begin(), ob[q].end());
             }
         }
+        for (auto &x : L.idx)   // no index may keep pointing at the old table's copy
+            if (x.P == &oldP) { x.P = nullptr; x.nbx = 0; x.nby = 0; }
         L.dOlds.upload(L.olds, st);
         finish_level(lf);
         if (!fresh.empty()) {

@@ -1131,6 +1131,54 @@ int k_pack_flags(const uint8_t *N, int nx, int i0, int j0, int w, int h, int ps,
     return (int)cudaGetLastError();
 }
 
+// Coarse maps of a level (levels >= 2): cell (mi, mj) of patch p's map holds
+// the coarse patch covering coarse cell (cmap_i0 + mi, cmap_j0 + mj), or -1.
+// The few coarse patches overlapping the footprint come as the patch's
+// candidate list; coarse patches of a scenario do not overlap, so the first
+// candidate containing the cell is the only one.  One block per patch.
+__global__ void fill_cmap_kernel(const PatchDesc *descs, const PatchDesc *cdescs, const int *cand, int npatch,
+                                 int *cmap)
+{
+    __shared__ int4 cb[32];
+    __shared__ int cid[32];
+    for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+        const PatchDesc P = descs[p];
+        const int nc = P.ccand_cnt < 32 ? P.ccand_cnt : 32;
+        __syncthreads();
+        for (int m = threadIdx.x; m < nc; m += blockDim.x) {
+            const int q = cand[P.ccand_off + m];
+            const PatchDesc &Q = cdescs[q];
+            cb[m] = make_int4(Q.i0, Q.j0, Q.i0 + Q.nx, Q.j0 + Q.ny);
+            cid[m] = q;
+        }
+        __syncthreads();
+        const int n = P.cmap_w * P.cmap_h;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            const int mj = c / P.cmap_w, mi = c - mj * P.cmap_w;
+            const int I = P.cmap_i0 + mi, J = P.cmap_j0 + mj;
+            int v = -1;
+            for (int m = 0; m < nc && v < 0; m++) {
+                const int4 b = cb[m];
+                if (I >= b.x && I < b.z && J >= b.y && J < b.w) v = cid[m];
+            }
+            for (int m = nc; m < P.ccand_cnt && v < 0; m++) {   // more candidates than staged
+                const int q = cand[P.ccand_off + m];
+                const PatchDesc &Q = cdescs[q];
+                if (I >= Q.i0 && I < Q.i0 + Q.nx && J >= Q.j0 && J < Q.j0 + Q.ny) v = q;
+            }
+            cmap[(size_t)P.cmap_off + c] = v;
+        }
+    }
+}
+
+int k_fill_cmap(const PatchDesc *descs, const PatchDesc *cdescs, const int *cand, int npatch, int *cmap, cudaStream_t st)
+{
+    if (npatch <= 0) return 0;
+    const int blocks = npatch < 152 * 16 ? npatch : 152 * 16;
+    fill_cmap_kernel<<<blocks, 128, 0, st>>>(descs, cdescs, cand, npatch, cmap);
+    return (int)cudaGetLastError();
+}
+
 int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st, const Win *W)
 {
     const Win w = W ? *W : Win{0, 0, nx, ny};

@@ -116,6 +116,8 @@ int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int 
 // bounding box (min i, min j, max i, max j) of the flagged cells of each plane
 // (within the window W, null: the whole plane); box preset to (nx, ny, -1, -1)
 int k_flag_bbox(const uint8_t *F, int nx, int ny, int nplanes, int *box, cudaStream_t st, const Win *W = nullptr);
+// coarse maps of a level's npatch patches from their coarse candidate lists
+int k_fill_cmap(const PatchDesc *descs, const PatchDesc *cdescs, const int *cand, int npatch, int *cmap, cudaStream_t st);
 // box (i0, j0, w, h) of the nx-wide byte plane N (bit 0 flag, bit 1 nestable)
 // packed 4 cells per byte, rows ps bytes apart (ps >= (w + 3) / 4)
 int k_pack_flags(const uint8_t *N, int nx, int i0, int j0, int w, int h, int ps, uint8_t *out, cudaStream_t st);

@@ -262,12 +262,11 @@ struct Lvl {
     std::vector<StepItem> items, items_y;   // patch update work items (items_y: FP32 split y kernel)
     std::vector<int> nbrs, bclist, olds;
     std::vector<BoxIndex> idx;   // per scenario spatial index of P, rebuilt by every finish_level of the level
-    PinnedHost hcmap;   // coarse-patch maps of this level, built in page-locked memory for an async upload
-    cudaEvent_t cmap_ev = nullptr;   // recorded after that upload: hcmap is free again once it completes
+    std::vector<int> ccand;   // coarse patches overlapping each patch's coarse-map footprint
     DevBuf<PatchDesc> dP;
     DevBuf<StepItem> dItems, dItemsY;
     DevBuf<float> dScratch;                 // FP32 split update: Q* of every patch (3 fields each)
-    DevBuf<int> dNbrs, dCmap, dBc, dOlds, dList;
+    DevBuf<int> dNbrs, dCmap, dCcand, dBc, dOlds, dList;
     int cur = 0, maxring = 0, maxcells = 0;
     int nxl = 0, nyl = 0;
     double dx = 0, dy = 0, R = 1;
@@ -585,20 +584,17 @@ struct tsu_ctx {
                 p.cmap_off = (int)tot;
                 tot += (size_t)p.cmap_w * p.cmap_h;
             }
-            // the last upload from this buffer must be done before it is rewritten
-            if (L.cmap_ev) CK(cudaEventSynchronize(L.cmap_ev));
-            L.hcmap.ensure(std::max<size_t>(tot, 1) * sizeof(int));
             cmap_n = tot;
         }
-        int *cmap = reinterpret_cast<int *>(L.hcmap.p);
-        // neighbour lists and coarse maps, patch ranges on host threads; each
-        // range's neighbour ids go to its own buffer, joined in order afterwards
-        std::vector<std::vector<int>> nb(16);
+        // neighbour lists and the coarse patches overlapping each coarse-map
+        // footprint, patch ranges on host threads; each range's ids go to its
+        // own buffers, joined in order afterwards (the device paints the maps)
+        std::vector<std::vector<int>> nb(16), cb(16);
         std::array<std::array<int, 2>, 16> rng{};
         parallel_ranges(n, [&](int q, int b, int e) {
             rng[q] = {b, e};
-            std::vector<int> tmp, ctmp;
-            std::vector<int> &out = nb[q];
+            std::vector<int> tmp;
+            std::vector<int> &out = nb[q], &cout_ = cb[q];
             for (int o = b; o < e; o++) {
                 const int k = order[o];
                 PatchDesc &p = L.P[k];
@@ -607,32 +603,32 @@ struct tsu_ctx {
                 p.nbr_cnt = 0;
                 for (int x : tmp)
                     if (x != k) { out.push_back(x); p.nbr_cnt++; }
+                p.ccand_off = (int)cout_.size();
+                p.ccand_cnt = 0;
                 if (l > 0) {
-                    // coarse patch of every coarse cell of the footprint (-1: none):
-                    // patches of one level and scenario do not overlap, so painting
-                    // the few overlapping ones gives each cell its unique patch
-                    const int ci0 = p.cmap_i0, cj0 = p.cmap_j0, cw = p.cmap_w;
-                    const int ci1 = ci0 + cw - 1, cj1 = cj0 + p.cmap_h - 1;
-                    const size_t base = (size_t)p.cmap_off;
-                    std::fill(cmap + base, cmap + base + (size_t)cw * p.cmap_h, -1);
-                    cis[p.scen].overlapping(ci0, cj0, ci1 + 1, cj1 + 1, ctmp);
-                    for (int x : ctmp) {
-                        const PatchDesc &c2 = lv[l - 1].P[x];
-                        const int ia = std::max(ci0, c2.i0), ib = std::min(ci1 + 1, c2.i0 + c2.nx);
-                        const int ja = std::max(cj0, c2.j0), jb = std::min(cj1 + 1, c2.j0 + c2.ny);
-                        for (int J = ja; J < jb; J++)
-                            for (int I = ia; I < ib; I++) cmap[base + (size_t)(J - cj0) * cw + (I - ci0)] = x;
-                    }
+                    cis[p.scen].overlapping(p.cmap_i0, p.cmap_j0, p.cmap_i0 + p.cmap_w, p.cmap_j0 + p.cmap_h, tmp);
+                    for (int x : tmp) { cout_.push_back(x); p.ccand_cnt++; }
                 }
             }
         });
         {
-            std::vector<int> shift(17, 0);
-            for (int q = 0; q < 16; q++) shift[q + 1] = shift[q] + (int)nb[q].size();
+            std::vector<int> shift(17, 0), cshift(17, 0);
+            for (int q = 0; q < 16; q++) {
+                shift[q + 1] = shift[q] + (int)nb[q].size();
+                cshift[q + 1] = cshift[q] + (int)cb[q].size();
+            }
             L.nbrs.reserve(shift[16]);
-            for (int q = 0; q < 16; q++) L.nbrs.insert(L.nbrs.end(), nb[q].begin(), nb[q].end());
+            L.ccand.clear();
+            L.ccand.reserve(cshift[16]);
+            for (int q = 0; q < 16; q++) {
+                L.nbrs.insert(L.nbrs.end(), nb[q].begin(), nb[q].end());
+                L.ccand.insert(L.ccand.end(), cb[q].begin(), cb[q].end());
+            }
             for (int q = 0; q < 16; q++)
-                for (int o = rng[q][0]; o < rng[q][1]; o++) L.P[order[o]].nbr_off += shift[q];
+                for (int o = rng[q][0]; o < rng[q][1]; o++) {
+                    L.P[order[o]].nbr_off += shift[q];
+                    L.P[order[o]].ccand_off += cshift[q];
+                }
         }
         if (split) L.dScratch.ensure(std::max<size_t>(soff, 64), st);
         L.dP.upload(L.P, st);
@@ -640,10 +636,10 @@ struct tsu_ctx {
         L.dItemsY.upload(L.items_y, st);
         L.dNbrs.upload(L.nbrs, st);
         if (l > 0) {
+            // the coarse table's device copy is current: its finish_level ran first
             L.dCmap.ensure(std::max<size_t>(cmap_n, 1), st);
-            if (cmap_n) CK(cudaMemcpyAsync(L.dCmap.p, cmap, cmap_n * sizeof(int), cudaMemcpyHostToDevice, st));
-            if (!L.cmap_ev) CK(cudaEventCreateWithFlags(&L.cmap_ev, cudaEventDisableTiming));
-            CK(cudaEventRecord(L.cmap_ev, st));
+            L.dCcand.upload(L.ccand, st);
+            kl(k_fill_cmap(L.dP.p, lv[l - 1].dP.p, L.dCcand.p, n, L.dCmap.p, st), "coarse maps");
         }
         L.dBc.upload(L.bclist, st);
         for (int s = 0; s < nscen; s++) cells_h[(size_t)s * kMaxLevels + l] = 0.0;
@@ -1644,11 +1640,10 @@ struct tsu_ctx {
         for (auto &e : stage_ev)
             if (e) cudaEventDestroy(e);
         for (auto &L : lv) {
-            L.dP.release(); L.dItems.release(); L.dNbrs.release(); L.dCmap.release(); L.dBc.release();
+            L.dP.release(); L.dItems.release(); L.dNbrs.release(); L.dCmap.release(); L.dCcand.release(); L.dBc.release();
             L.dOlds.release(); L.dList.release();
             L.dKap.release(); L.dCed.release(); L.dKapF.release(); L.dCedF.release();
             L.dItemsY.release(); L.dScratch.release();
-            if (L.cmap_ev) cudaEventDestroy(L.cmap_ev);
         }
         for (auto &g : grids) if (g.dev) cudaFreeAsync(g.dev, st);
         dGrids.release(); dGridScen.release(); dEtaIdx.release();

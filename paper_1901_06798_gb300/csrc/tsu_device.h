@@ -19,6 +19,7 @@ struct PatchDesc {
     int bcmask;         // 1 left, 2 right, 4 bottom, 8 top: ghost cells reach past that domain edge
     int nbr_off, nbr_cnt;      // same-level patches whose interior may feed this patch's ghosts
     int cmap_off, cmap_i0, cmap_j0, cmap_w, cmap_h;  // coarse-level patch index per coarse cell (levels >= 2)
+    int ccand_off, ccand_cnt;  // coarse patches overlapping the coarse map's footprint (the map's painters)
     int old_off, old_cnt;      // old same-level patches overlapping (regrid initialisation)
     long long soff;            // FP32 split update: element offset of the patch's Q* (3 fields of fs) in the scratch
 };

@@ -203,7 +203,7 @@ struct PinnedHost {
 // Spatial buckets of one scenario's patches on one level, for neighbour and
 // covering-patch lookups while tables are rebuilt.
 struct BoxIndex {
-    // patches bucketed by 64 x 64 cell tiles, in compressed rows: bucket k
+    // patches bucketed by bs x bs cell tiles, in compressed rows: bucket k
     // holds ids[start[k] .. start[k+1])
     int bs = 64, nbx = 0, nby = 0;
     std::vector<int> start, ids, fillv;   // kept between builds (no fresh pages per regrid)
@@ -211,6 +211,10 @@ struct BoxIndex {
     void build(const std::vector<PatchDesc> &Pv, const std::vector<int> &which, int nxl, int nyl)
     {
         P = &Pv;
+        // tiles of 64 cells, doubled until there are at most 2^14 of them: a
+        // build is linear in the tiles, a query in the patches per tile
+        bs = 64;
+        while ((size_t)((nxl + bs - 1) / bs) * (size_t)((nyl + bs - 1) / bs) > (1u << 14)) bs *= 2;
         nbx = (nxl + bs - 1) / bs;
         nby = (nyl + bs - 1) / bs;
         start.assign((size_t)nbx * nby + 1, 0);

@@ -991,7 +991,9 @@ int k_ghost_fill(int prec, const LevelView &L, const LevelView &C, int npatch, i
                  int ratio, double alpha, double drytol, int *err, cudaStream_t st)
 {
     if (npatch <= 0) return 0;
-    dim3 g = grid_for(maxring, npatch, 128);
+    // many patches: one CTA per patch (its neighbour boxes are staged once);
+    // few: their ghost rings spread over more CTAs
+    dim3 g = npatch >= 152 * 8 ? dim3(1, npatch) : grid_for(maxring, npatch, 128);
     TSU_DISPATCH(prec, ghost_fill_kernel, <<<g, 128, 0, st>>>(L, C, cur, cur_c, ratio, alpha, drytol, err));
     return (int)cudaGetLastError();
 }

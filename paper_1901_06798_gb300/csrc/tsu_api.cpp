@@ -187,10 +187,10 @@ struct PinnedHost {
     void ensure(size_t n)
     {
         if (n <= cap) return;
+        const size_t nc = std::max(n, cap + cap / 2);
         if (p) cudaFreeHost(p);
         p = nullptr;
         cap = 0;
-        const size_t nc = std::max(n, cap + cap / 2);
         CK(cudaMallocHost((void **)&p, nc));
         cap = nc;
     }
@@ -389,7 +389,6 @@ struct tsu_ctx {
     DevBuf<double> dstage;
     DevBuf<double> massParts;                  // per-block partial masses of tsu_get_stats
     PinnedHost hsmall;                         // page-locked readback of error flag, CFL counts, times
-    PinnedHost hstage;                         // page-locked double buffer of staged device-to-host reads
     cudaEvent_t stage_ev[8] = {};
     int device = 0;                            // the CUDA device current at tsu_create
 
@@ -1360,6 +1359,12 @@ struct tsu_ctx {
         }
         const size_t nch = (n + kChunk - 1) / kChunk;
         const int T = (int)std::min<size_t>(kWorkers, nch);
+        // one page-locked staging buffer for the process, kept between contexts
+        // (allocating it costs milliseconds); contexts on other threads take turns
+        static std::mutex stage_mu;
+        static PinnedHost *stage = new PinnedHost();   // never freed: outlives every context
+        std::lock_guard<std::mutex> lk(stage_mu);
+        PinnedHost &hstage = *stage;
         hstage.ensure((size_t)T * kChunk * sizeof(double));
         for (int w = 0; w < T; w++)
             if (!stage_ev[w]) CK(cudaEventCreateWithFlags(&stage_ev[w], cudaEventDisableTiming));
@@ -2032,6 +2037,15 @@ int tsu_read_field(tsu_ctx *ctx, int scen, int level, int field, double *dst, in
                                  L.cur, scen, field, ctx->dstage.p, nx, ny, x0, y0, dx, dy, ctx->c.x0, ctx->c.y0, L.dx,
                                  L.dy, ctx->st),
                     "read field");
+        }
+        // while the kernels run, host threads write the caller's pages once, so
+        // the copies below do not stop at first-touch page faults
+        if (n * sizeof(double) >= ((size_t)8 << 20)) {
+            const int T = tsu::HostPool::get().size();
+            tsu::HostPool::get().run(T, [&](int k) {
+                const size_t a = n * (size_t)k / T, b = n * (size_t)(k + 1) / T;
+                for (size_t i = a; i < b; i += 512) dst[i] = 0.0;   // one write per 4 KiB
+            });
         }
         ctx->d2h_staged(dst, ctx->dstage.p, n);
     });

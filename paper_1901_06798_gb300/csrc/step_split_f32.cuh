@@ -37,6 +37,9 @@ template <int NT, int RING, bool GEO, bool BULK = false>
 __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
 {
     using namespace x2;
+    // one warp per CTA: neighbours' values move by warp shuffles, and each thread
+    // reads only its own ring columns, so the row loop needs no block barrier
+    constexpr bool WARP = NT == 32 && !BULK;
     static_assert(RING >= 3, "the derived values of row k+1 need its copy complete at iteration k");
     constexpr int NC = 2 * NT;
     __shared__ __align__(16) float ring[RING][4][NC];
@@ -140,8 +143,13 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
         z.q0 = ld2(&ring[slot][0][c0]); z.hn = ld2(&ring[slot][1][c0]);
         z.ht = ld2(&ring[slot][2][c0]); z.B = ld2(&ring[slot][3][c0]);
         derive(z, sqrtg, drytol);
-        sDb[k & 1][0][t] = z.u.y; sDb[k & 1][1][t] = z.v.y; sDb[k & 1][2][t] = z.c.y; sDb[k & 1][3][t] = z.sq.y;
+        if (!WARP) {
+            sDb[k & 1][0][t] = z.u.y; sDb[k & 1][1][t] = z.v.y; sDb[k & 1][2][t] = z.c.y; sDb[k & 1][3][t] = z.sq.y;
+        }
     };
+    // from the thread on the left (lane 0: its own value), on the right (lane 31: its own)
+    auto from_left = [](float v) { return __shfl_up_sync(0xffffffffu, v, 1); };
+    auto from_right = [](float v) { return __shfl_down_sync(0xffffffffu, v, 1); };
 
 #pragma unroll
     for (int k = 0; k < RING - 1; k++) prefetch(k);
@@ -159,7 +167,7 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
     for (int k = 0; k < nrows; k++) {
         prefetch(k + RING - 1);
         await_row(k + 1);
-        __syncthreads();
+        if (!WARP) __syncthreads();
         const int slot = k % RING;
         const int j = y0 + k;
         const bool rowint = j >= 0 && j < P.ny;
@@ -172,49 +180,90 @@ __global__ void __launch_bounds__(NT) step_x_f32x2(StepArgs a)
 
         // ---- x edges 2t (cells 2t-1 | 2t) and 2t+1 (cells 2t | 2t+1)
         C2 L;
-        L.q0 = make_float2(ring[slot][0][c0 > 0 ? c0 - 1 : 0], xc.q0.x);
-        L.hn = make_float2(ring[slot][1][c0 > 0 ? c0 - 1 : 0], xc.hn.x);
-        L.ht = make_float2(ring[slot][2][c0 > 0 ? c0 - 1 : 0], xc.ht.x);
-        L.B = make_float2(ring[slot][3][c0 > 0 ? c0 - 1 : 0], xc.B.x);
+        if (WARP) {   // the left cell is the left thread's lane y
+            L.q0 = make_float2(from_left(xc.q0.y), xc.q0.x);
+            L.hn = make_float2(from_left(xc.hn.y), xc.hn.x);
+            L.ht = make_float2(from_left(xc.ht.y), xc.ht.x);
+            L.B = make_float2(from_left(xc.B.y), xc.B.x);
+            L.u = make_float2(from_left(xc.u.y), xc.u.x); L.v = make_float2(from_left(xc.v.y), xc.v.x);
+            L.c = make_float2(from_left(xc.c.y), xc.c.x); L.sq = make_float2(from_left(xc.sq.y), xc.sq.x);
+        } else {
+            L.q0 = make_float2(ring[slot][0][c0 > 0 ? c0 - 1 : 0], xc.q0.x);
+            L.hn = make_float2(ring[slot][1][c0 > 0 ? c0 - 1 : 0], xc.hn.x);
+            L.ht = make_float2(ring[slot][2][c0 > 0 ? c0 - 1 : 0], xc.ht.x);
+            L.B = make_float2(ring[slot][3][c0 > 0 ? c0 - 1 : 0], xc.B.x);
+            L.u = make_float2(sDb[k & 1][0][tl], xc.u.x); L.v = make_float2(sDb[k & 1][1][tl], xc.v.x);
+            L.c = make_float2(sDb[k & 1][2][tl], xc.c.x); L.sq = make_float2(sDb[k & 1][3][tl], xc.sq.x);
+        }
         L.h = sub(L.q0, L.B);
         L.wx = L.h.x >= drytol; L.wy = xc.wx;
-        L.u = make_float2(sDb[k & 1][0][tl], xc.u.x); L.v = make_float2(sDb[k & 1][1][tl], xc.v.x);
-        L.c = make_float2(sDb[k & 1][2][tl], xc.c.x); L.sq = make_float2(sDb[k & 1][3][tl], xc.sq.x);
         W2 xw;
         riemann2(g, L, xc, xw);
-        sZx[0][t] = xw.z0m.x; sZx[1][t] = xw.z0n.x; sZx[2][t] = xw.z0t.x; sZx[3][t] = xw.z1t.x;
-        sZx[4][t] = xw.z2m.x; sZx[5][t] = xw.z2n.x; sZx[6][t] = xw.z2t.x;
-        sZy[0][t] = xw.z0m.y; sZy[1][t] = xw.z0n.y; sZy[2][t] = xw.z0t.y; sZy[3][t] = xw.z1t.y;
-        sZy[4][t] = xw.z2m.y; sZy[5][t] = xw.z2n.y; sZy[6][t] = xw.z2t.y;
-        __syncthreads();
+        if (!WARP) {
+            sZx[0][t] = xw.z0m.x; sZx[1][t] = xw.z0n.x; sZx[2][t] = xw.z0t.x; sZx[3][t] = xw.z1t.x;
+            sZx[4][t] = xw.z2m.x; sZx[5][t] = xw.z2n.x; sZx[6][t] = xw.z2t.x;
+            sZy[0][t] = xw.z0m.y; sZy[1][t] = xw.z0n.y; sZy[2][t] = xw.z0t.y; sZy[3][t] = xw.z1t.y;
+            sZy[4][t] = xw.z2m.y; sZy[5][t] = xw.z2n.y; sZy[6][t] = xw.z2t.y;
+            __syncthreads();
+        }
 
         // ---- limit both edges (upwind neighbours as in the fused kernel)
         float2 xam[3], xap[3], xF[3];
+        float sPr[3];   // WARP: A-dQ + F~ of the right thread's edge 2t + 2
         {
             I2 I;
-            const int a0 = xw.s0.x >= 0.0f ? tl : t, a1 = xw.s1.x >= 0.0f ? tl : t, a2 = xw.s2.x >= 0.0f ? tl : t;
-            const int b0 = xw.s0.y >= 0.0f ? t : tr, b1 = xw.s1.y >= 0.0f ? t : tr, b2 = xw.s2.y >= 0.0f ? t : tr;
-            I.m0 = make_float2(sZy[0][a0], sZx[0][b0]);
-            I.n0 = make_float2(sZy[1][a0], sZx[1][b0]);
-            I.t0 = make_float2(sZy[2][a0], sZx[2][b0]);
-            I.t1 = make_float2(sZy[3][a1], sZx[3][b1]);
-            I.m2 = make_float2(sZy[4][a2], sZx[4][b2]);
-            I.n2 = make_float2(sZy[5][a2], sZx[5][b2]);
-            I.t2 = make_float2(sZy[6][a2], sZx[6][b2]);
+            if (WARP) {
+                // upwind of edge 2t: 2t-1 (left thread's lane y) or 2t+1 (own lane y);
+                // of edge 2t+1: 2t (own lane x) or 2t+2 (right thread's lane x)
+                const bool a0 = xw.s0.x >= 0.0f, a1 = xw.s1.x >= 0.0f, a2 = xw.s2.x >= 0.0f;
+                const bool b0 = xw.s0.y >= 0.0f, b1 = xw.s1.y >= 0.0f, b2 = xw.s2.y >= 0.0f;
+                const float l0 = from_left(xw.z0m.y), l1 = from_left(xw.z0n.y), l2 = from_left(xw.z0t.y);
+                const float l3 = from_left(xw.z1t.y), l4 = from_left(xw.z2m.y), l5 = from_left(xw.z2n.y);
+                const float l6 = from_left(xw.z2t.y);
+                const float r0_ = from_right(xw.z0m.x), r1_ = from_right(xw.z0n.x), r2_ = from_right(xw.z0t.x);
+                const float r3_ = from_right(xw.z1t.x), r4_ = from_right(xw.z2m.x), r5_ = from_right(xw.z2n.x);
+                const float r6_ = from_right(xw.z2t.x);
+                I.m0 = make_float2(a0 ? l0 : xw.z0m.y, b0 ? xw.z0m.x : r0_);
+                I.n0 = make_float2(a0 ? l1 : xw.z0n.y, b0 ? xw.z0n.x : r1_);
+                I.t0 = make_float2(a0 ? l2 : xw.z0t.y, b0 ? xw.z0t.x : r2_);
+                I.t1 = make_float2(a1 ? l3 : xw.z1t.y, b1 ? xw.z1t.x : r3_);
+                I.m2 = make_float2(a2 ? l4 : xw.z2m.y, b2 ? xw.z2m.x : r4_);
+                I.n2 = make_float2(a2 ? l5 : xw.z2n.y, b2 ? xw.z2n.x : r5_);
+                I.t2 = make_float2(a2 ? l6 : xw.z2t.y, b2 ? xw.z2t.x : r6_);
+            } else {
+                const int a0 = xw.s0.x >= 0.0f ? tl : t, a1 = xw.s1.x >= 0.0f ? tl : t, a2 = xw.s2.x >= 0.0f ? tl : t;
+                const int b0 = xw.s0.y >= 0.0f ? t : tr, b1 = xw.s1.y >= 0.0f ? t : tr, b2 = xw.s2.y >= 0.0f ? t : tr;
+                I.m0 = make_float2(sZy[0][a0], sZx[0][b0]);
+                I.n0 = make_float2(sZy[1][a0], sZx[1][b0]);
+                I.t0 = make_float2(sZy[2][a0], sZx[2][b0]);
+                I.t1 = make_float2(sZy[3][a1], sZx[3][b1]);
+                I.m2 = make_float2(sZy[4][a2], sZx[4][b2]);
+                I.n2 = make_float2(sZy[5][a2], sZx[5][b2]);
+                I.t2 = make_float2(sZy[6][a2], sZx[6][b2]);
+            }
             limit2(xw, I, dtdxr, xam, xap, xF);
-            sP[0][t] = xam[0].x + xF[0].x; sP[1][t] = xam[1].x + xF[1].x; sP[2][t] = xam[2].x + xF[2].x;
+            if (WARP) {
+#pragma unroll
+                for (int m = 0; m < 3; m++) sPr[m] = from_right(xam[m].x + xF[m].x);
+            } else {
+                sP[0][t] = xam[0].x + xF[0].x; sP[1][t] = xam[1].x + xF[1].x; sP[2][t] = xam[2].x + xF[2].x;
+            }
             if (rowint) {
                 if (limx) smx = fmaxf(smx, fmaxf(-xw.s0.x, xw.s2.x) * rk);
                 if (limy) smx = fmaxf(smx, fmaxf(-xw.s0.y, xw.s2.y) * rk);
             }
         }
-        __syncthreads();
+        if (!WARP) {
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < 3; m++) sPr[m] = sP[m][tr];
+        }
 
         if (upd) {
             float2 q0 = xc.q0, q1 = xc.hn, q2 = xc.ht;
-            const float2 r0 = make_float2(xam[0].y + xF[0].y, sP[0][tr]);
-            const float2 r1 = make_float2(xam[1].y + xF[1].y, sP[1][tr]);
-            const float2 r2 = make_float2(xam[2].y + xF[2].y, sP[2][tr]);
+            const float2 r0 = make_float2(xam[0].y + xF[0].y, sPr[0]);
+            const float2 r1 = make_float2(xam[1].y + xF[1].y, sPr[1]);
+            const float2 r2 = make_float2(xam[2].y + xF[2].y, sPr[2]);
             q0 = fnma(dtdxr, add(sub(xap[0], xF[0]), r0), q0);
             q1 = fnma(dtdxr, add(sub(xap[1], xF[1]), r1), q1);
             q2 = fnma(dtdxr, add(sub(xap[2], xF[2]), r2), q2);

@@ -398,7 +398,7 @@ struct tsu_ctx {
     int nt() const
     {
         if (step_nt > 0) return step_nt;
-        return prec == TSU_F64 ? step_threads_f64() : (split_f32() ? 64 : step_threads_f32p());
+        return prec == TSU_F64 ? step_threads_f64() : (split_f32() ? 32 : step_threads_f32p());
     }
     // physical cell sizes of level l (of an equatorial cell on latitude-longitude grids)
     double pdx(int l) const { return c.spherical ? lv[l].dxp : lv[l].dx; }

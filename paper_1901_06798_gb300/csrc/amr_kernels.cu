@@ -516,17 +516,35 @@ __global__ void flag_kernel(LevelView L, int cur, FlagArgs fa)
         int i = c % P.nx, j = c / P.nx;
         int I = P.i0 + i, J = P.j0 + j;
         long long k = a.idx(i, j);
-        double B = (double)a.Bp()[k];
-        double q0 = (double)a.f(cur, 0)[k];
-        double h = PERT ? q0 - B : q0;
-        double eta = PERT ? q0 : h + B;
         int f = 0;
-        if (fa.eta_tol > 0.0 && h >= fa.drytol && fabs(eta) > fa.eta_tol) f = 1;
-        if (fa.depth_below > 0.0 && -B < fa.depth_below) f = 1;
-        double x = fa.x0 + ((double)I + 0.5) * fa.dxl, y = fa.y0 + ((double)J + 0.5) * fa.dyl;
-        for (int rg = 0; rg < fa.n_regions; rg++) {
-            const double *R = fa.regions + 6 * rg;
-            if (x >= R[0] && x <= R[2] && y >= R[1] && y <= R[3] && (double)fa.newlev <= R[4]) f = 1;
+        if (PERT) {
+            // the FP64 tests below decided in FP32: a float exceeds a double t
+            // exactly when it exceeds the largest float <= t; the depth eta' - B,
+            // rounded in FP32, decides unless it lies within rounding of drytol,
+            // where the exact FP64 difference does
+            const float qf = (float)a.f(cur, 0)[k], Bf = (float)a.Bp()[k];
+            if (fa.eta_tol > 0.0 && fabsf(qf) > fa.eta_tol_f) {
+                const float hf = qf - Bf;
+                bool wet;
+                if (fa.drytol_f > 0.0f && hf > fa.drytol_f * 1.000001f) wet = true;
+                else if (fa.drytol_f > 0.0f && hf < fa.drytol_f * 0.999999f) wet = false;
+                else wet = (double)qf - (double)Bf >= fa.drytol;
+                if (wet) f = 1;
+            }
+            if (fa.depth_below > 0.0 && Bf > fa.depth_neg_f) f = 1;
+        } else {
+            double B = (double)a.Bp()[k];
+            double h = (double)a.f(cur, 0)[k];
+            double eta = h + B;
+            if (fa.eta_tol > 0.0 && h >= fa.drytol && fabs(eta) > fa.eta_tol) f = 1;
+            if (fa.depth_below > 0.0 && -B < fa.depth_below) f = 1;
+        }
+        if (fa.n_regions > 0) {
+            double x = fa.x0 + ((double)I + 0.5) * fa.dxl, y = fa.y0 + ((double)J + 0.5) * fa.dyl;
+            for (int rg = 0; rg < fa.n_regions; rg++) {
+                const double *R = fa.regions + 6 * rg;
+                if (x >= R[0] && x <= R[2] && y >= R[1] && y <= R[3] && (double)fa.newlev <= R[4]) f = 1;
+            }
         }
         long long gk = (long long)J * L.nxl + I;
         raw[gk] = (uint8_t)f;
@@ -559,13 +577,30 @@ __global__ void dilate_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, 
     }
 }
 
-// region caps and proper nesting: F &= N, N = every cell within 2 covered or
-// outside; over the window W of plane blockIdx.y
-__global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, FlagArgs fa, Win W)
+// Proper nesting, separable: E(I, J) = every in-domain cell within 2 of I in row J
+// is covered (the x pass, over the rows within 2 of the window W) ...
+__global__ void erode_x_kernel(const uint8_t *cov, uint8_t *E, int nx, int ny, Win W)
 {
     const int ncb = (W.w + blockDim.x - 1) / blockDim.x;
     const size_t pl = (size_t)blockIdx.y * nx * ny;
-    const uint8_t *cv = cov + pl;
+    for (int rb = blockIdx.x; rb < W.h * ncb; rb += gridDim.x) {
+        const int jr = rb / ncb, ir = (rb - jr * ncb) * blockDim.x + threadIdx.x;
+        if (ir >= W.w) continue;
+        const int J = W.j0 + jr, I = W.i0 + ir;
+        const uint8_t *r = cov + pl + (size_t)J * nx;
+        uint8_t ok = 1;
+        for (int a2 = max(I - 2, 0); a2 <= min(I + 2, nx - 1) && ok; a2++) ok = r[a2] ? 1 : 0;
+        E[pl + (size_t)J * nx + I] = ok;
+    }
+}
+
+// ... then over W: N = every in-domain cell within 2 is covered (E of the rows
+// within 2), region caps and F &= N
+__global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *E, int nx, int ny, FlagArgs fa, Win W)
+{
+    const int ncb = (W.w + blockDim.x - 1) / blockDim.x;
+    const size_t pl = (size_t)blockIdx.y * nx * ny;
+    const uint8_t *ep = E + pl;
     for (int rb = blockIdx.x; rb < W.h * ncb; rb += gridDim.x) {
         const int jr = rb / ncb, ir = (rb - jr * ncb) * blockDim.x + threadIdx.x;
         if (ir >= W.w) continue;
@@ -580,11 +615,7 @@ __global__ void nest_kernel(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, 
             }
         }
         int ok = 1;
-        for (int b2 = max(J - 2, 0); b2 <= min(J + 2, ny - 1) && ok; b2++) {
-            const uint8_t *r = cv + (size_t)b2 * nx;
-            for (int a2 = max(I - 2, 0); a2 <= min(I + 2, nx - 1); a2++)
-                if (!r[a2]) { ok = 0; break; }
-        }
+        for (int b2 = max(J - 2, 0); b2 <= min(J + 2, ny - 1) && ok; b2++) ok = ep[(size_t)b2 * nx + I] ? 1 : 0;
         // N: bit 0 the final flag, bit 1 nestable -- the one plane the host clusters
         const uint8_t ff = ok ? f : 0;
         N[c] = (uint8_t)((ok << 1) | (ff ? 1 : 0));
@@ -1064,13 +1095,18 @@ int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int 
     return (int)cudaGetLastError();
 }
 
-int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa, const Win &W,
-           cudaStream_t st)
+int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, uint8_t *tmp, int nx, int ny, int nplanes, const FlagArgs &fa,
+           const Win &W, cudaStream_t st)
 {
     if (nplanes <= 0 || W.w <= 0 || W.h <= 0) return 0;
-    const long long rows = (long long)W.h * ((W.w + 255) / 256);
-    const int blocks = (int)std::min<long long>(rows, 152LL * 16);
-    nest_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(F, N, cov, nx, ny, fa, W);
+    const int ja = std::max(0, W.j0 - 2), jb = std::min(ny, W.j0 + W.h + 2);
+    const Win Wx{W.i0, ja, W.w, jb - ja};
+    long long rows = (long long)Wx.h * ((W.w + 255) / 256);
+    int blocks = (int)std::min<long long>(rows, 152LL * 16);
+    erode_x_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(cov, tmp, nx, ny, Wx);
+    rows = (long long)W.h * ((W.w + 255) / 256);
+    blocks = (int)std::min<long long>(rows, 152LL * 16);
+    nest_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(F, N, tmp, nx, ny, fa, W);
     return (int)cudaGetLastError();
 }
 

@@ -64,6 +64,8 @@ struct FlagArgs {
     uint8_t *raw, *cov;
     const int *scen_slot;        // plane of each scenario or -1
     double eta_tol, depth_below, drytol;
+    // FP32 state: the largest floats <= eta_tol and <= -depth_below, and drytol in FP32
+    float eta_tol_f, depth_neg_f, drytol_f;
     double x0, y0, dxl, dyl;
     int n_regions, newlev;
     double regions[6 * kMaxLevels];
@@ -121,8 +123,9 @@ int k_fill_cmap(const PatchDesc *descs, const PatchDesc *cdescs, const int *cand
 // box (i0, j0, w, h) of the nx-wide byte plane N (bit 0 flag, bit 1 nestable)
 // packed 4 cells per byte, rows ps bytes apart (ps >= (w + 3) / 4)
 int k_pack_flags(const uint8_t *N, int nx, int i0, int j0, int w, int h, int ps, uint8_t *out, cudaStream_t st);
-int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, int nx, int ny, int nplanes, const FlagArgs &fa, const Win &W,
-           cudaStream_t st);
+// proper nesting over the window W (tmp: a plane set of scratch, the x pass of the erosion)
+int k_nest(uint8_t *F, uint8_t *N, const uint8_t *cov, uint8_t *tmp, int nx, int ny, int nplanes, const FlagArgs &fa,
+           const Win &W, cudaStream_t st);
 // count of interior cells with a negative depth over a level's patches (into *count)
 int k_depth_check(int prec, const LevelView &L, int npatch, int maxcells, int cur, int *count, cudaStream_t st);
 int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int maxcells, int cur, double g,

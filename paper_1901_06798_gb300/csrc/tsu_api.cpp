@@ -53,6 +53,14 @@ struct Err : std::runtime_error {
 
 int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// the largest float <= t: a float x exceeds t exactly when x exceeds it
+float float_at_most(double t)
+{
+    float f = (float)t;
+    if ((double)f > t) f = std::nextafter(f, -std::numeric_limits<float>::infinity());
+    return f;
+}
+
 // f(q, begin, end) over contiguous ranges of [0, n), ranges in order q = 0, 1, ..;
 // on the host pool (up to 16 threads) when n is large enough to pay for it
 template <typename F> void parallel_ranges(int n, F &&f)
@@ -817,6 +825,9 @@ struct tsu_ctx {
             FlagArgs fa{};
             fa.raw = fraw.p; fa.cov = fcov.p; fa.scen_slot = fslot.p;
             fa.eta_tol = c.flag_eta_tol; fa.depth_below = c.flag_depth_below; fa.drytol = c.drytol;
+            fa.eta_tol_f = float_at_most(c.flag_eta_tol);
+            fa.depth_neg_f = float_at_most(-c.flag_depth_below);
+            fa.drytol_f = (float)c.drytol;
             fa.x0 = c.x0; fa.y0 = c.y0; fa.dxl = C.dx; fa.dyl = C.dy;
             fa.n_regions = c.n_regions; fa.newlev = l + 2;
             for (int k = 0; k < c.n_regions; k++)
@@ -843,7 +854,7 @@ struct tsu_ctx {
             const Win Wx{wi0, xj0, W.w, std::max(0, xj1 - xj0)};
             kl(k_dilate(fraw.p, ftmp.p, nx, ny, np, b, 0, Wx, st), "dilate x");
             kl(k_dilate(ftmp.p, fF.p, nx, ny, np, b, 1, W, st), "dilate y");
-            kl(k_nest(fF.p, fN.p, fcov.p, nx, ny, np, fa, W, st), "nest");
+            kl(k_nest(fF.p, fN.p, fcov.p, ftmp.p, nx, ny, np, fa, W, st), "nest");   // ftmp is free again
             // only the flags' bounding box of each plane comes to the host (the
             // clustering starts from that box, so the boxes are the same)
             std::vector<int> bb(4 * (size_t)np);
@@ -2245,6 +2256,9 @@ int tsu_cnn_features(tsu_ctx *ctx, int scen, int level, float *features, unsigne
         FlagArgs fa{};
         fa.raw = ctx->fraw.p; fa.cov = ctx->fcov.p; fa.scen_slot = ctx->fslot.p;
         fa.eta_tol = ctx->c.flag_eta_tol; fa.depth_below = ctx->c.flag_depth_below; fa.drytol = ctx->c.drytol;
+        fa.eta_tol_f = float_at_most(ctx->c.flag_eta_tol);
+        fa.depth_neg_f = float_at_most(-ctx->c.flag_depth_below);
+        fa.drytol_f = (float)ctx->c.drytol;
         fa.x0 = ctx->c.x0; fa.y0 = ctx->c.y0; fa.dxl = C.dx; fa.dyl = C.dy;
         fa.n_regions = ctx->c.n_regions; fa.newlev = level + 1;
         for (int k = 0; k < ctx->c.n_regions; k++)

@@ -552,28 +552,63 @@ __global__ void flag_kernel(LevelView L, int cur, FlagArgs fa)
     }
 }
 
-// Chebyshev dilation, separable: dir 0 dilates along x, dir 1 along y, over the
-// window W = (wi0, wj0, ww, wh) of each plane.  Blocks walk (row, 256-column
-// segment) pairs of W in plane blockIdx.y: 32-bit indices, and a thread's
-// neighbours along x are its warp's cells (coalesced, cached).
-__global__ void dilate_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, int b, int dir, Win W)
+// Chebyshev dilation, separable, over the window W = (wi0, wj0, ww, wh) of each
+// plane (plane blockIdx.y).
+//   dir 0 (along x): a warp holds 32 consecutive cells of a row; its lanes'
+//     flags, and those of the b cells on either side, form one 64-bit mask
+//     (warp ballots), and a cell is set when any of the 2b + 1 bits around it
+//     is (b <= 16; larger b reads the cells one by one).
+//   dir 1 (along y): a thread walks down a column segment keeping the count of
+//     set cells among rows J - b .. J + b: two reads per cell.
+__global__ void dilate_x_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, int b, Win W)
 {
     const int ncb = (W.w + blockDim.x - 1) / blockDim.x;
     const size_t pl = (size_t)blockIdx.y * nx * ny;
     const uint8_t *s = src + pl;
     uint8_t *d = dst + pl;
-    for (int rb = blockIdx.x; rb < W.h * ncb; rb += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int rb = blockIdx.x; rb < W.h * ncb; rb += gridDim.x) {   // uniform over the block
         const int jr = rb / ncb, ir = (rb - jr * ncb) * blockDim.x + threadIdx.x;
-        if (ir >= W.w) continue;
         const int J = W.j0 + jr, I = W.i0 + ir;
+        const uint8_t *r = s + (size_t)J * nx;
         uint8_t v = 0;
-        if (dir == 0) {
-            const uint8_t *r = s + (size_t)J * nx;
+        if (b <= 16) {
+            const int I0 = I - lane;   // the warp's first cell
+            const bool own = I < nx && r[I] != 0;
+            const int il = I0 - b + lane, irr = I0 + 32 + (lane - (32 - b));
+            const bool left = lane < b && il >= 0 && r[il] != 0;
+            const bool right = lane >= 32 - b && irr < nx && r[irr] != 0;
+            const unsigned mo = __ballot_sync(0xffffffffu, own);
+            const unsigned ml = __ballot_sync(0xffffffffu, left) & ((1u << b) - 1u);
+            const unsigned mr = b > 0 ? (__ballot_sync(0xffffffffu, right) >> (32 - b)) : 0u;
+            const unsigned long long m = (unsigned long long)ml | ((unsigned long long)mo << b) |
+                                         ((unsigned long long)mr << (32 + b));
+            const unsigned long long win = (2ull << (2 * b)) - 1ull;   // 2b + 1 bits
+            v = ((m >> lane) & win) != 0ull;
+        } else if (ir < W.w) {
             for (int a = max(I - b, 0); a <= min(I + b, nx - 1) && !v; a++) v = r[a];
-        } else {
-            for (int a = max(J - b, 0); a <= min(J + b, ny - 1) && !v; a++) v = s[(size_t)a * nx + I];
         }
-        d[(size_t)J * nx + I] = v ? 1 : 0;
+        if (ir < W.w) d[(size_t)J * nx + I] = v ? 1 : 0;
+    }
+}
+
+__global__ void dilate_y_kernel(const uint8_t *src, uint8_t *dst, int nx, int ny, int b, Win W, int seg)
+{
+    const size_t pl = (size_t)blockIdx.y * nx * ny;
+    const uint8_t *s = src + pl;
+    uint8_t *d = dst + pl;
+    const int ncb = (W.w + blockDim.x - 1) / blockDim.x, nseg = (W.h + seg - 1) / seg;
+    for (int q = blockIdx.x; q < ncb * nseg; q += gridDim.x) {
+        const int sg = q / ncb, ir = (q - sg * ncb) * blockDim.x + threadIdx.x;
+        if (ir >= W.w) continue;
+        const int I = W.i0 + ir, ja = W.j0 + sg * seg, jb = min(W.j0 + W.h, ja + seg);
+        int cnt = 0;   // set cells among rows J - b .. J + b (inside the plane)
+        for (int a = max(ja - b, 0); a <= min(ja + b, ny - 1); a++) cnt += s[(size_t)a * nx + I] ? 1 : 0;
+        for (int J = ja; J < jb; J++) {
+            d[(size_t)J * nx + I] = cnt > 0 ? 1 : 0;
+            if (J - b >= 0) cnt -= s[(size_t)(J - b) * nx + I] ? 1 : 0;
+            if (J + b + 1 < ny) cnt += s[(size_t)(J + b + 1) * nx + I] ? 1 : 0;
+        }
     }
 }
 
@@ -1089,9 +1124,16 @@ int k_dilate(const uint8_t *src, uint8_t *dst, int nx, int ny, int nplanes, int 
              cudaStream_t st)
 {
     if (nplanes <= 0 || W.w <= 0 || W.h <= 0) return 0;
-    const long long rows = (long long)W.h * ((W.w + 255) / 256);
-    const int blocks = (int)std::min<long long>(rows, 152LL * 16);
-    dilate_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(src, dst, nx, ny, b, dir, W);
+    if (dir == 0) {
+        const long long rows = (long long)W.h * ((W.w + 255) / 256);
+        const int blocks = (int)std::min<long long>(rows, 152LL * 16);
+        dilate_x_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(src, dst, nx, ny, b, W);
+    } else {
+        constexpr int kSeg = 64;   // rows per column segment
+        const long long items = (long long)((W.h + kSeg - 1) / kSeg) * ((W.w + 255) / 256);
+        const int blocks = (int)std::min<long long>(items, 152LL * 16);
+        dilate_y_kernel<<<dim3(blocks, nplanes), 256, 0, st>>>(src, dst, nx, ny, b, W, kSeg);
+    }
     return (int)cudaGetLastError();
 }
 

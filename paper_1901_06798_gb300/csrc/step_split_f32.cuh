@@ -4,27 +4,30 @@
 // step_x_f32x2: one CTA per strip of 2 NT - 4 columns and a segment of rows,
 //   ghost rows included (Q* is needed there by the y sweep).  Rows stream
 //   through a cp.async ring as in the fused kernel, two columns per thread on
-//   the paired FP32 instructions, x-edge waves exchanged in shared memory.  A
-//   row needs no other row, so segments carry no halo rows.  It writes Q* of
-//   its interior columns and reduces the max x wave speed of interior rows.
+//   the paired FP32 instructions.  With one warp per CTA (NT = 32, the default)
+//   the neighbours' x-edge values move by warp shuffles and the row loop has
+//   no block barrier; wider CTAs exchange them in shared memory.  A row needs
+//   no other row, so segments carry no halo rows.  It writes Q* of its
+//   interior columns and reduces the max x wave speed of interior rows.
 //   BULK: one thread copies each field's row segment into the ring with a bulk
 //   copy (cp.async.bulk) that completes on the slot's mbarrier, which every
 //   thread polls with a bounded budget (patch rows start 16-byte aligned, the
 //   pitch is a multiple of 4 floats and strips start at multiples of 4
 //   columns).  Measured slower than the per-thread copies; kept as an option.
-// step_y_f32x2: one CTA of 32 threads per strip of 64 columns (two per
+// step_y_f32x2: one CTA of 64 threads per strip of 64 columns (one per
 //   thread) and a segment of interior rows; reads Q* and B of the segment plus
-//   two rows above and below, runs the y sweep of its columns in registers
-//   (no halo columns, no barriers) and writes Q^{n+1}.  Each thread streams
-//   its own two columns through a cp.async ring in shared memory, YRING - 1
-//   rows ahead, so the loads' latency hides behind the rows in flight.
+//   two rows above and below, runs the y sweep of its column in registers, two
+//   rows per iteration on the paired instructions (no halo columns, no
+//   barriers), and writes Q^{n+1}.  Each thread streams its own column through
+//   a cp.async ring in shared memory, two row pairs ahead, so the loads'
+//   latency hides behind the rows in flight.
 //
 // Against the fused kernel (step_f32x2.cuh) the split pays 24 B per cell more
 // HBM traffic (Q* out and back in), which the 4096^2 update has room for: the
 // fused kernel is bound by instruction issue and latency.  What the split
 // saves is the recomputed halo work (4 rows per row segment, 4 columns per
 // y strip) and the register pressure of carrying both sweeps: the x kernel
-// runs at about 84 registers (24 warps per SM) instead of 168 (12).  The
+// runs at about 82 registers and the y kernel at 124 instead of 168.  The
 // arithmetic per cell is the fused kernel's, operation for operation, so the
 // two give the same bits.  GEO: latitude-longitude grid in capacity form, as
 // in the fused kernel.

@@ -163,15 +163,17 @@ __device__ bool interp_fine(const LevelView &C, int cur_c, const int *cmap, cons
 
 // ---------------------------------------------------------------- ghost fill
 
-template <typename T, bool PERT>
-__global__ void ghost_fill_kernel(LevelView L, LevelView C, int cur, int cur_c, int ratio, double alpha, double drytol,
-                                  int *err)
+// The source of every ghost cell of a patch (one CTA row per patch): a
+// same-level neighbour whose interior holds the cell, else the coarser level
+// (space-time interpolation), else none (a tiling error on the coarsest
+// level).  Same-level patches do not overlap, so the source is unique.  The
+// interpolated cells also go to a compact list (in no particular order: each
+// is computed on its own).  Runs once per patch table; the fills gather.
+__global__ void ghost_map_kernel(LevelView L, GhostSrc *gmap, int2 *ilist, int *icount, int ratio)
 {
     const PatchDesc P = L.descs[blockIdx.y];
     const int n = ring_count(P);
-    Acc<T> a = acc<T>(L.arena, P);
-    T *q0 = a.f(cur, 0), *q1 = a.f(cur, 1), *q2 = a.f(cur, 2);
-    const T *Bp = a.Bp();
+    GhostSrc *out = gmap + L.goff[blockIdx.y];
     // the patch's neighbour boxes, staged once per CTA (each ghost cell searches them)
     constexpr int kStaged = 32;
     __shared__ int4 nbox[kStaged];
@@ -187,33 +189,79 @@ __global__ void ghost_fill_kernel(LevelView L, LevelView C, int cur, int cur_c, 
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
         int i, j;
         ring_cell(P, g, i, j);
-        int I = P.i0 + i, J = P.j0 + j;
-        if (I < 0 || I >= L.nxl || J < 0 || J >= L.nyl) continue;
-        long long k = a.idx(i, j);
-        int src = -1;
-        for (int m = 0; m < ns; m++) {
-            const int4 b = nbox[m];
-            if (I >= b.x && I < b.z && J >= b.y && J < b.w) { src = nid[m]; break; }
-        }
-        for (int m = ns; src < 0 && m < P.nbr_cnt; m++) {   // more neighbours than staged
-            int qi = L.nbrs[P.nbr_off + m];
-            const PatchDesc &Q = L.descs[qi];
-            if (I >= Q.i0 && I < Q.i0 + Q.nx && J >= Q.j0 && J < Q.j0 + Q.ny) { src = qi; break; }
-        }
-        if (src >= 0) {
-            const PatchDesc Q = L.descs[src];
-            Acc<T> b = acc<T>(L.arena, Q);
-            long long kq = b.idx(I - Q.i0, J - Q.j0);
-            q0[k] = b.f(cur, 0)[kq];
-            q1[k] = b.f(cur, 1)[kq];
-            q2[k] = b.f(cur, 2)[kq];
-        } else if (ratio > 0) {
-            T o0, o1, o2;
-            if (interp_fine<T, PERT>(C, cur_c, L.cmap, P, ratio, I, J, (double)Bp[k], alpha, drytol, o0, o1, o2)) {
-                q0[k] = o0; q1[k] = o1; q2[k] = o2;
-            } else {
-                atomicOr(err, 1);
+        const int I = P.i0 + i, J = P.j0 + j;
+        GhostSrc e;
+        e.src = kGhostSkip;
+        e.sfs = 0;
+        if (I >= 0 && I < L.nxl && J >= 0 && J < L.nyl) {
+            int src = -1;
+            for (int m = 0; m < ns; m++) {
+                const int4 b = nbox[m];
+                if (I >= b.x && I < b.z && J >= b.y && J < b.w) { src = nid[m]; break; }
             }
+            for (int m = ns; src < 0 && m < P.nbr_cnt; m++) {   // more neighbours than staged
+                const int qi = L.nbrs[P.nbr_off + m];
+                const PatchDesc &Q = L.descs[qi];
+                if (I >= Q.i0 && I < Q.i0 + Q.nx && J >= Q.j0 && J < Q.j0 + Q.ny) { src = qi; break; }
+            }
+            if (src >= 0) {
+                const PatchDesc &Q = L.descs[src];
+                e.src = Q.off + (long long)(J - Q.j0 + 2) * Q.pitch + (I - Q.i0 + 2);
+                e.sfs = Q.fs;
+            } else if (ratio > 0) {
+                e.src = kGhostInterp;
+                ilist[atomicAdd(icount, 1)] = make_int2((int)blockIdx.y, g);
+            } else {
+                e.src = kGhostNone;
+            }
+        }
+        out[g] = e;
+    }
+}
+
+// Ghost cells of the current state copied from the same-level interior cells
+// the map names.  The interpolated cells are left to the kernel below, so
+// that no CTA here waits on their long chains of dependent loads.
+template <typename T>
+__global__ void ghost_copy_kernel(LevelView L, int cur, int *err)
+{
+    const PatchDesc P = L.descs[blockIdx.y];
+    const int n = ring_count(P);
+    Acc<T> a = acc<T>(L.arena, P);
+    T *q0 = a.f(cur, 0), *q1 = a.f(cur, 1), *q2 = a.f(cur, 2);
+    const T *ar = reinterpret_cast<const T *>(L.arena);
+    const GhostSrc *gm = L.gmap + L.goff[blockIdx.y];
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const GhostSrc s = gm[g];
+        if (s.src == kGhostSkip || s.src == kGhostInterp) continue;
+        if (s.src < 0) { atomicOr(err, 1); continue; }
+        int i, j;
+        ring_cell(P, g, i, j);
+        const long long k = a.idx(i, j);
+        const T *q = ar + s.src + (long long)(cur * 3) * s.sfs;
+        const T v0 = q[0], v1 = q[s.sfs], v2 = q[2 * s.sfs];
+        q0[k] = v0; q1[k] = v1; q2[k] = v2;
+    }
+}
+
+// The ghost cells with no same-level source, one thread each: space-time
+// interpolation from the coarser level at time fraction alpha.
+template <typename T, bool PERT>
+__global__ void ghost_interp_kernel(LevelView L, LevelView C, int cur, int cur_c, int ratio, double alpha,
+                                    double drytol, int *err)
+{
+    const int ni = *L.icount;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ni; e += gridDim.x * blockDim.x) {
+        const int2 pg = L.ilist[e];
+        const PatchDesc P = L.descs[pg.x];
+        Acc<T> a = acc<T>(L.arena, P);
+        int i, j;
+        ring_cell(P, pg.y, i, j);
+        const long long k = a.idx(i, j);
+        T o0, o1, o2;
+        if (interp_fine<T, PERT>(C, cur_c, L.cmap, P, ratio, P.i0 + i, P.j0 + j, (double)a.Bp()[k], alpha, drytol, o0,
+                                 o1, o2)) {
+            a.f(cur, 0)[k] = o0; a.f(cur, 1)[k] = o1; a.f(cur, 2)[k] = o2;
         } else {
             atomicOr(err, 1);
         }
@@ -743,31 +791,50 @@ __global__ void __launch_bounds__(256) depth_check_kernel(LevelView L, int npatc
     if (tx == 0 && n) atomicAdd(count, n);
 }
 
+// Max wave speeds of a list of patches (new patches after a regrid, or all of
+// them at initialisation).  One CTA row per patch; the CTAs of a row split its
+// interior cells, flat in row-major order, and each thread loads the fields
+// of kU cells before it uses any, so that many loads are in flight.  The
+// maxima are order-free (a speed that is not a number never wins a compare).
 template <typename T, bool PERT>
 __global__ void __launch_bounds__(256) cell_speed_kernel(LevelView L, const int *list, int nlist, int cur, double g,
                                                          double drytol, unsigned long long *smax)
 {
+    constexpr int kU = 4;
     __shared__ double red[2][8];
-    const int tx = threadIdx.x, ty = threadIdx.y, lane = ty * 32 + tx;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int pi = blockIdx.y; pi < nlist; pi += gridDim.y) {
         const PatchDesc P = L.descs[list ? list[pi] : pi];
         Acc<T> a = acc<T>(L.arena, P);
+        const T *r0 = a.f(cur, 0), *r1 = a.f(cur, 1), *r2 = a.f(cur, 2), *rB = a.Bp();
+        const int ncell = P.nx * P.ny;
+        const int stride = gridDim.x * blockDim.x;
         T sxT = T(0), syT = T(0);   // running maxima in the state's precision (no FP64 work per cell in FP32)
-        for (int j = blockIdx.x * 8 + ty; j < P.ny; j += gridDim.x * 8) {
-            const T *r0 = a.f(cur, 0) + a.idx(0, j), *r1 = a.f(cur, 1) + a.idx(0, j), *r2 = a.f(cur, 2) + a.idx(0, j);
-            const T *rB = a.Bp() + a.idx(0, j);
-            for (int i = tx; i < P.nx; i += 32) {
-                T q0 = r0[i];
-                T h = PERT ? q0 - rB[i] : q0;
+        for (int e0 = blockIdx.x * blockDim.x + t; e0 < ncell; e0 += kU * stride) {
+            T q0[kU], qB[kU], qu[kU], qv[kU];
+            int jr[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                const int e = e0 + u * stride;
+                const int j = e < ncell ? e / P.nx : 0, i = e < ncell ? e - j * P.nx : 0;
+                const long long k = a.idx(i, j);
+                jr[u] = e < ncell ? j : -1;
+                q0[u] = r0[k]; qB[u] = rB[k]; qu[u] = r1[k]; qv[u] = r2[k];
+            }
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                if (jr[u] < 0) continue;
+                const T h = PERT ? q0[u] - qB[u] : q0[u];
                 if (h < (T)drytol) continue;
-                T cc = PERT ? (T)sqrtf((float)((T)g * h)) : (T)sqrt((double)((T)g * h));
-                T ux = r1[i] / h, uy = r2[i] / h;
+                const T cc = PERT ? (T)sqrtf((float)((T)g * h)) : (T)sqrt((double)((T)g * h));
+                const T ux = qu[u] / h, uy = qv[u] / h;
                 T ax = (ux < T(0) ? -ux : ux) + cc, ay = (uy < T(0) ? -uy : uy) + cc;
                 if (L.kap) {   // latitude-longitude grids: x speeds over the row's capacity, y speeds
                                // times the larger edge length over it (the sweeps' Courant numbers)
-                    const double kd = L.kap[P.j0 + j + 2];
+                    const int jj = P.j0 + jr[u] + 2;
+                    const double kd = L.kap[jj];
                     const T kj = (T)kd;
-                    const T cj = (T)(fmax(L.ced[P.j0 + j + 2], L.ced[P.j0 + j + 3]) / kd);
+                    const T cj = (T)(fmax(L.ced[jj], L.ced[jj + 1]) / kd);
                     ax = ax / kj;
                     ay = ay * cj;
                 }
@@ -780,11 +847,11 @@ __global__ void __launch_bounds__(256) cell_speed_kernel(LevelView L, const int 
             sx = fmax(sx, __shfl_xor_sync(0xffffffffu, sx, o));
             sy = fmax(sy, __shfl_xor_sync(0xffffffffu, sy, o));
         }
-        if (tx == 0) { red[0][ty] = sx; red[1][ty] = sy; }
+        if (lane == 0) { red[0][warp] = sx; red[1][warp] = sy; }
         __syncthreads();
-        if (lane == 0) {
+        if (t == 0) {
             double mx = 0.0, my = 0.0;
-            for (int k = 0; k < 8; k++) { mx = fmax(mx, red[0][k]); my = fmax(my, red[1][k]); }
+            for (int k = 0; k < (int)(blockDim.x >> 5); k++) { mx = fmax(mx, red[0][k]); my = fmax(my, red[1][k]); }
             if (mx > 0.0) atomicMax(smax + 2 * P.scen, (unsigned long long)__double_as_longlong(mx));
             if (my > 0.0) atomicMax(smax + 2 * P.scen + 1, (unsigned long long)__double_as_longlong(my));
         }
@@ -1053,14 +1120,29 @@ __global__ void halo_unpack_kernel(LevelView L, const HaloMsg *msgs, int cur, co
         else KERNEL<float, true>__VA_ARGS__;                             \
     } while (0)
 
+int k_ghost_map(const LevelView &L, GhostSrc *gmap, int2 *ilist, int *icount, int npatch, int maxring, int ratio,
+                cudaStream_t st)
+{
+    int e = (int)cudaMemsetAsync(icount, 0, sizeof(int), st);
+    if (e != 0 || npatch <= 0) return e;
+    // many patches: one CTA per patch (its neighbour boxes are staged once);
+    // few: their ghost rings spread over more CTAs
+    dim3 g = npatch >= 152 * 8 ? dim3(1, npatch) : grid_for(maxring, npatch, 128);
+    ghost_map_kernel<<<g, 128, 0, st>>>(L, gmap, ilist, icount, ratio);
+    return (int)cudaGetLastError();
+}
+
 int k_ghost_fill(int prec, const LevelView &L, const LevelView &C, int npatch, int maxring, int cur, int cur_c,
                  int ratio, double alpha, double drytol, int *err, cudaStream_t st)
 {
     if (npatch <= 0) return 0;
-    // many patches: one CTA per patch (its neighbour boxes are staged once);
-    // few: their ghost rings spread over more CTAs
     dim3 g = npatch >= 152 * 8 ? dim3(1, npatch) : grid_for(maxring, npatch, 128);
-    TSU_DISPATCH(prec, ghost_fill_kernel, <<<g, 128, 0, st>>>(L, C, cur, cur_c, ratio, alpha, drytol, err));
+    if (prec == 0) ghost_copy_kernel<double><<<g, 128, 0, st>>>(L, cur, err);
+    else ghost_copy_kernel<float><<<g, 128, 0, st>>>(L, cur, err);
+    int e = (int)cudaGetLastError();
+    if (e != 0 || ratio <= 0) return e;
+    // the list's length is known on the device only: a fixed grid strides over it
+    TSU_DISPATCH(prec, ghost_interp_kernel, <<<152 * 8, 128, 0, st>>>(L, C, cur, cur_c, ratio, alpha, drytol, err));
     return (int)cudaGetLastError();
 }
 
@@ -1285,13 +1367,15 @@ int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int m
                  double drytol, unsigned long long *smax, cudaStream_t st)
 {
     if (nlist <= 0) return 0;
-    // about 8 blocks of 256 threads per SM in all: patches first, then row groups within a patch
-    constexpr int kBlocks = 152 * 8;
-    const int by = nlist < kBlocks ? nlist : kBlocks;
-    int bx = (maxcells + 256 * 32 - 1) / (256 * 32);   // about 32 cells per thread
-    if (bx > kBlocks / by) bx = kBlocks / by;
+    // one CTA row per patch (up to the grid's limit); a large patch spreads over
+    // more CTAs, about 16 cells per thread, while the launch stays near 32 CTAs
+    // of 256 threads per SM
+    const int by = nlist < 65535 ? nlist : 65535;
+    int bx = (maxcells + 256 * 16 - 1) / (256 * 16);
+    const int cap = (152 * 32) / by;
+    if (bx > cap) bx = cap;
     if (bx < 1) bx = 1;
-    TSU_DISPATCH(prec, cell_speed_kernel, <<<dim3(bx, by), dim3(32, 8), 0, st>>>(L, list, nlist, cur, g, drytol, smax));
+    TSU_DISPATCH(prec, cell_speed_kernel, <<<dim3(bx, by), 256, 0, st>>>(L, list, nlist, cur, g, drytol, smax));
     return (int)cudaGetLastError();
 }
 

@@ -8,6 +8,19 @@ namespace tsu {
 
 constexpr int kMaxLevels = 8;
 
+// Where one ghost cell of a patch takes its value from, found once per patch
+// table (the search over the neighbour boxes does not run at every fill):
+// src >= 0 is the element offset in the arena of the same-level neighbour's
+// interior cell in field 0 of buffer 0, sfs that patch's field stride; the
+// negative codes below mark the other cases.
+struct __align__(16) GhostSrc {
+    long long src;
+    long long sfs;
+};
+constexpr long long kGhostSkip = -1;     // outside the level's index space (physical boundary)
+constexpr long long kGhostInterp = -2;   // no same-level neighbour: space-time interpolation from the coarser level
+constexpr long long kGhostNone = -3;     // no neighbour on the coarsest level: a tiling error
+
 // Device view of one level's tables (all scenarios).
 struct LevelView {
     const PatchDesc *descs;
@@ -18,6 +31,10 @@ struct LevelView {
     const int *olds;        // regrid: overlapping old patches
     const double *kap;      // latitude-longitude grids: capacity of row J at [J + 2]; null on Cartesian grids
     const double *ced;      // latitude-longitude grids: relative length of the latitude edge below row J at [J + 2]
+    const GhostSrc *gmap;   // ghost-cell sources, patch after patch in ghost-ring order
+    const long long *goff;  // first entry of each patch in gmap
+    const int2 *ilist;      // ghost cells interpolated from the coarser level: (patch, ghost-ring index)
+    const int *icount;      // entries of ilist
 };
 
 // Device control block of a context: per scenario dt, time, rates, counters.
@@ -92,6 +109,11 @@ struct GaugeArgs {
     double dxl[kMaxLevels], dyl[kMaxLevels];
 };
 
+// ghost-cell sources of every patch of a level (L.gmap, L.goff), after its patch table or neighbour lists
+// change; ratio 0 on the coarsest level
+// (ilist, icount: the interpolated cells' list and its length, zeroed here; ilist holds one entry per ghost cell)
+int k_ghost_map(const LevelView &L, GhostSrc *gmap, int2 *ilist, int *icount, int npatch, int maxring, int ratio,
+                cudaStream_t st);
 int k_ghost_fill(int prec, const LevelView &L, const LevelView &C, int npatch, int maxring, int cur, int cur_c,
                  int ratio, double alpha, double drytol, int *err, cudaStream_t st);
 int k_bc(int prec, const LevelView &L, const BcArgs &b, int nlist, int maxring, int cur, int do_state, int do_B,

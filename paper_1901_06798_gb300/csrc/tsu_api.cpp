@@ -279,6 +279,11 @@ struct Lvl {
     DevBuf<StepItem> dItems, dItemsY;
     DevBuf<float> dScratch;                 // FP32 split update: Q* of every patch (3 fields each)
     DevBuf<int> dNbrs, dCmap, dCcand, dBc, dOlds, dList;
+    DevBuf<GhostSrc> dGmap;      // ghost-cell sources of every patch, in ghost-ring order
+    DevBuf<long long> dGoff;     // first dGmap entry of each patch
+    DevBuf<int2> dGinterp;       // ghost cells interpolated from the coarser level (patch, ring index)
+    DevBuf<int> dGcount;         // entries of dGinterp
+    std::vector<long long> goff;
     int cur = 0, maxring = 0, maxcells = 0;
     int nxl = 0, nyl = 0;
     double dx = 0, dy = 0, R = 1;
@@ -455,6 +460,8 @@ struct tsu_ctx {
         v.nbrs = lv[l].dNbrs.p; v.cmap = lv[l].dCmap.p; v.olds = lv[l].dOlds.p;
         v.kap = c.spherical ? lv[l].dKap.p : nullptr;
         v.ced = c.spherical ? lv[l].dCed.p : nullptr;
+        v.gmap = lv[l].dGmap.p; v.goff = lv[l].dGoff.p;
+        v.ilist = lv[l].dGinterp.p; v.icount = lv[l].dGcount.p;
         return v;
     }
     TopoSet topo()
@@ -653,6 +660,23 @@ struct tsu_ctx {
             kl(k_fill_cmap(L.dP.p, lv[l - 1].dP.p, L.dCcand.p, n, L.dCmap.p, st), "coarse maps");
         }
         L.dBc.upload(L.bclist, st);
+        // ghost-cell sources of the new table: the fills of every step until the
+        // next change gather from them
+        {
+            L.goff.resize(n);
+            long long gtot = 0;
+            for (int k = 0; k < n; k++) {
+                const PatchDesc &p = L.P[k];
+                L.goff[k] = gtot;
+                gtot += (long long)(p.nx + 4) * (p.ny + 4) - (long long)p.nx * p.ny;
+            }
+            L.dGoff.upload(L.goff, st);
+            L.dGmap.ensure((size_t)std::max<long long>(gtot, 1), st);
+            L.dGinterp.ensure((size_t)std::max<long long>(gtot, 1), st);
+            L.dGcount.ensure(1, st);
+            kl(k_ghost_map(view(l), L.dGmap.p, L.dGinterp.p, L.dGcount.p, n, L.maxring, l > 0 ? ratio[l - 1] : 0, st),
+               "ghost map");
+        }
         for (int s = 0; s < nscen; s++) cells_h[(size_t)s * kMaxLevels + l] = 0.0;
         for (const auto &p : L.P) cells_h[(size_t)p.scen * kMaxLevels + l] += (double)p.nx * p.ny;
         cells.upload(cells_h, st);
@@ -855,6 +879,7 @@ struct tsu_ctx {
             kl(k_dilate(fraw.p, ftmp.p, nx, ny, np, b, 0, Wx, st), "dilate x");
             kl(k_dilate(ftmp.p, fF.p, nx, ny, np, b, 1, W, st), "dilate y");
             kl(k_nest(fF.p, fN.p, fcov.p, ftmp.p, nx, ny, np, fa, W, st), "nest");   // ftmp is free again
+            launches++;   // k_nest runs two kernels
             // only the flags' bounding box of each plane comes to the host (the
             // clustering starts from that box, so the boxes are the same)
             std::vector<int> bb(4 * (size_t)np);
@@ -1076,6 +1101,7 @@ struct tsu_ctx {
                 LevelView Cv = l > 0 ? view(l - 1) : view(l);
                 kl(k_ghost_fill(prec, view(l), Cv, n, L.maxring, L.cur, l > 0 ? lv[l - 1].cur : 0,
                                 l > 0 ? ratio[l - 1] : 0, alpha, c.drytol, derr.p, st), "ghost fill");
+                if (l > 0) launches++;   // the interpolated cells' kernel
             }
             if (!L.bclist.empty()) {
                 BcArgs ba{L.dBc.p, {c.bc[0], c.bc[1], c.bc[2], c.bc[3]}};

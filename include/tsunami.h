@@ -238,7 +238,11 @@ int tsu_get_patch(tsu_ctx *ctx, int scenario, int level, int k, double *h, doubl
  * piecewise constant from the finest patch (level == 0) or from level
  * `level` only; NaN where nothing covers a point.  Fields: TSU_H, TSU_HU,
  * TSU_HV, TSU_ETA (h + B), TSU_ZETA (Eq. zeta: h where B > 0, else h + B),
- * TSU_B.  dst: nx*ny host doubles. */
+ * TSU_B.  dst: nx*ny host doubles, owned by the caller; the call writes
+ * every element and returns after the copy has landed.  Large fields are
+ * copied straight into dst where the device reaches pageable host memory
+ * through the host's page tables (coherent CPU-GPU platforms), else through
+ * a page-locked staging buffer. */
 int tsu_read_field(tsu_ctx *ctx, int scenario, int level, int field, double *dst, int nx, int ny,
                    double x0, double y0, double dx, double dy);
 

@@ -1383,6 +1383,21 @@ struct tsu_ctx {
     // round-robin to up to kWorkers host threads, each with its own staging
     // slot and event: the link copies one chunk while the other threads move
     // theirs into dst (and take dst's first-touch page faults) in parallel.
+    // 1 when the device reaches pageable host memory through the host's page
+    // tables (coherent platforms): a copy into resident pageable pages then runs
+    // at the pinned rate without a staging buffer
+    int pageable_ = -1;
+    bool pageable_access()
+    {
+        if (pageable_ < 0) {
+            int a = 0, b = 0;
+            if (cudaDeviceGetAttribute(&a, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess) a = 0;
+            if (cudaDeviceGetAttribute(&b, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device) != cudaSuccess) b = 0;
+            pageable_ = (a && b) ? 1 : 0;
+        }
+        return pageable_ == 1;
+    }
+
     void d2h_staged(double *dst, const double *src, size_t n)
     {
         constexpr size_t kChunk = (size_t)1 << 19;   // doubles per chunk (4 MiB)
@@ -2077,14 +2092,21 @@ int tsu_read_field(tsu_ctx *ctx, int scen, int level, int field, double *dst, in
         }
         // while the kernels run, host threads write the caller's pages once, so
         // the copies below do not stop at first-touch page faults
-        if (n * sizeof(double) >= ((size_t)8 << 20)) {
+        const bool touched = n * sizeof(double) >= ((size_t)8 << 20);
+        if (touched) {
             const int T = tsu::HostPool::get().size();
             tsu::HostPool::get().run(T, [&](int k) {
                 const size_t a = n * (size_t)k / T, b = n * (size_t)(k + 1) / T;
                 for (size_t i = a; i < b; i += 512) dst[i] = 0.0;   // one write per 4 KiB
             });
         }
-        ctx->d2h_staged(dst, ctx->dstage.p, n);
+        if (touched && ctx->pageable_access()) {
+            // the copy engine reaches the caller's (now resident) pages itself
+            CK(cudaMemcpyAsync(dst, ctx->dstage.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+            ctx->sync();
+        } else {
+            ctx->d2h_staged(dst, ctx->dstage.p, n);
+        }
     });
 }
 

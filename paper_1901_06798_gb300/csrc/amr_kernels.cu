@@ -163,7 +163,7 @@ __device__ bool interp_fine(const LevelView &C, int cur_c, const int *cmap, cons
 
 // ---------------------------------------------------------------- ghost fill
 
-// The source of every ghost cell of a patch (one CTA row per patch): a
+// The source of every ghost cell of a patch (blockIdx.x the patch): a
 // same-level neighbour whose interior holds the cell, else the coarser level
 // (space-time interpolation), else none (a tiling error on the coarsest
 // level).  Same-level patches do not overlap, so the source is unique.  The
@@ -171,9 +171,9 @@ __device__ bool interp_fine(const LevelView &C, int cur_c, const int *cmap, cons
 // is computed on its own).  Runs once per patch table; the fills gather.
 __global__ void ghost_map_kernel(LevelView L, GhostSrc *gmap, int2 *ilist, int *icount, int ratio)
 {
-    const PatchDesc P = L.descs[blockIdx.y];
+    const PatchDesc P = L.descs[blockIdx.x];
     const int n = ring_count(P);
-    GhostSrc *out = gmap + L.goff[blockIdx.y];
+    GhostSrc *out = gmap + L.goff[blockIdx.x];
     // the patch's neighbour boxes, staged once per CTA (each ghost cell searches them)
     constexpr int kStaged = 32;
     __shared__ int4 nbox[kStaged];
@@ -186,7 +186,7 @@ __global__ void ghost_map_kernel(LevelView L, GhostSrc *gmap, int2 *ilist, int *
         nid[m] = qi;
     }
     __syncthreads();
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+    for (int g = blockIdx.y * blockDim.x + threadIdx.x; g < n; g += gridDim.y * blockDim.x) {
         int i, j;
         ring_cell(P, g, i, j);
         const int I = P.i0 + i, J = P.j0 + j;
@@ -210,7 +210,7 @@ __global__ void ghost_map_kernel(LevelView L, GhostSrc *gmap, int2 *ilist, int *
                 e.sfs = Q.fs;
             } else if (ratio > 0) {
                 e.src = kGhostInterp;
-                ilist[atomicAdd(icount, 1)] = make_int2((int)blockIdx.y, g);
+                ilist[atomicAdd(icount, 1)] = make_int2((int)blockIdx.x, g);
             } else {
                 e.src = kGhostNone;
             }
@@ -225,13 +225,13 @@ __global__ void ghost_map_kernel(LevelView L, GhostSrc *gmap, int2 *ilist, int *
 template <typename T>
 __global__ void ghost_copy_kernel(LevelView L, int cur, int *err)
 {
-    const PatchDesc P = L.descs[blockIdx.y];
+    const PatchDesc P = L.descs[blockIdx.x];
     const int n = ring_count(P);
     Acc<T> a = acc<T>(L.arena, P);
     T *q0 = a.f(cur, 0), *q1 = a.f(cur, 1), *q2 = a.f(cur, 2);
     const T *ar = reinterpret_cast<const T *>(L.arena);
-    const GhostSrc *gm = L.gmap + L.goff[blockIdx.y];
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+    const GhostSrc *gm = L.gmap + L.goff[blockIdx.x];
+    for (int g = blockIdx.y * blockDim.x + threadIdx.x; g < n; g += gridDim.y * blockDim.x) {
         const GhostSrc s = gm[g];
         if (s.src == kGhostSkip || s.src == kGhostInterp) continue;
         if (s.src < 0) { atomicOr(err, 1); continue; }
@@ -300,10 +300,10 @@ __device__ __forceinline__ bool bc_source(const PatchDesc &P, int nxl, int nyl, 
 template <typename T>
 __global__ void bc_kernel(LevelView L, int cur, BcArgs bcs, int do_state, int do_B)
 {
-    const PatchDesc P = L.descs[bcs.list[blockIdx.y]];
+    const PatchDesc P = L.descs[bcs.list[blockIdx.x]];
     const int n = ring_count(P);
     Acc<T> a = acc<T>(L.arena, P);
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+    for (int g = blockIdx.y * blockDim.x + threadIdx.x; g < n; g += gridDim.y * blockDim.x) {
         int i, j, si, sj;
         bool nx_, ny_;
         ring_cell(P, g, i, j);
@@ -332,12 +332,12 @@ __global__ void average_kernel(LevelView Fv, LevelView C, int cur_f, int cur_c, 
 {
     using W = InterpT<PERT>;
     const W drytol = (W)drytold;
-    const PatchDesc F = Fv.descs[blockIdx.y];
+    const PatchDesc F = Fv.descs[blockIdx.x];
     const int cw = F.nx / r, ch = F.ny / r;
     const int n = cw * ch;
     Acc<T> fa = acc<T>(Fv.arena, F);
     const T *f0 = fa.f(cur_f, 0), *f1 = fa.f(cur_f, 1), *f2 = fa.f(cur_f, 2), *fB = fa.Bp();
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < n; c += gridDim.y * blockDim.x) {
         int Ic = F.i0 / r + c % cw, Jc = F.j0 / r + c / cw;
         int mi = Ic - F.cmap_i0, mj = Jc - F.cmap_j0;
         int cp = Fv.cmap[F.cmap_off + mj * F.cmap_w + mi];
@@ -442,10 +442,10 @@ template <typename T, bool PERT>
 __global__ void init_patch_kernel(LevelView L, LevelView Old, const int *list, TopoSet ts, int cur, int set_state,
                                   double x0, double y0, double dxl, double dyl)
 {
-    const PatchDesc P = L.descs[list[blockIdx.y]];
+    const PatchDesc P = L.descs[list[blockIdx.x]];
     const int n = (P.nx + 4) * (P.ny + 4);
     Acc<T> a = acc<T>(L.arena, P);
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < n; c += gridDim.y * blockDim.x) {
         int i = c % (P.nx + 4) - 2, j = c / (P.nx + 4) - 2;
         int I = P.i0 + i, J = P.j0 + j;
         if (I < 0 || I >= L.nxl || J < 0 || J >= L.nyl) continue;
@@ -489,11 +489,11 @@ __global__ void init_patch_kernel(LevelView L, LevelView Old, const int *list, T
 template <typename T, bool PERT>
 __global__ void uplift_kernel(LevelView L, TopoDev U, int scen, int cur, double x0, double y0, double dxl, double dyl)
 {
-    const PatchDesc P = L.descs[blockIdx.y];
+    const PatchDesc P = L.descs[blockIdx.x];
     if (P.scen != scen) return;
     const int n = (P.nx + 4) * (P.ny + 4);
     Acc<T> a = acc<T>(L.arena, P);
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < n; c += gridDim.y * blockDim.x) {
         int i = c % (P.nx + 4) - 2, j = c / (P.nx + 4) - 2;
         int I = P.i0 + i, J = P.j0 + j;
         if (I < 0 || I >= L.nxl || J < 0 || J >= L.nyl) continue;
@@ -517,10 +517,10 @@ template <typename T, bool PERT>
 __global__ void regrid_init_kernel(LevelView L, LevelView Old, LevelView C, const int *list, int cur, int cur_c,
                                    int ratio, double drytol, int *err)
 {
-    const PatchDesc P = L.descs[list[blockIdx.y]];
+    const PatchDesc P = L.descs[list[blockIdx.x]];
     const int n = P.nx * P.ny;
     Acc<T> a = acc<T>(L.arena, P);
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < n; c += gridDim.y * blockDim.x) {
         int i = c % P.nx, j = c / P.nx;
         int I = P.i0 + i, J = P.j0 + j;
         long long k = a.idx(i, j);
@@ -553,14 +553,14 @@ __global__ void regrid_init_kernel(LevelView L, LevelView Old, LevelView C, cons
 template <typename T, bool PERT>
 __global__ void flag_kernel(LevelView L, int cur, FlagArgs fa)
 {
-    const PatchDesc P = L.descs[blockIdx.y];
+    const PatchDesc P = L.descs[blockIdx.x];
     const int n = P.nx * P.ny;
     Acc<T> a = acc<T>(L.arena, P);
     const long long plane = (long long)L.nxl * L.nyl;
     uint8_t *raw = fa.raw + plane * fa.scen_slot[P.scen];
     uint8_t *cov = fa.cov + plane * fa.scen_slot[P.scen];
     if (fa.scen_slot[P.scen] < 0) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < n; c += gridDim.y * blockDim.x) {
         int i = c % P.nx, j = c / P.nx;
         int I = P.i0 + i, J = P.j0 + j;
         long long k = a.idx(i, j);
@@ -713,7 +713,7 @@ template <typename T, bool PERT>
 __global__ void cnn_features_kernel(LevelView L, int cur, const int *scen_slot, const uint8_t *raw, float *feat,
                                     double drytol, CnnWindow win)
 {
-    const PatchDesc P = L.descs[blockIdx.y];
+    const PatchDesc P = L.descs[blockIdx.x];
     const int slot = scen_slot[P.scen];
     if (slot < 0) return;
     if (P.i0 >= win.x0 + win.w || P.i0 + P.nx <= win.x0 || P.j0 >= win.y0 + win.h || P.j0 + P.ny <= win.y0) return;
@@ -723,7 +723,7 @@ __global__ void cnn_features_kernel(LevelView L, int cur, const int *scen_slot, 
     const long long plane = (long long)win.w * win.h;   // features of the window only
     float *f = feat + (long long)slot * 5 * plane;
     const uint8_t *rw = raw + (long long)slot * lplane;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < n; c += gridDim.y * blockDim.x) {
         int i = c % P.nx, j = c / P.nx;
         const int I = P.i0 + i - win.x0, J = P.j0 + j - win.y0;
         if (I < 0 || J < 0 || I >= win.w || J >= win.h) continue;
@@ -973,7 +973,7 @@ template <typename T, bool PERT>
 __global__ void read_field_kernel(LevelView L, int cur, int scen, int field, double *dst, int nx, int ny, double x0,
                                   double y0, double dx, double dy, double X0, double Y0, double dxl, double dyl)
 {
-    const PatchDesc P = L.descs[blockIdx.y];
+    const PatchDesc P = L.descs[blockIdx.x];
     if (P.scen != scen) return;
     // output index range whose points fall inside the patch interior
     double xl = X0 + (double)P.i0 * dxl, xh = X0 + (double)(P.i0 + P.nx) * dxl;
@@ -987,7 +987,7 @@ __global__ void read_field_kernel(LevelView L, int cur, int scen, int field, dou
     if (ia >= ib || ja >= jb) return;
     Acc<T> a = acc<T>(L.arena, P);
     const int w = ib - ia, n = w * (jb - ja);
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < n; c += gridDim.y * blockDim.x) {
         int i = ia + c % w, j = ja + c / w;
         double x = x0 + (double)i * dx, y = y0 + (double)j * dy;
         int I = (int)floor((x - X0) / dxl), J = (int)floor((y - Y0) / dyl);
@@ -1029,17 +1029,18 @@ __global__ void patch_out_kernel(LevelView L, int p, int cur, double *out)
 // Mass of each scenario over level 1 (the composite mass once finer levels
 // are averaged down), in FP64 and in a fixed order, so it is reproducible to
 // the last bit: block b of patch p sums its cells (capacity-weighted on
-// latitude-longitude grids), reduces by a fixed tree and writes parts[p B + b];
+// latitude-longitude grids), reduces by a fixed tree and writes parts[p B + b]
+// (p = blockIdx.x, b = blockIdx.y, B CTAs per patch);
 // mass_sum_kernel adds the parts of each scenario in (p, b) order.
 template <typename T, bool PERT>
 __global__ void __launch_bounds__(256) mass_kernel(LevelView L, int cur, double *parts)
 {
     __shared__ double red[256];
-    const PatchDesc P = L.descs[blockIdx.y];
+    const PatchDesc P = L.descs[blockIdx.x];
     const int n = P.nx * P.ny;
     Acc<T> a = acc<T>(L.arena, P);
     double s = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < n; c += gridDim.y * blockDim.x) {
         long long k = a.idx(c % P.nx, c / P.nx);
         double q0 = (double)a.f(cur, 0)[k];
         double h = PERT ? q0 - (double)a.Bp()[k] : q0;
@@ -1051,7 +1052,7 @@ __global__ void __launch_bounds__(256) mass_kernel(LevelView L, int cur, double 
         if ((int)threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) parts[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+    if (threadIdx.x == 0) parts[(size_t)blockIdx.x * gridDim.y + blockIdx.y] = red[0];
 }
 
 __global__ void mass_sum_kernel(const PatchDesc *descs, int npatch, int nb, const double *parts, double *mass,
@@ -1068,16 +1069,18 @@ __global__ void mass_sum_kernel(const PatchDesc *descs, int npatch, int nb, cons
 
 // ---------------------------------------------------------------- launchers
 
-// CTAs per patch: enough to cover its work, at most 64 when there are many
-// patches, and up to 16 per SM over the whole grid when there are few (a
+// Grid of a patch-batched launch: blockIdx.x is the patch (or list entry), so
+// a level may hold more patches than a grid's y extent allows, and blockIdx.y
+// the CTA within it: enough CTAs to cover its work, at most 64 when there are
+// many patches, and up to 16 per SM over the whole grid when there are few (a
 // single large patch must still fill the GPU)
 static dim3 grid_for(int per_patch, int npatch, int threads)
 {
-    int bx = (per_patch + threads - 1) / threads;
+    int by = (per_patch + threads - 1) / threads;
     const int cap = npatch >= 38 ? 64 : (152 * 16) / (npatch > 0 ? npatch : 1);
-    if (bx < 1) bx = 1;
-    if (bx > cap) bx = cap;
-    return dim3(bx, npatch);
+    if (by < 1) by = 1;
+    if (by > cap) by = cap;
+    return dim3(npatch, by);
 }
 
 // ---------------------------------------------------------------- halo exchange
@@ -1127,7 +1130,7 @@ int k_ghost_map(const LevelView &L, GhostSrc *gmap, int2 *ilist, int *icount, in
     if (e != 0 || npatch <= 0) return e;
     // many patches: one CTA per patch (its neighbour boxes are staged once);
     // few: their ghost rings spread over more CTAs
-    dim3 g = npatch >= 152 * 8 ? dim3(1, npatch) : grid_for(maxring, npatch, 128);
+    dim3 g = npatch >= 152 * 8 ? dim3(npatch, 1) : grid_for(maxring, npatch, 128);
     ghost_map_kernel<<<g, 128, 0, st>>>(L, gmap, ilist, icount, ratio);
     return (int)cudaGetLastError();
 }
@@ -1136,7 +1139,7 @@ int k_ghost_fill(int prec, const LevelView &L, const LevelView &C, int npatch, i
                  int ratio, double alpha, double drytol, int *err, cudaStream_t st)
 {
     if (npatch <= 0) return 0;
-    dim3 g = npatch >= 152 * 8 ? dim3(1, npatch) : grid_for(maxring, npatch, 128);
+    dim3 g = npatch >= 152 * 8 ? dim3(npatch, 1) : grid_for(maxring, npatch, 128);
     if (prec == 0) ghost_copy_kernel<double><<<g, 128, 0, st>>>(L, cur, err);
     else ghost_copy_kernel<float><<<g, 128, 0, st>>>(L, cur, err);
     int e = (int)cudaGetLastError();
@@ -1460,7 +1463,7 @@ int k_cnn_union(uint8_t *raw, const uint8_t *cov, const float *logits, int nx, i
     return (int)cudaGetLastError();
 }
 
-int k_mass_parts(int npatch, int maxcells) { return npatch * (int)grid_for(maxcells, npatch, 256).x; }
+int k_mass_parts(int npatch, int maxcells) { return npatch * (int)grid_for(maxcells, npatch, 256).y; }
 
 int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, double *parts, double *mass, int nscen,
            cudaStream_t st)
@@ -1470,7 +1473,7 @@ int k_mass(int prec, const LevelView &L, int npatch, int maxcells, int cur, doub
     TSU_DISPATCH(prec, mass_kernel, <<<g, 256, 0, st>>>(L, cur, parts));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
-    mass_sum_kernel<<<(nscen + 127) / 128, 128, 0, st>>>(L.descs, npatch, (int)g.x, parts, mass, nscen);
+    mass_sum_kernel<<<(nscen + 127) / 128, 128, 0, st>>>(L.descs, npatch, (int)g.y, parts, mass, nscen);
     return (int)cudaGetLastError();
 }
 

@@ -2101,7 +2101,9 @@ int tsu_read_field(tsu_ctx *ctx, int scen, int level, int field, double *dst, in
             });
         }
         if (touched && ctx->pageable_access()) {
-            // the copy engine reaches the caller's (now resident) pages itself
+            // the copy engine reaches the caller's (now resident) pages itself; one
+            // copy (copies into pageable memory issued from several threads at
+            // once were measured far slower)
             CK(cudaMemcpyAsync(dst, ctx->dstage.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
             ctx->sync();
         } else {

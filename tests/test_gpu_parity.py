@@ -89,6 +89,44 @@ def test_tiny_grid_and_single_column_patches():
     compare_levels(o, g, 1, bitwise=True)
 
 
+def test_more_patches_than_a_grid_y_extent():
+    """70,225 patches on one level (2 x 2 tiles of a 530^2 shelf with beach and
+    dry land), more than the 65,535 rows a CUDA grid's y extent allows: the
+    patch-batched kernels (ghost fill, boundaries, field reads, mass) index the
+    patch by blockIdx.x.  The tiled level steps to the same bits as one patch
+    in FP64; in the FP32 perturbation form it stays within 1e-5 m of it."""
+    from paper_1901_06798_gb300 import binding
+    w = W.shelf(n=530, dx=2000.0, steps=20)
+    tiled = dict(w["cfg"], level1_tile=2)
+    pts = (530, 530, 1000.0, 1000.0, 2000.0, 2000.0)
+    for prec in (binding.TSU_F64, binding.TSU_F32P):
+        one = W.load(_gpu(w["cfg"], prec), w)
+        many = W.load(_gpu(tiled, prec), dict(w, cfg=tiled))
+        assert many.num_patches(0, 1) == 265 * 265
+        one.step(20)
+        many.step(20)
+        t1, t2 = one.stats()["t"], many.stats()["t"]
+        assert t1 == t2 if prec == binding.TSU_F64 else abs(t1 - t2) <= 1e-6 * t1
+        got = {}
+        for f in ("eta", "hu", "hv"):
+            a = one.read_field(0, 1, f, *pts)
+            got[f] = many.read_field(0, 1, f, *pts)
+            assert not np.isnan(got[f]).any()
+            if prec == binding.TSU_F64:
+                assert np.array_equal(a, got[f]), f
+            else:
+                assert np.abs(a - got[f]).max() <= 1e-5, (f, np.abs(a - got[f]).max())
+        # a field of more than 8 MiB takes the read-back path for large fields:
+        # four points per cell, piecewise constant
+        big = many.read_field(0, 1, "eta", 1060, 1060, 500.0, 500.0, 1000.0, 1000.0)
+        assert np.array_equal(big[::2, ::2], got["eta"]) and np.array_equal(big[1::2, 1::2], got["eta"])
+        if prec == binding.TSU_F64:
+            # the same cells summed in another order (per patch, then patch by patch)
+            assert abs(one.stats()["mass"] - many.stats()["mass"]) <= 1e-10 * abs(one.stats()["mass"])
+        one.close()
+        many.close()
+
+
 def test_shelf_with_dry_land_f64():
     w = W.shelf(n=192, dx=2000.0, steps=60)
     o, g = run_pair(w, 60)

@@ -410,24 +410,75 @@ __device__ double grid_bilinear(const TopoDev &g, double x, double y)
     return a + ty * (b - a);
 }
 
-__device__ double base_topo(const TopoSet &ts, double x, double y)
+// The per-column and per-row parts of sampling every grid at a level's cell
+// centres (x_I = x0 + (I + 1/2) dx, y_J likewise): the operations of
+// grid_contains and grid_bilinear on one coordinate, so the values are the ones
+// computed at each cell.
+__global__ void axis_tab_kernel(TopoSet ts, double x0, double y0, double dxl, double dyl)
+{
+    const AxisTab &T = ts.tab;
+    const long long ncol = (long long)ts.ngrids * T.nx, nall = ncol + (long long)ts.ngrids * T.ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nall; q += (long long)gridDim.x * blockDim.x) {
+        const bool col = q < ncol;
+        const long long r = col ? q : q - ncol;
+        const int n = col ? T.nx : T.ny;
+        const int k = (int)(r / n), I = (int)(r - (long long)k * n);
+        const TopoDev &g = ts.grids[k];
+        const double o = col ? g.x0 : g.y0, d = col ? g.dx : g.dy;
+        const int gn = col ? g.nx : g.ny;
+        const double x = col ? x0 + ((double)I + 0.5) * dxl : y0 + ((double)I + 0.5) * dyl;
+        const unsigned char in = x >= o && x <= o + (double)(gn - 1) * d;
+        const double f = (x - o) / d;
+        int i = (int)floor(f);
+        if (i < 0) i = 0;
+        if (i > gn - 2) i = gn - 2;
+        double t = f - (double)i;
+        if (t < 0.0) t = 0.0;
+        if (t > 1.0) t = 1.0;
+        if (col) { T.ci[r] = i; T.ct[r] = t; T.cin[r] = in; }
+        else { T.rj[r] = i; T.rt[r] = t; T.rin[r] = in; }
+    }
+}
+
+__device__ __forceinline__ bool tab_contains(const TopoSet &ts, int k, int I, int J)
+{
+    return ts.tab.cin[(long long)k * ts.tab.nx + I] && ts.tab.rin[(long long)k * ts.tab.ny + J];
+}
+
+// grid_bilinear of grid k at the centre of cell (I, J), from the axis table
+__device__ double tab_bilinear(const TopoSet &ts, int k, int I, int J)
+{
+    const TopoDev &g = ts.grids[k];
+    const long long c = (long long)k * ts.tab.nx + I, r = (long long)k * ts.tab.ny + J;
+    const int i = ts.tab.ci[c], j = ts.tab.rj[r];
+    const double tx = ts.tab.ct[c], ty = ts.tab.rt[r];
+    const double *v = g.v;
+    double v00 = v[(long long)j * g.nx + i], v10 = v[(long long)j * g.nx + i + 1];
+    double v01 = v[(long long)(j + 1) * g.nx + i], v11 = v[(long long)(j + 1) * g.nx + i + 1];
+    double a = v00 + tx * (v10 - v00);
+    double b = v01 + tx * (v11 - v01);
+    return a + ty * (b - a);
+}
+
+// base_topo and uplift_sum at the centre of cell (I, J), from the axis table
+__device__ double base_topo_tab(const TopoSet &ts, int I, int J)
 {
     int best = -1;
     double barea = 0.0;
     for (int k = 0; k < ts.nbase; k++) {
-        if (!grid_contains(ts.grids[k], x, y)) continue;
+        if (!tab_contains(ts, k, I, J)) continue;
         double area = ts.grids[k].dx * ts.grids[k].dy;
         if (best < 0 || area <= barea) { best = k; barea = area; }
     }
     if (best < 0) best = 0;
-    return grid_bilinear(ts.grids[best], x, y);
+    return tab_bilinear(ts, best, I, J);
 }
 
-__device__ double uplift_sum(const TopoSet &ts, int scen, double B, double x, double y)
+__device__ double uplift_sum_tab(const TopoSet &ts, int scen, double B, int I, int J)
 {
     for (int k = ts.nbase; k < ts.ngrids; k++) {
         if (ts.scen[k] != scen) continue;
-        if (grid_contains(ts.grids[k], x, y)) B = B + grid_bilinear(ts.grids[k], x, y);
+        if (tab_contains(ts, k, I, J)) B = B + tab_bilinear(ts, k, I, J);
     }
     return B;
 }
@@ -437,7 +488,10 @@ __device__ double uplift_sum(const TopoSet &ts, int scen, double B, double x, do
 // at every cell inside the domain; cells outside are filled by bc_kernel.  At a
 // regrid (Old.descs set) a cell that an old patch of the level held in its
 // interior takes that patch's B -- the same value, without sampling the
-// topography again -- and only the other cells are sampled.
+// topography again -- and only the other cells are sampled.  Sampling picks the
+// finest base grid holding the cell centre (the last of equal ones), adds the
+// scenario's uplift layers holding it, and reads the per-column and per-row
+// parts of each grid's bilinear interpolation from the axis table.
 template <typename T, bool PERT>
 __global__ void init_patch_kernel(LevelView L, LevelView Old, const int *list, TopoSet ts, int cur, int set_state,
                                   double x0, double y0, double dxl, double dyl)
@@ -462,21 +516,20 @@ __global__ void init_patch_kernel(LevelView L, LevelView Old, const int *list, T
             }
             if (held) continue;
         }
-        double x = x0 + ((double)I + 0.5) * dxl, y = y0 + ((double)J + 0.5) * dyl;
-        double B0 = base_topo(ts, x, y);
-        double B = uplift_sum(ts, P.scen, B0, x, y);
+        double B0 = base_topo_tab(ts, I, J);
+        double B = uplift_sum_tab(ts, P.scen, B0, I, J);
         a.Bp()[k] = (T)B;
         if (set_state) {
             double eta = 0.0;
             int eg = ts.eta_index[3 * P.scen];
-            if (eg >= 0 && grid_contains(ts.grids[eg], x, y)) eta = grid_bilinear(ts.grids[eg], x, y);
+            if (eg >= 0 && tab_contains(ts, eg, I, J)) eta = tab_bilinear(ts, eg, I, J);
             double hh = eta - B0;
             if (hh < 0.0) hh = 0.0;
             double hu = 0.0, hv = 0.0;
             const int ug = ts.eta_index[3 * P.scen + 1], vg = ts.eta_index[3 * P.scen + 2];
-            if (ug >= 0 && hh >= ts.drytol && grid_contains(ts.grids[ug], x, y)) {
-                hu = hh * grid_bilinear(ts.grids[ug], x, y);
-                hv = hh * grid_bilinear(ts.grids[vg], x, y);
+            if (ug >= 0 && hh >= ts.drytol && tab_contains(ts, ug, I, J)) {
+                hu = hh * tab_bilinear(ts, ug, I, J);
+                hv = hh * tab_bilinear(ts, vg, I, J);
             }
             a.f(cur, 0)[k] = PERT ? (T)(hh + B) : (T)hh;
             a.f(cur, 1)[k] = (T)hu;
@@ -1174,8 +1227,16 @@ int k_init_patches(int prec, const LevelView &L, const LevelView &Old, const int
                    int set_state, double x0, double y0, double dxl, double dyl, cudaStream_t st)
 {
     if (nlist <= 0) return 0;
+    // the sampling's per-column and per-row parts at this level's cell centres
+    TopoSet t = ts;
+    t.tab.nx = L.nxl;
+    t.tab.ny = L.nyl;
+    const long long nt = (long long)ts.ngrids * (L.nxl + L.nyl);
+    axis_tab_kernel<<<(int)std::min<long long>((nt + 255) / 256, 152 * 8), 256, 0, st>>>(t, x0, y0, dxl, dyl);
+    int e = (int)cudaGetLastError();
+    if (e != 0) return e;
     dim3 g = grid_for(maxcells, nlist, 128);
-    TSU_DISPATCH(prec, init_patch_kernel, <<<g, 128, 0, st>>>(L, Old, list, ts, cur, set_state, x0, y0, dxl, dyl));
+    TSU_DISPATCH(prec, init_patch_kernel, <<<g, 128, 0, st>>>(L, Old, list, t, cur, set_state, x0, y0, dxl, dyl));
     return (int)cudaGetLastError();
 }
 

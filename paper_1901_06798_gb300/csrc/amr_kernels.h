@@ -59,6 +59,18 @@ struct TopoDev {
     const double *v;
 };
 
+// Sampling grid k at the cell centres of one level is separable: whether the
+// centre lies in the grid's extent, and the clamped node index and fraction
+// of the bilinear interpolation, depend on the column alone in x and on the
+// row alone in y.  AxisTab holds them per grid and column ([k nx + I]) and per
+// grid and row ([k ny + J]), computed by the same operations as at the cell.
+struct AxisTab {
+    int *ci, *rj;                // node index i of column I, j of row J
+    double *ct, *rt;             // interpolation fractions tx, ty
+    unsigned char *cin, *rin;    // x_I within [x0, x0 + (nx - 1) dx], y_J likewise
+    int nx, ny;                  // the level's columns and rows
+};
+
 // Base topography grids [0, nbase), then uplift layers and surface grids;
 // scen[k] tells which scenario a layer belongs to (-1: not an uplift layer).
 struct TopoSet {
@@ -67,6 +79,7 @@ struct TopoSet {
     const int *eta_index;        // per scenario s: [3s] initial surface, [3s+1] u, [3s+2] v grid index or -1
     int nbase, ngrids;
     double drytol;               // initial velocities apply to wet cells only
+    AxisTab tab;                 // storage for k_init_patches: ngrids (nx + ny) entries of each array
 };
 
 // Window of a level plane on which the flag predictor runs (x0, y0, w, h), and

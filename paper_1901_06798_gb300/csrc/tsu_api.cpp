@@ -464,9 +464,27 @@ struct tsu_ctx {
         v.ilist = lv[l].dGinterp.p; v.icount = lv[l].dGcount.p;
         return v;
     }
+    // the topography set with axis-table storage for a level of nx x ny cells
+    DevBuf<int> tabI;
+    DevBuf<double> tabT;
+    DevBuf<unsigned char> tabIn;
+    TopoSet topo(int l)
+    {
+        TopoSet ts = topo();
+        const size_t n = (size_t)grids.size() * (size_t)(lv[l].nxl + lv[l].nyl);
+        tabI.ensure(n, st);
+        tabT.ensure(n, st);
+        tabIn.ensure(n, st);
+        const size_t nc = (size_t)grids.size() * lv[l].nxl;
+        ts.tab.ci = tabI.p; ts.tab.rj = tabI.p + nc;
+        ts.tab.ct = tabT.p; ts.tab.rt = tabT.p + nc;
+        ts.tab.cin = tabIn.p; ts.tab.rin = tabIn.p + nc;
+        ts.tab.nx = lv[l].nxl; ts.tab.ny = lv[l].nyl;
+        return ts;
+    }
     TopoSet topo()
     {
-        TopoSet ts;
+        TopoSet ts{};
         ts.grids = dGrids.p; ts.scen = dGridScen.p; ts.eta_index = dEtaIdx.p;
         ts.nbase = nbase; ts.ngrids = (int)grids.size();
         ts.drytol = c.drytol;
@@ -1050,7 +1068,7 @@ struct tsu_ctx {
         if (!fresh.empty()) {
             L.dList.upload(fresh, st);
             // B: copied where an old patch of the level held the cell, else sampled
-            kl(k_init_patches(prec, view(lf), view(lf, oldD.p), L.dList.p, (int)fresh.size(), L.maxcells, topo(), L.cur,
+            kl(k_init_patches(prec, view(lf), view(lf, oldD.p), L.dList.p, (int)fresh.size(), L.maxcells, topo(lf), L.cur,
                               0, c.x0, c.y0, L.dx, L.dy, st),
                "init B");
             // B outside the domain for new boundary patches
@@ -1479,7 +1497,7 @@ struct tsu_ctx {
         finish_level(0);
         L.dList.upload(all, st);
         LevelView none{};
-        kl(k_init_patches(prec, view(0), none, L.dList.p, (int)all.size(), L.maxcells, topo(), L.cur, 1, c.x0, c.y0,
+        kl(k_init_patches(prec, view(0), none, L.dList.p, (int)all.size(), L.maxcells, topo(0), L.cur, 1, c.x0, c.y0,
                           L.dx, L.dy, st),
            "init level 1");
         if (!L.bclist.empty()) {

@@ -926,9 +926,9 @@ __global__ void __launch_bounds__(256) cell_speed_kernel(LevelView L, const int 
 //           buffer); otherwise keep it as in mode 0;
 //   mode 3: after the retake launch -- keep the retaken steps as in mode 0.
 // A rate that is not a finite number (a NaN or infinite speed) sets the error
-// flag to TSU_DEV_ERR_NAN.
+// flag to TSU_DEV_ERR_NAN.  end_step (mode 0): then t += dt^1, as end_step_kernel.
 __global__ void post_level_kernel(CtrlView cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
-                                  double cfl_desired, int mode)
+                                  double cfl_desired, int mode, int end_step)
 {
     for (int s = threadIdx.x; s < nscen; s += blockDim.x) {
         unsigned long long *sm = cv.smax + 2 * s;
@@ -956,6 +956,7 @@ __global__ void post_level_kernel(CtrlView cv, int level, int nscen, double R, d
             cv.cell_updates[s] += cv.cells[(long long)s * cv.max_levels + level];
         }
         *ra = fmax(*ra, rate);
+        if (end_step) cv.t[s] = cv.t[s] + cv.dt1[s];
     }
 }
 
@@ -1445,9 +1446,10 @@ int k_cell_speed(int prec, const LevelView &L, const int *list, int nlist, int m
 
 int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
                  double cfl_desired, int mode,
-                 cudaStream_t st)
+                 cudaStream_t st, int end_step)
 {
-    post_level_kernel<<<1, 128, 0, st>>>(cv, level, nscen, R, dx, dy, cfl_max, cfl_desired, mode);
+    post_level_kernel<<<1, 128, 0, st>>>(cv, level, nscen, R, dx, dy, cfl_max, cfl_desired, mode,
+                                         mode == 0 ? end_step : 0);
     return (int)cudaGetLastError();
 }
 

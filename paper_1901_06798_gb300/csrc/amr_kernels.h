@@ -174,9 +174,11 @@ struct HaloMsg {
 // pack (unpack = 0: patch buffers -> buf) or unpack (buf -> patch buffers) n boxes
 int k_halo(int prec, const LevelView &L, const HaloMsg *msgs, int n, int cur, void *buf, int unpack, cudaStream_t st);
 
+// end_step 1 (mode 0 only): the step was a one-level grid's whole coarse step, and the kernel also
+// advances t by dt^1 (the work of k_end_step, saving its launch)
 int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
                  double cfl_desired, int mode,
-                 cudaStream_t st);
+                 cudaStream_t st, int end_step = 0);
 int k_begin_step(const CtrlView &cv, int nscen, int nlev, const double *Rl, double cfl_desired, double dt_max,
                  cudaStream_t st);
 int k_end_step(const CtrlView &cv, int nscen, cudaStream_t st);

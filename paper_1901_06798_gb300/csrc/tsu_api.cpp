@@ -73,6 +73,54 @@ template <typename F> void parallel_ranges(int n, F &&f)
     tsu::HostPool::get().run(T, [&](int q) { f(q, (int)((long long)n * q / T), (int)((long long)n * (q + 1) / T)); });
 }
 
+// Host-to-device uploads of the tables a regrid rebuilds go through a
+// page-locked ring.  A copy from pageable memory first waits for all the work
+// queued on the stream; one from page-locked memory does not, so the host goes
+// on building the next tables while the device runs the regrid's kernels.  A
+// part of the ring is written again only once the copies out of it have
+// landed: the ring is filled front to back, and before it starts over (or
+// grows) the host waits for the last copy queued.
+struct UploadRing {
+    uint8_t *p = nullptr;
+    size_t cap = 0, head = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+    void copy(void *dst, const void *src, size_t bytes, cudaStream_t st)
+    {
+        if (bytes == 0) return;
+        const size_t need = (bytes + 255) & ~(size_t)255;
+        if (head + need > cap) {
+            if (pending) {
+                CK(cudaEventSynchronize(ev));
+                pending = false;
+            }
+            head = 0;
+            if (need > cap) {
+                const size_t nc = std::max(need, std::max((size_t)16 << 20, cap * 2));
+                if (p) cudaFreeHost(p);
+                p = nullptr;
+                cap = 0;
+                CK(cudaMallocHost((void **)&p, nc));
+                cap = nc;
+            }
+        }
+        std::memcpy(p + head, src, bytes);
+        CK(cudaMemcpyAsync(dst, p + head, bytes, cudaMemcpyHostToDevice, st));
+        if (!ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, st));
+        pending = true;
+        head += need;
+    }
+    ~UploadRing()
+    {
+        if (ev) {
+            cudaEventSynchronize(ev);
+            cudaEventDestroy(ev);
+        }
+        if (p) cudaFreeHost(p);
+    }
+};
+
 template <typename T> struct DevBuf {
     T *p = nullptr;
     size_t cap = 0;
@@ -91,6 +139,12 @@ template <typename T> struct DevBuf {
     {
         ensure(v.size(), s);
         if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    // through the page-locked ring: no wait for the stream's queued work
+    void upload(const std::vector<T> &v, cudaStream_t s, UploadRing &r)
+    {
+        ensure(v.size(), s);
+        r.copy(p, v.data(), v.size() * sizeof(T), s);
     }
     void release()
     {
@@ -306,6 +360,7 @@ struct tsu_ctx {
     bool own_stream = false;
     std::string err;
     Arena arena;
+    UploadRing uring;   // regrid table uploads (declared before the levels: destroyed after them)
     Lvl lv[kMaxLevels];
     std::vector<Grid> grids;   // base topography first, then layers and surfaces in call order
     int nbase = 0;
@@ -667,17 +722,17 @@ struct tsu_ctx {
                 }
         }
         if (split) L.dScratch.ensure(std::max<size_t>(soff, 64), st);
-        L.dP.upload(L.P, st);
-        L.dItems.upload(L.items, st);
-        L.dItemsY.upload(L.items_y, st);
-        L.dNbrs.upload(L.nbrs, st);
+        L.dP.upload(L.P, st, uring);
+        L.dItems.upload(L.items, st, uring);
+        L.dItemsY.upload(L.items_y, st, uring);
+        L.dNbrs.upload(L.nbrs, st, uring);
         if (l > 0) {
             // the coarse table's device copy is current: its finish_level ran first
             L.dCmap.ensure(std::max<size_t>(cmap_n, 1), st);
-            L.dCcand.upload(L.ccand, st);
+            L.dCcand.upload(L.ccand, st, uring);
             kl(k_fill_cmap(L.dP.p, lv[l - 1].dP.p, L.dCcand.p, n, L.dCmap.p, st), "coarse maps");
         }
-        L.dBc.upload(L.bclist, st);
+        L.dBc.upload(L.bclist, st, uring);
         // ghost-cell sources of the new table: the fills of every step until the
         // next change gather from them
         {
@@ -688,7 +743,7 @@ struct tsu_ctx {
                 L.goff[k] = gtot;
                 gtot += (long long)(p.nx + 4) * (p.ny + 4) - (long long)p.nx * p.ny;
             }
-            L.dGoff.upload(L.goff, st);
+            L.dGoff.upload(L.goff, st, uring);
             L.dGmap.ensure((size_t)std::max<long long>(gtot, 1), st);
             L.dGinterp.ensure((size_t)std::max<long long>(gtot, 1), st);
             L.dGcount.ensure(1, st);
@@ -697,7 +752,7 @@ struct tsu_ctx {
         }
         for (int s = 0; s < nscen; s++) cells_h[(size_t)s * kMaxLevels + l] = 0.0;
         for (const auto &p : L.P) cells_h[(size_t)p.scen * kMaxLevels + l] += (double)p.nx * p.ny;
-        cells.upload(cells_h, st);
+        cells.upload(cells_h, st, uring);
         hier_version++;
     }
 
@@ -724,7 +779,7 @@ struct tsu_ctx {
                 }
                 loc[(size_t)s * ng + g] = gl;
             }
-        dgloc.upload(loc, st);
+        dgloc.upload(loc, st, uring);
     }
 
     void ensure_samples(long long n)
@@ -1063,10 +1118,10 @@ struct tsu_ctx {
         }
         for (auto &x : L.idx)   // no index may keep pointing at the old table's copy
             if (x.P == &oldP) { x.P = nullptr; x.nbx = 0; x.nby = 0; }
-        L.dOlds.upload(L.olds, st);
+        L.dOlds.upload(L.olds, st, uring);
         finish_level(lf);
         if (!fresh.empty()) {
-            L.dList.upload(fresh, st);
+            L.dList.upload(fresh, st, uring);
             // B: copied where an old patch of the level held the cell, else sampled
             kl(k_init_patches(prec, view(lf), view(lf, oldD.p), L.dList.p, (int)fresh.size(), L.maxcells, topo(lf), L.cur,
                               0, c.x0, c.y0, L.dx, L.dy, st),
@@ -1076,7 +1131,7 @@ struct tsu_ctx {
             for (int k : fresh) if (L.P[k].bcmask) bl.push_back(k);
             if (!bl.empty()) {
                 DevBuf<int> dbl;
-                dbl.upload(bl, st);
+                dbl.upload(bl, st, uring);
                 BcArgs ba{dbl.p, {c.bc[0], c.bc[1], c.bc[2], c.bc[3]}};
                 kl(k_bc(prec, view(lf), ba, (int)bl.size(), L.maxring, L.cur, 0, 1, st), "bc B");
                 dbl.release();
@@ -1086,7 +1141,7 @@ struct tsu_ctx {
         }
         if (!renewed.empty()) {
             // wave-speed rate of every new patch (kept blocks included) for the next dt
-            L.dList.upload(renewed, st);
+            L.dList.upload(renewed, st, uring);
             kl(k_cell_speed(prec, view(lf), L.dList.p, (int)renewed.size(), L.maxcells, L.cur, c.g, c.drytol, smax.p, st),
                "cell speed");
             kl(k_post_level(ctrl(), lf, nscen, L.R, pdx(lf), pdy(lf), c.cfl_max, c.cfl_desired, 1, st), "post rate");
@@ -1152,8 +1207,11 @@ struct tsu_ctx {
             // untouched, and the retake launch runs only the work items of the
             // scenarios whose post-level kernel set their gate.
             const bool retake = l == 0 && c.cfl_retake;
-            kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, c.cfl_desired, retake ? 2 : 0, st),
+            const bool ends = l == 0 && end_in_post_ && !retake;
+            kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, c.cfl_desired, retake ? 2 : 0, st,
+                            ends ? 1 : 0),
                "post step");
+            if (ends) end_done_ = true;
             if (retake) {
                 a.gate = retake_gate();
                 e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
@@ -1221,11 +1279,17 @@ struct tsu_ctx {
         return false;
     }
 
+    // On a one-level grid the level-1 step's post-level kernel also ends the
+    // coarse step (t += dt), which saves a launch per step.
+    bool end_in_post_ = false, end_done_ = false;
     void coarse_step()
     {
         kl(k_begin_step(ctrl(), nscen, nlev, Rl.p, c.cfl_desired, c.dt_max, st), "begin step");
+        end_in_post_ = nlev == 1;
+        end_done_ = false;
         advance(0, 0);
-        kl(k_end_step(ctrl(), nscen, st), "end step");
+        end_in_post_ = false;
+        if (!end_done_) kl(k_end_step(ctrl(), nscen, st), "end step");
         sample_gauges();
     }
 
@@ -1723,11 +1787,13 @@ struct tsu_ctx {
             L.dOlds.release(); L.dList.release();
             L.dKap.release(); L.dCed.release(); L.dKapF.release(); L.dCedF.release();
             L.dItemsY.release(); L.dScratch.release();
+            L.dGmap.release(); L.dGoff.release(); L.dGinterp.release(); L.dGcount.release();
         }
         for (auto &g : grids) if (g.dev) cudaFreeAsync(g.dev, st);
         dGrids.release(); dGridScen.release(); dEtaIdx.release();
         dt1.release(); dt1f.release(); t.release(); rate.release(); cellupd.release(); cells.release(); Rl.release(); mass.release();
-        viol.release(); smax.release(); derr.release();
+        viol.release(); smax.release(); derr.release(); retake.release(); retakes.release(); dneg.release();
+        tabI.release(); tabT.release(); tabIn.release();
         dgxy.release(); dgeta.release(); dgt.release(); dnsamp.release(); dgloc.release();
         fraw.release(); fcov.release(); ftmp.release(); fF.release(); fN.release(); fpack.release(); fslot.release(); fbox.release();
         dstage.release(); zero_dt.release(); zero_dtf.release(); massParts.release();
@@ -2437,11 +2503,11 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
             ctx->kl(e, "patch step");
             ctx->launches += ctx->step_kernels() - 1;
             CK(cudaEventRecord(ev[2 * k + 1], ctx->st));
+            // the post-level kernel also ends the coarse step (t += dt), as in coarse_step
             ctx->kl(k_post_level(ctx->ctrl(), 0, ctx->nscen, L.R, ctx->pdx(0), ctx->pdy(0), ctx->c.cfl_max,
-                                 ctx->c.cfl_desired, 0, ctx->st),
+                                 ctx->c.cfl_desired, 0, ctx->st, 1),
                     "post step");
             L.cur ^= 1;
-            ctx->kl(k_end_step(ctx->ctrl(), ctx->nscen, ctx->st), "end step");
             for (int s = 0; s < ctx->nscen; s++) ctx->nsteps[s][0]++;
         }
         CK(cudaEventRecord(ev[2 * n + 1], ctx->st));

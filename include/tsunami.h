@@ -359,10 +359,13 @@ int tsu_halo_pack(tsu_ctx *ctx, int scenario, int level, const int *msgs, int n_
 int tsu_halo_unpack(tsu_ctx *ctx, int scenario, int level, const int *msgs, int n_msgs, const void *dev_buf,
                     long long buf_elems);
 
-/* Time n level-1 steps of the patch update alone (no AMR bookkeeping) with CUDA
- * events on the library's stream after `warmup` untimed steps; ms_out gets the
- * mean milliseconds of the step kernel per step and total_ms_out the whole
- * step (ghost fill + update + reductions).  Advances the solution. */
+/* Time n steps of a one-level context with CUDA events on the library's stream
+ * after `warmup` untimed steps, each step the kernels tsu_step launches for it
+ * (start of the step, ghost fill, boundaries, the patch update, the CFL check
+ * and, with cfl_retake, the retake launch and its check, end of the step);
+ * kernel_ms_out gets the mean milliseconds of the patch update's launches per
+ * step and step_ms_out those of the whole step.  Advances the solution.
+ * Errors: TSU_ERR_ARG (more than one level, n < 1, before tsu_init). */
 int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out, double *step_ms_out);
 
 /* ---------------------------------------------------------------------------

@@ -926,36 +926,39 @@ __global__ void __launch_bounds__(256) cell_speed_kernel(LevelView L, const int 
 //           buffer); otherwise keep it as in mode 0;
 //   mode 3: after the retake launch -- keep the retaken steps as in mode 0.
 // A rate that is not a finite number (a NaN or infinite speed) sets the error
-// flag to TSU_DEV_ERR_NAN.  end_step (mode 0): then t += dt^1, as end_step_kernel.
+// flag to TSU_DEV_ERR_NAN.  end_step (modes 0 and 3, every scenario): then
+// t += dt^1, as end_step_kernel.
 __global__ void post_level_kernel(CtrlView cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
                                   double cfl_desired, int mode, int end_step)
 {
     for (int s = threadIdx.x; s < nscen; s += blockDim.x) {
-        unsigned long long *sm = cv.smax + 2 * s;
-        double sx = __longlong_as_double((long long)sm[0]);
-        double sy = __longlong_as_double((long long)sm[1]);
-        sm[0] = 0ull;
-        sm[1] = 0ull;
-        if (mode == 3 && cv.retake[s] == 0) continue;
-        double rate = fmax(sx / dx, sy / dy);
-        if (!(sx <= 1.0e300 && sy <= 1.0e300)) atomicOr(cv.err, TSU_DEV_ERR_NAN);
-        double *ra = cv.rate + (long long)s * cv.max_levels + level;
-        if (mode != 1) {
-            double dt = cv.dt1[s] / R;
-            if (dt * rate > cfl_max) {
-                if (mode == 2) {
-                    cv.retake[s] = 1;
-                    cv.retakes[s] += 1;
-                    cv.dt1[s] = cfl_desired / rate;
-                    cv.dt1f[s] = (float)cv.dt1[s];
-                    continue;
+        do {
+            unsigned long long *sm = cv.smax + 2 * s;
+            double sx = __longlong_as_double((long long)sm[0]);
+            double sy = __longlong_as_double((long long)sm[1]);
+            sm[0] = 0ull;
+            sm[1] = 0ull;
+            if (mode == 3 && cv.retake[s] == 0) break;
+            double rate = fmax(sx / dx, sy / dy);
+            if (!(sx <= 1.0e300 && sy <= 1.0e300)) atomicOr(cv.err, TSU_DEV_ERR_NAN);
+            double *ra = cv.rate + (long long)s * cv.max_levels + level;
+            if (mode != 1) {
+                double dt = cv.dt1[s] / R;
+                if (dt * rate > cfl_max) {
+                    if (mode == 2) {
+                        cv.retake[s] = 1;
+                        cv.retakes[s] += 1;
+                        cv.dt1[s] = cfl_desired / rate;
+                        cv.dt1f[s] = (float)cv.dt1[s];
+                        break;
+                    }
+                    cv.cfl_viol[s] += 1;
                 }
-                cv.cfl_viol[s] += 1;
+                if (mode == 2 || mode == 3) cv.retake[s] = 0;
+                cv.cell_updates[s] += cv.cells[(long long)s * cv.max_levels + level];
             }
-            if (mode == 2 || mode == 3) cv.retake[s] = 0;
-            cv.cell_updates[s] += cv.cells[(long long)s * cv.max_levels + level];
-        }
-        *ra = fmax(*ra, rate);
+            *ra = fmax(*ra, rate);
+        } while (false);
         if (end_step) cv.t[s] = cv.t[s] + cv.dt1[s];
     }
 }
@@ -1449,7 +1452,7 @@ int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, 
                  cudaStream_t st, int end_step)
 {
     post_level_kernel<<<1, 128, 0, st>>>(cv, level, nscen, R, dx, dy, cfl_max, cfl_desired, mode,
-                                         mode == 0 ? end_step : 0);
+                                         (mode == 0 || mode == 3) ? end_step : 0);
     return (int)cudaGetLastError();
 }
 

@@ -174,8 +174,8 @@ struct HaloMsg {
 // pack (unpack = 0: patch buffers -> buf) or unpack (buf -> patch buffers) n boxes
 int k_halo(int prec, const LevelView &L, const HaloMsg *msgs, int n, int cur, void *buf, int unpack, cudaStream_t st);
 
-// end_step 1 (mode 0 only): the step was a one-level grid's whole coarse step, and the kernel also
-// advances t by dt^1 (the work of k_end_step, saving its launch)
+// end_step 1 (modes 0 and 3): the step was a one-level grid's whole coarse step (mode 3: after its
+// retake launch), and the kernel also advances t by dt^1 (the work of k_end_step, saving its launch)
 int k_post_level(const CtrlView &cv, int level, int nscen, double R, double dx, double dy, double cfl_max,
                  double cfl_desired, int mode,
                  cudaStream_t st, int end_step = 0);

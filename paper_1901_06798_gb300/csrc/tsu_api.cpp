@@ -322,15 +322,18 @@ struct BoxIndex {
     }
 };
 
+constexpr int kRetakeThreads = 256, kRetakeRows = 64;   // x-sweep shape of the level-1 retake launch
+
 struct Lvl {
     std::vector<PatchDesc> P;
     std::vector<size_t> blk, blkbytes;
     std::vector<StepItem> items, items_y;   // patch update work items (items_y: FP32 split y kernel)
+    std::vector<StepItem> items_rt;         // level 1, FP32 split update: x-sweep items of the retake launch
     std::vector<int> nbrs, bclist, olds;
     std::vector<BoxIndex> idx;   // per scenario spatial index of P, rebuilt by every finish_level of the level
     std::vector<int> ccand;   // coarse patches overlapping each patch's coarse-map footprint
     DevBuf<PatchDesc> dP;
-    DevBuf<StepItem> dItems, dItemsY;
+    DevBuf<StepItem> dItems, dItemsY, dItemsRt;
     DevBuf<float> dScratch;                 // FP32 split update: Q* of every patch (3 fields each)
     DevBuf<int> dNbrs, dCmap, dCcand, dBc, dOlds, dList;
     DevBuf<GhostSrc> dGmap;      // ghost-cell sources of every patch, in ghost-ring order
@@ -493,6 +496,17 @@ struct tsu_ctx {
     // kernels one patch-update launch of level l runs
     int step_kernels() const { return split_f32() ? 2 : 1; }
     int seg() const { return seg_rows > 0 ? seg_rows : (prec == TSU_F64 ? 128 : (split_f32() ? 16 : 64)); }
+    // the level-1 retake launch (a.gate set): the FP32 split update sweeps x with
+    // its own wide items, the rest as the step itself
+    int retake_launch(StepArgs a, const Lvl &L)
+    {
+        if (prec != TSU_F64 && !L.items_rt.empty() && a.scratch != nullptr && !a.transverse) {
+            a.items = L.dItemsRt.p;
+            return launch_step_f32p(a, (int)L.items_rt.size(), kRetakeThreads, st);
+        }
+        return prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
+                               : launch_step_f32p(a, (int)L.items.size(), nt(), st);
+    }
     void kl(int e, const char *what)
     {
         launches++;
@@ -646,6 +660,19 @@ struct tsu_ctx {
                 L.items_y.insert(L.items_y.end(), yi[q].begin(), yi[q].end());
             }
         }
+        // the level-1 retake launch of the FP32 split update: its CTAs exit unless
+        // their scenario is retaken, so its x sweep runs the widest CTAs (every
+        // launch shape gives the same bits), about 30 times fewer than the default
+        L.items_rt.clear();
+        if (split && l == 0 && c.cfl_retake) {
+            const int Wr = step_strip_width_f32p(kRetakeThreads, 0);
+            for (int k = 0; k < n; k++) {
+                const PatchDesc &p = L.P[k];
+                for (int x0 = 0; x0 < p.nx; x0 += Wr)
+                    for (int y0 = -2; y0 < p.ny + 2; y0 += kRetakeRows)
+                        L.items_rt.push_back(StepItem{k, x0, y0, std::min(Wr, p.nx - x0), std::min(kRetakeRows, p.ny + 2 - y0)});
+            }
+        }
         // per scenario spatial indices of this level and the coarser one
         std::vector<std::vector<int>> ids(nscen);
         for (int k = 0; k < n; k++) ids[L.P[k].scen].push_back(k);
@@ -725,6 +752,7 @@ struct tsu_ctx {
         L.dP.upload(L.P, st, uring);
         L.dItems.upload(L.items, st, uring);
         L.dItemsY.upload(L.items_y, st, uring);
+        if (!L.items_rt.empty()) L.dItemsRt.upload(L.items_rt, st, uring);
         L.dNbrs.upload(L.nbrs, st, uring);
         if (l > 0) {
             // the coarse table's device copy is current: its finish_level ran first
@@ -806,6 +834,9 @@ struct tsu_ctx {
     {
         int ng = (int)gxy.size() / 2;
         if (!ng) return;
+        // room for this sample (a no-op inside a captured step: tsu_step made
+        // room for all of its steps before capturing)
+        ensure_samples(nsamp + 1);
         GaugeArgs ga{};
         ga.loc = dgloc.p; ga.xy = dgxy.p; ga.eta = dgeta.p; ga.t = dgt.p; ga.nsamp = dnsamp.p;
         ga.nscen = nscen; ga.ngauges = ng; ga.x0 = c.x0; ga.y0 = c.y0;
@@ -1207,21 +1238,21 @@ struct tsu_ctx {
             // untouched, and the retake launch runs only the work items of the
             // scenarios whose post-level kernel set their gate.
             const bool retake = l == 0 && c.cfl_retake;
-            const bool ends = l == 0 && end_in_post_ && !retake;
+            // on a one-level grid the last post-level kernel also ends the coarse step
+            const bool ends = l == 0 && end_in_post_;
             kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, c.cfl_desired, retake ? 2 : 0, st,
-                            ends ? 1 : 0),
+                            ends && !retake ? 1 : 0),
                "post step");
-            if (ends) end_done_ = true;
             if (retake) {
                 a.gate = retake_gate();
-                e = prec == TSU_F64 ? launch_step_f64(a, (int)L.items.size(), nt(), st)
-                                    : launch_step_f32p(a, (int)L.items.size(), nt(), st);
+                e = retake_launch(a, L);
                 kl(e, "patch step (retake)");
                 launches += step_kernels() - 1;
-                kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, c.cfl_desired, 3, st),
+                kl(k_post_level(ctrl(), l, nscen, L.R, pdx(l), pdy(l), c.cfl_max, c.cfl_desired, 3, st, ends ? 1 : 0),
                    "post step (retake)");
                 ps.kernels += step_kernels() + 1;
             }
+            if (ends) end_done_ = true;
             if (prof) {
                 CK(cudaEventRecord(ps.e1, st));
                 prof_steps.push_back(ps);
@@ -1787,7 +1818,7 @@ struct tsu_ctx {
             L.dOlds.release(); L.dList.release();
             L.dKap.release(); L.dCed.release(); L.dKapF.release(); L.dCedF.release();
             L.dItemsY.release(); L.dScratch.release();
-            L.dGmap.release(); L.dGoff.release(); L.dGinterp.release(); L.dGcount.release();
+            L.dGmap.release(); L.dGoff.release(); L.dGinterp.release(); L.dGcount.release(); L.dItemsRt.release();
         }
         for (auto &g : grids) if (g.dev) cudaFreeAsync(g.dev, st);
         dGrids.release(); dGridScen.release(); dEtaIdx.release();
@@ -2473,6 +2504,7 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
     return guard(ctx, [&] {
         if (!ctx->initialized || ctx->nlev != 1 || n < 1 || warmup < 0)
             throw Err(TSU_ERR_ARG, "single-level context after tsu_init required");
+        ctx->ensure_samples(ctx->nsamp + warmup + n + 2);
         for (int k = 0; k < warmup; k++) ctx->coarse_step();
         std::vector<cudaEvent_t> ev(2 * n + 2);
         for (auto &e : ev) CK(cudaEventCreate(&e));
@@ -2503,12 +2535,27 @@ int tsu_time_level1_steps(tsu_ctx *ctx, int warmup, int n, double *kernel_ms_out
             ctx->kl(e, "patch step");
             ctx->launches += ctx->step_kernels() - 1;
             CK(cudaEventRecord(ev[2 * k + 1], ctx->st));
-            // the post-level kernel also ends the coarse step (t += dt), as in coarse_step
+            // the rest of the step exactly as level_step and coarse_step run it: with
+            // the CFL retake on, the post-level check, the retake launch (its CTAs
+            // exit unless their scenario is retaken) and the check after it, then
+            // the end of the coarse step; without it, the post-level kernel also ends
+            // the coarse step
+            const bool retake = ctx->c.cfl_retake != 0;
             ctx->kl(k_post_level(ctx->ctrl(), 0, ctx->nscen, L.R, ctx->pdx(0), ctx->pdy(0), ctx->c.cfl_max,
-                                 ctx->c.cfl_desired, 0, ctx->st, 1),
+                                 ctx->c.cfl_desired, retake ? 2 : 0, ctx->st, retake ? 0 : 1),
                     "post step");
+            if (retake) {
+                a.gate = ctx->retake_gate();
+                e = ctx->retake_launch(a, L);
+                ctx->kl(e, "patch step (retake)");
+                ctx->launches += ctx->step_kernels() - 1;
+                ctx->kl(k_post_level(ctx->ctrl(), 0, ctx->nscen, L.R, ctx->pdx(0), ctx->pdy(0), ctx->c.cfl_max,
+                                     ctx->c.cfl_desired, 3, ctx->st, 1),
+                        "post step (retake)");
+            }
             L.cur ^= 1;
             for (int s = 0; s < ctx->nscen; s++) ctx->nsteps[s][0]++;
+            ctx->sample_gauges();
         }
         CK(cudaEventRecord(ev[2 * n + 1], ctx->st));
         ctx->sync();

@@ -127,6 +127,23 @@ def test_more_patches_than_a_grid_y_extent():
         many.close()
 
 
+@pytest.mark.parametrize("retake", [0, 1])
+def test_timed_steps_are_the_steps_tsu_step_takes(retake):
+    """The bench times steps with tsu_time_level1_steps: they must be the steps
+    tsu_step takes (the same kernels, the CFL retake pass included when it is
+    on), so both contexts end with the same bits and the same time."""
+    w = W.shelf(n=192, dx=2000.0, steps=12)
+    cfg = dict(w["cfg"], cfl_retake=retake)
+    a = W.load(_gpu(cfg, 1, use_graphs=False), dict(w, cfg=cfg))
+    b = W.load(_gpu(cfg, 1), dict(w, cfg=cfg))
+    km, sm = a.time_level1_steps(2, 10)
+    assert 0.0 < km <= sm
+    b.step(12)
+    assert a.stats()["t"] == b.stats()["t"] and a.stats()["dt"] == b.stats()["dt"]
+    for f in ("eta", "hu", "hv"):
+        assert np.array_equal(a.level_array(0, 1, f), b.level_array(0, 1, f)), f
+
+
 def test_shelf_with_dry_land_f64():
     w = W.shelf(n=192, dx=2000.0, steps=60)
     o, g = run_pair(w, 60)

@@ -672,7 +672,9 @@ def main():
                        "precision": "FP32 surface-perturbation form (eta', hu, hv, B in FP32)",
                        "l2": "inputs larger than L2 (state 537 MB FP32 / 1.07 GB FP64); no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "launch_shape": r["tune"]},
+                       "launch_shape": r["tune"],
+                       "step": "the kernels tsu_step runs per coarse step: dt, boundaries, the patch update, "
+                               "the CFL check, the level-1 retake launch and its check, gauge sampling"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": "patch update = step_x_f32x2 + step_y_f32x2 (one launch each per step)",

@@ -19,9 +19,12 @@
  *                     non-negative depths of every state of its fan (bed
  *                     steps, dry fronts, overtopping, supersonic flow) and
  *                     of the first-order update built on it at Courant 1/2
- *                     (Sec. 2.2).  Fidelity to George (2008) beyond these
- *                     invariants: parity unpinned (the paper only cites the
- *                     solver).
+ *                     (Sec. 2.2); a single shock is one wave at the
+ *                     Rankine-Hugoniot speed.  Agreement with George's
+ *                     (2008) augmented solver in particular is not checked:
+ *                     the paper cites that solver without stating it, and
+ *                     the construction here is the one the design records
+ *                     (reading r1).
  *   ora_mc_limiter    pinned: MC table values (textbook closed form).
  *   patch step        pinned: 1D dam break (Stoker, Ritter) closed forms,
  *                     mass conservation with walls, lake at rest,
